@@ -1,0 +1,598 @@
+"""Plain CPU oracle of SecPE's encrypted ensemble Argmax on RNS-CKKS.
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only tests/, the smoke check and the
+benchmark's CPU-baseline leg may import this module.  It shares no code with
+the CUDA library; the ring arithmetic is the plain C in ring.c, the rest is
+numpy / Python integers in the order the paper (or the stated reading) gives.
+
+Parity status per function:
+  ring ops, NTT, basis conversion, rescale, key switching, encode/decode,
+  Sign/Max/QuickMax/Argmax: pinned (see tests/test_oracle_*.py).
+  Residue-level intermediate values of the encrypted circuit: the paper prints
+  none (its worked example is a missing figure), so residues are defined by
+  this oracle; the decoded values and the returned index are pinned by
+  mathematics (plaintext simulation, exact argmax).
+
+Scheme summary (SecPE Sec. 2.2 and Sec. 3.2, readings where the paper is
+silent are marked READING):
+  * ciphertext (c0, c1) in NTT form over q_0..q_l, decrypting to c0 + c1*s;
+  * READING: secret-key encryption, ternary secret, centred-binomial (eta=21)
+    errors, randomness from counter-based SplitMix64 streams;
+  * hybrid key switching with dnum digits and n_p special primes;
+  * rescale by the last prime with rounding;
+  * Sign = f^df o g^dg (Eq. comp) with the degree-9 f_4, g_4 of Cheon et al.
+    (Asiacrypt 2020), each evaluated by the fixed depth-4 baby-step
+    giant-step DAG in `poly9`;
+  * Max(a, b) = (a+b)/2 + (a-b)/2 * Sign(a-b) (Eq. max);
+  * Argmax = Alg. 1 (duplicate, QuickMax over rotations by 2^i, subtract the
+    max, Sign, add 1).
+"""
+import math
+
+import numpy as np
+
+from . import _lib
+from .params import Context
+from .signpoly import sign_coeffs_float
+
+U64 = np.uint64
+
+# stream domains of the counter-based sampler (shared convention)
+DOM_SECRET, DOM_KSK_A, DOM_KSK_E, DOM_ENC_A, DOM_ENC_E, DOM_REFRESH = 1, 2, 3, 4, 5, 6
+
+
+def round_half_away(v):
+    """Round a double to the nearest integer, halves away from zero (exact)."""
+    a = abs(v)
+    f = math.floor(a)
+    r = f + (1 if a - f >= 0.5 else 0)
+    return int(r) if v >= 0 else -int(r)
+
+
+class Ct:
+    """Ciphertext: c[2][level+1][N] uint64 (NTT form), level, scale."""
+
+    def __init__(self, c, level, scale):
+        self.c = c
+        self.level = level
+        self.scale = scale
+
+    def copy(self):
+        return Ct(self.c.copy(), self.level, self.scale)
+
+
+class Oracle:
+    """RNS-CKKS scheme + SecPE circuit on the CPU."""
+
+    def __init__(self, params):
+        self.ctx = Context(params)
+        self.p = params
+        self.n = self.ctx.n
+        self.log_n = self.ctx.log_n
+        self.lib = _lib.lib()
+        self.primes = self.ctx.all_primes
+        self.nq = len(self.ctx.q)
+        self.counters = {}
+        self.ridx = 0
+        self.qseed = 0
+        self.reset_counters()
+
+    def reset_counters(self):
+        self.counters = dict(rotations=0, signs=0, relins=0, refreshes=0,
+                             keyswitches=0)
+
+    # ------------------------------------------------------------ ring layer
+    def ntt(self, a, pi):
+        """In-place forward NTT of one limb (prime index pi)."""
+        self.lib.or_ntt_fwd(_lib.ptr(a), self.log_n, self.primes[pi], self.ctx.psi[pi])
+
+    def intt(self, a, pi):
+        self.lib.or_ntt_inv(_lib.ptr(a), self.log_n, self.primes[pi], self.ctx.psi[pi])
+
+    def _binop(self, fn, a, b, pi):
+        out = np.empty(self.n, dtype=U64)
+        fn(_lib.ptr(a), _lib.ptr(b), _lib.ptr(out), self.n, self.primes[pi])
+        return out
+
+    def vmul(self, a, b, pi):
+        return self._binop(self.lib.or_vmul, a, b, pi)
+
+    def vadd(self, a, b, pi):
+        return self._binop(self.lib.or_vadd, a, b, pi)
+
+    def vsub(self, a, b, pi):
+        return self._binop(self.lib.or_vsub, a, b, pi)
+
+    def vscale(self, a, c, pi):
+        out = np.empty(self.n, dtype=U64)
+        self.lib.or_vscale(_lib.ptr(a), int(c) % self.primes[pi], _lib.ptr(out),
+                           self.n, self.primes[pi])
+        return out
+
+    def vaddc(self, a, c, pi):
+        out = np.empty(self.n, dtype=U64)
+        self.lib.or_vaddc(_lib.ptr(a), int(c) % self.primes[pi], _lib.ptr(out),
+                          self.n, self.primes[pi])
+        return out
+
+    def vreduce(self, a, pi):
+        out = np.empty(self.n, dtype=U64)
+        self.lib.or_vreduce(_lib.ptr(a), _lib.ptr(out), self.n, self.primes[pi])
+        return out
+
+    def from_signed(self, coeffs, pi):
+        """int64 coefficients -> residues mod prime pi."""
+        c = np.ascontiguousarray(coeffs, dtype=np.int64)
+        out = np.empty(self.n, dtype=U64)
+        self.lib.or_vfrom_signed(_lib.ptr(c), _lib.ptr(out), self.n, self.primes[pi])
+        return out
+
+    def fast_bconv(self, x, src_idx, dst_idx):
+        """FastBConv of coefficient-form limbs x[len(src)][N] to dst primes."""
+        qin = _lib.u64arr([self.primes[i] for i in src_idx])
+        qout = _lib.u64arr([self.primes[i] for i in dst_idx])
+        xin = np.ascontiguousarray(x, dtype=U64)
+        out = np.empty((len(dst_idx), self.n), dtype=U64)
+        self.lib.or_fast_bconv(_lib.ptr(xin), _lib.ptr(qin), len(src_idx),
+                               _lib.ptr(qout), len(dst_idx), _lib.ptr(out), self.n)
+        return out
+
+    def automorph_ntt(self, a, pi, g):
+        """X -> X^g on an NTT-form limb, done in the coefficient domain."""
+        x = a.copy()
+        self.intt(x, pi)
+        out = np.empty(self.n, dtype=U64)
+        self.lib.or_automorph_coeff(_lib.ptr(x), _lib.ptr(out), self.log_n,
+                                    self.primes[pi], g)
+        self.ntt(out, pi)
+        return out
+
+    # --------------------------------------------------------------- sampling
+    def stream(self, seed, domain, index):
+        return int(self.lib.or_sm_stream(seed & (2**64 - 1), domain, index))
+
+    def sample_ternary(self, key):
+        out = np.empty(self.n, dtype=np.int64)
+        self.lib.or_sample_ternary(key, _lib.ptr(out), self.n)
+        return out
+
+    def sample_cbd(self, key):
+        out = np.empty(self.n, dtype=np.int64)
+        self.lib.or_sample_cbd21(key, _lib.ptr(out), self.n)
+        return out
+
+    def sample_uniform(self, key, pi):
+        """Uniform NTT-form limb for prime index pi (stream offset pi*N)."""
+        out = np.empty(self.n, dtype=U64)
+        self.lib.or_sample_uniform(key, pi * self.n, self.primes[pi], _lib.ptr(out), self.n)
+        return out
+
+    def ntt_of_signed(self, coeffs, idx):
+        """NTT over the prime indices idx of an int64 coefficient vector."""
+        out = np.empty((len(idx), self.n), dtype=U64)
+        for r, pi in enumerate(idx):
+            out[r] = self.from_signed(coeffs, pi)
+            self.ntt(out[r], pi)
+        return out
+
+    # ------------------------------------------------------------- encoding
+    def _pow5(self, count):
+        two_n = 2 * self.n
+        out = np.empty(count, dtype=np.int64)
+        e = 1
+        for j in range(count):
+            out[j] = e
+            e = e * 5 % two_n
+        return out
+
+    def encode_coeffs(self, v, scale):
+        """Canonical-embedding encoding of a real vector into slots 0..len(v)-1
+        (zeros beyond): m_k = round(scale * (2/N) * sum_j v_j cos(pi 5^j k / N)),
+        i.e. the inverse of m -> (m(zeta^(5^j)))_j, zeta = exp(i pi / N),
+        taking the real coefficients (SecPE Sec. 2.2 SIMD packing)."""
+        v = np.asarray(v, dtype=np.float64)
+        n_s = len(v)
+        assert n_s <= self.n // 2
+        two_n = 2 * self.n
+        p5 = self._pow5(n_s)
+        ks = np.arange(self.n, dtype=np.int64)
+        acc = np.zeros(self.n, dtype=np.float64)
+        for j in range(n_s):
+            e = (p5[j] * ks) % two_n
+            acc += v[j] * np.cos(np.pi * e.astype(np.float64) / self.n)
+        vals = acc * (2.0 / self.n) * scale
+        return np.array([round_half_away(float(x)) for x in vals], dtype=object)
+
+    def decode_coeffs(self, m, scale, n_slots):
+        """Slots 0..n_slots-1 of the real part of m(zeta^(5^j)) / scale."""
+        mf = np.array([float(x) for x in m], dtype=np.float64)
+        two_n = 2 * self.n
+        p5 = self._pow5(n_slots)
+        ks = np.arange(self.n, dtype=np.int64)
+        out = np.empty(n_slots, dtype=np.float64)
+        for j in range(n_slots):
+            e = (p5[j] * ks) % two_n
+            out[j] = np.dot(mf, np.cos(np.pi * e.astype(np.float64) / self.n))
+        return out / scale
+
+    # ------------------------------------------------------------------ keys
+    def keygen(self, seed, rot_steps=()):
+        """Secret key, relinearisation key and Galois keys for RotL(r), r in
+        rot_steps (negative r means RotR(-r))."""
+        all_idx = list(range(len(self.primes)))
+        s = self.sample_ternary(self.stream(seed, DOM_SECRET, 0))
+        self.s_coeffs = s
+        self.s_ntt = self.ntt_of_signed(s, all_idx)
+        self.seed = seed
+        s2 = np.stack([self.vmul(self.s_ntt[pi], self.s_ntt[pi], pi) for pi in all_idx])
+        self.rlk = self.make_ksk(s2, 0)
+        self.gks = {}
+        for r in rot_steps:
+            g = self.galois(r)
+            if g in self.gks:
+                continue
+            sg = np.stack([self.automorph_ntt(self.s_ntt[pi], pi, g) for pi in all_idx])
+            self.gks[g] = self.make_ksk(sg, g)
+
+    def make_ksk(self, s_new, kid):
+        """Hybrid key-switching key from s_new to s: per digit j,
+        b_j = -a_j s + e_j + [P]_{q_i} s_new on primes of digit j (0 on the
+        other primes, where the CRT gadget vanishes, and on the special primes,
+        where P vanishes), a_j uniform.  Returns array [dnum][2][nprimes][N]."""
+        nprimes = len(self.primes)
+        full_digits = self.ctx.digits(self.ctx.L)
+        out = np.empty((len(full_digits), 2, nprimes, self.n), dtype=U64)
+        for j, dig in enumerate(full_digits):
+            ka = self.stream(self.seed, DOM_KSK_A, kid * 64 + j)
+            ke = self.stream(self.seed, DOM_KSK_E, kid * 64 + j)
+            e = self.sample_cbd(ke)
+            e_ntt = self.ntt_of_signed(e, list(range(nprimes)))
+            for pi in range(nprimes):
+                a = self.sample_uniform(ka, pi)
+                b = self.vsub(e_ntt[pi], self.vmul(a, self.s_ntt[pi], pi), pi)
+                if pi in dig:
+                    pm = self.ctx.P % self.primes[pi]
+                    b = self.vadd(b, self.vscale(s_new[pi], pm, pi), pi)
+                out[j, 0, pi] = b
+                out[j, 1, pi] = a
+        return out
+
+    def galois(self, r):
+        """Galois element of RotL(r) (RotR(r') = RotL(N/2 - r'))."""
+        two_n = 2 * self.n
+        if r < 0:
+            r = self.n // 2 + r
+        return pow(5, r % (self.n // 2), two_n)
+
+    # ---------------------------------------------------- encrypt / decrypt
+    def encrypt_coeffs(self, m, level, scale, seed):
+        """Secret-key encryption of integer coefficients m (list/array of
+        Python ints, |m| < q_0/2 not required): c1 = a, c0 = -a s + m + e."""
+        idx = list(range(level + 1))
+        ka = self.stream(seed, DOM_ENC_A, 0)
+        e = self.sample_cbd(self.stream(seed, DOM_ENC_E, 0))
+        c = np.empty((2, level + 1, self.n), dtype=U64)
+        mm = [int(x) for x in m]
+        for pi in idx:
+            q = self.primes[pi]
+            mres = np.array([(x + int(ei)) % q for x, ei in zip(mm, e)], dtype=U64)
+            self.ntt(mres, pi)
+            a = self.sample_uniform(ka, pi)
+            c[0, pi] = self.vsub(mres, self.vmul(a, self.s_ntt[pi], pi), pi)
+            c[1, pi] = a
+        return Ct(c, level, scale)
+
+    def encrypt(self, v, seed, level=None, scale=None):
+        level = self.ctx.L if level is None else level
+        scale = self.p.scale if scale is None else scale
+        return self.encrypt_coeffs(self.encode_coeffs(v, scale), level, scale, seed)
+
+    def encrypt_logits(self, v, n_classes, d_min, seed):
+        """Client-side encryption of one prompt's logit vector (SecPE Sec. 3.1
+        step 1, Eq. argmax layout): slots 0..C-1 hold the logits; READING for
+        C not a power of two: slots C..C'-1 hold d_min, so that after the
+        normalisation they sit at the bottom of the range; zeros beyond C'."""
+        cp = 1 << (n_classes - 1).bit_length()
+        v = np.asarray(v, dtype=np.float64)
+        assert len(v) == n_classes
+        full = np.concatenate([v, np.full(cp - n_classes, float(d_min))])
+        return self.encrypt(full, seed)
+
+    def decrypt_coeffs(self, ct):
+        """Centred integer coefficients of c0 + c1*s by exact CRT."""
+        lv = ct.level
+        res = []
+        for pi in range(lv + 1):
+            x = self.vadd(ct.c[0, pi], self.vmul(ct.c[1, pi], self.s_ntt[pi], pi), pi)
+            self.intt(x, pi)
+            res.append(x)
+        return self.crt_centred(res, lv)
+
+    def crt_centred(self, res, lv):
+        qs = self.ctx.q[: lv + 1]
+        Q = 1
+        for q in qs:
+            Q *= q
+        acc = np.zeros(self.n, dtype=object)
+        for pi, q in enumerate(qs):
+            Mi = Q // q
+            coef = Mi * pow(Mi % q, -1, q)
+            acc = acc + res[pi].astype(object) * coef
+        acc = acc % Q
+        half = Q // 2
+        return np.where(acc > half, acc - Q, acc)
+
+    def decrypt(self, ct, n_slots):
+        return self.decode_coeffs(self.decrypt_coeffs(ct), ct.scale, n_slots)
+
+    # ------------------------------------------------------ key switching
+    def keyswitch(self, d, level, ksk):
+        """Hybrid key switching of d (NTT form, limbs 0..level) with key ksk:
+        ModUp per digit (INTT, FastBConv to the other primes, NTT), inner
+        product with the key over Q_l u P, then ModDown (INTT of the special
+        limbs, FastBConv to q_i, NTT, (x - conv) * P^-1)."""
+        self.counters["keyswitches"] += 1
+        q_idx = list(range(level + 1))
+        sp_idx = self.ctx.special_idx()
+        tgt = q_idx + sp_idx
+        coef = d.copy()
+        for pi in q_idx:
+            self.intt(coef[pi], pi)
+        acc0 = {t: np.zeros(self.n, dtype=U64) for t in tgt}
+        acc1 = {t: np.zeros(self.n, dtype=U64) for t in tgt}
+        for j, dig in enumerate(self.ctx.digits(level)):
+            others = [t for t in tgt if t not in dig]
+            conv = self.fast_bconv(np.stack([coef[pi] for pi in dig]), dig, others)
+            ext = {}
+            for r, t in enumerate(others):
+                x = conv[r].copy()
+                self.ntt(x, t)
+                ext[t] = x
+            for pi in dig:
+                ext[pi] = d[pi]
+            for t in tgt:
+                acc0[t] = self.vadd(acc0[t], self.vmul(ext[t], ksk[j, 0, t], t), t)
+                acc1[t] = self.vadd(acc1[t], self.vmul(ext[t], ksk[j, 1, t], t), t)
+        return self.moddown(acc0, level), self.moddown(acc1, level)
+
+    def moddown(self, acc, level):
+        """Rounded division by P of x given over Q_l u P (READING: rounding,
+        like the rescale): y = [x + h]_P with h = floor(P/2) on the special
+        limbs (coefficient form), conv_i = FastBConv(y -> q_i) - h,
+        out_i = (x_i - conv_i) * P^-1 mod q_i."""
+        sp_idx = self.ctx.special_idx()
+        hP = self.ctx.P // 2
+        pc = np.stack([acc[t].copy() for t in sp_idx])
+        for r, t in enumerate(sp_idx):
+            self.intt(pc[r], t)
+            pc[r] = self.vaddc(pc[r], hP % self.primes[t], t)
+        q_idx = list(range(level + 1))
+        conv = self.fast_bconv(pc, sp_idx, q_idx)
+        out = np.empty((level + 1, self.n), dtype=U64)
+        for pi in q_idx:
+            q = self.primes[pi]
+            x = self.vaddc(conv[pi], -hP % q, pi)
+            self.ntt(x, pi)
+            pinv = pow(self.ctx.P % q, -1, q)
+            out[pi] = self.vscale(self.vsub(acc[pi], x, pi), pinv, pi)
+        return out
+
+    # --------------------------------------------------------- evaluator
+    def drop(self, ct, level):
+        """Modulus drop: keep limbs 0..level (scale unchanged)."""
+        assert level <= ct.level
+        return Ct(np.ascontiguousarray(ct.c[:, : level + 1]), level, ct.scale)
+
+    def _check_scales(self, a, b):
+        if abs(a.scale - b.scale) > a.scale * 2.0 ** -40:
+            raise ValueError("scale mismatch %r vs %r" % (a.scale, b.scale))
+
+    def add(self, a, b):
+        lv = min(a.level, b.level)
+        a, b = self.drop(a, lv), self.drop(b, lv)
+        self._check_scales(a, b)
+        c = np.empty_like(a.c)
+        for k in range(2):
+            for pi in range(lv + 1):
+                c[k, pi] = self.vadd(a.c[k, pi], b.c[k, pi], pi)
+        return Ct(c, lv, a.scale)
+
+    def sub(self, a, b):
+        lv = min(a.level, b.level)
+        a, b = self.drop(a, lv), self.drop(b, lv)
+        self._check_scales(a, b)
+        c = np.empty_like(a.c)
+        for k in range(2):
+            for pi in range(lv + 1):
+                c[k, pi] = self.vsub(a.c[k, pi], b.c[k, pi], pi)
+        return Ct(c, lv, a.scale)
+
+    def rescale(self, ct):
+        """Divide by q_l with rounding: c' = (c + h - [c + h]_{q_l}) / q_l,
+        h = floor(q_l / 2), [.] the remainder in [0, q_l)."""
+        lv = ct.level
+        ql = self.primes[lv]
+        h = ql // 2
+        out = np.empty((2, lv, self.n), dtype=U64)
+        for k in range(2):
+            y = ct.c[k, lv].copy()
+            self.intt(y, lv)
+            y = self.vaddc(y, h, lv)
+            for pi in range(lv):
+                # z = [c + h]_{q_l} - h, per coefficient, reduced mod q_i
+                z = self.vaddc(self.vreduce(y, pi), -h % self.primes[pi], pi)
+                self.ntt(z, pi)
+                t = self.vsub(ct.c[k, pi], z, pi)
+                out[k, pi] = self.vscale(t, pow(ql % self.primes[pi], -1, self.primes[pi]), pi)
+        return Ct(out, lv - 1, ct.scale / float(ql))
+
+    def mul(self, a, b):
+        """Tensor, relinearise, rescale (SecPE Sec. 2.2 slot-wise product)."""
+        lv = min(a.level, b.level)
+        if lv < 1 + self.p.reserve:
+            raise ValueError("not enough levels")
+        a, b = self.drop(a, lv), self.drop(b, lv)
+        d0 = np.empty((lv + 1, self.n), dtype=U64)
+        d1 = np.empty_like(d0)
+        d2 = np.empty_like(d0)
+        for pi in range(lv + 1):
+            d0[pi] = self.vmul(a.c[0, pi], b.c[0, pi], pi)
+            d1[pi] = self.vadd(self.vmul(a.c[0, pi], b.c[1, pi], pi),
+                               self.vmul(a.c[1, pi], b.c[0, pi], pi), pi)
+            d2[pi] = self.vmul(a.c[1, pi], b.c[1, pi], pi)
+        self.counters["relins"] += 1
+        k0, k1 = self.keyswitch(d2, lv, self.rlk)
+        c = np.empty((2, lv + 1, self.n), dtype=U64)
+        for pi in range(lv + 1):
+            c[0, pi] = self.vadd(d0[pi], k0[pi], pi)
+            c[1, pi] = self.vadd(d1[pi], k1[pi], pi)
+        return self.rescale(Ct(c, lv, a.scale * b.scale))
+
+    def mul_const(self, x, c, target, out_level):
+        """x * c landing at out_level with scale exactly `target`: drop x to
+        out_level+1, multiply by the integer k = round(c * target / s_x * q),
+        q = q_{out_level+1}, rescale."""
+        if x.level < out_level + 1:
+            raise ValueError("not enough levels for mul_const")
+        if out_level < self.p.reserve:
+            raise ValueError("not enough levels")
+        xd = self.drop(x, out_level + 1)
+        qf = float(self.primes[out_level + 1])
+        factor = target / xd.scale * qf
+        k = round_half_away(c * factor)
+        cc = np.empty_like(xd.c)
+        for kk in range(2):
+            for pi in range(out_level + 2):
+                cc[kk, pi] = self.vscale(xd.c[kk, pi], k % self.primes[pi], pi)
+        r = self.rescale(Ct(cc, out_level + 1, xd.scale))
+        r.scale = target
+        return r
+
+    def add_const(self, x, c):
+        """x + c: the constant polynomial round(c * s_x) added to c0."""
+        k = round_half_away(c * x.scale)
+        out = x.copy()
+        for pi in range(x.level + 1):
+            out.c[0, pi] = self.vaddc(x.c[0, pi], k % self.primes[pi], pi)
+        return out
+
+    def rotate(self, ct, r):
+        """RotL(ct, r) for r > 0, RotR(ct, -r) for r < 0 (SecPE Sec. 2.2):
+        automorphism X -> X^g, g = 5^r mod 2N, then key switching of c1."""
+        g = self.galois(r)
+        if g not in self.gks:
+            raise KeyError("missing Galois key for rotation %d" % r)
+        self.counters["rotations"] += 1
+        lv = ct.level
+        t0 = np.stack([self.automorph_ntt(ct.c[0, pi], pi, g) for pi in range(lv + 1)])
+        t1 = np.stack([self.automorph_ntt(ct.c[1, pi], pi, g) for pi in range(lv + 1)])
+        k0, k1 = self.keyswitch(t1, lv, self.gks[g])
+        c = np.empty((2, lv + 1, self.n), dtype=U64)
+        for pi in range(lv + 1):
+            c[0, pi] = self.vadd(t0[pi], k0[pi], pi)
+            c[1, pi] = k1[pi]
+        return Ct(c, lv, ct.scale)
+
+    def refresh(self, ct, qseed):
+        """Test-only, insecure stand-in for bootstrapping (READING of SecPE
+        Sec. 2.2/4.1, which rely on bootstrapping without describing it):
+        decrypt, lift exactly by CRT to centred integers, re-encrypt at the top
+        level with the same scale, randomness from stream (qseed, refresh#)."""
+        m = self.decrypt_coeffs(ct)
+        idx = self.ridx
+        self.ridx += 1
+        self.counters["refreshes"] += 1
+        seed = self.stream(qseed, DOM_REFRESH, idx)
+        return self.encrypt_coeffs(m, self.ctx.L, ct.scale, seed)
+
+    # ------------------------------------------------------ SecPE circuit
+    def ensure(self, ct, k):
+        """Refresh ct if fewer than k + reserve levels remain."""
+        if ct.level < k + self.p.reserve:
+            return self.refresh(ct, self.qseed)
+        return ct
+
+    def poly9(self, x, c, s_out):
+        """Odd degree-9 p(x) = c1 x + c3 x^3 + c5 x^5 + c7 x^7 + c9 x^9 by the
+        fixed depth-4 baby-step giant-step DAG:
+          x2 = x*x, x3 = x*x2, x4 = x2*x2, x8 = x4*x4,
+          B = c5 x + c7 x3, T = x4 * B, U = x8 * (c9 x), A = c1 x + c3 x3,
+          p = A + T + U,
+        the constant multiplies landing at the scales that make the three
+        addends' scales equal to s_out."""
+        c1, c3, c5, c7, c9 = c
+        lv = x.level
+        q3 = float(self.primes[lv - 3])
+        x2 = self.mul(x, x)
+        x3 = self.mul(x, x2)
+        x4 = self.mul(x2, x2)
+        x8 = self.mul(x4, x4)
+        sB = s_out * q3 / x4.scale
+        B = self.add(self.mul_const(x, c5, sB, lv - 3), self.mul_const(x3, c7, sB, lv - 3))
+        T = self.mul(x4, B)
+        s9 = s_out * q3 / x8.scale
+        U = self.mul(x8, self.mul_const(x, c9, s9, lv - 3))
+        A = self.add(self.mul_const(x, c1, s_out, lv - 4), self.mul_const(x3, c3, s_out, lv - 4))
+        return self.add(self.add(A, T), U)
+
+    def sign(self, x, out_levels):
+        """Sign(x) = f^df(g^dg(x)) (SecPE Eq. comp); before each polynomial,
+        refresh if fewer than 4 (+ out_levels for the last) levels remain."""
+        self.counters["signs"] += 1
+        g, f = sign_coeffs_float()
+        polys = [g] * self.p.sign_dg + [f] * self.p.sign_df
+        for i, c in enumerate(polys):
+            need = 4 + (out_levels if i == len(polys) - 1 else 0)
+            x = self.ensure(x, need)
+            x = self.poly9(x, c, self.p.scale)
+        return x
+
+    def max(self, a, y):
+        """Max(a, y) = (a+y)/2 + (a-y)/2 * Sign(a-y) (SecPE Eq. max).
+        t = d * Sign(d) with d = a - y encodes d*s at scale S; declaring its
+        scale 2S makes it encode d*s/2 at no cost.  u = (a+y) * 1/2 is then
+        brought to t's level with scale exactly 2S, and max = t + u."""
+        d = self.sub(a, y)
+        s = self.sign(d, 1)
+        t = self.mul(d, s)
+        t.scale = 2.0 * t.scale
+        u = self.mul_const(self.add(a, y), 0.5, t.scale, t.level)
+        return self.add(t, u)
+
+    def argmax(self, y, n_classes, qseed):
+        """SecPE Alg. 1 on a normalised ciphertext y with n_classes valid
+        slots (padded to C' = 2^ceil(log2 C)): y <- y + RotR(y, C');
+        QuickMax: for i < log2 C': y <- Max(RotL(y, 2^i), y); then
+        z = Sign(y_dup - y_max) + 1."""
+        if n_classes < 2:
+            raise ValueError("argmax needs at least 2 classes")
+        self.qseed = qseed
+        self.ridx = 0
+        cp = 1 << (n_classes - 1).bit_length()
+        r = cp.bit_length() - 1
+        if 2 * cp > self.n // 2:
+            raise ValueError("2*C' exceeds the slot count")
+        y = self.add(y, self.rotate(y, -cp))
+        y_dup = y
+        for i in range(r):
+            y = self.ensure(y, 1)
+            a = self.rotate(y, 1 << i)
+            y = self.max(a, y)
+        al = self.mul_const(y_dup, 1.0, y.scale, y.level)
+        d = self.sub(al, y)
+        s = self.sign(d, 0)
+        return self.add_const(s, 1.0)
+
+    def aggregate(self, cts, d_min, d_max):
+        """Ensemble aggregation (SecPE Sec. 3.1 step 3) with the normalisation
+        of Eq. norm folded into one constant: y = (sum_i ct_i) * w,
+        w = 1 / (K (D_max - D_min)), landing at level L-1 with scale Delta.
+        The shift -D_min/(D_max-D_min) of Eq. norm is dropped: Alg. 1's output
+        is invariant under a common shift, and an unmasked shift would break
+        the zero padding that Alg. 1's duplication step relies on."""
+        K = len(cts)
+        y = cts[0]
+        for c in cts[1:]:
+            y = self.add(y, c)
+        w = 1.0 / (K * (d_max - d_min))
+        return self.mul_const(y, w, self.p.scale, y.level - 1)

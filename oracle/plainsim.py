@@ -1,0 +1,74 @@
+"""FP64 plaintext simulation of the SecPE circuit (slot values only).
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE.
+
+The same op sequence as the encrypted circuit in ckks.py, applied to real
+slot vectors: rotations are np.roll over N/2 slots, Sign is the composite
+polynomial evaluated by the same BSGS DAG in exact real arithmetic.  Used to
+pin decoded values (layer 2 of parity) and the returned index (layer 3).
+"""
+import numpy as np
+
+from .signpoly import sign_coeffs_float
+
+
+def poly9(x, c):
+    c1, c3, c5, c7, c9 = c
+    x2 = x * x
+    x3 = x * x2
+    x4 = x2 * x2
+    x8 = x4 * x4
+    B = c5 * x + c7 * x3
+    T = x4 * B
+    U = x8 * (c9 * x)
+    A = c1 * x + c3 * x3
+    return (A + T) + U
+
+
+def sign(x, dg=2, df=2):
+    g, f = sign_coeffs_float()
+    for c in [g] * dg + [f] * df:
+        x = poly9(x, c)
+    return x
+
+
+def rotl(v, r):
+    return np.roll(v, -r)
+
+
+def vmax(a, y, dg=2, df=2):
+    d = a - y
+    return (a + y) / 2 + (d / 2) * sign(d, dg, df)
+
+
+def argmax_slots(y, n_classes, dg=2, df=2):
+    """Alg. 1 on a slot vector y (normalised, zero beyond C')."""
+    cp = 1 << (n_classes - 1).bit_length()
+    r = cp.bit_length() - 1
+    y = y + rotl(y, -cp)
+    y_dup = y
+    for i in range(r):
+        y = vmax(rotl(y, 1 << i), y, dg, df)
+    return sign(y_dup - y, dg, df) + 1.0
+
+
+def pad_logits(v, n_classes, d_min):
+    """Client-side layout (READING for C not a power of two): slots 0..C-1
+    hold the logits, slots C..C'-1 hold d_min, zeros beyond."""
+    cp = 1 << (n_classes - 1).bit_length()
+    out = np.zeros(cp, dtype=np.float64)
+    out[:n_classes] = v
+    out[n_classes:cp] = d_min
+    return out
+
+
+def ensemble_argmax(logits, d_min, d_max, slots, dg=2, df=2):
+    """logits[K][C] -> z over the first C slots (plaintext Alg. 1 pipeline)."""
+    logits = np.asarray(logits, dtype=np.float64)
+    K, C = logits.shape
+    y = np.zeros(slots)
+    for i in range(K):
+        p = pad_logits(logits[i], C, d_min)
+        y[: len(p)] += p
+    y = y * (1.0 / (K * (d_max - d_min)))
+    return argmax_slots(y, C, dg, df)[:C]
