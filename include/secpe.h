@@ -1,0 +1,218 @@
+/*
+ * secpe.h - C ABI of a GB300 (sm_103a) library for SecPE's encrypted
+ * prompt-ensemble aggregation and encrypted Argmax on RNS-CKKS
+ * (Zhang et al., "SecPE: Secure Prompt Ensembling for Private and Robust
+ * Large Language Models", arXiv 2502.00847).
+ *
+ * Conventions
+ * -----------
+ * - Every call returns an int status: SECPE_OK (0) or a negative SECPE_E*.
+ *   Host-side validation errors are returned synchronously and nothing is
+ *   launched.  Calls that take a cudaStream_t (passed as void*) are
+ *   asynchronous on that stream; device-side failures (a bounded wait that
+ *   gave up) are recorded in a per-context status word read by
+ *   secpe_stream_status.
+ * - Ciphertext data is caller-owned device memory laid out as
+ *   [2][cap][N] uint64 words, cap >= level+1: polynomial c0 then c1, each a
+ *   stack of cap RNS limbs of N residues in NTT (evaluation) form, limb i
+ *   modulo q_i.  Only limbs 0..level are meaningful.  The library never
+ *   frees caller buffers.  Batched calls take arrays of secpe_ct.
+ * - The context and key objects own their device memory (allocated with the
+ *   CUDA stream-ordered allocator) and release it in *_destroy.
+ * - There is no CPU fallback: without a usable CUDA device every call that
+ *   needs one returns SECPE_ECUDA.
+ */
+#ifndef SECPE_H
+#define SECPE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SECPE_OK 0
+#define SECPE_EINVAL -1   /* bad argument (sizes, levels, pointers) */
+#define SECPE_ENOMEM -2   /* device allocation failed */
+#define SECPE_ELEVEL -3   /* not enough levels for the operation */
+#define SECPE_ESCALE -4   /* operand scales differ */
+#define SECPE_EKEY -5     /* a needed Galois / relinearisation key is missing */
+#define SECPE_ECUDA -6    /* CUDA runtime error */
+#define SECPE_ETIMEOUT -7 /* a bounded device-side wait gave up */
+#define SECPE_EADMIT -8   /* request does not fit the admission budget */
+
+/*
+ * Parameter set.  Ring R_Q = Z_Q[X]/(X^N + 1), Q = q_0 ... q_L (SecPE
+ * Sec. 2.2).  Primes (all = 1 mod 2N, all below 2^60):
+ *   special primes: the n_p largest below 2^p_bits;
+ *   q_0: the largest below 2^q0_bits not already taken when q0_bits differs
+ *        from q_bits, otherwise the first prime of the sequence below;
+ *   q_1..: alternately the nearest below and above 2^q_bits, below first.
+ * Key switching is hybrid with dnum digits of alpha = ceil(n_q/dnum) primes.
+ * Sign = f^sign_df(g^sign_dg(x)) (SecPE Eq. comp); `reserve` levels are
+ * kept below each depth-4 polynomial block before a refresh is forced.
+ */
+typedef struct {
+    int32_t log_n;      /* 12..16 on the fast paths; 4..17 accepted */
+    int32_t q0_bits;
+    int32_t q_bits;
+    int32_t n_q;        /* number of ciphertext primes, L + 1 (<= 48) */
+    int32_t p_bits;
+    int32_t n_p;        /* number of special primes (1..8) */
+    int32_t dnum;       /* digits; dnum <= 15 and alpha <= 15 */
+    int32_t log_scale;  /* scale Delta = 2^log_scale */
+    int32_t sign_dg;    /* repetitions of g (paper: 2) */
+    int32_t sign_df;    /* repetitions of f (paper: 2) */
+    int32_t reserve;    /* levels kept in reserve (>= 1) */
+} secpe_params;
+
+typedef struct secpe_ctx secpe_ctx;   /* primes, NTT tables, base-conversion tables */
+typedef struct secpe_keys secpe_keys; /* secret key (device), relin + Galois keys */
+
+typedef struct {
+    uint64_t *data;   /* device, [2][cap][N] */
+    int32_t level;    /* limbs 0..level valid */
+    int32_t cap;      /* allocated limbs per polynomial */
+    double scale;     /* CKKS scale of the encoded message */
+} secpe_ct;
+
+/* ---- context ---------------------------------------------------------- */
+/* Builds primes/roots/tables on the host and uploads them to the current
+ * device.  The prime values can be read back with secpe_ctx_primes. */
+int secpe_ctx_create(const secpe_params *p, secpe_ctx **out);
+void secpe_ctx_destroy(secpe_ctx *ctx);
+/* Copies the n_q ciphertext primes then the n_p special primes to out
+ * (host array of n_q + n_p words). */
+int secpe_ctx_primes(const secpe_ctx *ctx, uint64_t *out);
+/* Host-only (no device needed): runs the prime selection rule above and
+ * writes n_q ciphertext primes then n_p special primes into out, which must
+ * hold `capacity` >= n_q + n_p words.  Returns SECPE_EINVAL for parameters
+ * outside the supported ranges. */
+int secpe_select_primes(const secpe_params *p, uint64_t *out, int capacity);
+int secpe_ctx_n(const secpe_ctx *ctx);
+/* Device-side status word (0 = ok, else a SECPE_E* recorded by a kernel);
+ * synchronises `stream` first, then clears the word. */
+int secpe_stream_status(secpe_ctx *ctx, void *stream, int *device_status);
+const char *secpe_strerror(int code);
+
+/* ---- keys ------------------------------------------------------------- */
+/* Secret key s (ternary), relinearisation key (s^2 -> s) and one Galois key
+ * per rotation step in rot_steps (r > 0: RotL by r; r < 0: RotR by -r), all
+ * drawn from the counter-based SplitMix64 streams of `seed` (same streams
+ * as the CPU oracle).  Synchronous. */
+int secpe_keygen(secpe_ctx *ctx, uint64_t seed, const int32_t *rot_steps, int n_rot,
+                 secpe_keys **out);
+void secpe_keys_destroy(secpe_keys *keys);
+/* Copies key material to host, converted to plain residues: which = 0
+ * secret key NTT form [n_q+n_p][N]; which = 1 relinearisation key
+ * [dnum][2][n_q+n_p][N]; which = 2 Galois key of rotation step `step`. */
+int secpe_keys_export(const secpe_ctx *ctx, const secpe_keys *keys, int which, int32_t step,
+                      uint64_t *host_out, size_t words);
+
+/* ---- client side: encode + encrypt, decrypt + decode ------------------- */
+/* Secret-key encryption (reading of SecPE Sec. 3.1 step 1) of integer
+ * coefficients m[N] (host int64) at `level` with metadata `scale`:
+ * c1 = a, c0 = -a*s + m + e, randomness from the streams of `seed`. */
+int secpe_encrypt_coeffs(secpe_ctx *ctx, const secpe_keys *keys, const int64_t *m, int level,
+                         double scale, uint64_t seed, secpe_ct *out, void *stream);
+/* Encodes n real values into slots 0..n-1 (canonical embedding, slot j at
+ * zeta^(5^j); host FP64) and encrypts them at the top level, scale Delta. */
+int secpe_encrypt(secpe_ctx *ctx, const secpe_keys *keys, const double *v, int n, uint64_t seed,
+                  secpe_ct *out, void *stream);
+/* One prompt's logits (SecPE Sec. 3.1 step 1 / Eq. argmax layout): slots
+ * 0..C-1 hold v, slots C..C'-1 hold d_min (C' = next power of two), zeros
+ * beyond. */
+int secpe_encrypt_logits(secpe_ctx *ctx, const secpe_keys *keys, const double *v, int C,
+                         double d_min, uint64_t seed, secpe_ct *out, void *stream);
+/* Decrypts and decodes slots 0..n-1 to host doubles.  Synchronous. */
+int secpe_decrypt(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *ct, double *v_out,
+                  int n, void *stream);
+/* Centred coefficients of c0 + c1*s as doubles (host, N values). */
+int secpe_decrypt_coeffs(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *ct,
+                         double *coeffs_out, void *stream);
+
+/* ---- primitives (SecPE Sec. 2.2 operation list) ------------------------ */
+/* Forward (inverse = 0) or inverse negacyclic NTT, in place, of `count`
+ * limbs: limb k is at limbs + k*N, taken modulo the prime of index
+ * prime_idx[k] (host array; 0..n_q-1 ciphertext primes, n_q.. special).
+ * Forward: out[j] = sum_k a[k] psi^((2 brv(j) + 1) k), bit-reversed order. */
+int secpe_ntt(secpe_ctx *ctx, uint64_t *limbs, const int32_t *prime_idx, int count, int inverse,
+              void *stream);
+/* Same transform on `batch` ciphertexts laid out contiguously with a stride
+ * of `ct_stride` words: both polynomials, limbs 0..level. */
+int secpe_ntt_cts(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, int cap, int level,
+                  int inverse, void *stream);
+int secpe_add(secpe_ctx *ctx, const secpe_ct *a, const secpe_ct *b, secpe_ct *out, void *stream);
+int secpe_sub(secpe_ctx *ctx, const secpe_ct *a, const secpe_ct *b, secpe_ct *out, void *stream);
+/* out = a * c landing at out_level with scale exactly `target_scale`
+ * (constant round(c * target/scale_a * q_{out_level+1}), then rescale). */
+int secpe_mul_const(secpe_ctx *ctx, const secpe_ct *a, double c, double target_scale,
+                    int out_level, secpe_ct *out, void *stream);
+int secpe_add_const(secpe_ctx *ctx, const secpe_ct *a, double c, secpe_ct *out, void *stream);
+/* Tensor, relinearise, rescale: out at level min(level_a, level_b) - 1. */
+int secpe_mul_relin(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *a, const secpe_ct *b,
+                    secpe_ct *out, void *stream);
+/* Rounded division by the last prime; out may alias in. */
+int secpe_rescale(secpe_ctx *ctx, const secpe_ct *in, secpe_ct *out, void *stream);
+/* RotL(in, steps) for steps > 0, RotR(in, -steps) for steps < 0. */
+int secpe_rotate(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *in, int steps,
+                 secpe_ct *out, void *stream);
+/* Hybrid key switching of one polynomial d ([cap][N], limbs 0..level, NTT
+ * form) with the relinearisation key (galois_step = 0) or the Galois key of
+ * a rotation step: writes ks0, ks1 ([cap][N] each). */
+int secpe_keyswitch(secpe_ctx *ctx, const secpe_keys *keys, int galois_step, const uint64_t *d,
+                    int level, int cap, uint64_t *ks0, uint64_t *ks1, void *stream);
+/* Test-only, INSECURE stand-in for bootstrapping: decrypt, exact CRT lift,
+ * re-encrypt at the top level with the same scale; randomness from the
+ * stream (qseed, refresh_index). */
+int secpe_refresh_testonly(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *in,
+                           uint64_t qseed, uint64_t refresh_index, secpe_ct *out, void *stream);
+
+/* ---- SecPE circuit ----------------------------------------------------- */
+/* Sign(x) = f^df(g^dg(x)) (SecPE Eq. comp), each degree-9 polynomial by a
+ * depth-4 baby-step giant-step DAG; refreshes (counter from *refresh_index,
+ * advanced) when fewer than 4 (+ out_levels for the last) levels remain. */
+int secpe_sign(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *x, int out_levels,
+               uint64_t qseed, uint64_t *refresh_index, secpe_ct *out, void *stream);
+/* Max(a, y) = (a+y)/2 + (a-y)/2 * Sign(a-y) (SecPE Eq. max). */
+int secpe_max(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *a, const secpe_ct *y,
+              uint64_t qseed, uint64_t *refresh_index, secpe_ct *out, void *stream);
+/* Ensemble aggregation (SecPE Sec. 3.1 step 3, Eq. norm scale):
+ * out = (sum of the K cts) * 1/(K (d_max - d_min)) at level L-1, scale Delta. */
+int secpe_ensemble_aggregate(secpe_ctx *ctx, const secpe_ct *cts, int K, double d_min,
+                             double d_max, secpe_ct *out, void *stream);
+/* SecPE Alg. 1 on a normalised ciphertext y with C >= 2 classes: returns z
+ * with z ~ 1 at the argmax slot and ~ 0 at the other slots 0..C-1.
+ * Needs Galois keys for RotR(C') and RotL(2^i), i < log2 C'. */
+int secpe_encrypted_argmax(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *y, int C,
+                           uint64_t qseed, secpe_ct *z_out, void *stream);
+
+/* One ensemble query for the batched driver. */
+typedef struct {
+    const secpe_ct *cts;  /* K input ciphertexts (top level, scale Delta) */
+    int32_t K;
+    int32_t C;
+    double d_min, d_max;
+    uint64_t qseed;       /* refresh randomness */
+    secpe_ct *z_out;      /* output ciphertext (cap >= top level + 1) */
+} secpe_query;
+
+/* Aggregation + Argmax of n_queries independent queries, batched: every
+ * homomorphic operation runs once for all queries that take it at that
+ * point of the circuit.  Results equal the one-query calls bit for bit. */
+int secpe_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q,
+                       int n_queries, void *stream);
+
+/* Counters of the last circuit call on this context (rotations, Sign
+ * calls, relinearisations, refreshes, key switches, kernel launches). */
+typedef struct {
+    int64_t rotations, signs, relins, refreshes, keyswitches, launches;
+} secpe_counters;
+int secpe_get_counters(const secpe_ctx *ctx, secpe_counters *out);
+int secpe_reset_counters(secpe_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SECPE_H */

@@ -1,0 +1,504 @@
+// extern "C" entry points declared in include/secpe.h.
+#include <cmath>
+#include <cstring>
+
+#include "eval.h"
+
+namespace enc {
+bool encode_real(int n, const double *v, int nv, double scale, std::vector<long long> &m);
+void decode_real(int n, const double *coeffs, double scale, int nslots, double *out);
+}  // namespace enc
+
+int argmax_batch_impl(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_);
+
+namespace {
+
+// Per-call guard: sets the stream, and turns a sticky CUDA error into ECUDA.
+struct CallScope {
+    secpe_ctx *ctx;
+    CallScope(secpe_ctx *c, void *stream) : ctx(c) { c->stream = (cudaStream_t)stream; }
+};
+
+Ct view(secpe_ctx *ctx, const secpe_ct *c) {
+    Ct r;
+    r.v.data = (u64 *)c->data;
+    r.v.B = 1;
+    r.v.cap = c->cap;
+    r.v.stride = 2ll * c->cap * ctx->n;
+    r.v.level = c->level;
+    r.v.scale = c->scale;
+    r.v.n = ctx->n;
+    return r;
+}
+
+int check_ct(const secpe_ctx *ctx, const secpe_ct *c) {
+    if (!c || !c->data || c->level < 0 || c->level > ctx->L || c->cap < c->level + 1) return SECPE_EINVAL;
+    if (!(c->scale > 0.0)) return SECPE_EINVAL;
+    return SECPE_OK;
+}
+
+int copy_out(secpe_ctx *ctx, const Ct &src, secpe_ct *dst) {
+    if (!dst || !dst->data || dst->cap < src.level() + 1) return SECPE_EINVAL;
+    const size_t n = ctx->n;
+    if ((u64 *)dst->data != src.v.data)
+        SECPE_CUDA(cudaMemcpy2DAsync(dst->data, sizeof(u64) * dst->cap * n, src.v.data, sizeof(u64) * src.v.cap * n,
+                                     sizeof(u64) * (src.level() + 1) * n, 2, cudaMemcpyDeviceToDevice, ctx->stream));
+    dst->level = src.level();
+    dst->scale = src.scale();
+    return SECPE_OK;
+}
+
+int finish(secpe_ctx *ctx, int st) {
+    if (st != SECPE_OK) return st;
+    return cudaGetLastError() == cudaSuccess ? SECPE_OK : SECPE_ECUDA;
+}
+
+int make_ksk(secpe_ctx *ctx, secpe_keys *keys, const u64 *s_new, uint64_t kid, u64 **out) {
+    const int n = ctx->n, np = ctx->nprimes, L = ctx->L, alpha = ctx->alpha;
+    const int ndig = (L + 1 + alpha - 1) / alpha;
+    u64 *key = nullptr;
+    SECPE_CUDA(cudaMalloc(&key, sizeof(u64) * (size_t)ndig * 2 * np * n));
+    *out = key;
+    DevBuf a, e, en, pm;
+    SECPE_CHECK(a.alloc(ctx, sizeof(u64) * (size_t)np * n));
+    SECPE_CHECK(e.alloc(ctx, sizeof(long long) * (size_t)n));
+    SECPE_CHECK(en.alloc(ctx, sizeof(u64) * (size_t)np * n));
+    // [P]_{q_t}
+    std::vector<u64> pmod(np);
+    for (int t = 0; t < np; t++) {
+        u64 x = 1;
+        for (int j = 0; j < ctx->npsp; j++) x = hm::mulmod(x, ctx->primes[ctx->nq + j] % ctx->primes[t], ctx->primes[t]);
+        pmod[t] = x;
+    }
+    SECPE_CHECK(pm.alloc(ctx, sizeof(u64) * np));
+    SECPE_CUDA(cudaMemcpyAsync(pm.p, pmod.data(), sizeof(u64) * np, cudaMemcpyHostToDevice, ctx->stream));
+    PrimeList pl;
+    pl.n = np;
+    for (int t = 0; t < np; t++) pl.p[t] = t;
+    LimbSet ls = make_limbset(en.u(), 1, 0, 1, 0, np, 0);
+    for (int j = 0; j < ndig; j++) {
+        const int lo = j * alpha, hi = std::min((j + 1) * alpha, L + 1);
+        std::vector<u64> ka(1, hm::sm_stream(keys->seed, DOM_KSK_A, kid * 64 + j));
+        std::vector<u64> ke(1, hm::sm_stream(keys->seed, DOM_KSK_E, kid * 64 + j));
+        SECPE_CHECK(launch_sample_uniform(ctx, ka, a.u(), 0, pl));
+        SECPE_CHECK(launch_sample_small(ctx, ke, (long long *)e.p, 1));
+        SECPE_CHECK(launch_signed_to_limbs(ctx, (const long long *)e.p, nullptr, en.u(), 0, 1, pl));
+        SECPE_CHECK(ntt_limbset(ctx, ls, false));
+        SECPE_CHECK(launch_ksk_gen(ctx, a.u(), en.u(), keys->s_ntt, s_new, pm.u(),
+                                   key + (size_t)j * 2 * np * n, lo, hi));
+    }
+    return SECPE_OK;
+}
+
+}  // namespace
+
+extern "C" const char *secpe_strerror(int code) {
+    switch (code) {
+        case SECPE_OK: return "ok";
+        case SECPE_EINVAL: return "invalid argument";
+        case SECPE_ENOMEM: return "device allocation failed";
+        case SECPE_ELEVEL: return "not enough levels";
+        case SECPE_ESCALE: return "scale mismatch";
+        case SECPE_EKEY: return "missing key";
+        case SECPE_ECUDA: return "CUDA error";
+        case SECPE_ETIMEOUT: return "device wait timed out";
+        case SECPE_EADMIT: return "admission budget exceeded";
+        default: return "unknown error";
+    }
+}
+
+extern "C" int secpe_stream_status(secpe_ctx *ctx, void *stream, int *device_status) {
+    if (!ctx || !device_status) return SECPE_EINVAL;
+    SECPE_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int v = 0;
+    SECPE_CUDA(cudaMemcpy(&v, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    int z = 0;
+    SECPE_CUDA(cudaMemcpy(ctx->d_status, &z, sizeof(int), cudaMemcpyHostToDevice));
+    *device_status = v;
+    return SECPE_OK;
+}
+
+extern "C" int secpe_get_counters(const secpe_ctx *ctx, secpe_counters *out) {
+    if (!ctx || !out) return SECPE_EINVAL;
+    *out = ctx->counters;
+    return SECPE_OK;
+}
+
+extern "C" int secpe_reset_counters(secpe_ctx *ctx) {
+    if (!ctx) return SECPE_EINVAL;
+    std::memset(&ctx->counters, 0, sizeof(ctx->counters));
+    return SECPE_OK;
+}
+
+// ---------------------------------------------------------------- keys
+extern "C" int secpe_keygen(secpe_ctx *ctx, uint64_t seed, const int32_t *rot_steps, int n_rot,
+                            secpe_keys **out) {
+    if (!ctx || !out || n_rot < 0 || (n_rot > 0 && !rot_steps)) return SECPE_EINVAL;
+    *out = nullptr;
+    CallScope cs(ctx, nullptr);
+    const int n = ctx->n, np = ctx->nprimes;
+    secpe_keys *k = new secpe_keys();
+    k->seed = seed;
+    k->seed_set = 1;
+    k->s_ntt = nullptr;
+    k->rlk = nullptr;
+    int st = SECPE_OK;
+    do {
+        if (cudaMalloc(&k->s_ntt, sizeof(u64) * (size_t)np * n) != cudaSuccess) {
+            st = SECPE_ENOMEM;
+            break;
+        }
+        DevBuf s, s2;
+        if ((st = s.alloc(ctx, sizeof(long long) * n)) != SECPE_OK) break;
+        std::vector<u64> ks(1, hm::sm_stream(seed, DOM_SECRET, 0));
+        if ((st = launch_sample_small(ctx, ks, (long long *)s.p, 0)) != SECPE_OK) break;
+        PrimeList pl;
+        pl.n = np;
+        for (int t = 0; t < np; t++) pl.p[t] = t;
+        if ((st = launch_signed_to_limbs(ctx, (const long long *)s.p, nullptr, k->s_ntt, 0, 1, pl)) != SECPE_OK) break;
+        LimbSet ls = make_limbset(k->s_ntt, 1, 0, 1, 0, np, 0);
+        if ((st = ntt_limbset(ctx, ls, false)) != SECPE_OK) break;
+        if ((st = s2.alloc(ctx, sizeof(u64) * (size_t)np * n)) != SECPE_OK) break;
+        if ((st = launch_limb_mul(ctx, k->s_ntt, k->s_ntt, s2.u())) != SECPE_OK) break;
+        if ((st = make_ksk(ctx, k, s2.u(), 0, &k->rlk)) != SECPE_OK) break;
+        for (int r = 0; r < n_rot && st == SECPE_OK; r++) {
+            const unsigned g = galois_elt(ctx, rot_steps[r]);
+            if (k->gks.count(g)) continue;
+            DevBuf sg;
+            if ((st = sg.alloc(ctx, sizeof(u64) * (size_t)np * n)) != SECPE_OK) break;
+            if ((st = launch_limb_automorph(ctx, k->s_ntt, sg.u(), g)) != SECPE_OK) break;
+            u64 *key = nullptr;
+            st = make_ksk(ctx, k, sg.u(), g, &key);
+            if (key) k->gks[g] = key;
+        }
+    } while (0);
+    if (st == SECPE_OK && cudaStreamSynchronize(0) != cudaSuccess) st = SECPE_ECUDA;
+    if (st != SECPE_OK) {
+        secpe_keys_destroy(k);
+        return st;
+    }
+    *out = k;
+    return SECPE_OK;
+}
+
+extern "C" void secpe_keys_destroy(secpe_keys *keys) {
+    if (!keys) return;
+    cudaDeviceSynchronize();
+    if (keys->s_ntt) cudaFree(keys->s_ntt);
+    if (keys->rlk) cudaFree(keys->rlk);
+    for (auto &kv : keys->gks) cudaFree(kv.second);
+    delete keys;
+}
+
+extern "C" int secpe_keys_export(const secpe_ctx *cctx, const secpe_keys *keys, int which, int32_t step,
+                                 uint64_t *host_out, size_t words) {
+    secpe_ctx *ctx = const_cast<secpe_ctx *>(cctx);
+    if (!ctx || !keys || !host_out) return SECPE_EINVAL;
+    CallScope cs(ctx, nullptr);
+    const size_t n = ctx->n, np = ctx->nprimes;
+    const int ndig = (ctx->L + 1 + ctx->alpha - 1) / ctx->alpha;
+    if (which == 0) {
+        if (words < np * n) return SECPE_EINVAL;
+        SECPE_CUDA(cudaMemcpy(host_out, keys->s_ntt, sizeof(u64) * np * n, cudaMemcpyDeviceToHost));
+        return SECPE_OK;
+    }
+    const u64 *src = nullptr;
+    if (which == 1) src = keys->rlk;
+    else if (which == 2) src = galois_key(keys, galois_elt(ctx, step));
+    if (!src) return SECPE_EKEY;
+    const size_t total = (size_t)ndig * 2 * np * n;
+    if (words < total) return SECPE_EINVAL;
+    DevBuf tmp;
+    SECPE_CHECK(tmp.alloc(ctx, sizeof(u64) * total));
+    SECPE_CHECK(launch_from_mont(ctx, src, tmp.u(), ndig * 2 * (int)np));
+    SECPE_CUDA(cudaMemcpyAsync(host_out, tmp.p, sizeof(u64) * total, cudaMemcpyDeviceToHost, ctx->stream));
+    SECPE_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SECPE_OK;
+}
+
+// ---------------------------------------------------------------- client
+extern "C" int secpe_encrypt_coeffs(secpe_ctx *ctx, const secpe_keys *keys, const int64_t *m, int level,
+                                    double scale, uint64_t seed, secpe_ct *out, void *stream) {
+    if (!ctx || !keys || !m || !out || !out->data || level < 0 || level > ctx->L || out->cap < level + 1 ||
+        !(scale > 0))
+        return SECPE_EINVAL;
+    CallScope cs(ctx, stream);
+    const int n = ctx->n;
+    DevBuf dm, e, M, a;
+    SECPE_CHECK(dm.alloc(ctx, sizeof(long long) * n));
+    SECPE_CUDA(cudaMemcpyAsync(dm.p, m, sizeof(long long) * n, cudaMemcpyHostToDevice, ctx->stream));
+    SECPE_CHECK(e.alloc(ctx, sizeof(long long) * n));
+    std::vector<u64> ke(1, hm::sm_stream(seed, DOM_ENC_E, 0)), ka(1, hm::sm_stream(seed, DOM_ENC_A, 0));
+    SECPE_CHECK(launch_sample_small(ctx, ke, (long long *)e.p, 1));
+    PrimeList pl;
+    pl.n = level + 1;
+    for (int i = 0; i <= level; i++) pl.p[i] = i;
+    SECPE_CHECK(M.alloc(ctx, sizeof(u64) * (size_t)(level + 1) * n));
+    SECPE_CHECK(launch_signed_to_limbs(ctx, (const long long *)dm.p, (const long long *)e.p, M.u(), 0, 1, pl));
+    LimbSet ls = make_limbset(M.u(), 1, 0, 1, 0, level + 1, 0);
+    SECPE_CHECK(ntt_limbset(ctx, ls, false));
+    SECPE_CHECK(a.alloc(ctx, sizeof(u64) * (size_t)(level + 1) * n));
+    SECPE_CHECK(launch_sample_uniform(ctx, ka, a.u(), 0, pl));
+    Ct o = view(ctx, out);
+    o.v.level = level;
+    SECPE_CHECK(launch_enc_finish(ctx, M.u(), 0, a.u(), 0, keys->s_ntt, o.v, level + 1));
+    out->level = level;
+    out->scale = scale;
+    return finish(ctx, SECPE_OK);
+}
+
+extern "C" int secpe_encrypt(secpe_ctx *ctx, const secpe_keys *keys, const double *v, int n, uint64_t seed,
+                             secpe_ct *out, void *stream) {
+    if (!ctx || (!v && n > 0) || n < 0 || n > ctx->n / 2) return SECPE_EINVAL;
+    std::vector<long long> m;
+    if (!enc::encode_real(ctx->n, v, n, ctx->scale, m)) return SECPE_EINVAL;
+    return secpe_encrypt_coeffs(ctx, keys, (const int64_t *)m.data(), ctx->L, ctx->scale, seed, out, stream);
+}
+
+extern "C" int secpe_encrypt_logits(secpe_ctx *ctx, const secpe_keys *keys, const double *v, int C, double d_min,
+                                    uint64_t seed, secpe_ct *out, void *stream) {
+    if (!ctx || !v || C < 1) return SECPE_EINVAL;
+    int cp = 1;
+    while (cp < C) cp <<= 1;
+    if (cp > ctx->n / 2) return SECPE_EINVAL;
+    std::vector<double> full(cp, d_min);
+    for (int i = 0; i < C; i++) full[i] = v[i];
+    return secpe_encrypt(ctx, keys, full.data(), cp, seed, out, stream);
+}
+
+static int decrypt_to_host_coeffs(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *ct,
+                                  std::vector<double> &coeffs) {
+    const int n = ctx->n, lv = ct->level;
+    DevBuf m, dbl;
+    SECPE_CHECK(m.alloc(ctx, sizeof(u64) * (size_t)(lv + 1) * n));
+    Ct x = view(ctx, ct);
+    SECPE_CHECK(launch_dec_dot(ctx, x.v, keys->s_ntt, m.u(), lv + 1));
+    LimbSet ls = make_limbset(m.u(), 1, 0, 1, 0, lv + 1, 0);
+    SECPE_CHECK(ntt_limbset(ctx, ls, true));
+    SECPE_CHECK(dbl.alloc(ctx, sizeof(double) * n));
+    SECPE_CHECK(launch_crt_double(ctx, m.u(), lv, (double *)dbl.p));
+    coeffs.resize(n);
+    SECPE_CUDA(cudaMemcpyAsync(coeffs.data(), dbl.p, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    SECPE_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SECPE_OK;
+}
+
+extern "C" int secpe_decrypt_coeffs(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *ct,
+                                    double *coeffs_out, void *stream) {
+    if (!ctx || !keys || !coeffs_out) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, ct));
+    CallScope cs(ctx, stream);
+    std::vector<double> c;
+    SECPE_CHECK(decrypt_to_host_coeffs(ctx, keys, ct, c));
+    std::memcpy(coeffs_out, c.data(), sizeof(double) * ctx->n);
+    return SECPE_OK;
+}
+
+extern "C" int secpe_decrypt(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *ct, double *v_out, int n,
+                             void *stream) {
+    if (!ctx || !keys || !v_out || n < 0 || n > ctx->n / 2) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, ct));
+    CallScope cs(ctx, stream);
+    std::vector<double> c;
+    SECPE_CHECK(decrypt_to_host_coeffs(ctx, keys, ct, c));
+    enc::decode_real(ctx->n, c.data(), ct->scale, n, v_out);
+    return SECPE_OK;
+}
+
+// ---------------------------------------------------------------- primitives
+extern "C" int secpe_ntt(secpe_ctx *ctx, uint64_t *limbs, const int32_t *prime_idx, int count, int inverse,
+                         void *stream) {
+    if (!ctx || !limbs || !prime_idx || count < 0) return SECPE_EINVAL;
+    CallScope cs(ctx, stream);
+    for (int s = 0; s < count; s += SECPE_MAX_LIMBSET) {
+        const int c = std::min(SECPE_MAX_LIMBSET, count - s);
+        LimbSet ls = make_limbset((u64 *)limbs + (size_t)s * ctx->n, 1, 0, 1, 0, c, 0);
+        for (int j = 0; j < c; j++) {
+            if (prime_idx[s + j] < 0 || prime_idx[s + j] >= ctx->nprimes) return SECPE_EINVAL;
+            ls.prime_of[j] = (int8_t)prime_idx[s + j];
+        }
+        SECPE_CHECK(ntt_limbset(ctx, ls, inverse != 0));
+    }
+    return finish(ctx, SECPE_OK);
+}
+
+extern "C" int secpe_ntt_cts(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, int cap, int level,
+                             int inverse, void *stream) {
+    if (!ctx || !base || batch < 0 || level < 0 || level >= cap || level > ctx->L ||
+        ct_stride < 2ull * cap * ctx->n)
+        return SECPE_EINVAL;
+    CallScope cs(ctx, stream);
+    LimbSet ls = make_limbset((u64 *)base, batch, (long long)ct_stride, 2, (long long)cap * ctx->n, level + 1, 0);
+    return finish(ctx, ntt_limbset(ctx, ls, inverse != 0));
+}
+
+#define EVAL_PROLOGUE(ctx, stream) \
+    CallScope cs(ctx, stream);     \
+    Eval E{ctx, keys_, {}, 0};
+
+extern "C" int secpe_add(secpe_ctx *ctx, const secpe_ct *a, const secpe_ct *b, secpe_ct *out, void *stream) {
+    if (!ctx) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, a));
+    SECPE_CHECK(check_ct(ctx, b));
+    const secpe_keys *keys_ = nullptr;
+    EVAL_PROLOGUE(ctx, stream);
+    Ct r;
+    SECPE_CHECK(E.add(view(ctx, a), view(ctx, b), r));
+    return finish(ctx, copy_out(ctx, r, out));
+}
+
+extern "C" int secpe_sub(secpe_ctx *ctx, const secpe_ct *a, const secpe_ct *b, secpe_ct *out, void *stream) {
+    if (!ctx) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, a));
+    SECPE_CHECK(check_ct(ctx, b));
+    const secpe_keys *keys_ = nullptr;
+    EVAL_PROLOGUE(ctx, stream);
+    Ct r;
+    SECPE_CHECK(E.sub(view(ctx, a), view(ctx, b), r));
+    return finish(ctx, copy_out(ctx, r, out));
+}
+
+extern "C" int secpe_mul_const(secpe_ctx *ctx, const secpe_ct *a, double c, double target_scale, int out_level,
+                               secpe_ct *out, void *stream) {
+    if (!ctx || !(target_scale > 0)) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, a));
+    const secpe_keys *keys_ = nullptr;
+    EVAL_PROLOGUE(ctx, stream);
+    Ct r;
+    SECPE_CHECK(E.mul_const(view(ctx, a), {c}, target_scale, out_level, r));
+    return finish(ctx, copy_out(ctx, r, out));
+}
+
+extern "C" int secpe_add_const(secpe_ctx *ctx, const secpe_ct *a, double c, secpe_ct *out, void *stream) {
+    if (!ctx) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, a));
+    const secpe_keys *keys_ = nullptr;
+    EVAL_PROLOGUE(ctx, stream);
+    Ct r;
+    SECPE_CHECK(E.add_const(view(ctx, a), c, r));
+    return finish(ctx, copy_out(ctx, r, out));
+}
+
+extern "C" int secpe_mul_relin(secpe_ctx *ctx, const secpe_keys *keys_, const secpe_ct *a, const secpe_ct *b,
+                               secpe_ct *out, void *stream) {
+    if (!ctx || !keys_) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, a));
+    SECPE_CHECK(check_ct(ctx, b));
+    EVAL_PROLOGUE(ctx, stream);
+    Ct r;
+    SECPE_CHECK(E.mul(view(ctx, a), view(ctx, b), r));
+    return finish(ctx, copy_out(ctx, r, out));
+}
+
+extern "C" int secpe_rescale(secpe_ctx *ctx, const secpe_ct *in, secpe_ct *out, void *stream) {
+    if (!ctx) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, in));
+    const secpe_keys *keys_ = nullptr;
+    EVAL_PROLOGUE(ctx, stream);
+    Ct r;
+    SECPE_CHECK(E.rescale(view(ctx, in), r));
+    return finish(ctx, copy_out(ctx, r, out));
+}
+
+extern "C" int secpe_rotate(secpe_ctx *ctx, const secpe_keys *keys_, const secpe_ct *in, int steps, secpe_ct *out,
+                            void *stream) {
+    if (!ctx || !keys_) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, in));
+    EVAL_PROLOGUE(ctx, stream);
+    Ct r;
+    SECPE_CHECK(E.rotate(view(ctx, in), steps, r));
+    return finish(ctx, copy_out(ctx, r, out));
+}
+
+extern "C" int secpe_keyswitch(secpe_ctx *ctx, const secpe_keys *keys, int galois_step, const uint64_t *d,
+                               int level, int cap, uint64_t *ks0, uint64_t *ks1, void *stream) {
+    if (!ctx || !keys || !d || !ks0 || !ks1 || level < 0 || level > ctx->L || cap < level + 1) return SECPE_EINVAL;
+    CallScope cs(ctx, stream);
+    const u64 *key = galois_step == 0 ? keys->rlk : galois_key(keys, galois_elt(ctx, galois_step));
+    if (!key) return SECPE_EKEY;
+    const int n = ctx->n;
+    // result polys are written into a temporary [2][level+1][N] and copied
+    Ct o;
+    SECPE_CHECK(ct_alloc(ctx, 1, level, 1.0, o));
+    SECPE_CHECK(keyswitch(ctx, (const u64 *)d, 0, 1, level, key, o.v, false, false));
+    SECPE_CUDA(cudaMemcpyAsync(ks0, o.v.data, sizeof(u64) * (level + 1) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    SECPE_CUDA(cudaMemcpyAsync(ks1, o.v.data + o.v.pstride(), sizeof(u64) * (level + 1) * n,
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+    return finish(ctx, SECPE_OK);
+}
+
+extern "C" int secpe_refresh_testonly(secpe_ctx *ctx, const secpe_keys *keys_, const secpe_ct *in, uint64_t qseed,
+                                      uint64_t refresh_index, secpe_ct *out, void *stream) {
+    if (!ctx || !keys_) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, in));
+    EVAL_PROLOGUE(ctx, stream);
+    E.qseeds.assign(1, qseed);
+    E.ridx = refresh_index;
+    Ct r;
+    SECPE_CHECK(E.refresh(view(ctx, in), r));
+    return finish(ctx, copy_out(ctx, r, out));
+}
+
+extern "C" int secpe_sign(secpe_ctx *ctx, const secpe_keys *keys_, const secpe_ct *x, int out_levels, uint64_t qseed,
+                          uint64_t *refresh_index, secpe_ct *out, void *stream) {
+    if (!ctx || !keys_ || !refresh_index || out_levels < 0) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, x));
+    EVAL_PROLOGUE(ctx, stream);
+    E.qseeds.assign(1, qseed);
+    E.ridx = *refresh_index;
+    Ct r;
+    SECPE_CHECK(E.sign(view(ctx, x), out_levels, r));
+    *refresh_index = E.ridx;
+    return finish(ctx, copy_out(ctx, r, out));
+}
+
+extern "C" int secpe_max(secpe_ctx *ctx, const secpe_keys *keys_, const secpe_ct *a, const secpe_ct *y,
+                         uint64_t qseed, uint64_t *refresh_index, secpe_ct *out, void *stream) {
+    if (!ctx || !keys_ || !refresh_index) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, a));
+    SECPE_CHECK(check_ct(ctx, y));
+    EVAL_PROLOGUE(ctx, stream);
+    E.qseeds.assign(1, qseed);
+    E.ridx = *refresh_index;
+    Ct r;
+    SECPE_CHECK(E.max(view(ctx, a), view(ctx, y), r));
+    *refresh_index = E.ridx;
+    return finish(ctx, copy_out(ctx, r, out));
+}
+
+extern "C" int secpe_ensemble_aggregate(secpe_ctx *ctx, const secpe_ct *cts, int K, double d_min, double d_max,
+                                        secpe_ct *out, void *stream) {
+    if (!ctx || !cts || K < 1 || !(d_max > d_min)) return SECPE_EINVAL;
+    for (int i = 0; i < K; i++) SECPE_CHECK(check_ct(ctx, &cts[i]));
+    const secpe_keys *keys_ = nullptr;
+    EVAL_PROLOGUE(ctx, stream);
+    Ct y = view(ctx, &cts[0]);
+    for (int i = 1; i < K; i++) {
+        Ct t;
+        SECPE_CHECK(E.add(y, view(ctx, &cts[i]), t));
+        y = t;
+    }
+    const double w = 1.0 / (K * (d_max - d_min));
+    Ct r;
+    SECPE_CHECK(E.mul_const(y, {w}, ctx->scale, y.level() - 1, r));
+    return finish(ctx, copy_out(ctx, r, out));
+}
+
+extern "C" int secpe_encrypted_argmax(secpe_ctx *ctx, const secpe_keys *keys_, const secpe_ct *y, int C,
+                                      uint64_t qseed, secpe_ct *z_out, void *stream) {
+    if (!ctx || !keys_) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, y));
+    EVAL_PROLOGUE(ctx, stream);
+    E.qseeds.assign(1, qseed);
+    Ct r;
+    SECPE_CHECK(E.argmax(view(ctx, y), C, r));
+    return finish(ctx, copy_out(ctx, r, z_out));
+}
+
+extern "C" int secpe_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int n_queries,
+                                  void *stream) {
+    if (!ctx || !keys || !q || n_queries < 0) return SECPE_EINVAL;
+    if (n_queries == 0) return SECPE_OK;
+    CallScope cs(ctx, stream);
+    return finish(ctx, argmax_batch_impl(ctx, keys, q, n_queries));
+}

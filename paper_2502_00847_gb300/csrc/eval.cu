@@ -1,0 +1,409 @@
+// Batched evaluator: every operation acts on B ciphertexts at once (same
+// level and scale), so one launch per kernel serves the whole batch.  The
+// circuit follows SecPE Sec. 3.2 / Alg. 1 with the readings stated in the
+// header: Sign = f^df(g^dg) by a fixed depth-4 baby-step giant-step DAG per
+// polynomial, Max by Eq. max, QuickMax over rotations by 2^i, refresh when a
+// polynomial block would run out of levels.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "eval.h"
+
+int ct_alloc(secpe_ctx *ctx, int B, int level, double scale, Ct &out) {
+    out.buf = std::make_shared<DevBuf>();
+    SECPE_CHECK(out.buf->alloc(ctx, sizeof(u64) * (size_t)B * 2 * (level + 1) * ctx->n));
+    out.v.data = out.buf->u();
+    out.v.B = B;
+    out.v.cap = level + 1;
+    out.v.stride = 2ll * (level + 1) * ctx->n;
+    out.v.level = level;
+    out.v.scale = scale;
+    out.v.n = ctx->n;
+    return SECPE_OK;
+}
+
+Ct ct_slice(const Ct &x, int s, int e) {
+    Ct r = x;
+    r.v.data = x.v.data + (long long)s * x.v.stride;
+    r.v.B = e - s;
+    return r;
+}
+
+Ct ct_drop(const Ct &x, int level) {
+    Ct r = x;
+    r.v.level = level;
+    return r;
+}
+
+unsigned galois_elt(const secpe_ctx *ctx, int steps) {
+    const int half = ctx->n / 2;
+    long long r = steps;
+    if (r < 0) r = half + r;
+    r %= half;
+    if (r < 0) r += half;
+    unsigned long long g = 1, b = 5, m = 2ull * ctx->n;
+    while (r) {
+        if (r & 1) g = g * b % m;
+        b = b * b % m;
+        r >>= 1;
+    }
+    return (unsigned)g;
+}
+
+const u64 *galois_key(const secpe_keys *keys, unsigned g) {
+    auto it = keys->gks.find(g);
+    return it == keys->gks.end() ? nullptr : it->second;
+}
+
+// f_4 and g_4 of Cheon, Kim, Kim, Lee, Lee (Asiacrypt 2020), odd powers 1..9.
+int sign_coeffs(double g[5], double f[5]) {
+    static const double G[5] = {5850.0 / 1024, -34974.0 / 1024, 97015.0 / 1024, -113492.0 / 1024,
+                                46623.0 / 1024};
+    static const double F[5] = {315.0 / 128, -420.0 / 128, 378.0 / 128, -180.0 / 128, 35.0 / 128};
+    for (int i = 0; i < 5; i++) {
+        g[i] = G[i];
+        f[i] = F[i];
+    }
+    return SECPE_OK;
+}
+
+static bool scales_match(double a, double b) { return std::fabs(a - b) <= a * std::ldexp(1.0, -40); }
+
+int Eval::add(const Ct &a, const Ct &b, Ct &out) {
+    if (a.B() != b.B()) return SECPE_EINVAL;
+    if (!scales_match(a.scale(), b.scale())) return SECPE_ESCALE;
+    const int lv = std::min(a.level(), b.level());
+    Ct o;
+    SECPE_CHECK(ct_alloc(ctx, a.B(), lv, a.scale(), o));
+    SECPE_CHECK(launch_addsub(ctx, a.v, b.v, o.v, lv + 1, false));
+    out = o;
+    return SECPE_OK;
+}
+
+int Eval::sub(const Ct &a, const Ct &b, Ct &out) {
+    if (a.B() != b.B()) return SECPE_EINVAL;
+    if (!scales_match(a.scale(), b.scale())) return SECPE_ESCALE;
+    const int lv = std::min(a.level(), b.level());
+    Ct o;
+    SECPE_CHECK(ct_alloc(ctx, a.B(), lv, a.scale(), o));
+    SECPE_CHECK(launch_addsub(ctx, a.v, b.v, o.v, lv + 1, true));
+    out = o;
+    return SECPE_OK;
+}
+
+int Eval::rescale(const Ct &in, Ct &out) {
+    const int lv = in.level();
+    if (lv < 1) return SECPE_ELEVEL;
+    Ct o;
+    SECPE_CHECK(ct_alloc(ctx, in.B(), lv - 1, in.scale() / (double)ctx->primes[lv], o));
+    SECPE_CHECK(rescale_batch(ctx, in.v, o.v));
+    out = o;
+    return SECPE_OK;
+}
+
+int Eval::mul(const Ct &a, const Ct &b, Ct &out) {
+    if (a.B() != b.B()) return SECPE_EINVAL;
+    const int lv = std::min(a.level(), b.level());
+    if (lv < 1 + ctx->p.reserve) return SECPE_ELEVEL;
+    if (!keys || !keys->rlk) return SECPE_EKEY;
+    const int B = a.B(), n = ctx->n;
+    Ct d;  // (d0, d1, d2) per item, viewed as a 2-poly batch with stride 3 limb stacks
+    d.buf = std::make_shared<DevBuf>();
+    SECPE_CHECK(d.buf->alloc(ctx, sizeof(u64) * (size_t)B * 3 * (lv + 1) * n));
+    SECPE_CHECK(launch_tensor(ctx, a.v, b.v, d.buf->u(), lv + 1));
+    d.v.data = d.buf->u();
+    d.v.B = B;
+    d.v.cap = lv + 1;
+    d.v.stride = 3ll * (lv + 1) * n;
+    d.v.level = lv;
+    d.v.scale = a.scale() * b.scale();
+    d.v.n = n;
+    ctx->counters.relins += B;
+    SECPE_CHECK(keyswitch(ctx, d.v.data + 2ll * (lv + 1) * n, d.v.stride, B, lv, keys->rlk, d.v, true, true));
+    return rescale(d, out);
+}
+
+int Eval::mul_const(const Ct &x, const std::vector<double> &c, double target, int out_level, Ct &out) {
+    if (x.level() < out_level + 1 || out_level < ctx->p.reserve) return SECPE_ELEVEL;
+    if (c.size() != 1 && (int)c.size() != x.B()) return SECPE_EINVAL;
+    Ct xd = ct_drop(x, out_level + 1);
+    const double qf = (double)ctx->primes[out_level + 1];
+    const double factor = target / xd.scale() * qf;
+    std::vector<long long> k(c.size());
+    for (size_t i = 0; i < c.size(); i++) {
+        const double v = c[i] * factor;
+        if (!(std::fabs(v) < 4.0e18)) return SECPE_EINVAL;
+        k[i] = hm::round_half_away(v);
+    }
+    Ct t;
+    SECPE_CHECK(ct_alloc(ctx, x.B(), out_level + 1, xd.scale(), t));
+    SECPE_CHECK(launch_mulconst(ctx, xd.v, t.v, out_level + 2, k));
+    SECPE_CHECK(rescale(t, out));
+    out.v.scale = target;
+    return SECPE_OK;
+}
+
+int Eval::add_const(const Ct &x, double c, Ct &out) {
+    const double v = c * x.scale();
+    if (!(std::fabs(v) < 4.0e18)) return SECPE_EINVAL;
+    std::vector<long long> k(1, hm::round_half_away(v));
+    Ct o;
+    SECPE_CHECK(ct_alloc(ctx, x.B(), x.level(), x.scale(), o));
+    SECPE_CHECK(launch_addconst(ctx, x.v, o.v, x.level() + 1, k));
+    out = o;
+    return SECPE_OK;
+}
+
+int Eval::rotate(const Ct &x, int steps, Ct &out) {
+    const unsigned g = galois_elt(ctx, steps);
+    const u64 *key = keys ? galois_key(keys, g) : nullptr;
+    if (!key) return SECPE_EKEY;
+    const int lv = x.level();
+    Ct o;
+    SECPE_CHECK(ct_alloc(ctx, x.B(), lv, x.scale(), o));
+    SECPE_CHECK(launch_automorph(ctx, x.v, o.v, lv + 1, g));
+    ctx->counters.rotations += x.B();
+    SECPE_CHECK(keyswitch(ctx, o.v.data + o.v.pstride(), o.v.stride, x.B(), lv, key, o.v, true, false));
+    out = o;
+    return SECPE_OK;
+}
+
+int Eval::refresh(const Ct &x, Ct &out) {
+    if (!keys || !keys->s_ntt) return SECPE_EKEY;
+    const int B = x.B(), lv = x.level(), n = ctx->n, L = ctx->L;
+    if ((int)qseeds.size() != B || B > SECPE_MAX_BATCH_CONST) return SECPE_EINVAL;
+    DevBuf m, e, M, a;
+    SECPE_CHECK(m.alloc(ctx, sizeof(u64) * (size_t)B * (lv + 1) * n));
+    SECPE_CHECK(launch_dec_dot(ctx, x.v, keys->s_ntt, m.u(), lv + 1));
+    LimbSet mls = make_limbset(m.u(), B, (long long)(lv + 1) * n, 1, 0, lv + 1, 0);
+    SECPE_CHECK(ntt_limbset(ctx, mls, true));
+    std::vector<u64> ke(B), ka(B);
+    for (int b = 0; b < B; b++) {
+        const u64 sd = hm::sm_stream(qseeds[b], DOM_REFRESH, ridx);
+        ke[b] = hm::sm_stream(sd, DOM_ENC_E, 0);
+        ka[b] = hm::sm_stream(sd, DOM_ENC_A, 0);
+    }
+    ridx++;
+    SECPE_CHECK(e.alloc(ctx, sizeof(long long) * (size_t)B * n));
+    SECPE_CHECK(launch_sample_small(ctx, ke, (long long *)e.p, 1));
+    SECPE_CHECK(M.alloc(ctx, sizeof(u64) * (size_t)B * (L + 1) * n));
+    SECPE_CHECK(launch_crt_lift(ctx, m.u(), lv, (const long long *)e.p, M.u(), (long long)(L + 1) * n, L + 1, B));
+    LimbSet Mls = make_limbset(M.u(), B, (long long)(L + 1) * n, 1, 0, L + 1, 0);
+    SECPE_CHECK(ntt_limbset(ctx, Mls, false));
+    SECPE_CHECK(a.alloc(ctx, sizeof(u64) * (size_t)B * (L + 1) * n));
+    PrimeList pl;
+    pl.n = L + 1;
+    for (int i = 0; i <= L; i++) pl.p[i] = i;
+    SECPE_CHECK(launch_sample_uniform(ctx, ka, a.u(), (long long)(L + 1) * n, pl));
+    Ct o;
+    SECPE_CHECK(ct_alloc(ctx, B, L, x.scale(), o));
+    SECPE_CHECK(launch_enc_finish(ctx, M.u(), (long long)(L + 1) * n, a.u(), (long long)(L + 1) * n, keys->s_ntt,
+                                  o.v, L + 1));
+    ctx->counters.refreshes += B;
+    out = o;
+    return SECPE_OK;
+}
+
+int Eval::ensure(const Ct &x, int k, Ct &out) {
+    if (x.level() < k + ctx->p.reserve) return refresh(x, out);
+    out = x;
+    return SECPE_OK;
+}
+
+int Eval::poly9(const Ct &x, const double *c, double s_out, Ct &out) {
+    const int lv = x.level();
+    if (lv < 4 + ctx->p.reserve) return SECPE_ELEVEL;
+    const double q3 = (double)ctx->primes[lv - 3];
+    Ct x2, x3, x4, x8, t1, t2, Bv, T, t3, U, t4, t5, A, AT;
+    SECPE_CHECK(mul(x, x, x2));
+    SECPE_CHECK(mul(x, x2, x3));
+    SECPE_CHECK(mul(x2, x2, x4));
+    SECPE_CHECK(mul(x4, x4, x8));
+    const double sB = s_out * q3 / x4.scale();
+    SECPE_CHECK(mul_const(x, {c[2]}, sB, lv - 3, t1));
+    SECPE_CHECK(mul_const(x3, {c[3]}, sB, lv - 3, t2));
+    SECPE_CHECK(add(t1, t2, Bv));
+    SECPE_CHECK(mul(x4, Bv, T));
+    const double s9 = s_out * q3 / x8.scale();
+    SECPE_CHECK(mul_const(x, {c[4]}, s9, lv - 3, t3));
+    SECPE_CHECK(mul(x8, t3, U));
+    SECPE_CHECK(mul_const(x, {c[0]}, s_out, lv - 4, t4));
+    SECPE_CHECK(mul_const(x3, {c[1]}, s_out, lv - 4, t5));
+    SECPE_CHECK(add(t4, t5, A));
+    SECPE_CHECK(add(A, T, AT));
+    return add(AT, U, out);
+}
+
+int Eval::sign(const Ct &x, int out_levels, Ct &out) {
+    double g[5], f[5];
+    sign_coeffs(g, f);
+    ctx->counters.signs += x.B();
+    const int np = ctx->p.sign_dg + ctx->p.sign_df;
+    Ct cur = x;
+    for (int i = 0; i < np; i++) {
+        const int need = 4 + (i == np - 1 ? out_levels : 0);
+        Ct e, p;
+        SECPE_CHECK(ensure(cur, need, e));
+        SECPE_CHECK(poly9(e, i < ctx->p.sign_dg ? g : f, ctx->scale, p));
+        cur = p;
+    }
+    out = cur;
+    return SECPE_OK;
+}
+
+int Eval::max(const Ct &a, const Ct &y, Ct &out) {
+    Ct d, s, t, apy, u;
+    SECPE_CHECK(sub(a, y, d));
+    SECPE_CHECK(sign(d, 1, s));
+    SECPE_CHECK(mul(d, s, t));
+    t.v.scale = 2.0 * t.v.scale;
+    SECPE_CHECK(add(a, y, apy));
+    SECPE_CHECK(mul_const(apy, {0.5}, t.scale(), t.level(), u));
+    return add(t, u, out);
+}
+
+static int log2_ceil_pow(int C, int &cp) {
+    cp = 1;
+    int r = 0;
+    while (cp < C) {
+        cp <<= 1;
+        r++;
+    }
+    return r;
+}
+
+int Eval::argmax(const Ct &y, int C, Ct &out) {
+    if (C < 2) return SECPE_EINVAL;
+    int cp;
+    const int r = log2_ceil_pow(C, cp);
+    if (2 * cp > ctx->n / 2) return SECPE_EINVAL;
+    Ct rot, y1, ydup;
+    SECPE_CHECK(rotate(y, -cp, rot));
+    SECPE_CHECK(add(y, rot, y1));
+    ydup = y1;
+    for (int i = 0; i < r; i++) {
+        Ct ye, a, m;
+        SECPE_CHECK(ensure(y1, 1, ye));
+        SECPE_CHECK(rotate(ye, 1 << i, a));
+        SECPE_CHECK(max(a, ye, m));
+        y1 = m;
+    }
+    Ct al, d, s;
+    SECPE_CHECK(mul_const(ydup, {1.0}, y1.scale(), y1.level(), al));
+    SECPE_CHECK(sub(al, y1, d));
+    SECPE_CHECK(sign(d, 0, s));
+    return add_const(s, 1.0, out);
+}
+
+// ---------------------------------------------------------------- batch
+// Queries are ordered by r = log2 C' (descending) so that at phase k the
+// queries still in QuickMax form a prefix of the batch and the queries that
+// finish at phase k the following contiguous range.  All queries of one
+// range share level, scale and refresh history, so each range is a single
+// batched evaluation.
+int argmax_batch_impl(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_) {
+    const int n = ctx->n, L = ctx->L;
+    if (nq_ > SECPE_MAX_BATCH_CONST) return SECPE_EINVAL;
+    std::vector<int> order(nq_), rr(nq_), cps(nq_);
+    for (int b = 0; b < nq_; b++) {
+        if (q[b].C < 2 || q[b].K < 1 || !q[b].cts || !q[b].z_out) return SECPE_EINVAL;
+        rr[b] = log2_ceil_pow(q[b].C, cps[b]);
+        if (2 * cps[b] > n / 2) return SECPE_EINVAL;
+        for (int i = 0; i < q[b].K; i++) {
+            const secpe_ct &c = q[b].cts[i];
+            if (!c.data || c.level != L || c.cap < L + 1) return SECPE_EINVAL;
+            if (!scales_match(c.scale, ctx->scale)) return SECPE_ESCALE;
+        }
+    }
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return rr[x] > rr[y]; });
+    Eval E{ctx, keys, {}, 0};
+
+    // 1. aggregation into Y (sorted order), level L
+    Ct Y;
+    SECPE_CHECK(ct_alloc(ctx, nq_, L, ctx->scale, Y));
+    for (int s = 0; s < nq_; s++) {
+        const secpe_query &Q = q[order[s]];
+        CtB dst = ct_slice(Y, s, s + 1).v;
+        CtB c0 = {(u64 *)Q.cts[0].data, 1, 2ll * Q.cts[0].cap * n, Q.cts[0].cap, L, ctx->scale, n};
+        if (Q.K == 1) {
+            SECPE_CUDA(cudaMemcpy2DAsync(dst.data, sizeof(u64) * dst.cap * n, c0.data, sizeof(u64) * c0.cap * n,
+                                         sizeof(u64) * (L + 1) * n, 2, cudaMemcpyDeviceToDevice, ctx->stream));
+        } else {
+            CtB c1 = {(u64 *)Q.cts[1].data, 1, 2ll * Q.cts[1].cap * n, Q.cts[1].cap, L, ctx->scale, n};
+            SECPE_CHECK(launch_addsub(ctx, c0, c1, dst, L + 1, false));
+            for (int i = 2; i < Q.K; i++) {
+                CtB ci = {(u64 *)Q.cts[i].data, 1, 2ll * Q.cts[i].cap * n, Q.cts[i].cap, L, ctx->scale, n};
+                SECPE_CHECK(launch_addsub(ctx, dst, ci, dst, L + 1, false));
+            }
+        }
+    }
+    std::vector<double> w(nq_);
+    for (int s = 0; s < nq_; s++) {
+        const secpe_query &Q = q[order[s]];
+        w[s] = 1.0 / (Q.K * (Q.d_max - Q.d_min));
+    }
+    Ct Yn;
+    SECPE_CHECK(E.mul_const(Y, w, ctx->scale, L - 1, Yn));
+    Y = Ct();
+
+    // 2. duplication y + RotR(y, C') per group of equal r
+    std::vector<Ct> ydup_parts;
+    Ct Ydup;
+    SECPE_CHECK(ct_alloc(ctx, nq_, L - 1, ctx->scale, Ydup));
+    for (int s = 0; s < nq_;) {
+        int e = s;
+        while (e < nq_ && rr[order[e]] == rr[order[s]]) e++;
+        Eval Eg{ctx, keys, {}, 0};
+        Ct part = ct_slice(Yn, s, e), rot, sum;
+        SECPE_CHECK(Eg.rotate(part, -cps[order[s]], rot));
+        Ct dst = ct_slice(Ydup, s, e);
+        SECPE_CHECK(launch_addsub(ctx, part.v, rot.v, dst.v, L, false));
+        s = e;
+    }
+    Yn = Ct();
+
+    // 3. phases
+    const int rmax = rr[order[0]];
+    Ct ycur = Ydup;  // covers prefix [0, cnt_ge(k))
+    u64 ridx = 0;
+    for (int k = 0; k <= rmax; k++) {
+        int cnt_gt = 0, cnt_ge = 0;
+        for (int s = 0; s < nq_; s++) {
+            if (rr[order[s]] > k) cnt_gt++;
+            if (rr[order[s]] >= k) cnt_ge++;
+        }
+        // queries finishing now: [cnt_gt, cnt_ge)
+        if (cnt_ge > cnt_gt) {
+            Eval Ef{ctx, keys, {}, ridx};
+            for (int s = cnt_gt; s < cnt_ge; s++) Ef.qseeds.push_back(q[order[s]].qseed);
+            Ct yf = ct_slice(ycur, cnt_gt, cnt_ge), df = ct_slice(Ydup, cnt_gt, cnt_ge);
+            Ct al, d, sgn, z;
+            SECPE_CHECK(Ef.mul_const(df, {1.0}, yf.scale(), yf.level(), al));
+            SECPE_CHECK(Ef.sub(al, yf, d));
+            SECPE_CHECK(Ef.sign(d, 0, sgn));
+            SECPE_CHECK(Ef.add_const(sgn, 1.0, z));
+            for (int s = cnt_gt; s < cnt_ge; s++) {
+                secpe_ct *zo = q[order[s]].z_out;
+                if (zo->cap < z.level() + 1) return SECPE_EINVAL;
+                const u64 *src = z.v.data + (long long)(s - cnt_gt) * z.v.stride;
+                SECPE_CUDA(cudaMemcpy2DAsync(zo->data, sizeof(u64) * zo->cap * n, src, sizeof(u64) * z.v.cap * n,
+                                             sizeof(u64) * (z.level() + 1) * n, 2, cudaMemcpyDeviceToDevice,
+                                             ctx->stream));
+                zo->level = z.level();
+                zo->scale = z.scale();
+            }
+        }
+        if (cnt_gt == 0) break;
+        Eval Er{ctx, keys, {}, ridx};
+        for (int s = 0; s < cnt_gt; s++) Er.qseeds.push_back(q[order[s]].qseed);
+        Ct yr = ct_slice(ycur, 0, cnt_gt), ye, a, m;
+        SECPE_CHECK(Er.ensure(yr, 1, ye));
+        SECPE_CHECK(Er.rotate(ye, 1 << k, a));
+        SECPE_CHECK(Er.max(a, ye, m));
+        ridx = Er.ridx;
+        ycur = m;
+    }
+    return SECPE_OK;
+}

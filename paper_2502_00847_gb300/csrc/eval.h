@@ -1,0 +1,81 @@
+// Batched homomorphic evaluator (internal).
+#pragma once
+#include <memory>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.h"
+#include "launch.h"
+
+// Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync on the
+// stream of the call in progress).
+struct DevBuf {
+    secpe_ctx *ctx = nullptr;
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    int alloc(secpe_ctx *c, size_t b) {
+        ctx = c;
+        bytes = b;
+        if (b == 0) return SECPE_OK;
+        if (cudaMallocAsync(&p, b, c->stream) != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            return SECPE_ENOMEM;
+        }
+        return SECPE_OK;
+    }
+    ~DevBuf() {
+        if (p) cudaFreeAsync(p, ctx->stream);
+    }
+    u64 *u() const { return (u64 *)p; }
+};
+
+// A batch ciphertext value: a CtB view plus (optionally) the buffer owning it.
+struct Ct {
+    std::shared_ptr<DevBuf> buf;
+    CtB v;
+    int level() const { return v.level; }
+    double scale() const { return v.scale; }
+    int B() const { return v.B; }
+};
+
+// allocate a compact batch [B][2][level+1][N]
+int ct_alloc(secpe_ctx *ctx, int B, int level, double scale, Ct &out);
+// view of items [s, e) of a batch
+Ct ct_slice(const Ct &x, int s, int e);
+// same data, lower level (modulus drop)
+Ct ct_drop(const Ct &x, int level);
+
+struct Eval {
+    secpe_ctx *ctx;
+    const secpe_keys *keys;
+    std::vector<u64> qseeds;  // per item, refresh randomness
+    u64 ridx = 0;             // refresh counter (shared by the batch)
+
+    int add(const Ct &a, const Ct &b, Ct &out);
+    int sub(const Ct &a, const Ct &b, Ct &out);
+    int mul(const Ct &a, const Ct &b, Ct &out);
+    int mul_const(const Ct &x, const std::vector<double> &c, double target, int out_level, Ct &out);
+    int add_const(const Ct &x, double c, Ct &out);
+    int rescale(const Ct &in, Ct &out);
+    int rotate(const Ct &x, int steps, Ct &out);
+    int refresh(const Ct &x, Ct &out);
+    int ensure(const Ct &x, int k, Ct &out);
+    int poly9(const Ct &x, const double *c, double s_out, Ct &out);
+    int sign(const Ct &x, int out_levels, Ct &out);
+    int max(const Ct &a, const Ct &y, Ct &out);
+    int argmax(const Ct &y, int C, Ct &out);
+};
+
+// Hybrid key switching (keyswitch.cu): d = limbs 0..lv of one polynomial per
+// item (NTT form) at d + item*d_item_stride; writes (or adds, per poly) the
+// result into polys 0 and 1 of `out` (B items, level lv).
+int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int lv, const u64 *key,
+              const CtB &out, bool acc0, bool acc1);
+int rescale_batch(secpe_ctx *ctx, const CtB &in, const CtB &out);
+unsigned galois_elt(const secpe_ctx *ctx, int steps);
+const u64 *galois_key(const secpe_keys *keys, unsigned g);
+int sign_coeffs(double g[5], double f[5]);

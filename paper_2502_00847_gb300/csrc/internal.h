@@ -1,0 +1,121 @@
+// Internal declarations of the SecPE GB300 library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/secpe.h"
+#include "modarith.cuh"
+
+#define SECPE_MAX_PRIMES 64
+#define SECPE_MAX_LIMBSET 256
+
+// ---------------------------------------------------------------------------
+// Device-resident tables, passed to kernels by value.
+// ---------------------------------------------------------------------------
+struct DevCtx {
+    int log_n, n;
+    int nq, np_special, nprimes;  // nprimes = nq + np_special
+    int dnum, alpha;
+    const u64 *q;          // [nprimes]
+    const u64 *qinv_neg;   // [nprimes]  -q^-1 mod 2^64
+    const u64 *r2;         // [nprimes]  2^128 mod q
+    const u64 *mu;         // [nprimes]  floor(2^64 / q)
+    const ulonglong2 *tw_fwd;  // [nprimes][N]  (psi^brv(k), shoup)
+    const ulonglong2 *tw_inv;  // [nprimes][N]  (psi^-brv(k), shoup)
+    const ulonglong2 *ninv;    // [nprimes]     (N^-1, shoup)
+    const ulonglong2 *ninv_w1; // [nprimes]     (psi^-brv(1) * N^-1, shoup)
+    // ModUp base conversion, per (level, digit): digit prime i (< alpha)
+    const ulonglong2 *mu_inv;  // [(L+1)*dnum*alpha]  [Qhat_i^-1]_{q_i} (shoup)
+    const u64 *mu_hat;         // [(L+1)*dnum*alpha*nprimes] Montgomery form of Qhat_i mod t
+    // ModDown from the special primes
+    const ulonglong2 *md_inv;  // [np_special] [Phat_j^-1]_{p_j} (shoup)
+    const u64 *md_hat;         // [np_special*nq] Montgomery form of Phat_j mod q_i
+    const ulonglong2 *md_pinv; // [nq] P^-1 mod q_i (shoup)
+    const u64 *md_hP;          // [nprimes] floor(P/2) mod t
+    // Rescale by q_l, per level l: [l*nq + i]
+    const ulonglong2 *rs_qinv; // q_l^-1 mod q_i (shoup)
+    const u64 *rs_hmod;        // floor(q_l/2) mod q_i
+    // Mixed-radix CRT over q_0..q_l
+    const ulonglong2 *mr_inv;  // [nq*nq]  [j*nq+i] = q_j^-1 mod q_i (shoup)
+    const u64 *mr_M;           // [nq*nq]  [i*nq+t] = (q_0...q_{i-1}) mod q_t
+    const u64 *mr_H;           // [nq*nq]  [l*nq+i] mixed-radix digit i of (Q_l-1)/2
+    const u64 *mr_Q;           // [nq*nq]  [l*nq+t] = Q_l mod q_t
+    const double *mr_Mf;       // [nq] (q_0...q_{i-1}) as double
+    int *status;               // device status word
+};
+
+// A set of limbs for batched per-limb kernels: limb (item, poly, j) lives at
+// base + item*item_stride + poly*poly_stride + j*N and is taken modulo the
+// prime of index prime_of[poly*nlimb + j].
+struct LimbSet {
+    u64 *base;
+    long long item_stride, poly_stride;
+    int nitem, npoly, nlimb;
+    int8_t prime_of[SECPE_MAX_LIMBSET];
+};
+
+// A batch of B ciphertexts laid out [B][2][cap][N] with `stride` words
+// between items (stride >= 2*cap*N); limbs 0..level valid.
+struct CtB {
+    u64 *data = nullptr;
+    int B = 0;
+    long long stride = 0;
+    int cap = 0;
+    int level = 0;
+    double scale = 0.0;
+    int n = 0;
+    u64 *poly(int b, int k) const { return data + b * stride + (long long)k * cap * n; }
+    long long pstride() const { return (long long)cap * n; }
+};
+
+struct secpe_ctx {
+    secpe_params p;
+    int n, log_n, nq, npsp, nprimes, L, dnum, alpha;
+    std::vector<u64> primes;   // q_0..q_L, p_0..p_{k-1}
+    std::vector<u64> psi;
+    double scale;
+    DevCtx dev;
+    std::vector<void *> allocations;
+    int *d_status;
+    secpe_counters counters;
+    cudaStream_t stream;  // stream of the call in progress
+    // host copies used by host-side constant encoding
+    std::vector<u64> h_qinv_neg, h_r2, h_mu;
+};
+
+struct secpe_keys {
+    int seed_set;
+    uint64_t seed;
+    u64 *s_ntt;                        // [nprimes][N] plain residues
+    u64 *rlk;                          // [dnum][2][nprimes][N] Montgomery form
+    std::map<uint32_t, u64 *> gks;     // Galois element -> key
+};
+
+// ---------------------------------------------------------------------------
+// host math (hostmath.cpp)
+// ---------------------------------------------------------------------------
+namespace hm {
+u64 mulmod(u64 a, u64 b, u64 q);
+u64 powmod(u64 a, u64 e, u64 q);
+u64 invmod(u64 a, u64 q);
+u64 shoup(u64 w, u64 q);      // floor(w * 2^64 / q)
+u64 neg_inv64(u64 q);         // -q^-1 mod 2^64
+bool is_prime(u64 n);
+// Prime selection rule of secpe_params (see secpe.h); returns false when the
+// parameters are out of range.
+bool select_primes(const secpe_params &p, std::vector<u64> &q, std::vector<u64> &special);
+u64 find_psi(u64 q, u64 n);
+uint32_t bitrev(uint32_t x, int bits);
+// Counter-based SplitMix64 stream (Steele, Lea, Flood 2014).
+u64 sm_mix(u64 z);
+u64 sm_stream(u64 seed, u64 domain, u64 index);
+long long round_half_away(double v);
+}  // namespace hm
+
+// stream domains of the counter-based sampler
+enum { DOM_SECRET = 1, DOM_KSK_A = 2, DOM_KSK_E = 3, DOM_ENC_A = 4, DOM_ENC_E = 5,
+       DOM_REFRESH = 6 };

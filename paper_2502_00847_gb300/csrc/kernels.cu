@@ -1,0 +1,636 @@
+// Element-wise, sampling, CRT and key-switching building-block kernels.
+//
+// Layout conventions: a limb is N consecutive residues; a polynomial is a
+// stack of limbs (limb i modulo prime index i for ciphertext primes, nq + j
+// for special prime j); a ciphertext batch is [B][2][cap][N] (CtB).
+// Per-limb kernels use blockIdx.y for the limb and blockIdx.x * 256 +
+// threadIdx.x for a pair of coefficients (one 128-bit load per operand).
+#include "internal.h"
+#include "kernels.h"
+#include "launch.h"
+
+namespace {
+
+__device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *reinterpret_cast<const ulonglong2 *>(p); }
+__device__ __forceinline__ void st2(u64 *p, ulonglong2 v) { *reinterpret_cast<ulonglong2 *>(p) = v; }
+
+// residue of a signed 64-bit integer modulo q
+__device__ __forceinline__ u64 signed_mod(long long k, u64 q, u64 mu) {
+    if (k >= 0) return reduce64((u64)k, q, mu);
+    u64 r = reduce64((u64)(-(k + 1)) + 1, q, mu);
+    return r == 0 ? 0 : q - r;
+}
+
+// ------------------------------------------------------------ add / sub
+__global__ void k_addsub(DevCtx c, const u64 *a, long long as, const u64 *b, long long bs,
+                         u64 *o, long long os, int cap_a, int cap_b, int cap_o, int nl, int sub) {
+    const int li = blockIdx.y;
+    const int i = li % nl, k = (li / nl) & 1, item = li / (2 * nl);
+    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= c.n) return;
+    const u64 q = c.q[i];
+    const long long ao = item * as + ((long long)k * cap_a + i) * c.n + e;
+    const long long bo = item * bs + ((long long)k * cap_b + i) * c.n + e;
+    const long long oo = item * os + ((long long)k * cap_o + i) * c.n + e;
+    ulonglong2 x = ld2(a + ao), y = ld2(b + bo);
+    if (sub) {
+        x.x = sub_mod(x.x, y.x, q);
+        x.y = sub_mod(x.y, y.y, q);
+    } else {
+        x.x = add_mod(x.x, y.x, q);
+        x.y = add_mod(x.y, y.y, q);
+    }
+    st2(o + oo, x);
+}
+
+// ------------------------------------------------------------ tensor
+// d[item][0..2][i] = (a0 b0, a0 b1 + a1 b0, a1 b1), d has cap nl.
+__global__ void k_tensor(DevCtx c, const u64 *a, long long as, int cap_a, const u64 *b, long long bs,
+                         int cap_b, u64 *d, int nl) {
+    const int li = blockIdx.y;
+    const int i = li % nl, item = li / nl;
+    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= c.n) return;
+    const u64 q = c.q[i], qi = c.qinv_neg[i], r2 = c.r2[i];
+    const u64 *A = a + item * as + (long long)i * c.n + e;
+    const u64 *Bp = b + item * bs + (long long)i * c.n + e;
+    const ulonglong2 a0 = ld2(A), a1 = ld2(A + (long long)cap_a * c.n);
+    const ulonglong2 b0 = ld2(Bp), b1 = ld2(Bp + (long long)cap_b * c.n);
+    u64 *D = d + (long long)item * 3 * nl * c.n + (long long)i * c.n + e;
+    const long long ps = (long long)nl * c.n;
+    ulonglong2 r;
+    r.x = mul_mod(a0.x, b0.x, q, qi, r2);
+    r.y = mul_mod(a0.y, b0.y, q, qi, r2);
+    st2(D, r);
+    acc128 s0 = {0, 0}, s1 = {0, 0};
+    mac(s0, a0.x, b1.x);
+    mac(s0, a1.x, b0.x);
+    mac(s1, a0.y, b1.y);
+    mac(s1, a1.y, b0.y);
+    u64 t0 = redc(s0.hi, s0.lo, q, qi), t1 = redc(s1.hi, s1.lo, q, qi);
+    r.x = redc(mulhi64(t0, r2), t0 * r2, q, qi);
+    r.y = redc(mulhi64(t1, r2), t1 * r2, q, qi);
+    st2(D + ps, r);
+    r.x = mul_mod(a1.x, b1.x, q, qi, r2);
+    r.y = mul_mod(a1.y, b1.y, q, qi, r2);
+    st2(D + 2 * ps, r);
+}
+
+// ------------------------------------------------------------ constants
+struct KArr {
+    long long k[SECPE_MAX_BATCH_CONST];
+};
+
+// out = x * k_item mod q_i on both polynomials, limbs 0..nl-1
+__global__ void k_mulconst(DevCtx c, const u64 *x, long long xs, int cap_x, u64 *o, long long os,
+                           int cap_o, int nl, const __grid_constant__ KArr ka, int per_item) {
+    const int li = blockIdx.y;
+    const int i = li % nl, kk = (li / nl) & 1, item = li / (2 * nl);
+    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= c.n) return;
+    const u64 q = c.q[i], qi = c.qinv_neg[i], r2 = c.r2[i];
+    const u64 w = signed_mod(ka.k[per_item ? item : 0], q, c.mu[i]);
+    const u64 wm = redc(mulhi64(w, r2), w * r2, q, qi);  // w * 2^64 mod q
+    ulonglong2 v = ld2(x + item * xs + ((long long)kk * cap_x + i) * c.n + e);
+    v.x = redc(mulhi64(v.x, wm), v.x * wm, q, qi);
+    v.y = redc(mulhi64(v.y, wm), v.y * wm, q, qi);
+    st2(o + item * os + ((long long)kk * cap_o + i) * c.n + e, v);
+}
+
+// out = x with k_item added to every NTT value of c0 (the constant polynomial)
+__global__ void k_addconst(DevCtx c, const u64 *x, long long xs, int cap_x, u64 *o, long long os,
+                           int cap_o, int nl, const __grid_constant__ KArr ka, int per_item) {
+    const int li = blockIdx.y;
+    const int i = li % nl, kk = (li / nl) & 1, item = li / (2 * nl);
+    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= c.n) return;
+    const u64 q = c.q[i];
+    ulonglong2 v = ld2(x + item * xs + ((long long)kk * cap_x + i) * c.n + e);
+    if (kk == 0) {
+        const u64 w = signed_mod(ka.k[per_item ? item : 0], q, c.mu[i]);
+        v.x = add_mod(v.x, w, q);
+        v.y = add_mod(v.y, w, q);
+    }
+    st2(o + item * os + ((long long)kk * cap_o + i) * c.n + e, v);
+}
+
+// ------------------------------------------------------------ automorphism
+// In NTT form (bit-reversed evaluations at psi^(2 brv(j) + 1)), X -> X^g
+// is the permutation out[j] = in[sigma(j)], 2 brv(sigma(j)) + 1 = g (2 brv(j) + 1) mod 2N.
+__global__ void k_automorph(DevCtx c, const u64 *x, long long xs, int cap_x, u64 *o, long long os,
+                            int cap_o, int nl, unsigned g) {
+    const int li = blockIdx.y;
+    const int i = li % nl, kk = (li / nl) & 1, item = li / (2 * nl);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= c.n) return;
+    const unsigned sh = 32 - c.log_n;
+    const unsigned ev = 2u * (__brev((unsigned)j) >> sh) + 1u;
+    const unsigned e2 = (unsigned)(((unsigned long long)ev * g) & (2ull * c.n - 1));
+    const unsigned src = __brev((e2 - 1u) >> 1) >> sh;
+    o[item * os + ((long long)kk * cap_o + i) * c.n + j] = x[item * xs + ((long long)kk * cap_x + i) * c.n + src];
+}
+
+// ------------------------------------------------------------ rescale
+// y: coefficient form of the last limb (level l) of both polys, [item][2][N].
+// z[item][2][i] = ([y + h]_{q_l} - h) mod q_i for i < l (coefficient form).
+__global__ void k_rescale_prep(DevCtx c, const u64 *y, u64 *z, int lv) {
+    const int li = blockIdx.y;  // (item, poly, i), i < lv
+    const int i = li % lv, kp = li / lv;  // kp = item*2 + poly
+    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= c.n) return;
+    const u64 ql = c.q[lv], h = ql >> 1;
+    const u64 qi = c.q[i], mui = c.mu[i];
+    const u64 hm = c.rs_hmod[(size_t)lv * c.nq + i];
+    ulonglong2 v = ld2(y + (long long)kp * c.n + e);
+    u64 y0 = add_mod(v.x, h, ql), y1 = add_mod(v.y, h, ql);
+    ulonglong2 r;
+    r.x = sub_mod(reduce64(y0, qi, mui), hm, qi);
+    r.y = sub_mod(reduce64(y1, qi, mui), hm, qi);
+    st2(z + ((long long)kp * lv + i) * c.n + e, r);
+}
+
+// out_i = (x_i - Z_i) * q_l^-1 mod q_i (NTT form), i < lv
+__global__ void k_rescale_fin(DevCtx c, const u64 *x, long long xs, int cap_x, const u64 *z, u64 *o,
+                              long long os, int cap_o, int lv) {
+    const int li = blockIdx.y;
+    const int i = li % lv, kk = (li / lv) & 1, item = li / (2 * lv);
+    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= c.n) return;
+    const u64 q = c.q[i];
+    const ulonglong2 w = c.rs_qinv[(size_t)lv * c.nq + i];
+    ulonglong2 a = ld2(x + item * xs + ((long long)kk * cap_x + i) * c.n + e);
+    const ulonglong2 b = ld2(z + (((long long)item * 2 + kk) * lv + i) * c.n + e);
+    a.x = mul_shoup(sub_mod(a.x, b.x, q), w.x, w.y, q);
+    a.y = mul_shoup(sub_mod(a.y, b.y, q), w.x, w.y, q);
+    st2(o + item * os + ((long long)kk * cap_o + i) * c.n + e, a);
+}
+
+// ------------------------------------------------------------ key switching
+// ModUp base conversion of digit j: x = coefficient-form limbs of d
+// ([item][lv+1][N]); ext_j[item][t'] for the targets of digit j.
+__global__ void k_modup_bconv(DevCtx c, const u64 *x, u64 *ext, long long ext_item_stride,
+                              int ext_off, int lv, int j, int lo, int hi, int ntgt) {
+    const int item = blockIdx.y;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= c.n) return;
+    const int nd = hi - lo;
+    const size_t tb = ((size_t)lv * c.dnum + j) * c.alpha;
+    u64 y[16];
+#pragma unroll 4
+    for (int r = 0; r < nd; r++) {
+        const ulonglong2 w = c.mu_inv[tb + r];
+        y[r] = mul_shoup(x[((long long)item * (lv + 1) + lo + r) * c.n + e], w.x, w.y, c.q[lo + r]);
+    }
+    u64 *out = ext + item * ext_item_stride + (long long)ext_off * c.n + e;
+    int tt = 0;
+    for (int t = 0; t < lv + 1 + c.np_special; t++) {
+        if (t >= lo && t < hi) continue;
+        const int pt = t <= lv ? t : c.nq + (t - lv - 1);
+        const u64 q = c.q[pt];
+        acc128 s = {0, 0};
+        for (int r = 0; r < nd; r++) mac(s, y[r], c.mu_hat[(tb + r) * c.nprimes + pt]);
+        out[(long long)tt * c.n] = redc(s.hi, s.lo, q, c.qinv_neg[pt]);
+        tt++;
+    }
+}
+
+// Inner product with the key over digits: acc[item][0/1][t] for targets
+// t = 0..lv (q_t) and lv+1.. (special primes); key in Montgomery form.
+__global__ void k_ksk_ip(DevCtx c, const u64 *d, long long d_item_stride, const u64 *ext,
+                         long long ext_item_stride, const __grid_constant__ KsDigits dg,
+                         const u64 *key, u64 *acc, int lv) {
+    const int nt = lv + 1 + c.np_special;
+    const int t = blockIdx.y % nt, item = blockIdx.y / nt;
+    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= c.n) return;
+    const int pt = t <= lv ? t : c.nq + (t - lv - 1);
+    const u64 q = c.q[pt], qi = c.qinv_neg[pt];
+    acc128 s0a = {0, 0}, s0b = {0, 0}, s1a = {0, 0}, s1b = {0, 0};
+    const long long kpoly = (long long)c.nprimes * c.n;
+    for (int j = 0; j < dg.ndig; j++) {
+        const int lo = dg.lo[j], hi = dg.hi[j];
+        ulonglong2 xv;
+        if (t >= lo && t < hi) {
+            xv = ld2(d + item * d_item_stride + (long long)t * c.n + e);
+        } else {
+            const int tt = t < lo ? t : t - (hi - lo);
+            xv = ld2(ext + item * ext_item_stride + (long long)(dg.off[j] + tt) * c.n + e);
+        }
+        const u64 *kb = key + (long long)j * 2 * kpoly + (long long)pt * c.n + e;
+        const ulonglong2 k0 = ld2(kb), k1 = ld2(kb + kpoly);
+        mac(s0a, xv.x, k0.x);
+        mac(s0b, xv.y, k0.y);
+        mac(s1a, xv.x, k1.x);
+        mac(s1b, xv.y, k1.y);
+    }
+    u64 *o = acc + (long long)item * 2 * nt * c.n + (long long)t * c.n + e;
+    st2(o, make_ulonglong2(redc(s0a.hi, s0a.lo, q, qi), redc(s0b.hi, s0b.lo, q, qi)));
+    st2(o + (long long)nt * c.n,
+        make_ulonglong2(redc(s1a.hi, s1a.lo, q, qi), redc(s1b.hi, s1b.lo, q, qi)));
+}
+
+// ModDown base conversion: P-part limbs (coefficient form) of acc ->
+// conv[item][poly][i] = FastBConv([x + h]_P -> q_i) - h mod q_i.
+__global__ void k_moddown_bconv(DevCtx c, const u64 *acc, u64 *conv, int lv) {
+    const int nt = lv + 1 + c.np_special;
+    const int kp = blockIdx.y;  // item*2 + poly
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= c.n) return;
+    const int k = c.np_special;
+    u64 y[8];
+    for (int j = 0; j < k; j++) {
+        const int pj = c.nq + j;
+        u64 v = acc[((long long)kp * nt + lv + 1 + j) * c.n + e];
+        v = add_mod(v, c.md_hP[pj], c.q[pj]);
+        const ulonglong2 w = c.md_inv[j];
+        y[j] = mul_shoup(v, w.x, w.y, c.q[pj]);
+    }
+    for (int i = 0; i <= lv; i++) {
+        acc128 s = {0, 0};
+        for (int j = 0; j < k; j++) mac(s, y[j], c.md_hat[(size_t)j * c.nq + i]);
+        const u64 q = c.q[i];
+        const u64 r = redc(s.hi, s.lo, q, c.qinv_neg[i]);
+        conv[((long long)kp * (lv + 1) + i) * c.n + e] = sub_mod(r, c.md_hP[i], q);
+    }
+}
+
+// out[item][poly][i] (+)= (acc_i - conv_i) * P^-1 mod q_i (NTT form)
+__global__ void k_moddown_fin(DevCtx c, const u64 *acc, const u64 *conv, u64 *o, long long os, int cap_o,
+                              int lv, int accum0, int accum1) {
+    const int nl = lv + 1, nt = lv + 1 + c.np_special;
+    const int li = blockIdx.y;
+    const int i = li % nl, kp = li / nl, kk = kp & 1, item = kp >> 1;
+    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= c.n) return;
+    const u64 q = c.q[i];
+    const ulonglong2 w = c.md_pinv[i];
+    const ulonglong2 a = ld2(acc + ((long long)kp * nt + i) * c.n + e);
+    const ulonglong2 b = ld2(conv + ((long long)kp * nl + i) * c.n + e);
+    ulonglong2 r;
+    r.x = mul_shoup(sub_mod(a.x, b.x, q), w.x, w.y, q);
+    r.y = mul_shoup(sub_mod(a.y, b.y, q), w.x, w.y, q);
+    u64 *op = o + item * os + ((long long)kk * cap_o + i) * c.n + e;
+    if (kk == 0 ? accum0 : accum1) {
+        const ulonglong2 old = ld2(op);
+        r.x = add_mod(r.x, old.x, q);
+        r.y = add_mod(r.y, old.y, q);
+    }
+    st2(op, r);
+}
+
+// ------------------------------------------------------------ sampling
+__device__ __forceinline__ u64 sm_mix(u64 z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ u64 sm_word(u64 key, u64 ctr) { return sm_mix(key + (ctr + 1) * 0x9E3779B97F4A7C15ull); }
+
+// uniform residues: out limb r (prime prime_of[r]) at offset r*N of item `it`
+__global__ void k_sample_uniform(DevCtx c, const __grid_constant__ KeyArr keys, u64 *out,
+                                 long long item_stride, const __grid_constant__ PrimeList pl) {
+    const int r = blockIdx.y % pl.n, it = blockIdx.y / pl.n;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= c.n) return;
+    const int pi = pl.p[r];
+    const u64 q = c.q[pi];
+    const u64 key = keys.k[it];
+    const u64 ctr = 2ull * ((u64)pi * c.n + t);
+    const u64 w1 = sm_word(key, ctr), w2 = sm_word(key, ctr + 1);
+    const u128 hi = (u128)w1 * q;
+    const u64 lo_hi = mulhi64(w2, q);
+    out[it * item_stride + (long long)r * c.n + t] = (u64)((hi + lo_hi) >> 64);
+}
+
+// small integers: kind 0 = ternary, 1 = centred binomial eta = 21
+__global__ void k_sample_small(DevCtx c, const __grid_constant__ KeyArr keys, long long *out, int kind) {
+    const int it = blockIdx.y;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= c.n) return;
+    const u64 w = sm_word(keys.k[it], t);
+    long long v;
+    if (kind == 0) {
+        v = (long long)mulhi64(w, 3ull) - 1;
+    } else {
+        v = (long long)__popcll(w & 0x1FFFFFull) - (long long)__popcll((w >> 21) & 0x1FFFFFull);
+    }
+    out[(long long)it * c.n + t] = v;
+}
+
+// out[it][r][t] = (m[it][t] + e[it][t]) mod prime pl.p[r]  (e optional)
+__global__ void k_signed_to_limbs(DevCtx c, const long long *m, const long long *e, u64 *out,
+                                  long long item_stride, const __grid_constant__ PrimeList pl) {
+    const int r = blockIdx.y % pl.n, it = blockIdx.y / pl.n;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= c.n) return;
+    const int pi = pl.p[r];
+    long long v = m ? m[(long long)it * c.n + t] : 0;
+    if (e) v += e[(long long)it * c.n + t];
+    out[it * item_stride + (long long)r * c.n + t] = signed_mod(v, c.q[pi], c.mu[pi]);
+}
+
+// c0 = M - a*s, c1 = a (NTT form), limbs 0..nl-1, prime index = limb index
+__global__ void k_enc_finish(DevCtx c, const u64 *M, long long ms, const u64 *a, long long as,
+                             const u64 *s, u64 *o, long long os, int cap_o, int nl) {
+    const int li = blockIdx.y;
+    const int i = li % nl, it = li / nl;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= c.n) return;
+    const u64 q = c.q[i];
+    const u64 av = a[it * as + (long long)i * c.n + e];
+    const u64 as_ = mul_mod(av, s[(long long)i * c.n + e], q, c.qinv_neg[i], c.r2[i]);
+    u64 *op = o + it * os + (long long)i * c.n + e;
+    op[0] = sub_mod(M[it * ms + (long long)i * c.n + e], as_, q);
+    op[(long long)cap_o * c.n] = av;
+}
+
+// m_i = c0_i + c1_i * s_i
+__global__ void k_dec_dot(DevCtx c, const u64 *x, long long xs, int cap_x, const u64 *s, u64 *m, int nl) {
+    const int li = blockIdx.y;
+    const int i = li % nl, it = li / nl;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= c.n) return;
+    const u64 q = c.q[i];
+    const u64 *p = x + it * xs + (long long)i * c.n + e;
+    const u64 cs = mul_mod(p[(long long)cap_x * c.n], s[(long long)i * c.n + e], q, c.qinv_neg[i], c.r2[i]);
+    m[((long long)it * nl + i) * c.n + e] = add_mod(p[0], cs, q);
+}
+
+// Mixed-radix digits v_0..v_l of the residues x_0..x_l (Garner).
+__device__ __forceinline__ void mixed_radix(const DevCtx &c, const u64 *x, int lv, u64 *v) {
+    for (int i = 0; i <= lv; i++) {
+        const u64 q = c.q[i];
+        u64 a = x[i];
+        for (int j = 0; j < i; j++) {
+            const ulonglong2 w = c.mr_inv[(size_t)j * c.nq + i];
+            a = mul_shoup(sub_mod(a, reduce64(v[j], q, c.mu[i]), q), w.x, w.y, q);
+        }
+        v[i] = a;
+    }
+}
+
+// is X > (Q_l - 1)/2 ?  (compare mixed-radix digits from the top)
+__device__ __forceinline__ bool mr_greater_half(const DevCtx &c, const u64 *v, int lv) {
+    for (int i = lv; i >= 0; i--) {
+        const u64 h = c.mr_H[(size_t)lv * c.nq + i];
+        if (v[i] != h) return v[i] > h;
+    }
+    return false;
+}
+
+// Centred integer value of each coefficient as a double.
+__global__ void k_crt_double(DevCtx c, const u64 *m, int lv, double *out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= c.n) return;
+    u64 x[SECPE_MAX_PRIMES], v[SECPE_MAX_PRIMES];
+    for (int i = 0; i <= lv; i++) x[i] = m[(long long)i * c.n + e];
+    mixed_radix(c, x, lv, v);
+    const bool neg = mr_greater_half(c, v, lv);
+    double acc = 0.0;
+    for (int i = lv; i >= 0; i--) {
+        const double d = neg ? (double)(c.q[i] - 1 - v[i]) : (double)v[i];
+        acc = acc * (double)c.q[i] + d;
+    }
+    out[e] = neg ? -(acc + 1.0) : acc;
+}
+
+// Exact centred lift of m (coefficient form, level lv) plus e, reduced
+// modulo every ciphertext prime: out[it][t] for t = 0..ntop-1.
+__global__ void k_crt_lift(DevCtx c, const u64 *m, int lv, const long long *e, u64 *out,
+                           long long out_item_stride, int ntop) {
+    const int it = blockIdx.y;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= c.n) return;
+    u64 x[SECPE_MAX_PRIMES], v[SECPE_MAX_PRIMES];
+    for (int i = 0; i <= lv; i++) x[i] = m[((long long)it * (lv + 1) + i) * c.n + t];
+    mixed_radix(c, x, lv, v);
+    const bool neg = mr_greater_half(c, v, lv);
+    const long long ev = e[(long long)it * c.n + t];
+    for (int p = 0; p < ntop; p++) {
+        const u64 q = c.q[p], qi = c.qinv_neg[p], r2 = c.r2[p];
+        u64 acc = 0;
+        for (int i = 0; i <= lv; i++)
+            acc = add_mod(acc, mul_mod(reduce64(v[i], q, c.mu[p]), c.mr_M[(size_t)i * c.nq + p], q, qi, r2), q);
+        if (neg) acc = sub_mod(acc, c.mr_Q[(size_t)lv * c.nq + p], q);
+        acc = add_mod(acc, signed_mod(ev, q, c.mu[p]), q);
+        out[it * out_item_stride + (long long)p * c.n + t] = acc;
+    }
+}
+
+// Key-switching key of digit [lo, hi): over every prime t,
+// b = -a s + e + (lo <= t < hi ? [P]_{q_t} s' : 0), stored (b, a) in
+// Montgomery form at key[0][t], key[1][t].
+__global__ void k_ksk_gen(DevCtx c, const u64 *a, const u64 *e_ntt, const u64 *s, const u64 *sp,
+                          const u64 *pmod, u64 *key, int lo, int hi) {
+    const int t = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= c.n) return;
+    const u64 q = c.q[t], qi = c.qinv_neg[t], r2 = c.r2[t];
+    const long long o = (long long)t * c.n + x;
+    const u64 av = a[o];
+    u64 b = sub_mod(e_ntt[o], mul_mod(av, s[o], q, qi, r2), q);
+    if (t >= lo && t < hi) b = add_mod(b, mul_mod(pmod[t], sp[o], q, qi, r2), q);
+    const long long kp = (long long)c.nprimes * c.n;
+    key[o] = redc(mulhi64(b, r2), b * r2, q, qi);
+    key[kp + o] = redc(mulhi64(av, r2), av * r2, q, qi);
+}
+
+// Montgomery form -> plain residues (key export)
+__global__ void k_from_mont(DevCtx c, const u64 *in, u64 *out, int nlimb_total) {
+    const int li = blockIdx.y;
+    const int t = li % c.nprimes;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= c.n) return;
+    const long long o = (long long)li * c.n + x;
+    out[o] = redc(0, in[o], c.q[t], c.qinv_neg[t]);
+}
+
+// elementwise product of two limb stacks over primes 0..np-1 (s*s)
+__global__ void k_limb_mul(DevCtx c, const u64 *a, const u64 *b, u64 *o) {
+    const int t = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= c.n) return;
+    const long long i = (long long)t * c.n + x;
+    o[i] = mul_mod(a[i], b[i], c.q[t], c.qinv_neg[t], c.r2[t]);
+}
+
+// automorphism of one limb stack over all primes (NTT form)
+__global__ void k_limb_automorph(DevCtx c, const u64 *in, u64 *o, unsigned g) {
+    const int t = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= c.n) return;
+    const unsigned sh = 32 - c.log_n;
+    const unsigned ev = 2u * (__brev((unsigned)j) >> sh) + 1u;
+    const unsigned e2 = (unsigned)(((unsigned long long)ev * g) & (2ull * c.n - 1));
+    const unsigned src = __brev((e2 - 1u) >> 1) >> sh;
+    o[(long long)t * c.n + j] = in[(long long)t * c.n + src];
+}
+
+}  // namespace
+
+// ======================================================================
+// host launchers
+// ======================================================================
+static dim3 limb_grid(int n, int per_thread, long long nlimbs) {
+    return dim3((unsigned)((n / per_thread + 255) / 256), (unsigned)nlimbs);
+}
+
+int launch_addsub(secpe_ctx *ctx, const CtB &a, const CtB &b, const CtB &o, int nl, bool sub) {
+    if (nl <= 0 || a.B == 0) return SECPE_OK;
+    SECPE_LAUNCH(ctx, k_addsub, limb_grid(ctx->n, 2, (long long)a.B * 2 * nl), 256, 0, ctx->dev, a.data,
+                 a.stride, b.data, b.stride, o.data, o.stride, a.cap, b.cap, o.cap, nl, sub ? 1 : 0);
+    return SECPE_OK;
+}
+
+int launch_tensor(secpe_ctx *ctx, const CtB &a, const CtB &b, u64 *d, int nl) {
+    SECPE_LAUNCH(ctx, k_tensor, limb_grid(ctx->n, 2, (long long)a.B * nl), 256, 0, ctx->dev, a.data, a.stride,
+                 a.cap, b.data, b.stride, b.cap, d, nl);
+    return SECPE_OK;
+}
+
+static int fill_karr(KArr &ka, const std::vector<long long> &k, int B, int &per_item) {
+    if ((int)k.size() == 1) {
+        per_item = 0;
+        ka.k[0] = k[0];
+        return SECPE_OK;
+    }
+    if ((int)k.size() != B || B > SECPE_MAX_BATCH_CONST) return SECPE_EINVAL;
+    per_item = 1;
+    for (int i = 0; i < B; i++) ka.k[i] = k[i];
+    return SECPE_OK;
+}
+
+int launch_mulconst(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, const std::vector<long long> &k) {
+    KArr ka;
+    int per = 0;
+    SECPE_CHECK(fill_karr(ka, k, x.B, per));
+    SECPE_LAUNCH(ctx, k_mulconst, limb_grid(ctx->n, 2, (long long)x.B * 2 * nl), 256, 0, ctx->dev, x.data,
+                 x.stride, x.cap, o.data, o.stride, o.cap, nl, ka, per);
+    return SECPE_OK;
+}
+
+int launch_addconst(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, const std::vector<long long> &k) {
+    KArr ka;
+    int per = 0;
+    SECPE_CHECK(fill_karr(ka, k, x.B, per));
+    SECPE_LAUNCH(ctx, k_addconst, limb_grid(ctx->n, 2, (long long)x.B * 2 * nl), 256, 0, ctx->dev, x.data,
+                 x.stride, x.cap, o.data, o.stride, o.cap, nl, ka, per);
+    return SECPE_OK;
+}
+
+int launch_automorph(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, unsigned g) {
+    SECPE_LAUNCH(ctx, k_automorph, limb_grid(ctx->n, 1, (long long)x.B * 2 * nl), 256, 0, ctx->dev, x.data,
+                 x.stride, x.cap, o.data, o.stride, o.cap, nl, g);
+    return SECPE_OK;
+}
+
+int launch_rescale_prep(secpe_ctx *ctx, const u64 *y, u64 *z, int B, int lv) {
+    SECPE_LAUNCH(ctx, k_rescale_prep, limb_grid(ctx->n, 2, (long long)B * 2 * lv), 256, 0, ctx->dev, y, z, lv);
+    return SECPE_OK;
+}
+
+int launch_rescale_fin(secpe_ctx *ctx, const CtB &x, const u64 *z, const CtB &o, int lv) {
+    SECPE_LAUNCH(ctx, k_rescale_fin, limb_grid(ctx->n, 2, (long long)x.B * 2 * lv), 256, 0, ctx->dev, x.data,
+                 x.stride, x.cap, z, o.data, o.stride, o.cap, lv);
+    return SECPE_OK;
+}
+
+int launch_modup_bconv(secpe_ctx *ctx, const u64 *x, u64 *ext, long long ext_item_stride, int ext_off,
+                       int B, int lv, int j, int lo, int hi, int ntgt) {
+    SECPE_LAUNCH(ctx, k_modup_bconv, limb_grid(ctx->n, 1, B), 256, 0, ctx->dev, x, ext, ext_item_stride,
+                 ext_off, lv, j, lo, hi, ntgt);
+    return SECPE_OK;
+}
+
+int launch_ksk_ip(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const u64 *ext,
+                  long long ext_item_stride, const KsDigits &dg, const u64 *key, u64 *acc, int B, int lv) {
+    const int nt = lv + 1 + ctx->npsp;
+    SECPE_LAUNCH(ctx, k_ksk_ip, limb_grid(ctx->n, 2, (long long)B * nt), 256, 0, ctx->dev, d, d_item_stride,
+                 ext, ext_item_stride, dg, key, acc, lv);
+    return SECPE_OK;
+}
+
+int launch_moddown_bconv(secpe_ctx *ctx, const u64 *acc, u64 *conv, int B, int lv) {
+    SECPE_LAUNCH(ctx, k_moddown_bconv, limb_grid(ctx->n, 1, (long long)B * 2), 256, 0, ctx->dev, acc, conv, lv);
+    return SECPE_OK;
+}
+
+int launch_moddown_fin(secpe_ctx *ctx, const u64 *acc, const u64 *conv, const CtB &o, int lv, bool acc0,
+                       bool acc1) {
+    SECPE_LAUNCH(ctx, k_moddown_fin, limb_grid(ctx->n, 2, (long long)o.B * 2 * (lv + 1)), 256, 0, ctx->dev,
+                 acc, conv, o.data, o.stride, o.cap, lv, acc0 ? 1 : 0, acc1 ? 1 : 0);
+    return SECPE_OK;
+}
+
+int launch_sample_uniform(secpe_ctx *ctx, const std::vector<u64> &keys, u64 *out, long long item_stride,
+                          const PrimeList &pl) {
+    KeyArr ka;
+    if ((int)keys.size() > SECPE_MAX_BATCH_CONST) return SECPE_EINVAL;
+    for (size_t i = 0; i < keys.size(); i++) ka.k[i] = keys[i];
+    SECPE_LAUNCH(ctx, k_sample_uniform, limb_grid(ctx->n, 1, (long long)keys.size() * pl.n), 256, 0, ctx->dev,
+                 ka, out, item_stride, pl);
+    return SECPE_OK;
+}
+
+int launch_sample_small(secpe_ctx *ctx, const std::vector<u64> &keys, long long *out, int kind) {
+    KeyArr ka;
+    if ((int)keys.size() > SECPE_MAX_BATCH_CONST) return SECPE_EINVAL;
+    for (size_t i = 0; i < keys.size(); i++) ka.k[i] = keys[i];
+    SECPE_LAUNCH(ctx, k_sample_small, limb_grid(ctx->n, 1, (long long)keys.size()), 256, 0, ctx->dev, ka, out,
+                 kind);
+    return SECPE_OK;
+}
+
+int launch_signed_to_limbs(secpe_ctx *ctx, const long long *m, const long long *e, u64 *out,
+                           long long item_stride, int B, const PrimeList &pl) {
+    SECPE_LAUNCH(ctx, k_signed_to_limbs, limb_grid(ctx->n, 1, (long long)B * pl.n), 256, 0, ctx->dev, m, e, out,
+                 item_stride, pl);
+    return SECPE_OK;
+}
+
+int launch_enc_finish(secpe_ctx *ctx, const u64 *M, long long ms, const u64 *a, long long as, const u64 *s,
+                      const CtB &o, int nl) {
+    SECPE_LAUNCH(ctx, k_enc_finish, limb_grid(ctx->n, 1, (long long)o.B * nl), 256, 0, ctx->dev, M, ms, a, as, s,
+                 o.data, o.stride, o.cap, nl);
+    return SECPE_OK;
+}
+
+int launch_dec_dot(secpe_ctx *ctx, const CtB &x, const u64 *s, u64 *m, int nl) {
+    SECPE_LAUNCH(ctx, k_dec_dot, limb_grid(ctx->n, 1, (long long)x.B * nl), 256, 0, ctx->dev, x.data, x.stride,
+                 x.cap, s, m, nl);
+    return SECPE_OK;
+}
+
+int launch_crt_double(secpe_ctx *ctx, const u64 *m, int lv, double *out) {
+    SECPE_LAUNCH(ctx, k_crt_double, limb_grid(ctx->n, 1, 1), 256, 0, ctx->dev, m, lv, out);
+    return SECPE_OK;
+}
+
+int launch_crt_lift(secpe_ctx *ctx, const u64 *m, int lv, const long long *e, u64 *out,
+                    long long out_item_stride, int ntop, int B) {
+    SECPE_LAUNCH(ctx, k_crt_lift, limb_grid(ctx->n, 1, B), 256, 0, ctx->dev, m, lv, e, out, out_item_stride,
+                 ntop);
+    return SECPE_OK;
+}
+
+int launch_ksk_gen(secpe_ctx *ctx, const u64 *a, const u64 *e_ntt, const u64 *s, const u64 *sp,
+                   const u64 *pmod, u64 *key, int lo, int hi) {
+    SECPE_LAUNCH(ctx, k_ksk_gen, limb_grid(ctx->n, 1, ctx->nprimes), 256, 0, ctx->dev, a, e_ntt, s, sp, pmod,
+                 key, lo, hi);
+    return SECPE_OK;
+}
+
+int launch_from_mont(secpe_ctx *ctx, const u64 *in, u64 *out, int nlimb_total) {
+    SECPE_LAUNCH(ctx, k_from_mont, limb_grid(ctx->n, 1, nlimb_total), 256, 0, ctx->dev, in, out, nlimb_total);
+    return SECPE_OK;
+}
+
+int launch_limb_mul(secpe_ctx *ctx, const u64 *a, const u64 *b, u64 *o) {
+    SECPE_LAUNCH(ctx, k_limb_mul, limb_grid(ctx->n, 1, ctx->nprimes), 256, 0, ctx->dev, a, b, o);
+    return SECPE_OK;
+}
+
+int launch_limb_automorph(secpe_ctx *ctx, const u64 *in, u64 *o, unsigned g) {
+    SECPE_LAUNCH(ctx, k_limb_automorph, limb_grid(ctx->n, 1, ctx->nprimes), 256, 0, ctx->dev, in, o, g);
+    return SECPE_OK;
+}

@@ -1,0 +1,51 @@
+// Host launchers of the building-block kernels (kernels.cu).
+#pragma once
+#include <vector>
+
+#include "internal.h"
+
+#define SECPE_MAX_BATCH_CONST 1024
+
+// digit layout of one key switch at a given level
+struct KsDigits {
+    int ndig;
+    int lo[16], hi[16], off[16];  // prime range of digit j, offset of its targets in ext
+};
+struct KeyArr {
+    u64 k[SECPE_MAX_BATCH_CONST];
+};
+struct PrimeList {
+    int n;
+    int p[SECPE_MAX_PRIMES];
+};
+
+int launch_addsub(secpe_ctx *ctx, const CtB &a, const CtB &b, const CtB &o, int nl, bool sub);
+int launch_tensor(secpe_ctx *ctx, const CtB &a, const CtB &b, u64 *d, int nl);
+int launch_mulconst(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, const std::vector<long long> &k);
+int launch_addconst(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, const std::vector<long long> &k);
+int launch_automorph(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, unsigned g);
+int launch_rescale_prep(secpe_ctx *ctx, const u64 *y, u64 *z, int B, int lv);
+int launch_rescale_fin(secpe_ctx *ctx, const CtB &x, const u64 *z, const CtB &o, int lv);
+int launch_modup_bconv(secpe_ctx *ctx, const u64 *x, u64 *ext, long long ext_item_stride, int ext_off,
+                       int B, int lv, int j, int lo, int hi, int ntgt);
+int launch_ksk_ip(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const u64 *ext,
+                  long long ext_item_stride, const KsDigits &dg, const u64 *key, u64 *acc, int B, int lv);
+int launch_moddown_bconv(secpe_ctx *ctx, const u64 *acc, u64 *conv, int B, int lv);
+int launch_moddown_fin(secpe_ctx *ctx, const u64 *acc, const u64 *conv, const CtB &o, int lv, bool acc0,
+                       bool acc1);
+int launch_sample_uniform(secpe_ctx *ctx, const std::vector<u64> &keys, u64 *out, long long item_stride,
+                          const PrimeList &pl);
+int launch_sample_small(secpe_ctx *ctx, const std::vector<u64> &keys, long long *out, int kind);
+int launch_signed_to_limbs(secpe_ctx *ctx, const long long *m, const long long *e, u64 *out,
+                           long long item_stride, int B, const PrimeList &pl);
+int launch_enc_finish(secpe_ctx *ctx, const u64 *M, long long ms, const u64 *a, long long as, const u64 *s,
+                      const CtB &o, int nl);
+int launch_dec_dot(secpe_ctx *ctx, const CtB &x, const u64 *s, u64 *m, int nl);
+int launch_crt_double(secpe_ctx *ctx, const u64 *m, int lv, double *out);
+int launch_crt_lift(secpe_ctx *ctx, const u64 *m, int lv, const long long *e, u64 *out,
+                    long long out_item_stride, int ntop, int B);
+int launch_ksk_gen(secpe_ctx *ctx, const u64 *a, const u64 *e_ntt, const u64 *s, const u64 *sp,
+                   const u64 *pmod, u64 *key, int lo, int hi);
+int launch_from_mont(secpe_ctx *ctx, const u64 *in, u64 *out, int nlimb_total);
+int launch_limb_mul(secpe_ctx *ctx, const u64 *a, const u64 *b, u64 *o);
+int launch_limb_automorph(secpe_ctx *ctx, const u64 *in, u64 *o, unsigned g);

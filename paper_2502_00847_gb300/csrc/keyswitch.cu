@@ -1,0 +1,97 @@
+// Hybrid key switching (ModUp -> key inner product -> ModDown) and rescale,
+// orchestrated over batches of ciphertexts.
+//
+// Key switching of d (limbs 0..l, NTT form) with key (b_j, a_j), j < dnum:
+//  1. INTT of d.
+//  2. ModUp, per digit j = primes [j alpha, min((j+1) alpha, l+1)):
+//     FastBConv of the digit's limbs to every other prime of Q_l u P
+//     (no correction), then NTT of those limbs.  The digit's own limbs are d.
+//  3. Inner product over digits with the key, in Montgomery form, one
+//     reduction per output residue (lazy accumulation in 128 bits).
+//  4. ModDown: INTT of the special-prime limbs, rounded FastBConv to q_i
+//     (add floor(P/2) before, subtract it after), NTT, then
+//     (x_i - conv_i) * P^-1.
+// Rescale: INTT of the last limb, per other prime ([y + h]_{q_l} - h) mod
+// q_i, NTT, (x_i - z_i) * q_l^-1.
+#include "eval.h"
+
+int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int lv, const u64 *key,
+              const CtB &out, bool acc0, bool acc1) {
+    if (B == 0) return SECPE_OK;
+    const int n = ctx->n, k = ctx->npsp, alpha = ctx->alpha;
+    const int nt = lv + 1 + k;
+    KsDigits dg;
+    dg.ndig = 0;
+    int tot = 0;
+    LimbSet ext_ls;
+    ext_ls.npoly = 1;
+    for (int j = 0; j * alpha <= lv; j++) {
+        const int lo = j * alpha, hi = std::min((j + 1) * alpha, lv + 1);
+        dg.lo[j] = lo;
+        dg.hi[j] = hi;
+        dg.off[j] = tot;
+        for (int t = 0; t < nt; t++) {
+            if (t >= lo && t < hi) continue;
+            if (tot >= SECPE_MAX_LIMBSET) return SECPE_EINVAL;
+            ext_ls.prime_of[tot++] = (int8_t)(t <= lv ? t : ctx->nq + (t - lv - 1));
+        }
+        dg.ndig++;
+    }
+    ctx->counters.keyswitches++;
+
+    // 1. INTT of d into dcoef [B][lv+1][N]
+    DevBuf dcoef;
+    SECPE_CHECK(dcoef.alloc(ctx, sizeof(u64) * (size_t)B * (lv + 1) * n));
+    LimbSet dst = make_limbset(dcoef.u(), B, (long long)(lv + 1) * n, 1, 0, lv + 1, 0);
+    LimbSet src = make_limbset((u64 *)d, B, d_item_stride, 1, 0, lv + 1, 0);
+    SECPE_CHECK(ntt_limbset(ctx, dst, true, &src));
+
+    // 2. ModUp
+    DevBuf ext;
+    const long long ext_stride = (long long)tot * n;
+    SECPE_CHECK(ext.alloc(ctx, sizeof(u64) * (size_t)B * tot * n));
+    for (int j = 0; j < dg.ndig; j++) {
+        const int ntgt = nt - (dg.hi[j] - dg.lo[j]);
+        SECPE_CHECK(launch_modup_bconv(ctx, dcoef.u(), ext.u(), ext_stride, dg.off[j], B, lv, j, dg.lo[j],
+                                       dg.hi[j], ntgt));
+    }
+    ext_ls.base = ext.u();
+    ext_ls.nitem = B;
+    ext_ls.item_stride = ext_stride;
+    ext_ls.poly_stride = 0;
+    ext_ls.nlimb = tot;
+    SECPE_CHECK(ntt_limbset(ctx, ext_ls, false));
+
+    // 3. inner product -> acc [B][2][nt][N]
+    DevBuf acc;
+    SECPE_CHECK(acc.alloc(ctx, sizeof(u64) * (size_t)B * 2 * nt * n));
+    SECPE_CHECK(launch_ksk_ip(ctx, d, d_item_stride, ext.u(), ext_stride, dg, key, acc.u(), B, lv));
+
+    // 4. ModDown
+    LimbSet pls = make_limbset(acc.u() + (size_t)(lv + 1) * n, B, 2ll * nt * n, 2, (long long)nt * n, k,
+                               ctx->nq);
+    SECPE_CHECK(ntt_limbset(ctx, pls, true));
+    DevBuf conv;
+    SECPE_CHECK(conv.alloc(ctx, sizeof(u64) * (size_t)B * 2 * (lv + 1) * n));
+    SECPE_CHECK(launch_moddown_bconv(ctx, acc.u(), conv.u(), B, lv));
+    LimbSet cls = make_limbset(conv.u(), B, 2ll * (lv + 1) * n, 2, (long long)(lv + 1) * n, lv + 1, 0);
+    SECPE_CHECK(ntt_limbset(ctx, cls, false));
+    SECPE_CHECK(launch_moddown_fin(ctx, acc.u(), conv.u(), out, lv, acc0, acc1));
+    return SECPE_OK;
+}
+
+int rescale_batch(secpe_ctx *ctx, const CtB &in, const CtB &out) {
+    const int lv = in.level, n = ctx->n, B = in.B;
+    if (lv < 1) return SECPE_ELEVEL;
+    DevBuf y, z;
+    SECPE_CHECK(y.alloc(ctx, sizeof(u64) * (size_t)B * 2 * n));
+    SECPE_CHECK(z.alloc(ctx, sizeof(u64) * (size_t)B * 2 * lv * n));
+    LimbSet ysrc = make_limbset(in.data + (size_t)lv * n, B, in.stride, 2, in.pstride(), 1, lv);
+    LimbSet ydst = make_limbset(y.u(), B, 2ll * n, 2, n, 1, lv);
+    SECPE_CHECK(ntt_limbset(ctx, ydst, true, &ysrc));
+    SECPE_CHECK(launch_rescale_prep(ctx, y.u(), z.u(), B, lv));
+    LimbSet zls = make_limbset(z.u(), B, 2ll * lv * n, 2, (long long)lv * n, lv, 0);
+    SECPE_CHECK(ntt_limbset(ctx, zls, false));
+    SECPE_CHECK(launch_rescale_fin(ctx, in, z.u(), out, lv));
+    return SECPE_OK;
+}

@@ -1,0 +1,454 @@
+"""Thin ctypes binding of libsecpe.so (include/secpe.h): argument marshalling
+only.  Every homomorphic step runs in the library's CUDA kernels; device
+memory for ciphertexts comes from PyTorch tensors (uint64 words stored in
+int64 tensors), streams are PyTorch's current CUDA stream.
+
+The binding raises RuntimeError when the library is missing or a call
+returns an error; there is no fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsecpe.so")
+
+# names exported by include/secpe.h
+EXPORTS = [
+    "secpe_ctx_create", "secpe_ctx_destroy", "secpe_ctx_primes", "secpe_ctx_n", "secpe_stream_status",
+    "secpe_strerror", "secpe_keygen", "secpe_keys_destroy", "secpe_keys_export", "secpe_encrypt_coeffs",
+    "secpe_encrypt", "secpe_encrypt_logits", "secpe_decrypt", "secpe_decrypt_coeffs", "secpe_ntt",
+    "secpe_ntt_cts", "secpe_add", "secpe_sub", "secpe_mul_const", "secpe_add_const", "secpe_mul_relin",
+    "secpe_rescale", "secpe_rotate", "secpe_keyswitch", "secpe_refresh_testonly", "secpe_sign", "secpe_max",
+    "secpe_ensemble_aggregate", "secpe_encrypted_argmax", "secpe_argmax_batch", "secpe_get_counters",
+    "secpe_reset_counters", "secpe_select_primes",
+]
+
+
+class ParamsC(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int32) for name in (
+        "log_n", "q0_bits", "q_bits", "n_q", "p_bits", "n_p", "dnum", "log_scale", "sign_dg", "sign_df",
+        "reserve")]
+
+
+class CtC(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("level", ctypes.c_int32), ("cap", ctypes.c_int32),
+                ("scale", ctypes.c_double)]
+
+
+class QueryC(ctypes.Structure):
+    _fields_ = [("cts", ctypes.POINTER(CtC)), ("K", ctypes.c_int32), ("C", ctypes.c_int32),
+                ("d_min", ctypes.c_double), ("d_max", ctypes.c_double), ("qseed", ctypes.c_uint64),
+                ("z_out", ctypes.POINTER(CtC))]
+
+
+class CountersC(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "rotations", "signs", "relins", "refreshes", "keyswitches", "launches")]
+
+
+_lib = None
+
+
+def lib():
+    """Load libsecpe.so (built by paper_2502_00847_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libsecpe.so is not built (run paper_2502_00847_gb300.build.build()): %s" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "secpe_ctx_create": (i32, [P(ParamsC), P(vp)]),
+        "secpe_ctx_destroy": (None, [vp]),
+        "secpe_ctx_primes": (i32, [vp, P(u64)]),
+        "secpe_ctx_n": (i32, [vp]),
+        "secpe_stream_status": (i32, [vp, vp, P(i32)]),
+        "secpe_strerror": (ctypes.c_char_p, [i32]),
+        "secpe_keygen": (i32, [vp, u64, P(i32), i32, P(vp)]),
+        "secpe_keys_destroy": (None, [vp]),
+        "secpe_keys_export": (i32, [vp, vp, i32, i32, P(u64), ctypes.c_size_t]),
+        "secpe_encrypt_coeffs": (i32, [vp, vp, P(ctypes.c_int64), i32, dbl, u64, P(CtC), vp]),
+        "secpe_encrypt": (i32, [vp, vp, P(dbl), i32, u64, P(CtC), vp]),
+        "secpe_encrypt_logits": (i32, [vp, vp, P(dbl), i32, dbl, u64, P(CtC), vp]),
+        "secpe_decrypt": (i32, [vp, vp, P(CtC), P(dbl), i32, vp]),
+        "secpe_decrypt_coeffs": (i32, [vp, vp, P(CtC), P(dbl), vp]),
+        "secpe_ntt": (i32, [vp, vp, P(i32), i32, i32, vp]),
+        "secpe_ntt_cts": (i32, [vp, vp, i32, ctypes.c_size_t, i32, i32, i32, vp]),
+        "secpe_add": (i32, [vp, P(CtC), P(CtC), P(CtC), vp]),
+        "secpe_sub": (i32, [vp, P(CtC), P(CtC), P(CtC), vp]),
+        "secpe_mul_const": (i32, [vp, P(CtC), dbl, dbl, i32, P(CtC), vp]),
+        "secpe_add_const": (i32, [vp, P(CtC), dbl, P(CtC), vp]),
+        "secpe_mul_relin": (i32, [vp, vp, P(CtC), P(CtC), P(CtC), vp]),
+        "secpe_rescale": (i32, [vp, P(CtC), P(CtC), vp]),
+        "secpe_rotate": (i32, [vp, vp, P(CtC), i32, P(CtC), vp]),
+        "secpe_keyswitch": (i32, [vp, vp, i32, vp, i32, i32, vp, vp, vp]),
+        "secpe_refresh_testonly": (i32, [vp, vp, P(CtC), u64, u64, P(CtC), vp]),
+        "secpe_sign": (i32, [vp, vp, P(CtC), i32, u64, P(u64), P(CtC), vp]),
+        "secpe_max": (i32, [vp, vp, P(CtC), P(CtC), u64, P(u64), P(CtC), vp]),
+        "secpe_ensemble_aggregate": (i32, [vp, P(CtC), i32, dbl, dbl, P(CtC), vp]),
+        "secpe_encrypted_argmax": (i32, [vp, vp, P(CtC), i32, u64, P(CtC), vp]),
+        "secpe_argmax_batch": (i32, [vp, vp, P(QueryC), i32, vp]),
+        "secpe_get_counters": (i32, [vp, P(CountersC)]),
+        "secpe_reset_counters": (i32, [vp]),
+        "secpe_select_primes": (i32, [P(ParamsC), P(u64), i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def select_primes(**params):
+    """Host-only prime selection (no GPU needed): (ciphertext primes, special)."""
+    p = ParamsC(**{f[0]: params.get(f[0], 0) for f in ParamsC._fields_})
+    out = np.zeros(p.n_q + p.n_p, dtype=np.uint64)
+    _check(lib().secpe_select_primes(ctypes.byref(p), _u64p(out), len(out)), "secpe_select_primes")
+    vals = [int(x) for x in out]
+    return vals[: p.n_q], vals[p.n_q:]
+
+
+class SecpeError(RuntimeError):
+    def __init__(self, code, where):
+        msg = lib().secpe_strerror(code).decode()
+        super().__init__("%s failed: %s (%d)" % (where, msg, code))
+        self.code = code
+
+
+def _check(code, where):
+    if code != 0:
+        raise SecpeError(code, where)
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _u64p(arr):
+    return arr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
+class Context:
+    """secpe_ctx: primes, NTT and base-conversion tables on the device."""
+
+    def __init__(self, log_n, q0_bits, q_bits, n_q, p_bits, n_p, dnum, log_scale, sign_dg=2, sign_df=2,
+                 reserve=1):
+        self.params = dict(log_n=log_n, q0_bits=q0_bits, q_bits=q_bits, n_q=n_q, p_bits=p_bits, n_p=n_p,
+                           dnum=dnum, log_scale=log_scale, sign_dg=sign_dg, sign_df=sign_df, reserve=reserve)
+        p = ParamsC(**self.params)
+        h = ctypes.c_void_p()
+        _check(lib().secpe_ctx_create(ctypes.byref(p), ctypes.byref(h)), "secpe_ctx_create")
+        self.h = h
+        self.n = 1 << log_n
+        self.n_q, self.n_p = n_q, n_p
+        self.L = n_q - 1
+        self.scale = float(2 ** log_scale)
+
+    @classmethod
+    def from_params(cls, p):
+        """From any object with the secpe_params field names as attributes."""
+        return cls(**{f[0]: getattr(p, f[0]) for f in ParamsC._fields_})
+
+    def primes(self):
+        out = np.zeros(self.n_q + self.n_p, dtype=np.uint64)
+        _check(lib().secpe_ctx_primes(self.h, _u64p(out)), "secpe_ctx_primes")
+        return [int(x) for x in out]
+
+    def close(self):
+        if self.h:
+            lib().secpe_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def counters(self):
+        c = CountersC()
+        _check(lib().secpe_get_counters(self.h, ctypes.byref(c)), "secpe_get_counters")
+        return {f[0]: int(getattr(c, f[0])) for f in CountersC._fields_}
+
+    def reset_counters(self):
+        _check(lib().secpe_reset_counters(self.h), "secpe_reset_counters")
+
+    def stream_status(self):
+        v = ctypes.c_int32()
+        _check(lib().secpe_stream_status(self.h, _stream(), ctypes.byref(v)), "secpe_stream_status")
+        return int(v.value)
+
+    # ---------------------------------------------------------------- data
+    def new_ct(self, cap=None, device="cuda"):
+        """A zeroed ciphertext buffer [2][cap][N] (int64 storage of uint64)."""
+        import torch
+        cap = self.L + 1 if cap is None else cap
+        return Ciphertext(torch.zeros((2, cap, self.n), dtype=torch.int64, device=device), 0, self.scale)
+
+
+class Ciphertext:
+    """A device ciphertext: tensor [2][cap][N] plus level and scale."""
+
+    def __init__(self, data, level, scale):
+        self.data = data
+        self.level = level
+        self.scale = scale
+
+    @property
+    def cap(self):
+        return int(self.data.shape[1])
+
+    def struct(self):
+        return CtC(ctypes.c_void_p(self.data.data_ptr()), self.level, self.cap, self.scale)
+
+    def update(self, c):
+        self.level = int(c.level)
+        self.scale = float(c.scale)
+
+    def residues(self):
+        """Limbs 0..level of both polynomials as a numpy uint64 array."""
+        return self.data[:, : self.level + 1].cpu().numpy().view(np.uint64)
+
+    @staticmethod
+    def from_residues(arr, level, scale, cap=None):
+        import torch
+        arr = np.ascontiguousarray(arr, dtype=np.uint64)
+        cap = arr.shape[1] if cap is None else cap
+        t = torch.zeros((2, cap, arr.shape[2]), dtype=torch.int64)
+        t[:, : arr.shape[1]] = torch.from_numpy(arr.view(np.int64))
+        return Ciphertext(t.cuda(), level, scale)
+
+
+class Keys:
+    def __init__(self, ctx, seed, rot_steps=()):
+        steps = (ctypes.c_int32 * max(1, len(rot_steps)))(*rot_steps)
+        h = ctypes.c_void_p()
+        _check(lib().secpe_keygen(ctx.h, ctypes.c_uint64(seed), steps, len(rot_steps), ctypes.byref(h)),
+               "secpe_keygen")
+        self.h = h
+        self.ctx = ctx
+
+    def close(self):
+        if self.h:
+            lib().secpe_keys_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export(self, which, step=0):
+        n = self.ctx.n
+        npr = self.ctx.n_q + self.ctx.n_p
+        alpha = -(-self.ctx.n_q // self.ctx.params["dnum"])
+        ndig = -(-self.ctx.n_q // alpha)
+        words = npr * n if which == 0 else ndig * 2 * npr * n
+        out = np.zeros(words, dtype=np.uint64)
+        _check(lib().secpe_keys_export(self.ctx.h, self.h, which, step, _u64p(out), words), "secpe_keys_export")
+        return out.reshape((npr, n) if which == 0 else (ndig, 2, npr, n))
+
+
+# ------------------------------------------------------------------ client
+def encrypt_coeffs(ctx, keys, m, level, scale, seed, out=None):
+    m = np.ascontiguousarray(m, dtype=np.int64)
+    out = ctx.new_ct() if out is None else out
+    c = out.struct()
+    _check(lib().secpe_encrypt_coeffs(ctx.h, keys.h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), level,
+                                      scale, ctypes.c_uint64(seed), ctypes.byref(c), _stream()),
+           "secpe_encrypt_coeffs")
+    out.update(c)
+    return out
+
+
+def encrypt(ctx, keys, v, seed, out=None):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = ctx.new_ct() if out is None else out
+    c = out.struct()
+    _check(lib().secpe_encrypt(ctx.h, keys.h, v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(v),
+                               ctypes.c_uint64(seed), ctypes.byref(c), _stream()), "secpe_encrypt")
+    out.update(c)
+    return out
+
+
+def encrypt_logits(ctx, keys, v, d_min, seed, out=None):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = ctx.new_ct() if out is None else out
+    c = out.struct()
+    _check(lib().secpe_encrypt_logits(ctx.h, keys.h, v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(v),
+                                      d_min, ctypes.c_uint64(seed), ctypes.byref(c), _stream()),
+           "secpe_encrypt_logits")
+    out.update(c)
+    return out
+
+
+def decrypt(ctx, keys, ct, n):
+    out = np.zeros(n, dtype=np.float64)
+    c = ct.struct()
+    _check(lib().secpe_decrypt(ctx.h, keys.h, ctypes.byref(c), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               n, _stream()), "secpe_decrypt")
+    return out
+
+
+def decrypt_coeffs(ctx, keys, ct):
+    out = np.zeros(ctx.n, dtype=np.float64)
+    c = ct.struct()
+    _check(lib().secpe_decrypt_coeffs(ctx.h, keys.h, ctypes.byref(c),
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream()),
+           "secpe_decrypt_coeffs")
+    return out
+
+
+# -------------------------------------------------------------- primitives
+def ntt(ctx, limbs, prime_idx, inverse=False):
+    """In-place (I)NTT of a [count][N] int64 CUDA tensor of residues."""
+    pi = (ctypes.c_int32 * len(prime_idx))(*prime_idx)
+    _check(lib().secpe_ntt(ctx.h, ctypes.c_void_p(limbs.data_ptr()), pi, len(prime_idx), 1 if inverse else 0,
+                           _stream()), "secpe_ntt")
+    return limbs
+
+
+def ntt_cts(ctx, base, batch, ct_stride, cap, level, inverse=False):
+    _check(lib().secpe_ntt_cts(ctx.h, ctypes.c_void_p(base.data_ptr()), batch, ct_stride, cap, level,
+                               1 if inverse else 0, _stream()), "secpe_ntt_cts")
+
+
+def _binary(fn, name, ctx, a, b, out=None):
+    out = ctx.new_ct() if out is None else out
+    ca, cb, co = a.struct(), b.struct(), out.struct()
+    _check(fn(ctx.h, ctypes.byref(ca), ctypes.byref(cb), ctypes.byref(co), _stream()), name)
+    out.update(co)
+    return out
+
+
+def add(ctx, a, b, out=None):
+    return _binary(lib().secpe_add, "secpe_add", ctx, a, b, out)
+
+
+def sub(ctx, a, b, out=None):
+    return _binary(lib().secpe_sub, "secpe_sub", ctx, a, b, out)
+
+
+def mul_const(ctx, a, c, target_scale, out_level, out=None):
+    out = ctx.new_ct() if out is None else out
+    ca, co = a.struct(), out.struct()
+    _check(lib().secpe_mul_const(ctx.h, ctypes.byref(ca), c, target_scale, out_level, ctypes.byref(co), _stream()),
+           "secpe_mul_const")
+    out.update(co)
+    return out
+
+
+def add_const(ctx, a, c, out=None):
+    out = ctx.new_ct() if out is None else out
+    ca, co = a.struct(), out.struct()
+    _check(lib().secpe_add_const(ctx.h, ctypes.byref(ca), c, ctypes.byref(co), _stream()), "secpe_add_const")
+    out.update(co)
+    return out
+
+
+def mul_relin(ctx, keys, a, b, out=None):
+    out = ctx.new_ct() if out is None else out
+    ca, cb, co = a.struct(), b.struct(), out.struct()
+    _check(lib().secpe_mul_relin(ctx.h, keys.h, ctypes.byref(ca), ctypes.byref(cb), ctypes.byref(co), _stream()),
+           "secpe_mul_relin")
+    out.update(co)
+    return out
+
+
+def rescale(ctx, a, out=None):
+    out = ctx.new_ct() if out is None else out
+    ca, co = a.struct(), out.struct()
+    _check(lib().secpe_rescale(ctx.h, ctypes.byref(ca), ctypes.byref(co), _stream()), "secpe_rescale")
+    out.update(co)
+    return out
+
+
+def rotate(ctx, keys, a, steps, out=None):
+    out = ctx.new_ct() if out is None else out
+    ca, co = a.struct(), out.struct()
+    _check(lib().secpe_rotate(ctx.h, keys.h, ctypes.byref(ca), steps, ctypes.byref(co), _stream()), "secpe_rotate")
+    out.update(co)
+    return out
+
+
+def keyswitch(ctx, keys, galois_step, d, level):
+    """Key switching of one polynomial d (tensor [cap][N]); returns (ks0, ks1)."""
+    import torch
+    cap = int(d.shape[0])
+    ks0 = torch.zeros((cap, ctx.n), dtype=torch.int64, device=d.device)
+    ks1 = torch.zeros_like(ks0)
+    _check(lib().secpe_keyswitch(ctx.h, keys.h, galois_step, ctypes.c_void_p(d.data_ptr()), level, cap,
+                                 ctypes.c_void_p(ks0.data_ptr()), ctypes.c_void_p(ks1.data_ptr()), _stream()),
+           "secpe_keyswitch")
+    return ks0, ks1
+
+
+def refresh_testonly(ctx, keys, a, qseed, refresh_index, out=None):
+    out = ctx.new_ct() if out is None else out
+    ca, co = a.struct(), out.struct()
+    _check(lib().secpe_refresh_testonly(ctx.h, keys.h, ctypes.byref(ca), ctypes.c_uint64(qseed),
+                                        ctypes.c_uint64(refresh_index), ctypes.byref(co), _stream()),
+           "secpe_refresh_testonly")
+    out.update(co)
+    return out
+
+
+def sign(ctx, keys, x, out_levels, qseed, refresh_index=0, out=None):
+    out = ctx.new_ct() if out is None else out
+    cx, co = x.struct(), out.struct()
+    ri = ctypes.c_uint64(refresh_index)
+    _check(lib().secpe_sign(ctx.h, keys.h, ctypes.byref(cx), out_levels, ctypes.c_uint64(qseed), ctypes.byref(ri),
+                            ctypes.byref(co), _stream()), "secpe_sign")
+    out.update(co)
+    return out, int(ri.value)
+
+
+def vmax(ctx, keys, a, y, qseed, refresh_index=0, out=None):
+    out = ctx.new_ct() if out is None else out
+    ca, cy, co = a.struct(), y.struct(), out.struct()
+    ri = ctypes.c_uint64(refresh_index)
+    _check(lib().secpe_max(ctx.h, keys.h, ctypes.byref(ca), ctypes.byref(cy), ctypes.c_uint64(qseed),
+                           ctypes.byref(ri), ctypes.byref(co), _stream()), "secpe_max")
+    out.update(co)
+    return out, int(ri.value)
+
+
+def ensemble_aggregate(ctx, cts, d_min, d_max, out=None):
+    out = ctx.new_ct() if out is None else out
+    arr = (CtC * len(cts))(*[c.struct() for c in cts])
+    co = out.struct()
+    _check(lib().secpe_ensemble_aggregate(ctx.h, arr, len(cts), d_min, d_max, ctypes.byref(co), _stream()),
+           "secpe_ensemble_aggregate")
+    out.update(co)
+    return out
+
+
+def encrypted_argmax(ctx, keys, y, C, qseed, out=None):
+    out = ctx.new_ct() if out is None else out
+    cy, co = y.struct(), out.struct()
+    _check(lib().secpe_encrypted_argmax(ctx.h, keys.h, ctypes.byref(cy), C, ctypes.c_uint64(qseed),
+                                        ctypes.byref(co), _stream()), "secpe_encrypted_argmax")
+    out.update(co)
+    return out
+
+
+def argmax_batch(ctx, keys, queries):
+    """queries: list of dicts with cts (list of Ciphertext), C, d_min, d_max,
+    qseed, z_out (Ciphertext).  Updates each z_out's level/scale."""
+    keep = []
+    qarr = (QueryC * len(queries))()
+    for i, q in enumerate(queries):
+        cts = (CtC * len(q["cts"]))(*[c.struct() for c in q["cts"]])
+        z = q["z_out"].struct()
+        keep.append((cts, z))
+        qarr[i] = QueryC(cts, len(q["cts"]), q["C"], q["d_min"], q["d_max"], q["qseed"], ctypes.pointer(z))
+    _check(lib().secpe_argmax_batch(ctx.h, keys.h, qarr, len(queries), _stream()), "secpe_argmax_batch")
+    for q, (_, z) in zip(queries, keep):
+        q["z_out"].update(z)

@@ -1,0 +1,78 @@
+"""Seeded synthetic inputs (logit vectors) standing in for the paper's
+workloads: no homomorphic arithmetic here, only random draws.
+
+SecPE's experiments aggregate the logits of K prompted model runs over C
+classes (GLUE tasks: C = 2..3 with 4 templates; self-consistency and CLIP:
+many classes and 80..247 prompts).  Those datasets and model weights are not
+available, so the logits are drawn from fixed distributions:
+
+* toy:     K = 5 vectors of C = 2 classes, uniform in [-1, 1], redrawn until
+           the top-2 gap of the mean vector is >= 0.05; public bounds [-1, 1].
+* argmax:  per query K ~ U{4, 8, 16}, C ~ U{2, 3, 4, 6, 14, 64}; per-prompt
+           logits N(0, 1) (float32) clipped to [-4, 4]; if the mean vector's
+           top-1 gap is < 0.02, the gap is added to the top class of every
+           prompt; public bounds [-4.25, 4.25].
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+TOY_BOUNDS = (-1.0, 1.0)
+ARGMAX_BOUNDS = (-4.25, 4.25)
+ARGMAX_K = (4, 8, 16)
+ARGMAX_C = (2, 3, 4, 6, 14, 64)
+
+
+@dataclass
+class Query:
+    logits: np.ndarray  # [K][C] float64
+    d_min: float
+    d_max: float
+    qseed: int
+    enc_seeds: list     # one encryption seed per prompt
+
+    @property
+    def K(self):
+        return self.logits.shape[0]
+
+    @property
+    def C(self):
+        return self.logits.shape[1]
+
+
+def toy_query(seed=1, K=5, C=2):
+    rng = np.random.default_rng(seed)
+    while True:
+        logits = rng.uniform(-1.0, 1.0, (K, C))
+        srt = np.sort(logits.mean(0))
+        if srt[-1] - srt[-2] >= 0.05:
+            break
+    return Query(logits, TOY_BOUNDS[0], TOY_BOUNDS[1], qseed=seed * 7919 + 1,
+                 enc_seeds=[seed * 1000 + i for i in range(K)])
+
+
+def argmax_queries(n_queries, seed=4, K_choices=ARGMAX_K, C_choices=ARGMAX_C, margin=0.02):
+    rng = np.random.default_rng(seed)
+    out = []
+    for qi in range(n_queries):
+        K = int(rng.choice(K_choices))
+        C = int(rng.choice(C_choices))
+        logits = np.clip(rng.standard_normal((K, C)).astype(np.float32), -4.0, 4.0).astype(np.float64)
+        mean = logits.mean(0)
+        top = int(np.argmax(mean))
+        srt = np.sort(mean)
+        gap = srt[-1] - srt[-2]
+        if gap < margin:
+            logits[:, top] += margin - gap
+        out.append(Query(logits, ARGMAX_BOUNDS[0], ARGMAX_BOUNDS[1], qseed=(seed << 32) + qi,
+                         enc_seeds=[(seed << 40) + (qi << 8) + i for i in range(K)]))
+    return out
+
+
+def residues(shape, primes, seed):
+    """Uniform residues [..., len(primes), N] for primitive micro-benchmarks."""
+    rng = np.random.default_rng(seed)
+    out = np.empty(shape, dtype=np.uint64)
+    for i, q in enumerate(primes):
+        out[..., i, :] = rng.integers(0, q, size=out[..., i, :].shape, dtype=np.uint64)
+    return out

@@ -1,0 +1,127 @@
+"""GPU parity at full size (N = 2^16): the Argmax parameter set (q_0 60-bit +
+23 x 50-bit primes, 4 special primes, dnum = 6) and the primitive
+micro-benchmark set (24 x 50-bit, 4 special, dnum = 3).  Primitives are
+compared bit for bit with the CPU oracle; the batched circuit over a mix of
+queries is checked against the plaintext simulation, the exact argmax, and
+the one-query path (bit-identical)."""
+import numpy as np
+import pytest
+
+from oracle import ARGMAX, MICRO, Ct, Oracle, plainsim
+from paper_2502_00847_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+ROT = [1, -2]
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_2502_00847_gb300 import build as pkg_build
+    from paper_2502_00847_gb300 import secpe
+    pkg_build.build()
+    torch.cuda.set_device(0)
+    o = Oracle(ARGMAX)
+    o.keygen(2024, rot_steps=ROT)
+    ctx = secpe.Context.from_params(ARGMAX)
+    keys = secpe.Keys(ctx, 2024, ROT)
+    return o, ctx, keys, secpe
+
+
+def to_gpu(secpe, ctx, ct_o):
+    return secpe.Ciphertext.from_residues(ct_o.c, ct_o.level, ct_o.scale, cap=ctx.L + 1)
+
+
+def same(ct_g, ct_o):
+    assert ct_g.level == ct_o.level and ct_g.scale == ct_o.scale
+    assert np.array_equal(ct_g.residues(), ct_o.c)
+
+
+def test_keys_bit_exact(env):
+    o, ctx, keys, secpe = env
+    assert ctx.primes() == o.primes
+    assert np.array_equal(keys.export(0), o.s_ntt)
+    assert np.array_equal(keys.export(1), o.rlk)
+    assert np.array_equal(keys.export(2, -2), o.gks[o.galois(-2)])
+
+
+def test_ntt_bit_exact(env):
+    import torch
+    o, ctx, keys, secpe = env
+    rng = np.random.default_rng(16)
+    pidx = [(5 * i) % 28 for i in range(37)]
+    x = np.stack([rng.integers(0, o.primes[i], o.n, dtype=np.uint64) for i in pidx])
+    t = torch.from_numpy(x.view(np.int64)).cuda()
+    secpe.ntt(ctx, t, pidx)
+    got = t.cpu().numpy().view(np.uint64)
+    for r in (0, 1, 17, 36):
+        exp = x[r].copy()
+        o.ntt(exp, pidx[r])
+        assert np.array_equal(got[r], exp)
+    # property at every limb: INTT(NTT(x)) = x
+    secpe.ntt(ctx, t, pidx, inverse=True)
+    assert np.array_equal(t.cpu().numpy().view(np.uint64), x)
+
+
+def test_encrypt_mul_rotate_rescale_refresh_bit_exact(env):
+    o, ctx, keys, secpe = env
+    rng = np.random.default_rng(17)
+    m = o.encode_coeffs(rng.uniform(-1, 1, 16), o.p.scale)
+    a_o = o.encrypt_coeffs(m, o.ctx.L, o.p.scale, seed=71)
+    a = secpe.encrypt_coeffs(ctx, keys, np.array([int(v) for v in m], dtype=np.int64), ctx.L, o.p.scale, 71)
+    same(a, a_o)
+    b_o = o.encrypt(rng.uniform(-1, 1, 16), seed=72)
+    b = to_gpu(secpe, ctx, b_o)
+    same(secpe.mul_relin(ctx, keys, a, b), o.mul(a_o, b_o))
+    low_o = o.drop(b_o, 6)
+    same(secpe.mul_relin(ctx, keys, to_gpu(secpe, ctx, low_o), a), o.mul(low_o, a_o))
+    same(secpe.rotate(ctx, keys, a, 1), o.rotate(a_o, 1))
+    same(secpe.rotate(ctx, keys, to_gpu(secpe, ctx, low_o), -2), o.rotate(low_o, -2))
+    same(secpe.rescale(ctx, a), o.rescale(a_o))
+    o.ridx = 5
+    same(secpe.refresh_testonly(ctx, keys, to_gpu(secpe, ctx, o.drop(a_o, 1)), 8, 5), o.refresh(o.drop(a_o, 1), 8))
+
+
+def test_micro_keyswitch_dnum3_bit_exact():
+    import torch
+    from paper_2502_00847_gb300 import secpe
+    o = Oracle(MICRO)
+    o.keygen(3)
+    ctx = secpe.Context.from_params(MICRO)
+    keys = secpe.Keys(ctx, 3, [])
+    lv = ctx.L
+    d = workloads.residues((lv + 1, ctx.n), o.primes[: lv + 1], seed=2)
+    k0, k1 = o.keyswitch(d, lv, o.rlk)
+    dt = torch.from_numpy(d.view(np.int64)).cuda()
+    g0, g1 = secpe.keyswitch(ctx, keys, 0, dt, lv)
+    assert np.array_equal(g0.cpu().numpy().view(np.uint64), k0)
+    assert np.array_equal(g1.cpu().numpy().view(np.uint64), k1)
+
+
+def test_batched_argmax_mix(env):
+    o, ctx, keys, secpe = env
+    qs = workloads.argmax_queries(5, seed=4, K_choices=(4, 8), C_choices=(2, 3, 6, 14))
+    rot = sorted({-(1 << (q.C - 1).bit_length()) for q in qs} | {1 << i for i in range(4)})
+    k2 = secpe.Keys(ctx, 99, rot)
+    inputs = [[secpe.encrypt_logits(ctx, k2, q.logits[i], q.d_min, q.enc_seeds[i]) for i in range(q.K)]
+              for q in qs]
+    batch = [dict(cts=cts, C=q.C, d_min=q.d_min, d_max=q.d_max, qseed=q.qseed, z_out=ctx.new_ct())
+             for q, cts in zip(qs, inputs)]
+    secpe.argmax_batch(ctx, k2, batch)
+    for q, b, cts in zip(qs, batch, inputs):
+        zd = secpe.decrypt(ctx, k2, b["z_out"], q.C)
+        zp = plainsim.ensemble_argmax(q.logits, q.d_min, q.d_max, ctx.n // 2)
+        assert np.max(np.abs(zd - zp)) < 2.0 ** -12
+        assert int(np.argmax(zd)) == int(np.argmax(q.logits.mean(0)))
+    # the one-query path gives identical residues for two of them
+    for q, b, cts in list(zip(qs, batch, inputs))[:2]:
+        y = secpe.ensemble_aggregate(ctx, cts, q.d_min, q.d_max)
+        z = secpe.encrypted_argmax(ctx, k2, y, q.C, q.qseed)
+        assert z.level == b["z_out"].level and np.array_equal(z.residues(), b["z_out"].residues())
+    # the oracle decrypts the GPU output to the same values
+    z = batch[0]["z_out"]
+    o2 = Oracle(ARGMAX)
+    o2.keygen(99)
+    zo = o2.decrypt(Ct(z.residues(), z.level, z.scale), qs[0].C)
+    assert np.max(np.abs(zo - secpe.decrypt(ctx, k2, z, qs[0].C))) < 2.0 ** -30
