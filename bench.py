@@ -1,0 +1,372 @@
+"""Benchmark: encrypted ensemble Argmax at N = 2^16 on one GB300 (or N ranks,
+one per GPU, each with its own independent query mix: weak scaling, no
+collective on the data path).
+
+One step = aggregation + encrypted Argmax (SecPE Sec. 3.1 step 3, Alg. 1)
+of every query of the mix, batched (secpe_argmax_batch): every homomorphic
+operation (NTT, key switching, rescale, rotation, Sign, Max, refresh) runs in
+the library's CUDA kernels.  Inputs are encrypted logit ciphertexts resident
+in HBM before the timed region (57 GB at 256 queries: larger than L2).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+instead (a bounded sample per step) and prints the same line with
+"impl": "reference".
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted ensemble-Argmax/s at N=2^16, batched vs plain; keyswitch GB/s; p99"
+ROT_STEPS = [-2, -4, -8, -16, -64, 1, 2, 4, 8, 16, 32]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--queries", type=int, default=256)
+    ap.add_argument("--plain-queries", type=int, default=16,
+                    help="queries timed on the one-query-per-launch path")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--kprof", default="ntt16",
+                    help="kernel class timed live for the roofline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif args.impl == "ours":
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_sample(seconds_budget=20.0):
+    """Times the CPU oracle (single thread) on full-size primitives of the
+    workload and extrapolates queries/s with the per-query op mix."""
+    import numpy as np
+    from oracle import ARGMAX, Oracle
+    o = Oracle(ARGMAX)
+    t0 = time.perf_counter()
+    o.keygen(11, rot_steps=[1])
+    rng = np.random.default_rng(0)
+    a = o.encrypt(rng.uniform(-1, 1, 8), seed=1)
+    samples = []
+    for lv in (23, 15, 7):
+        x = o.drop(a, lv)
+        t = time.perf_counter()
+        o.mul(x, x)
+        samples.append(time.perf_counter() - t)
+        if time.perf_counter() - t0 > seconds_budget:
+            break
+    t = time.perf_counter()
+    o.rotate(o.drop(a, 12), 1)
+    t_rot = time.perf_counter() - t
+    return sum(samples) / len(samples), t_rot, time.perf_counter() - t0
+
+
+def op_mix_per_query(queries, reserve_params=None):
+    """Keyswitch-equivalent op counts of the workload (relins + rotations),
+    from the circuit's structure: per query with C' = 2^r,
+    relins = 24 (r + 1) + r, rotations = r + 1 (sign_dg = sign_df = 2)."""
+    tot_relin, tot_rot = 0, 0
+    for q in queries:
+        r = (q.C - 1).bit_length()
+        tot_relin += 24 * (r + 1) + r
+        tot_rot += r + 1
+    return tot_relin / len(queries), tot_rot / len(queries)
+
+
+def run_reference(args, world, rank):
+    from paper_2502_00847_gb300 import workloads
+    if rank != 0:
+        return
+    qs = workloads.argmax_queries(args.queries, seed=4)
+    relin_pq, rot_pq = op_mix_per_query(qs)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t_mul, t_rot, _ = oracle_sample(seconds_budget=5.0)
+        per_query = relin_pq * t_mul + rot_pq * t_rot
+        if i >= args.warmup:
+            times.append(per_query)
+    per_query = sum(times) / len(times)
+    value = 1.0 / per_query
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_query * 1e3 * args.queries,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "batched encrypted ensemble Argmax, N=2^16, %d queries, K~U{4,8,16}, "
+                               "C~U{2,3,4,6,14,64}" % args.queries, "queries": args.queries,
+                   "params": "q0 60-bit + 23x50-bit, 4 special, dnum=6, Delta=2^50"},
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step: oracle HMult+relin+rescale at levels 23/15/7 and one rotation "
+                                   "at level 12, N=2^16, single thread; queries/s extrapolated with the mix's "
+                                   "%.1f relins + %.1f rotations per query" % (relin_pq, rot_pq)},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- ours
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from oracle.params import ARGMAX
+    from paper_2502_00847_gb300 import build as pkg_build
+    from paper_2502_00847_gb300 import secpe, workloads
+
+    pkg_build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = secpe.Context.from_params(ARGMAX)
+    keys = secpe.Keys(ctx, 1000 + rank, ROT_STEPS)
+    n, cap = ctx.n, ctx.L + 1
+    ct_words = 2 * cap * n
+
+    qs = workloads.argmax_queries(args.queries, seed=4 + 1000 * rank)
+    n_cts = sum(q.K for q in qs)
+    # inputs: one big device tensor of ciphertexts, encrypted on the device
+    inputs = torch.empty((n_cts, 2, cap, n), dtype=torch.int64, device=dev)
+    views, off = [], 0
+    for q in qs:
+        cts = []
+        for i in range(q.K):
+            c = secpe.Ciphertext(inputs[off], 0, ctx.scale)
+            secpe.encrypt_logits(ctx, keys, q.logits[i], q.d_min, q.enc_seeds[i], out=c)
+            cts.append(c)
+            off += 1
+        views.append(cts)
+    zbuf = torch.zeros((len(qs), 2, cap, n), dtype=torch.int64, device=dev)
+    batch = [dict(cts=views[i], C=q.C, d_min=q.d_min, d_max=q.d_max, qseed=q.qseed,
+                  z_out=secpe.Ciphertext(zbuf[i], 0, ctx.scale)) for i, q in enumerate(qs)]
+    torch.cuda.synchronize()
+
+    def step():
+        secpe.argmax_batch(ctx, keys, batch)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness guard on the warm-up output: indices of the first queries
+    for i in range(min(4, len(qs))):
+        zd = secpe.decrypt(ctx, keys, batch[i]["z_out"], qs[i].C)
+        assert int(np.argmax(zd)) == int(np.argmax(qs[i].logits.mean(0))), "wrong argmax"
+
+    clocks = ClockSampler(local)
+    ctx.reset_counters()
+    ctx.kprof_begin(args.kprof)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    kp = ctx.kprof_end()
+    cnt = ctx.counters()
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(world, ms)
+    ms_per_step = ms / args.steps
+    value = world * len(qs) * args.steps / (ms / 1e3)
+
+    # plain path: the same kernels, one query per call, sequentially
+    plain = None
+    if args.plain_queries > 0 and rank == 0:
+        npq = min(args.plain_queries, len(qs))
+        # a sample of the mix with the same class-count distribution as the full mix
+        idx = list(range(npq))
+        zt = ctx.new_ct()
+        for i in idx[:2]:
+            y = secpe.ensemble_aggregate(ctx, batch[i]["cts"], qs[i].d_min, qs[i].d_max)
+            secpe.encrypted_argmax(ctx, keys, y, qs[i].C, qs[i].qseed, out=zt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in idx:
+            y = secpe.ensemble_aggregate(ctx, batch[i]["cts"], qs[i].d_min, qs[i].d_max)
+            secpe.encrypted_argmax(ctx, keys, y, qs[i].C, qs[i].qseed, out=zt)
+        e1.record()
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain = {"value": npq / (pms / 1e3), "unit": "queries/s", "queries": npq,
+                 "note": "one ciphertext batch of 1 per launch, sequential; first %d queries of the mix" % npq}
+
+    # end to end through host buffers (pinned), inputs copied in every step
+    e2e = None
+    if not args.no_e2e:
+        try:
+            host_in = torch.empty((n_cts, 2, cap, n), dtype=torch.int64, pin_memory=True)
+            host_in.copy_(inputs)
+            host_z = torch.empty((len(qs), 2, cap, n), dtype=torch.int64, pin_memory=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier(world)
+            e0.record()
+            d2h = 0
+            for _ in range(args.steps):
+                inputs.copy_(host_in, non_blocking=True)
+                step()
+                lv = batch[0]["z_out"].level
+                host_z[:, :, : lv + 1].copy_(zbuf[:, :, : lv + 1], non_blocking=True)
+                d2h = len(qs) * 2 * (lv + 1) * n * 8
+            e1.record()
+            torch.cuda.synchronize()
+            ems = max_over_ranks(world, e0.elapsed_time(e1))
+            e2e = {"value": world * len(qs) * args.steps / (ems / 1e3), "unit": "queries/s",
+                   "h2d_bytes_per_step": int(n_cts * ct_words * 8), "d2h_bytes_per_step": int(d2h)}
+            del host_in, host_z
+        except RuntimeError as e:
+            e2e = {"value": None, "unit": "queries/s", "error": str(e)[:200]}
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        t_mul, t_rot, wall = oracle_sample()
+        relin_pq, rot_pq = op_mix_per_query(qs)
+        per_query = relin_pq * t_mul + rot_pq * t_rot
+        cpu = {"value": 1.0 / per_query, "unit": "queries/s", "cores": 1, "kind": "oracle",
+               "sample": "oracle HMult+relin+rescale at levels 23/15/7 and one rotation at level 12, N=2^16, "
+                         "single thread (%.1f s), extrapolated with the mix's %.1f relins + %.1f rotations "
+                         "per query" % (wall, relin_pq, rot_pq)}
+
+    peak, peak_kind = hbm_peak()
+    achieved = kp["bytes"] / (kp["total_ms"] / 1e3) / 1e9 if kp["total_ms"] > 0 else None
+    roofline = {"bound": "hbm", "kernel": args.kprof, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+                "traffic": None, "launches": kp["launches"], "kernel_ms_per_step": kp["total_ms"] / args.steps,
+                "bytes_per_launch": kp["bytes"] / max(1, kp["launches"])}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "batched encrypted ensemble Argmax, N=2^16, %d queries per GPU, "
+                                   "K~U{4,8,16}, C~U{2,3,4,6,14,64}, seed 4" % len(qs),
+                       "queries_per_gpu": len(qs), "input_ciphertexts": n_cts,
+                       "params": "q0 60-bit + 23x50-bit, 4 special 60-bit, dnum=6, Delta=2^50",
+                       "l2": "inputs (%.1f GB) larger than L2" % (n_cts * ct_words * 8 / 1e9),
+                       "parallelism": "dp%d (independent queries per GPU)" % world},
+            "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clk, "gpu_launches": cnt["launches"],
+            "per_step_ops": {k: cnt[k] / args.steps for k in ("rotations", "signs", "relins", "refreshes",
+                                                               "keyswitches")},
+        }
+        print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -212,6 +212,22 @@ typedef struct {
 int secpe_get_counters(const secpe_ctx *ctx, secpe_counters *out);
 int secpe_reset_counters(secpe_ctx *ctx);
 
+/* ---- instrumentation --------------------------------------------------- */
+/* Times, with CUDA events recorded on the launching stream around each
+ * launch, every launch of the library kernels whose name contains
+ * name_filter ("ntt", "ksk_ip", "modup", "moddown", ...), up to
+ * max_launches launches, until secpe_kprof_end.  `bytes` accumulates each
+ * recorded launch's algorithmic bytes (the minimal DRAM traffic of the
+ * operation: operands read once, results written once). */
+typedef struct {
+    int64_t launches;
+    double total_ms;
+    double bytes;
+} secpe_kprof;
+int secpe_kprof_begin(secpe_ctx *ctx, const char *name_filter, int max_launches);
+/* Synchronises the device, sums the recorded durations, stops recording. */
+int secpe_kprof_end(secpe_ctx *ctx, secpe_kprof *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -502,3 +502,36 @@ extern "C" int secpe_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const 
     CallScope cs(ctx, stream);
     return finish(ctx, argmax_batch_impl(ctx, keys, q, n_queries));
 }
+
+extern "C" int secpe_kprof_begin(secpe_ctx *ctx, const char *name_filter, int max_launches) {
+    if (!ctx || !name_filter || max_launches < 1 || max_launches > (1 << 20)) return SECPE_EINVAL;
+    KProf &k = ctx->kprof;
+    while ((int)k.ev.size() < 2 * max_launches) {
+        cudaEvent_t e;
+        SECPE_CUDA(cudaEventCreate(&e));
+        k.ev.push_back(e);
+    }
+    k.filter = name_filter;
+    k.used = 0;
+    k.launches = 0;
+    k.bytes = 0.0;
+    k.active = true;
+    return SECPE_OK;
+}
+
+extern "C" int secpe_kprof_end(secpe_ctx *ctx, secpe_kprof *out) {
+    if (!ctx || !out) return SECPE_EINVAL;
+    KProf &k = ctx->kprof;
+    k.active = false;
+    SECPE_CUDA(cudaDeviceSynchronize());
+    double ms = 0.0;
+    for (int i = 0; i < k.used; i++) {
+        float t = 0.f;
+        SECPE_CUDA(cudaEventElapsedTime(&t, k.ev[2 * i], k.ev[2 * i + 1]));
+        ms += t;
+    }
+    out->launches = k.used;
+    out->total_ms = ms;
+    out->bytes = k.bytes;
+    return SECPE_OK;
+}

@@ -72,6 +72,16 @@ struct CtB {
     long long pstride() const { return (long long)cap * n; }
 };
 
+// event-based timing of selected kernel launches (secpe_kprof_*)
+struct KProf {
+    bool active = false;
+    std::string filter;
+    std::vector<cudaEvent_t> ev;  // pairs
+    int used = 0;                 // pairs recorded
+    int64_t launches = 0;
+    double bytes = 0.0;
+};
+
 struct secpe_ctx {
     secpe_params p;
     int n, log_n, nq, npsp, nprimes, L, dnum, alpha;
@@ -83,6 +93,7 @@ struct secpe_ctx {
     int *d_status;
     secpe_counters counters;
     cudaStream_t stream;  // stream of the call in progress
+    KProf kprof;
     // host copies used by host-side constant encoding
     std::vector<u64> h_qinv_neg, h_r2, h_mu;
 };

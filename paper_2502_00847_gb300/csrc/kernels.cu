@@ -537,6 +537,7 @@ int launch_rescale_fin(secpe_ctx *ctx, const CtB &x, const u64 *z, const CtB &o,
 
 int launch_modup_bconv(secpe_ctx *ctx, const u64 *x, u64 *ext, long long ext_item_stride, int ext_off,
                        int B, int lv, int j, int lo, int hi, int ntgt) {
+    KprofScope kp(ctx, "modup_bconv", 8.0 * ctx->n * B * ((hi - lo) + ntgt));
     SECPE_LAUNCH(ctx, k_modup_bconv, limb_grid(ctx->n, 1, B), 256, 0, ctx->dev, x, ext, ext_item_stride,
                  ext_off, lv, j, lo, hi, ntgt);
     return SECPE_OK;
@@ -545,12 +546,15 @@ int launch_modup_bconv(secpe_ctx *ctx, const u64 *x, u64 *ext, long long ext_ite
 int launch_ksk_ip(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const u64 *ext,
                   long long ext_item_stride, const KsDigits &dg, const u64 *key, u64 *acc, int B, int lv) {
     const int nt = lv + 1 + ctx->npsp;
+    // inputs (one residue per digit and target), key once, outputs (2 polys)
+    KprofScope kp(ctx, "ksk_ip", 8.0 * ctx->n * ((double)B * dg.ndig * nt + 2.0 * dg.ndig * nt + 2.0 * B * nt));
     SECPE_LAUNCH(ctx, k_ksk_ip, limb_grid(ctx->n, 2, (long long)B * nt), 256, 0, ctx->dev, d, d_item_stride,
                  ext, ext_item_stride, dg, key, acc, lv);
     return SECPE_OK;
 }
 
 int launch_moddown_bconv(secpe_ctx *ctx, const u64 *acc, u64 *conv, int B, int lv) {
+    KprofScope kp(ctx, "moddown_bconv", 8.0 * ctx->n * B * 2.0 * (ctx->npsp + lv + 1));
     SECPE_LAUNCH(ctx, k_moddown_bconv, limb_grid(ctx->n, 1, (long long)B * 2), 256, 0, ctx->dev, acc, conv, lv);
     return SECPE_OK;
 }

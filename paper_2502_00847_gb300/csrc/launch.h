@@ -22,6 +22,25 @@
         if ((expr) != cudaSuccess) return SECPE_ECUDA; \
     } while (0)
 
+// Records a CUDA event pair around the launches made in its lifetime when
+// the context's kernel profiler is active and `name` matches its filter.
+struct KprofScope {
+    secpe_ctx *ctx;
+    int idx = -1;
+    KprofScope(secpe_ctx *c, const char *name, double bytes) : ctx(c) {
+        KProf &k = c->kprof;
+        if (!k.active || std::string(name).find(k.filter) == std::string::npos) return;
+        if (2 * (k.used + 1) > (int)k.ev.size()) return;
+        idx = k.used++;
+        k.launches++;
+        k.bytes += bytes;
+        cudaEventRecord(k.ev[2 * idx], c->stream);
+    }
+    ~KprofScope() {
+        if (idx >= 0) cudaEventRecord(ctx->kprof.ev[2 * idx + 1], ctx->stream);
+    }
+};
+
 static inline unsigned grid1d(long long work, int block) {
     return (unsigned)((work + block - 1) / block);
 }

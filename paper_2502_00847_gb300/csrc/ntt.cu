@@ -346,11 +346,20 @@ int ntt_limbset(secpe_ctx *ctx, const LimbSet &ls, bool inverse, const LimbSet *
     if (ctx->log_n == 16) {
         a.tiles = 16;
         if (nl * 16 >= (1ll << 31)) return SECPE_EINVAL;
+        const double pass_bytes = 16.0 * ctx->n * nl;  // one read + one write per residue
         if (!inverse) {
-            SECPE_LAUNCH(ctx, k_ntt16_colpass<false>, (unsigned)(nl * 16), 256, 0, a);
+            {
+                KprofScope kp(ctx, "ntt16_colpass", pass_bytes);
+                SECPE_LAUNCH(ctx, k_ntt16_colpass<false>, (unsigned)(nl * 16), 256, 0, a);
+            }
+            KprofScope kp(ctx, "ntt16_rowpass", pass_bytes);
             SECPE_LAUNCH(ctx, k_ntt16_rowpass<false>, (unsigned)(nl * 16), 256, 0, a);
         } else {
-            SECPE_LAUNCH(ctx, k_ntt16_rowpass<true>, (unsigned)(nl * 16), 256, 0, a);
+            {
+                KprofScope kp(ctx, "intt16_rowpass", pass_bytes);
+                SECPE_LAUNCH(ctx, k_ntt16_rowpass<true>, (unsigned)(nl * 16), 256, 0, a);
+            }
+            KprofScope kp(ctx, "intt16_colpass", pass_bytes);
             SECPE_LAUNCH(ctx, k_ntt16_colpass<true>, (unsigned)(nl * 16), 256, 0, a);
         }
         return SECPE_OK;

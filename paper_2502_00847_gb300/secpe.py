@@ -22,7 +22,7 @@ EXPORTS = [
     "secpe_ntt_cts", "secpe_add", "secpe_sub", "secpe_mul_const", "secpe_add_const", "secpe_mul_relin",
     "secpe_rescale", "secpe_rotate", "secpe_keyswitch", "secpe_refresh_testonly", "secpe_sign", "secpe_max",
     "secpe_ensemble_aggregate", "secpe_encrypted_argmax", "secpe_argmax_batch", "secpe_get_counters",
-    "secpe_reset_counters", "secpe_select_primes",
+    "secpe_reset_counters", "secpe_select_primes", "secpe_kprof_begin", "secpe_kprof_end",
 ]
 
 
@@ -46,6 +46,10 @@ class QueryC(ctypes.Structure):
 class CountersC(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "rotations", "signs", "relins", "refreshes", "keyswitches", "launches")]
+
+
+class KprofC(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 _lib = None
@@ -95,6 +99,8 @@ def lib():
         "secpe_get_counters": (i32, [vp, P(CountersC)]),
         "secpe_reset_counters": (i32, [vp]),
         "secpe_select_primes": (i32, [P(ParamsC), P(u64), i32]),
+        "secpe_kprof_begin": (i32, [vp, ctypes.c_char_p, i32]),
+        "secpe_kprof_end": (i32, [vp, P(KprofC)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -178,6 +184,14 @@ class Context:
 
     def reset_counters(self):
         _check(lib().secpe_reset_counters(self.h), "secpe_reset_counters")
+
+    def kprof_begin(self, name_filter, max_launches=200000):
+        _check(lib().secpe_kprof_begin(self.h, name_filter.encode(), max_launches), "secpe_kprof_begin")
+
+    def kprof_end(self):
+        k = KprofC()
+        _check(lib().secpe_kprof_end(self.h, ctypes.byref(k)), "secpe_kprof_end")
+        return dict(launches=int(k.launches), total_ms=float(k.total_ms), bytes=float(k.bytes))
 
     def stream_status(self):
         v = ctypes.c_int32()
