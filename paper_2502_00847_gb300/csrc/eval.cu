@@ -215,23 +215,36 @@ int Eval::poly9(const Ct &x, const double *c, double s_out, Ct &out) {
     const int lv = x.level();
     if (lv < 4 + ctx->p.reserve) return SECPE_ELEVEL;
     const double q3 = (double)ctx->primes[lv - 3];
+    // temporaries are released as soon as they are dead (Ct() frees them)
     Ct x2, x3, x4, x8, t1, t2, Bv, T, t3, U, t4, t5, A, AT;
     SECPE_CHECK(mul(x, x, x2));
     SECPE_CHECK(mul(x, x2, x3));
     SECPE_CHECK(mul(x2, x2, x4));
+    x2 = Ct();
     SECPE_CHECK(mul(x4, x4, x8));
     const double sB = s_out * q3 / x4.scale();
     SECPE_CHECK(mul_const(x, {c[2]}, sB, lv - 3, t1));
     SECPE_CHECK(mul_const(x3, {c[3]}, sB, lv - 3, t2));
     SECPE_CHECK(add(t1, t2, Bv));
+    t1 = Ct();
+    t2 = Ct();
     SECPE_CHECK(mul(x4, Bv, T));
+    x4 = Ct();
+    Bv = Ct();
     const double s9 = s_out * q3 / x8.scale();
     SECPE_CHECK(mul_const(x, {c[4]}, s9, lv - 3, t3));
     SECPE_CHECK(mul(x8, t3, U));
+    x8 = Ct();
+    t3 = Ct();
     SECPE_CHECK(mul_const(x, {c[0]}, s_out, lv - 4, t4));
     SECPE_CHECK(mul_const(x3, {c[1]}, s_out, lv - 4, t5));
+    x3 = Ct();
     SECPE_CHECK(add(t4, t5, A));
+    t4 = Ct();
+    t5 = Ct();
     SECPE_CHECK(add(A, T, AT));
+    A = Ct();
+    T = Ct();
     return add(AT, U, out);
 }
 

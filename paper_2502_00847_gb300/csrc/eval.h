@@ -27,9 +27,11 @@ struct DevBuf {
         }
         return SECPE_OK;
     }
-    ~DevBuf() {
+    void release() {
         if (p) cudaFreeAsync(p, ctx->stream);
+        p = nullptr;
     }
+    ~DevBuf() { release(); }
     u64 *u() const { return (u64 *)p; }
 };
 

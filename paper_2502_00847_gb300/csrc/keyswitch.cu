@@ -55,6 +55,7 @@ int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int 
         SECPE_CHECK(launch_modup_bconv(ctx, dcoef.u(), ext.u(), ext_stride, dg.off[j], B, lv, j, dg.lo[j],
                                        dg.hi[j], ntgt));
     }
+    dcoef.release();
     ext_ls.base = ext.u();
     ext_ls.nitem = B;
     ext_ls.item_stride = ext_stride;
@@ -66,6 +67,7 @@ int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int 
     DevBuf acc;
     SECPE_CHECK(acc.alloc(ctx, sizeof(u64) * (size_t)B * 2 * nt * n));
     SECPE_CHECK(launch_ksk_ip(ctx, d, d_item_stride, ext.u(), ext_stride, dg, key, acc.u(), B, lv));
+    ext.release();
 
     // 4. ModDown
     LimbSet pls = make_limbset(acc.u() + (size_t)(lv + 1) * n, B, 2ll * nt * n, 2, (long long)nt * n, k,
