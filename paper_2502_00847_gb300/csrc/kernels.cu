@@ -168,29 +168,40 @@ __global__ void k_rescale_fin(DevCtx c, const u64 *x, long long xs, int cap_x, c
 // ------------------------------------------------------------ key switching
 // ModUp base conversion of digit j: x = coefficient-form limbs of d
 // ([item][lv+1][N]); ext_j[item][t'] for the targets of digit j.
+#define BCONV_TG 6
+// ND > 0: digit size known at compile time (registers); ND = 0: generic.
+template <int ND>
 __global__ void k_modup_bconv(DevCtx c, const u64 *x, u64 *ext, long long ext_item_stride,
                               int ext_off, int lv, int j, int lo, int hi, int ntgt) {
-    const int item = blockIdx.y;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ngrp = (ntgt + BCONV_TG - 1) / BCONV_TG;
+    const int item = blockIdx.y / ngrp, grp = blockIdx.y % ngrp;
+    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (e >= c.n) return;
-    const int nd = hi - lo;
+    const int nd = ND > 0 ? ND : hi - lo;
     const size_t tb = ((size_t)lv * c.dnum + j) * c.alpha;
-    u64 y[16];
-#pragma unroll 4
+    ulonglong2 y[ND > 0 ? ND : 16];
+#pragma unroll
     for (int r = 0; r < nd; r++) {
         const ulonglong2 w = c.mu_inv[tb + r];
-        y[r] = mul_shoup(x[((long long)item * (lv + 1) + lo + r) * c.n + e], w.x, w.y, c.q[lo + r]);
+        const u64 q = c.q[lo + r];
+        const ulonglong2 v = ld2(x + ((long long)item * (lv + 1) + lo + r) * c.n + e);
+        y[r] = make_ulonglong2(mul_shoup(v.x, w.x, w.y, q), mul_shoup(v.y, w.x, w.y, q));
     }
     u64 *out = ext + item * ext_item_stride + (long long)ext_off * c.n + e;
-    int tt = 0;
-    for (int t = 0; t < lv + 1 + c.np_special; t++) {
-        if (t >= lo && t < hi) continue;
+    const int t0 = grp * BCONV_TG, t1 = min(ntgt, t0 + BCONV_TG);
+    for (int tt = t0; tt < t1; tt++) {
+        // compact target index tt -> position t in [0, lv + 1 + k) skipping the digit
+        const int t = tt < lo ? tt : tt + nd;
         const int pt = t <= lv ? t : c.nq + (t - lv - 1);
-        const u64 q = c.q[pt];
-        acc128 s = {0, 0};
-        for (int r = 0; r < nd; r++) mac(s, y[r], c.mu_hat[(tb + r) * c.nprimes + pt]);
-        out[(long long)tt * c.n] = redc(s.hi, s.lo, q, c.qinv_neg[pt]);
-        tt++;
+        const u64 q = c.q[pt], qinv = c.qinv_neg[pt];
+        acc128 sa = {0, 0}, sb = {0, 0};
+#pragma unroll
+        for (int r = 0; r < nd; r++) {
+            const u64 h = c.mu_hat[(tb + r) * c.nprimes + pt];
+            mac(sa, y[r].x, h);
+            mac(sb, y[r].y, h);
+        }
+        st2(out + (long long)tt * c.n, make_ulonglong2(redc(sa.hi, sa.lo, q, qinv), redc(sb.hi, sb.lo, q, qinv)));
     }
 }
 
@@ -200,7 +211,9 @@ __global__ void k_ksk_ip(DevCtx c, const u64 *d, long long d_item_stride, const 
                          long long ext_item_stride, const __grid_constant__ KsDigits dg,
                          const u64 *key, u64 *acc, int lv) {
     const int nt = lv + 1 + c.np_special;
-    const int t = blockIdx.y % nt, item = blockIdx.y / nt;
+    const int nitem = gridDim.y / nt;
+    // target-major order: the items sharing one key limb run back to back
+    const int t = blockIdx.y / nitem, item = blockIdx.y % nitem;
     const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (e >= c.n) return;
     const int pt = t <= lv ? t : c.nq + (t - lv - 1);
@@ -231,26 +244,39 @@ __global__ void k_ksk_ip(DevCtx c, const u64 *d, long long d_item_stride, const 
 
 // ModDown base conversion: P-part limbs (coefficient form) of acc ->
 // conv[item][poly][i] = FastBConv([x + h]_P -> q_i) - h mod q_i.
+template <int KS>
 __global__ void k_moddown_bconv(DevCtx c, const u64 *acc, u64 *conv, int lv) {
     const int nt = lv + 1 + c.np_special;
-    const int kp = blockIdx.y;  // item*2 + poly
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ngrp = (lv + 1 + BCONV_TG - 1) / BCONV_TG;
+    const int kp = blockIdx.y / ngrp, grp = blockIdx.y % ngrp;  // kp = item*2 + poly
+    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (e >= c.n) return;
-    const int k = c.np_special;
-    u64 y[8];
+    const int k = KS > 0 ? KS : c.np_special;
+    ulonglong2 y[KS > 0 ? KS : 8];
+#pragma unroll
     for (int j = 0; j < k; j++) {
         const int pj = c.nq + j;
-        u64 v = acc[((long long)kp * nt + lv + 1 + j) * c.n + e];
-        v = add_mod(v, c.md_hP[pj], c.q[pj]);
+        const u64 q = c.q[pj];
+        ulonglong2 v = ld2(acc + ((long long)kp * nt + lv + 1 + j) * c.n + e);
+        v.x = add_mod(v.x, c.md_hP[pj], q);
+        v.y = add_mod(v.y, c.md_hP[pj], q);
         const ulonglong2 w = c.md_inv[j];
-        y[j] = mul_shoup(v, w.x, w.y, c.q[pj]);
+        y[j] = make_ulonglong2(mul_shoup(v.x, w.x, w.y, q), mul_shoup(v.y, w.x, w.y, q));
     }
-    for (int i = 0; i <= lv; i++) {
-        acc128 s = {0, 0};
-        for (int j = 0; j < k; j++) mac(s, y[j], c.md_hat[(size_t)j * c.nq + i]);
-        const u64 q = c.q[i];
-        const u64 r = redc(s.hi, s.lo, q, c.qinv_neg[i]);
-        conv[((long long)kp * (lv + 1) + i) * c.n + e] = sub_mod(r, c.md_hP[i], q);
+    const int i0 = grp * BCONV_TG, i1 = min(lv + 1, i0 + BCONV_TG);
+    for (int i = i0; i < i1; i++) {
+        acc128 sa = {0, 0}, sb = {0, 0};
+#pragma unroll
+        for (int j = 0; j < k; j++) {
+            const u64 h = c.md_hat[(size_t)j * c.nq + i];
+            mac(sa, y[j].x, h);
+            mac(sb, y[j].y, h);
+        }
+        const u64 q = c.q[i], qinv = c.qinv_neg[i];
+        ulonglong2 r = make_ulonglong2(redc(sa.hi, sa.lo, q, qinv), redc(sb.hi, sb.lo, q, qinv));
+        r.x = sub_mod(r.x, c.md_hP[i], q);
+        r.y = sub_mod(r.y, c.md_hP[i], q);
+        st2(conv + ((long long)kp * (lv + 1) + i) * c.n + e, r);
     }
 }
 
@@ -538,8 +564,27 @@ int launch_rescale_fin(secpe_ctx *ctx, const CtB &x, const u64 *z, const CtB &o,
 int launch_modup_bconv(secpe_ctx *ctx, const u64 *x, u64 *ext, long long ext_item_stride, int ext_off,
                        int B, int lv, int j, int lo, int hi, int ntgt) {
     KprofScope kp(ctx, "modup_bconv", 8.0 * ctx->n * B * ((hi - lo) + ntgt));
-    SECPE_LAUNCH(ctx, k_modup_bconv, limb_grid(ctx->n, 1, B), 256, 0, ctx->dev, x, ext, ext_item_stride,
-                 ext_off, lv, j, lo, hi, ntgt);
+    const int ngrp = (ntgt + BCONV_TG - 1) / BCONV_TG;
+    const dim3 grid = limb_grid(ctx->n, 2, (long long)B * ngrp);
+#define MODUP_CASE(ND)                                                                                   \
+    case ND:                                                                                             \
+        SECPE_LAUNCH(ctx, k_modup_bconv<ND>, grid, 256, 0, ctx->dev, x, ext, ext_item_stride, ext_off, lv, \
+                     j, lo, hi, ntgt);                                                                   \
+        break;
+    switch (hi - lo) {
+        MODUP_CASE(1)
+        MODUP_CASE(2)
+        MODUP_CASE(3)
+        MODUP_CASE(4)
+        MODUP_CASE(5)
+        MODUP_CASE(6)
+        MODUP_CASE(7)
+        MODUP_CASE(8)
+        default:
+            SECPE_LAUNCH(ctx, k_modup_bconv<0>, grid, 256, 0, ctx->dev, x, ext, ext_item_stride, ext_off, lv, j,
+                         lo, hi, ntgt);
+    }
+#undef MODUP_CASE
     return SECPE_OK;
 }
 
@@ -555,7 +600,14 @@ int launch_ksk_ip(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const u
 
 int launch_moddown_bconv(secpe_ctx *ctx, const u64 *acc, u64 *conv, int B, int lv) {
     KprofScope kp(ctx, "moddown_bconv", 8.0 * ctx->n * B * 2.0 * (ctx->npsp + lv + 1));
-    SECPE_LAUNCH(ctx, k_moddown_bconv, limb_grid(ctx->n, 1, (long long)B * 2), 256, 0, ctx->dev, acc, conv, lv);
+    const int ngrp = (lv + 1 + BCONV_TG - 1) / BCONV_TG;
+    const dim3 grid = limb_grid(ctx->n, 2, (long long)B * 2 * ngrp);
+    switch (ctx->npsp) {
+        case 1: SECPE_LAUNCH(ctx, k_moddown_bconv<1>, grid, 256, 0, ctx->dev, acc, conv, lv); break;
+        case 2: SECPE_LAUNCH(ctx, k_moddown_bconv<2>, grid, 256, 0, ctx->dev, acc, conv, lv); break;
+        case 4: SECPE_LAUNCH(ctx, k_moddown_bconv<4>, grid, 256, 0, ctx->dev, acc, conv, lv); break;
+        default: SECPE_LAUNCH(ctx, k_moddown_bconv<0>, grid, 256, 0, ctx->dev, acc, conv, lv);
+    }
     return SECPE_OK;
 }
 

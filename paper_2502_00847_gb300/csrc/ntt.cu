@@ -47,23 +47,34 @@ __device__ __forceinline__ LimbRef limb_of(const LimbSet &ls, int n, long long l
     return r;
 }
 
+// Butterflies use D. Harvey's lazy reduction ("Faster arithmetic for
+// number-theoretic transforms", 2014): the forward network keeps values in
+// [0, 4q), the inverse in [0, 2q); one correction to [0, q) is applied when
+// the last pass stores.  Within a round, the twiddle of stage bit sb for
+// register k depends only on k >> (sb + 1) (p0 has no bits in the round's
+// window), so each distinct twiddle is loaded once.
 template <int LOGP, int LO>
 __device__ __forceinline__ void fwd_round(u64 (&x)[16], int p0, const ulonglong2 *__restrict__ tw,
                                           int base, u64 q) {
+    const u64 q2 = 2 * q;
 #pragma unroll
     for (int sb = 3; sb >= 0; --sb) {
         const int s = LO + sb;
         const int st = LOGP - 1 - s;
+        const int ibase = (base << st) + (p0 >> (s + 1));
+        ulonglong2 w[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+            if (g < (8 >> sb)) w[g] = tw[ibase + g];
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             if (k & (1 << sb)) continue;
-            const int p = p0 | (k << LO);
-            const int i = p >> (s + 1);
-            const ulonglong2 w = tw[(base << st) + i];
-            const u64 v = mul_shoup(x[k | (1 << sb)], w.x, w.y, q);
-            const u64 u = x[k];
-            x[k] = add_mod(u, v, q);
-            x[k | (1 << sb)] = sub_mod(u, v, q);
+            const ulonglong2 ww = w[k >> (sb + 1)];
+            u64 u = x[k];
+            u = u >= q2 ? u - q2 : u;
+            const u64 t = mul_shoup_lazy(x[k | (1 << sb)], ww.x, ww.y, q);
+            x[k] = u + t;
+            x[k | (1 << sb)] = u - t + q2;
         }
     }
 }
@@ -71,28 +82,41 @@ __device__ __forceinline__ void fwd_round(u64 (&x)[16], int p0, const ulonglong2
 template <int LOGP, int LO, bool LAST>
 __device__ __forceinline__ void inv_round(u64 (&x)[16], int p0, const ulonglong2 *__restrict__ tw,
                                           int base, u64 q, ulonglong2 ninv, ulonglong2 ninv_w1) {
+    const u64 q2 = 2 * q;
 #pragma unroll
     for (int sb = 0; sb < 4; ++sb) {
         const int s = LO + sb;
         const int st = LOGP - 1 - s;
+        const bool last = LAST && s == LOGP - 1;
+        const int ibase = (base << st) + (p0 >> (s + 1));
+        ulonglong2 w[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+            if (g < (8 >> sb)) w[g] = last ? ninv_w1 : tw[ibase + g];
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             if (k & (1 << sb)) continue;
-            const int p = p0 | (k << LO);
-            const int i = p >> (s + 1);
+            const ulonglong2 ww = w[k >> (sb + 1)];
             const u64 u = x[k];
             const u64 v = x[k | (1 << sb)];
-            if (LAST && s == LOGP - 1) {
-                x[k] = mul_shoup(u + v, ninv.x, ninv.y, q);
-                x[k | (1 << sb)] = mul_shoup(u + q - v, ninv_w1.x, ninv_w1.y, q);
+            if (last) {
+                x[k] = mul_shoup_lazy(u + v, ninv.x, ninv.y, q);
             } else {
-                const ulonglong2 w = tw[(base << st) + i];
-                x[k] = add_mod(u, v, q);
-                x[k | (1 << sb)] = mul_shoup(u + q - v, w.x, w.y, q);
+                const u64 sum = u + v;
+                x[k] = sum >= q2 ? sum - q2 : sum;
             }
+            x[k | (1 << sb)] = mul_shoup_lazy(u - v + q2, ww.x, ww.y, q);
         }
     }
 }
+
+// [0, 4q) -> [0, q)
+__device__ __forceinline__ u64 reduce4(u64 v, u64 q) {
+    v = v >= 2 * q ? v - 2 * q : v;
+    return v >= q ? v - q : v;
+}
+// [0, 2q) -> [0, q)
+__device__ __forceinline__ u64 reduce2(u64 v, u64 q) { return v >= q ? v - q : v; }
 
 // ---------------------------------------------------------------- N = 2^16
 // Pass A: columns.  Tile = 16 adjacent columns c0..c0+15, all 256 rows.
@@ -134,7 +158,7 @@ __global__ void __launch_bounds__(256) k_ntt16_colpass(const __grid_constant__ N
         for (int k = 0; k < 16; k++) x[k] = sm[((k << 4) | u) * 16 + col];
         inv_round<8, 4, true>(x, u, tw, 1, q, ni, nw);
 #pragma unroll
-        for (int k = 0; k < 16; k++) g[((k << 4) | u) * 256 + c0 + col] = x[k];
+        for (int k = 0; k < 16; k++) g[((k << 4) | u) * 256 + c0 + col] = reduce2(x[k], q);
     }
 }
 
@@ -167,7 +191,7 @@ __global__ void __launch_bounds__(256) k_ntt16_rowpass(const __grid_constant__ N
         for (int k = 0; k < 16; k++) x[k] = srow[PADR((u << 4) | k)];
         fwd_round<8, 0>(x, u << 4, tw, base, q);
 #pragma unroll
-        for (int k = 0; k < 16; k++) srow[PADR((u << 4) | k)] = x[k];
+        for (int k = 0; k < 16; k++) srow[PADR((u << 4) | k)] = reduce4(x[k], q);
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; i++) {
@@ -230,7 +254,7 @@ __global__ void __launch_bounds__(256) k_ntt12(const __grid_constant__ NttArgs a
         for (int k = 0; k < 16; k++) x[k] = sm[PADR((u << 4) | k)];
         fwd_round<12, 0>(x, u << 4, tw, 1, q);
 #pragma unroll
-        for (int k = 0; k < 16; k++) sm[PADR((u << 4) | k)] = x[k];
+        for (int k = 0; k < 16; k++) sm[PADR((u << 4) | k)] = reduce4(x[k], q);
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; i++) {
@@ -263,7 +287,7 @@ __global__ void __launch_bounds__(256) k_ntt12(const __grid_constant__ NttArgs a
         for (int k = 0; k < 16; k++) x[k] = sm[PADR((k << 8) | u)];
         inv_round<12, 8, true>(x, u, tw, 1, q, ni, nw);
 #pragma unroll
-        for (int k = 0; k < 16; k++) g[(k << 8) | u] = x[k];
+        for (int k = 0; k < 16; k++) g[(k << 8) | u] = reduce2(x[k], q);
     }
 }
 
