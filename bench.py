@@ -41,6 +41,12 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--kprof", default="ntt16",
                     help="kernel class timed live for the roofline")
+    ap.add_argument("--micro", action="store_true",
+                    help="primitive micro-benchmark (N=2^16, 24+4 primes, dnum=3) instead of the Argmax step")
+    ap.add_argument("--micro-ops", default="ntt,keyswitch,hmult,rescale,rotate")
+    ap.add_argument("--micro-batch", default="1,8,64")
+    ap.add_argument("--micro-params", default="micro", choices=["micro", "argmax"],
+                    help="micro: 24+4 primes, dnum=3 (primitive config); argmax: the Argmax set (dnum=6)")
     return ap.parse_args()
 
 
@@ -356,10 +362,94 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line))
 
 
+def run_micro(args, rank):
+    """Config-2 primitives on random residues (seed 2): batched NTT/INTT,
+    key switching (algorithmic bytes = inputs + key + outputs), HMult +
+    relinearise + rescale, rescale, rotation by 2^j (j = 0..15)."""
+    import numpy as np
+    import torch
+
+    from oracle.params import ARGMAX, MICRO
+    from paper_2502_00847_gb300 import build as pkg_build
+    from paper_2502_00847_gb300 import secpe
+
+    pkg_build.build()
+    ops = args.micro_ops.split(",")
+    batches = [int(b) for b in args.micro_batch.split(",")]
+    P = MICRO if args.micro_params == "micro" else ARGMAX
+    ctx = secpe.Context.from_params(P)
+    rot = [1 << j for j in range(16)] if "rotate" in ops else []
+    keys = secpe.Keys(ctx, 2, rot)
+    n, cap, L = ctx.n, ctx.L + 1, ctx.L
+    primes = ctx.primes()
+    gen = torch.Generator(device="cpu").manual_seed(2)
+    limb = n * 8
+    dnum = -(-ctx.n_q // -(-ctx.n_q // P.dnum))
+    ksk_bytes = dnum * 2 * (cap + ctx.n_p) * limb
+
+    def rand_batch(B):
+        t = torch.empty((B, 2, cap, n), dtype=torch.int64)
+        for i in range(cap):
+            t[:, :, i] = torch.randint(0, primes[i], (B, 2, n), generator=gen, dtype=torch.int64)
+        return t.cuda()
+
+    def timed(fn):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    res = {}
+    for B in batches:
+        x = rand_batch(B)
+        y = rand_batch(B)
+        out = torch.zeros_like(x)
+        if "ntt" in ops:
+            ms = timed(lambda: secpe.ntt_cts(ctx, x, B, 2 * cap * n, cap, L))
+            res["ntt_B%d" % B] = {"ms": ms, "us_per_limb": ms * 1e3 / (B * 2 * cap),
+                                  "GBps_alg": B * 2 * cap * limb * 4 / (ms / 1e3) / 1e9}
+            ms = timed(lambda: secpe.ntt_cts(ctx, x, B, 2 * cap * n, cap, L, inverse=True))
+            res["intt_B%d" % B] = {"ms": ms, "us_per_limb": ms * 1e3 / (B * 2 * cap)}
+        a = secpe.CtBatch(x, L, ctx.scale)
+        b = secpe.CtBatch(y, L, ctx.scale)
+        o = secpe.CtBatch(out, 0, ctx.scale)
+        if "keyswitch" in ops:
+            ms = timed(lambda: secpe.keyswitch_batch(ctx, keys, 0, a, o))
+            alg = B * (cap * limb + 2 * cap * limb) + ksk_bytes
+            res["keyswitch_B%d" % B] = {"ms": ms, "GBps_alg": alg / (ms / 1e3) / 1e9, "alg_bytes": alg}
+        if "hmult" in ops:
+            ms = timed(lambda: secpe.mul_relin_batch(ctx, keys, a, b, o))
+            res["hmult_relin_rescale_B%d" % B] = {"ms": ms, "us_per_ct": ms * 1e3 / B}
+        if "rescale" in ops:
+            ms = timed(lambda: secpe.rescale_batch(ctx, a, o))
+            res["rescale_B%d" % B] = {"ms": ms, "us_per_ct": ms * 1e3 / B}
+        if "rotate" in ops:
+            per = []
+            for j in range(16):
+                per.append(timed(lambda: secpe.rotate_batch(ctx, keys, a, 1 << j, o)))
+            res["rotate_B%d" % B] = {"ms_mean": sum(per) / len(per), "ms_by_log2_step": per}
+        del x, y, out
+        torch.cuda.empty_cache()
+    if rank == 0:
+        desc = ("24x50-bit + 4x60-bit special primes, dnum=3" if args.micro_params == "micro" else
+                "q0 60-bit + 23x50-bit + 4x60-bit special primes, dnum=6")
+        print(json.dumps({"mode": "micro", "config": {"workload": "primitive micro-benchmark N=2^16, %s, random "
+                                                                  "residues seed 2" % desc},
+                          "steps": args.steps, "warmup": args.warmup, "results": res}))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
-    if args.impl == "reference":
+    if args.micro:
+        run_micro(args, rank)
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_ours(args, world, rank, local)

@@ -169,6 +169,28 @@ int secpe_keyswitch(secpe_ctx *ctx, const secpe_keys *keys, int galois_step, con
 int secpe_refresh_testonly(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *in,
                            uint64_t qseed, uint64_t refresh_index, secpe_ct *out, void *stream);
 
+/* ---- batched primitives -------------------------------------------------- */
+/* `batch` ciphertexts at data + i*stride (words), each [2][cap][N], all at
+ * the same level and scale.  Outputs are written to caller memory with the
+ * same conventions; the output level/scale fields are set by the call. */
+typedef struct {
+    uint64_t *data;
+    int32_t batch;
+    int32_t cap;
+    int32_t level;
+    double scale;
+    uint64_t stride;  /* words between items, >= 2*cap*N */
+} secpe_ctbatch;
+/* Key switching of polynomial 0 of every item of d (limbs 0..level); item i
+ * of out receives (ks0, ks1) in its polynomials 0 and 1 at d's level. */
+int secpe_keyswitch_batch(secpe_ctx *ctx, const secpe_keys *keys, int galois_step, const secpe_ctbatch *d,
+                          secpe_ctbatch *out, void *stream);
+int secpe_mul_relin_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ctbatch *a,
+                          const secpe_ctbatch *b, secpe_ctbatch *out, void *stream);
+int secpe_rotate_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ctbatch *in, int steps,
+                       secpe_ctbatch *out, void *stream);
+int secpe_rescale_batch(secpe_ctx *ctx, const secpe_ctbatch *in, secpe_ctbatch *out, void *stream);
+
 /* ---- SecPE circuit ----------------------------------------------------- */
 /* Sign(x) = f^df(g^dg(x)) (SecPE Eq. comp), each degree-9 polynomial by a
  * depth-4 baby-step giant-step DAG; refreshes (counter from *refresh_index,

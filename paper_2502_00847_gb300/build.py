@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libsecpe.so")
 
-SOURCES = ["hostmath.cpp", "context.cu", "ntt.cu", "kernels.cu", "keyswitch.cu", "eval.cu",
+SOURCES = ["hostmath.cpp", "context.cu", "ntt.cu", "ntt_fused.cu", "kernels.cu", "keyswitch.cu", "eval.cu",
            "capi.cu", "encode.cpp"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -535,3 +535,82 @@ extern "C" int secpe_kprof_end(secpe_ctx *ctx, secpe_kprof *out) {
     out->bytes = k.bytes;
     return SECPE_OK;
 }
+
+// ---------------------------------------------------------------- batched primitives
+namespace {
+int check_batch(const secpe_ctx *ctx, const secpe_ctbatch *b) {
+    if (!b || !b->data || b->batch < 1 || b->batch > SECPE_MAX_BATCH_CONST || b->level < 0 || b->level > ctx->L ||
+        b->cap < b->level + 1 || b->stride < 2ull * b->cap * ctx->n || !(b->scale > 0))
+        return SECPE_EINVAL;
+    return SECPE_OK;
+}
+Ct bview(secpe_ctx *ctx, const secpe_ctbatch *b) {
+    Ct r;
+    r.v.data = (u64 *)b->data;
+    r.v.B = b->batch;
+    r.v.cap = b->cap;
+    r.v.stride = (long long)b->stride;
+    r.v.level = b->level;
+    r.v.scale = b->scale;
+    r.v.n = ctx->n;
+    return r;
+}
+int copy_batch_out(secpe_ctx *ctx, const Ct &src, secpe_ctbatch *dst) {
+    if (dst->cap < src.level() + 1 || dst->batch != src.B()) return SECPE_EINVAL;
+    const size_t n = ctx->n;
+    for (int b = 0; b < src.B(); b++)
+        SECPE_CUDA(cudaMemcpy2DAsync((u64 *)dst->data + b * dst->stride, sizeof(u64) * dst->cap * n,
+                                     src.v.data + b * src.v.stride, sizeof(u64) * src.v.cap * n,
+                                     sizeof(u64) * (src.level() + 1) * n, 2, cudaMemcpyDeviceToDevice, ctx->stream));
+    dst->level = src.level();
+    dst->scale = src.scale();
+    return SECPE_OK;
+}
+}  // namespace
+
+extern "C" int secpe_keyswitch_batch(secpe_ctx *ctx, const secpe_keys *keys, int galois_step,
+                                     const secpe_ctbatch *d, secpe_ctbatch *out, void *stream) {
+    if (!ctx || !keys || !out) return SECPE_EINVAL;
+    SECPE_CHECK(check_batch(ctx, d));
+    if (!out->data || out->batch != d->batch || out->cap < d->level + 1 || out->stride < 2ull * out->cap * ctx->n)
+        return SECPE_EINVAL;
+    CallScope cs(ctx, stream);
+    const u64 *key = galois_step == 0 ? keys->rlk : galois_key(keys, galois_elt(ctx, galois_step));
+    if (!key) return SECPE_EKEY;
+    CtB o = {(u64 *)out->data, out->batch, (long long)out->stride, out->cap, d->level, d->scale, ctx->n};
+    SECPE_CHECK(keyswitch(ctx, (const u64 *)d->data, (long long)d->stride, d->batch, d->level, key, o, false, false));
+    out->level = d->level;
+    out->scale = d->scale;
+    return finish(ctx, SECPE_OK);
+}
+
+extern "C" int secpe_mul_relin_batch(secpe_ctx *ctx, const secpe_keys *keys_, const secpe_ctbatch *a,
+                                     const secpe_ctbatch *b, secpe_ctbatch *out, void *stream) {
+    if (!ctx || !keys_ || !out) return SECPE_EINVAL;
+    SECPE_CHECK(check_batch(ctx, a));
+    SECPE_CHECK(check_batch(ctx, b));
+    EVAL_PROLOGUE(ctx, stream);
+    Ct r;
+    SECPE_CHECK(E.mul(bview(ctx, a), bview(ctx, b), r));
+    return finish(ctx, copy_batch_out(ctx, r, out));
+}
+
+extern "C" int secpe_rotate_batch(secpe_ctx *ctx, const secpe_keys *keys_, const secpe_ctbatch *in, int steps,
+                                  secpe_ctbatch *out, void *stream) {
+    if (!ctx || !keys_ || !out) return SECPE_EINVAL;
+    SECPE_CHECK(check_batch(ctx, in));
+    EVAL_PROLOGUE(ctx, stream);
+    Ct r;
+    SECPE_CHECK(E.rotate(bview(ctx, in), steps, r));
+    return finish(ctx, copy_batch_out(ctx, r, out));
+}
+
+extern "C" int secpe_rescale_batch(secpe_ctx *ctx, const secpe_ctbatch *in, secpe_ctbatch *out, void *stream) {
+    if (!ctx || !out) return SECPE_EINVAL;
+    SECPE_CHECK(check_batch(ctx, in));
+    const secpe_keys *keys_ = nullptr;
+    EVAL_PROLOGUE(ctx, stream);
+    Ct r;
+    SECPE_CHECK(E.rescale(bview(ctx, in), r));
+    return finish(ctx, copy_batch_out(ctx, r, out));
+}

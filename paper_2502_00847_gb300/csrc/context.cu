@@ -61,13 +61,14 @@ extern "C" int secpe_ctx_create(const secpe_params *p, secpe_ctx **out) {
     const int n = ctx->n, np = ctx->nprimes, nq = ctx->nq, L = ctx->L, k = ctx->npsp;
     const std::vector<u64> &P = ctx->primes;
 
-    std::vector<u64> qinv(np), r2(np), mu(np);
+    std::vector<u64> qinv(np), r2(np), mu(np), mone(np);
     std::vector<ulonglong2> twf((size_t)np * n), twi((size_t)np * n), ninv(np), ninvw1(np);
     for (int t = 0; t < np; t++) {
         u64 q = P[t];
         qinv[t] = hm::neg_inv64(q);
         u64 r = (u64)((((u128)1) << 64) % q);
         r2[t] = hm::mulmod(r, r, q);
+        mone[t] = r;
         mu[t] = (u64)((((u128)1) << 64) / q);
         u64 psi = hm::find_psi(q, n);
         ctx->psi.push_back(psi);
@@ -115,6 +116,20 @@ extern "C" int secpe_ctx_create(const secpe_params *p, secpe_ctx **out) {
         }
     }
 
+    ctx->h_mu_inv = mu_inv;
+    std::vector<ulonglong2> ninv_modup((size_t)2 * nq * nq, make_ulonglong2(0, 0));
+    for (int lv = 0; lv <= L; lv++)
+        for (int i = 0; i <= lv; i++) {
+            const int j = i / alpha;
+            const size_t base = ((size_t)lv * ctx->dnum + j) * alpha + (i - j * alpha);
+            const u64 q = P[i];
+            const u64 ni = hm::invmod((u64)n, q);
+            const u64 s0 = hm::mulmod(ni, mu_inv[base].x, q);
+            const u64 w1 = hm::invmod(hm::powmod(ctx->psi[i], hm::bitrev(1, ctx->log_n), q), q);
+            ninv_modup[2 * ((size_t)lv * nq + i)] = sh(s0, q);
+            ninv_modup[2 * ((size_t)lv * nq + i) + 1] = sh(hm::mulmod(s0, w1, q), q);
+        }
+
     // ModDown tables
     std::vector<ulonglong2> md_inv(k), md_pinv(nq);
     std::vector<u64> md_hat((size_t)k * nq), md_hP(np);
@@ -135,6 +150,15 @@ extern "C" int secpe_ctx_create(const secpe_params *p, secpe_ctx **out) {
         u64 pm = 1;
         for (int j = 0; j < k; j++) pm = hm::mulmod(pm, P[nq + j] % P[i], P[i]);
         md_pinv[i] = sh(hm::invmod(pm, P[i]), P[i]);
+    }
+    std::vector<ulonglong2> ninv_moddown((size_t)2 * k);
+    for (int j = 0; j < k; j++) {
+        const u64 q = P[nq + j];
+        const u64 ni = hm::invmod((u64)n, q);
+        const u64 s0 = hm::mulmod(ni, md_inv[j].x, q);
+        const u64 w1 = hm::invmod(hm::powmod(ctx->psi[nq + j], hm::bitrev(1, ctx->log_n), q), q);
+        ninv_moddown[2 * j] = sh(s0, q);
+        ninv_moddown[2 * j + 1] = sh(hm::mulmod(s0, w1, q), q);
     }
     // floor(P/2) mod t: P is odd, so floor(P/2) = (P - 1)/2 = (P - 1) * 2^-1 mod t
     for (int t = 0; t < np; t++) {
@@ -203,10 +227,13 @@ extern "C" int secpe_ctx_create(const secpe_params *p, secpe_ctx **out) {
     UP(qinv_neg, qinv);
     UP(r2, r2);
     UP(mu, mu);
+    UP(mont_one, mone);
     UP(tw_fwd, twf);
     UP(tw_inv, twi);
     UP(ninv, ninv);
     UP(ninv_w1, ninvw1);
+    UP(ninv_modup, ninv_modup);
+    UP(ninv_moddown, ninv_moddown);
     UP(mu_inv, mu_inv);
     UP(mu_hat, mu_hat);
     UP(md_inv, md_inv);

@@ -81,3 +81,10 @@ int rescale_batch(secpe_ctx *ctx, const CtB &in, const CtB &out);
 unsigned galois_elt(const secpe_ctx *ctx, int steps);
 const u64 *galois_key(const secpe_keys *keys, unsigned g);
 int sign_coeffs(double g[5], double f[5]);
+
+// fused N = 2^16 paths (ntt_fused.cu)
+bool fused_path(const secpe_ctx *ctx);
+int modup_ip_fused(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const u64 *dcoef, int B, int lv,
+                   const KsDigits &dg, int tot, const u64 *key, u64 *ext, u64 *acc);
+int moddown_fused(secpe_ctx *ctx, const u64 *acc, int B, int lv, const CtB &out, bool acc0, bool acc1, u64 *tmp);
+int rescale_fused(secpe_ctx *ctx, const CtB &in, const u64 *y, const CtB &out, u64 *tmp);

@@ -24,10 +24,16 @@ struct DevCtx {
     const u64 *qinv_neg;   // [nprimes]  -q^-1 mod 2^64
     const u64 *r2;         // [nprimes]  2^128 mod q
     const u64 *mu;         // [nprimes]  floor(2^64 / q)
+    const u64 *mont_one;   // [nprimes]  2^64 mod q (Montgomery form of 1)
     const ulonglong2 *tw_fwd;  // [nprimes][N]  (psi^brv(k), shoup)
     const ulonglong2 *tw_inv;  // [nprimes][N]  (psi^-brv(k), shoup)
     const ulonglong2 *ninv;    // [nprimes]     (N^-1, shoup)
     const ulonglong2 *ninv_w1; // [nprimes]     (psi^-brv(1) * N^-1, shoup)
+    // INTT final scalings that also apply a base-conversion pre-multiplier:
+    // [lv*nq + i][2]: N^-1 * [Qhat_i^-1]_{q_i} of prime i's digit at level lv (and * psi^-brv(1))
+    const ulonglong2 *ninv_modup;
+    // [j][2]: N^-1 * [Phat_j^-1]_{p_j} (and * psi^-brv(1)) for special prime j
+    const ulonglong2 *ninv_moddown;
     // ModUp base conversion, per (level, digit): digit prime i (< alpha)
     const ulonglong2 *mu_inv;  // [(L+1)*dnum*alpha]  [Qhat_i^-1]_{q_i} (shoup)
     const u64 *mu_hat;         // [(L+1)*dnum*alpha*nprimes] Montgomery form of Qhat_i mod t
@@ -56,6 +62,7 @@ struct LimbSet {
     long long item_stride, poly_stride;
     int nitem, npoly, nlimb;
     int8_t prime_of[SECPE_MAX_LIMBSET];
+    int8_t aux[SECPE_MAX_LIMBSET];  // per-limb group (which base-conversion source)
 };
 
 // A batch of B ciphertexts laid out [B][2][cap][N] with `stride` words
@@ -96,6 +103,7 @@ struct secpe_ctx {
     KProf kprof;
     // host copies used by host-side constant encoding
     std::vector<u64> h_qinv_neg, h_r2, h_mu;
+    std::vector<ulonglong2> h_mu_inv;  // host mirror of DevCtx::mu_inv
 };
 
 struct secpe_keys {

@@ -39,12 +39,28 @@ int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int 
     }
     ctx->counters.keyswitches++;
 
-    // 1. INTT of d into dcoef [B][lv+1][N]
+    // 1. INTT of d into dcoef [B][lv+1][N] (on the fused path the INTT also
+    //    applies the ModUp pre-multiplier [Qhat_i^-1]_{q_i})
     DevBuf dcoef;
     SECPE_CHECK(dcoef.alloc(ctx, sizeof(u64) * (size_t)B * (lv + 1) * n));
     LimbSet dst = make_limbset(dcoef.u(), B, (long long)(lv + 1) * n, 1, 0, lv + 1, 0);
     LimbSet src = make_limbset((u64 *)d, B, d_item_stride, 1, 0, lv + 1, 0);
-    SECPE_CHECK(ntt_limbset(ctx, dst, true, &src));
+    const bool fused = fused_path(ctx);
+    SECPE_CHECK(ntt_limbset(ctx, dst, true, &src, fused ? ctx->dev.ninv_modup : nullptr, lv * ctx->nq));
+
+    if (fused) {
+        DevBuf ext, acc, tmp;
+        SECPE_CHECK(ext.alloc(ctx, sizeof(u64) * (size_t)B * tot * n));
+        SECPE_CHECK(acc.alloc(ctx, sizeof(u64) * (size_t)B * 2 * nt * n));
+        SECPE_CHECK(modup_ip_fused(ctx, d, d_item_stride, dcoef.u(), B, lv, dg, tot, key, ext.u(), acc.u()));
+        ext.release();
+        dcoef.release();
+        LimbSet pls = make_limbset(acc.u() + (size_t)(lv + 1) * n, B, 2ll * nt * n, 2, (long long)nt * n, k,
+                                   ctx->nq);
+        SECPE_CHECK(ntt_limbset(ctx, pls, true, nullptr, ctx->dev.ninv_moddown, 0));
+        SECPE_CHECK(tmp.alloc(ctx, sizeof(u64) * (size_t)B * 2 * (lv + 1) * n));
+        return moddown_fused(ctx, acc.u(), B, lv, out, acc0, acc1, tmp.u());
+    }
 
     // 2. ModUp
     DevBuf ext;
@@ -91,6 +107,7 @@ int rescale_batch(secpe_ctx *ctx, const CtB &in, const CtB &out) {
     LimbSet ysrc = make_limbset(in.data + (size_t)lv * n, B, in.stride, 2, in.pstride(), 1, lv);
     LimbSet ydst = make_limbset(y.u(), B, 2ll * n, 2, n, 1, lv);
     SECPE_CHECK(ntt_limbset(ctx, ydst, true, &ysrc));
+    if (fused_path(ctx)) return rescale_fused(ctx, in, y.u(), out, z.u());
     SECPE_CHECK(launch_rescale_prep(ctx, y.u(), z.u(), B, lv));
     LimbSet zls = make_limbset(z.u(), B, 2ll * lv * n, 2, (long long)lv * n, lv, 0);
     SECPE_CHECK(ntt_limbset(ctx, zls, false));

@@ -50,7 +50,11 @@ static inline unsigned grid1d(long long work, int block) {
 // ---------------------------------------------------------------------------
 // Forward or inverse NTT of every limb of `ls`; in place, or reading from
 // the limbs of `src` (same shape) when src is not null.
-int ntt_limbset(secpe_ctx *ctx, const LimbSet &ls, bool inverse, const LimbSet *src = nullptr);
+// For the N = 2^16 inverse, `scale_tab` (device, pairs) replaces the final
+// N^-1 of limb j by scale_tab[2 (scale_off + j)] (and the folded twiddle by
+// the next entry): the INTT then also applies a per-limb constant.
+int ntt_limbset(secpe_ctx *ctx, const LimbSet &ls, bool inverse, const LimbSet *src = nullptr,
+                const ulonglong2 *scale_tab = nullptr, int scale_off = 0);
 
 // Convenience: LimbSet for `nitem` ciphertext-like objects of `npoly`
 // polynomials, limbs [l0, l0 + nlimb) mapped to primes [p0, p0 + nlimb).

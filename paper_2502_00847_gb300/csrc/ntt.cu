@@ -20,6 +20,7 @@
 // pass A / single pass, base = 256 + row for the rows of pass B.
 #include "internal.h"
 #include "launch.h"
+#include "ntt_core.cuh"
 
 namespace {
 
@@ -29,94 +30,11 @@ struct NttArgs {
     LimbSet src;  // source of the first pass when has_src != 0
     int has_src;
     int tiles;    // CTAs per limb
+    // inverse only: final scaling of limb j is scale_tab[2 (scale_off + j)] (and
+    // [.. + 1] for the folded twiddle) instead of N^-1, when not null
+    const ulonglong2 *scale_tab;
+    int scale_off;
 };
-
-struct LimbRef {
-    u64 *ptr;
-    int prime;
-};
-
-__device__ __forceinline__ LimbRef limb_of(const LimbSet &ls, int n, long long lid) {
-    int j = (int)(lid % ls.nlimb);
-    long long t2 = lid / ls.nlimb;
-    int poly = (int)(t2 % ls.npoly);
-    long long item = t2 / ls.npoly;
-    LimbRef r;
-    r.ptr = ls.base + item * ls.item_stride + poly * ls.poly_stride + (long long)j * n;
-    r.prime = ls.prime_of[poly * ls.nlimb + j];
-    return r;
-}
-
-// Butterflies use D. Harvey's lazy reduction ("Faster arithmetic for
-// number-theoretic transforms", 2014): the forward network keeps values in
-// [0, 4q), the inverse in [0, 2q); one correction to [0, q) is applied when
-// the last pass stores.  Within a round, the twiddle of stage bit sb for
-// register k depends only on k >> (sb + 1) (p0 has no bits in the round's
-// window), so each distinct twiddle is loaded once.
-template <int LOGP, int LO>
-__device__ __forceinline__ void fwd_round(u64 (&x)[16], int p0, const ulonglong2 *__restrict__ tw,
-                                          int base, u64 q) {
-    const u64 q2 = 2 * q;
-#pragma unroll
-    for (int sb = 3; sb >= 0; --sb) {
-        const int s = LO + sb;
-        const int st = LOGP - 1 - s;
-        const int ibase = (base << st) + (p0 >> (s + 1));
-        ulonglong2 w[8];
-#pragma unroll
-        for (int g = 0; g < 8; ++g)
-            if (g < (8 >> sb)) w[g] = tw[ibase + g];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            if (k & (1 << sb)) continue;
-            const ulonglong2 ww = w[k >> (sb + 1)];
-            u64 u = x[k];
-            u = u >= q2 ? u - q2 : u;
-            const u64 t = mul_shoup_lazy(x[k | (1 << sb)], ww.x, ww.y, q);
-            x[k] = u + t;
-            x[k | (1 << sb)] = u - t + q2;
-        }
-    }
-}
-
-template <int LOGP, int LO, bool LAST>
-__device__ __forceinline__ void inv_round(u64 (&x)[16], int p0, const ulonglong2 *__restrict__ tw,
-                                          int base, u64 q, ulonglong2 ninv, ulonglong2 ninv_w1) {
-    const u64 q2 = 2 * q;
-#pragma unroll
-    for (int sb = 0; sb < 4; ++sb) {
-        const int s = LO + sb;
-        const int st = LOGP - 1 - s;
-        const bool last = LAST && s == LOGP - 1;
-        const int ibase = (base << st) + (p0 >> (s + 1));
-        ulonglong2 w[8];
-#pragma unroll
-        for (int g = 0; g < 8; ++g)
-            if (g < (8 >> sb)) w[g] = last ? ninv_w1 : tw[ibase + g];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            if (k & (1 << sb)) continue;
-            const ulonglong2 ww = w[k >> (sb + 1)];
-            const u64 u = x[k];
-            const u64 v = x[k | (1 << sb)];
-            if (last) {
-                x[k] = mul_shoup_lazy(u + v, ninv.x, ninv.y, q);
-            } else {
-                const u64 sum = u + v;
-                x[k] = sum >= q2 ? sum - q2 : sum;
-            }
-            x[k | (1 << sb)] = mul_shoup_lazy(u - v + q2, ww.x, ww.y, q);
-        }
-    }
-}
-
-// [0, 4q) -> [0, q)
-__device__ __forceinline__ u64 reduce4(u64 v, u64 q) {
-    v = v >= 2 * q ? v - 2 * q : v;
-    return v >= q ? v - q : v;
-}
-// [0, 2q) -> [0, q)
-__device__ __forceinline__ u64 reduce2(u64 v, u64 q) { return v >= q ? v - q : v; }
 
 // ---------------------------------------------------------------- N = 2^16
 // Pass A: columns.  Tile = 16 adjacent columns c0..c0+15, all 256 rows.
@@ -147,7 +65,9 @@ __global__ void __launch_bounds__(256) k_ntt16_colpass(const __grid_constant__ N
         for (int k = 0; k < 16; k++) g[((u << 4) | k) * 256 + c0 + col] = x[k];
     } else {
         const ulonglong2 *tw = a.c.tw_inv + (size_t)L.prime * a.c.n;
-        const ulonglong2 ni = a.c.ninv[L.prime], nw = a.c.ninv_w1[L.prime];
+        const int sj = a.scale_off + (int)(lid % a.ls.nlimb);
+        const ulonglong2 ni = a.scale_tab ? a.scale_tab[2 * sj] : a.c.ninv[L.prime];
+        const ulonglong2 nw = a.scale_tab ? a.scale_tab[2 * sj + 1] : a.c.ninv_w1[L.prime];
 #pragma unroll
         for (int k = 0; k < 16; k++) x[k] = g[((u << 4) | k) * 256 + c0 + col];
         inv_round<8, 0, false>(x, u << 4, tw, 1, q, ni, nw);
@@ -166,7 +86,6 @@ __global__ void __launch_bounds__(256) k_ntt16_colpass(const __grid_constant__ N
 // each).  thread t: u = t & 15, row = t >> 4.  Shared layout per row is
 // padded (17 words per 16) so that both register assignments are free of
 // bank conflicts.
-#define PADR(p) ((p) + ((p) >> 4))
 template <bool INV>
 __global__ void __launch_bounds__(256) k_ntt16_rowpass(const __grid_constant__ NttArgs a) {
     __shared__ u64 sm[16 * 272];
@@ -349,17 +268,24 @@ LimbSet make_limbset(u64 *base, int nitem, long long item_stride, int npoly, lon
     ls.poly_stride = poly_stride;
     ls.nlimb = nlimb;
     for (int p = 0; p < npoly; p++)
-        for (int j = 0; j < nlimb; j++) ls.prime_of[p * nlimb + j] = (int8_t)(prime0 + j);
+        for (int j = 0; j < nlimb; j++) {
+            ls.prime_of[p * nlimb + j] = (int8_t)(prime0 + j);
+            ls.aux[p * nlimb + j] = 0;
+        }
     return ls;
 }
 
-int ntt_limbset(secpe_ctx *ctx, const LimbSet &ls, bool inverse, const LimbSet *src) {
+int ntt_limbset(secpe_ctx *ctx, const LimbSet &ls, bool inverse, const LimbSet *src, const ulonglong2 *scale_tab,
+                int scale_off) {
     const long long nl = (long long)ls.nitem * ls.npoly * ls.nlimb;
     if (nl == 0) return SECPE_OK;
     if (ls.npoly * ls.nlimb > SECPE_MAX_LIMBSET) return SECPE_EINVAL;
+    if (scale_tab && (!inverse || ctx->log_n != 16)) return SECPE_EINVAL;
     NttArgs a;
     a.c = ctx->dev;
     a.ls = ls;
+    a.scale_tab = scale_tab;
+    a.scale_off = scale_off;
     a.has_src = src ? 1 : 0;
     a.src = src ? *src : ls;
     if (src && ctx->log_n != 16 && ctx->log_n != 12) {

@@ -1,0 +1,95 @@
+// Device building blocks of the NTT kernels (shared by ntt.cu and
+// ntt_fused.cu): limb addressing, radix-16 register rounds with lazy
+// (Harvey) butterflies, final corrections.  See ntt.cu for the network.
+#pragma once
+#include "internal.h"
+
+#define PADR(p) ((p) + ((p) >> 4))
+
+struct LimbRef {
+    u64 *ptr;
+    int prime;
+};
+
+static __device__ __forceinline__ LimbRef limb_of(const LimbSet &ls, int n, long long lid) {
+    int j = (int)(lid % ls.nlimb);
+    long long t2 = lid / ls.nlimb;
+    int poly = (int)(t2 % ls.npoly);
+    long long item = t2 / ls.npoly;
+    LimbRef r;
+    r.ptr = ls.base + item * ls.item_stride + poly * ls.poly_stride + (long long)j * n;
+    r.prime = ls.prime_of[poly * ls.nlimb + j];
+    return r;
+}
+
+// Butterflies use D. Harvey's lazy reduction ("Faster arithmetic for
+// number-theoretic transforms", 2014): the forward network keeps values in
+// [0, 4q), the inverse in [0, 2q); one correction to [0, q) is applied when
+// the last pass stores.  Within a round, the twiddle of stage bit sb for
+// register k depends only on k >> (sb + 1) (p0 has no bits in the round's
+// window), so each distinct twiddle is loaded once.
+template <int LOGP, int LO>
+static __device__ __forceinline__ void fwd_round(u64 (&x)[16], int p0, const ulonglong2 *__restrict__ tw,
+                                          int base, u64 q) {
+    const u64 q2 = 2 * q;
+#pragma unroll
+    for (int sb = 3; sb >= 0; --sb) {
+        const int s = LO + sb;
+        const int st = LOGP - 1 - s;
+        const int ibase = (base << st) + (p0 >> (s + 1));
+        ulonglong2 w[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+            if (g < (8 >> sb)) w[g] = tw[ibase + g];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (k & (1 << sb)) continue;
+            const ulonglong2 ww = w[k >> (sb + 1)];
+            u64 u = x[k];
+            u = u >= q2 ? u - q2 : u;
+            const u64 t = mul_shoup_lazy(x[k | (1 << sb)], ww.x, ww.y, q);
+            x[k] = u + t;
+            x[k | (1 << sb)] = u - t + q2;
+        }
+    }
+}
+
+template <int LOGP, int LO, bool LAST>
+static __device__ __forceinline__ void inv_round(u64 (&x)[16], int p0, const ulonglong2 *__restrict__ tw,
+                                          int base, u64 q, ulonglong2 ninv, ulonglong2 ninv_w1) {
+    const u64 q2 = 2 * q;
+#pragma unroll
+    for (int sb = 0; sb < 4; ++sb) {
+        const int s = LO + sb;
+        const int st = LOGP - 1 - s;
+        const bool last = LAST && s == LOGP - 1;
+        const int ibase = (base << st) + (p0 >> (s + 1));
+        ulonglong2 w[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+            if (g < (8 >> sb)) w[g] = last ? ninv_w1 : tw[ibase + g];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (k & (1 << sb)) continue;
+            const ulonglong2 ww = w[k >> (sb + 1)];
+            const u64 u = x[k];
+            const u64 v = x[k | (1 << sb)];
+            if (last) {
+                x[k] = mul_shoup_lazy(u + v, ninv.x, ninv.y, q);
+            } else {
+                const u64 sum = u + v;
+                x[k] = sum >= q2 ? sum - q2 : sum;
+            }
+            x[k | (1 << sb)] = mul_shoup_lazy(u - v + q2, ww.x, ww.y, q);
+        }
+    }
+}
+
+// [0, 4q) -> [0, q)
+static __device__ __forceinline__ u64 reduce4(u64 v, u64 q) {
+    v = v >= 2 * q ? v - 2 * q : v;
+    return v >= q ? v - q : v;
+}
+// [0, 2q) -> [0, q)
+static __device__ __forceinline__ u64 reduce2(u64 v, u64 q) { return v >= q ? v - q : v; }
+

@@ -1,0 +1,393 @@
+// Fused N = 2^16 NTT passes for key switching and rescale.
+//
+//  * k_colpass_bconv: forward pass A whose load computes a fast base
+//    conversion (FastBConv) of coefficient-form source limbs to the target
+//    prime on the fly:  v = sum_j [y_j + pre_j]_{p_j} * hat_{j,t} mod t,
+//    minus post_t, where y_j = x_j * inv_j was already applied by the INTT
+//    that produced the source (its final N^-1 is replaced by N^-1 inv_j).
+//    It serves ModUp (source = one digit of d, inv_j = [Qhat_j^-1]), ModDown
+//    (source = the special-prime limbs, inv_j = [Phat_j^-1], rounded by
+//    pre_j = [floor(P/2) inv_j], post = floor(P/2)) and the rescale (source
+//    = the last limb, inv = hat = 1, pre = post = floor(q_l/2)).  The
+//    converted limb is never written before its first NTT pass.
+//  * k_rowpass_epi: forward pass B whose store computes
+//    out = (X - v) * w (+ out), the last step of ModDown (w = P^-1) and of
+//    the rescale (w = q_l^-1).
+//  * k_rowpass_ip: forward pass B of every digit's extended limb for one
+//    target prime and tile, multiplied by the key-switching key (Montgomery
+//    form) and accumulated in registers across digits: the key inner
+//    product happens while the tile is on chip, and only the two
+//    accumulated limbs are written.
+#include "eval.h"
+#include "ntt_core.cuh"
+
+namespace {
+
+struct BConvSrc {
+    const u64 *base;  // source limb r of (item, poly) at base + item*is + poly*ps + r*N
+    long long is, ps;
+    int nsrc;
+    int src_prime[16];
+    u64 pre[16];         // added (mod the source prime) before the multiply-accumulate
+    const u64 *hat;      // hat[r * hat_stride + target_prime] (Montgomery form)
+    int hat_stride;
+    const u64 *post;     // post[target_prime] or null
+};
+
+struct BConvArgs {
+    DevCtx c;
+    LimbSet ls;   // destination limbs (target primes), aux = source group
+    int ngroups;
+    BConvSrc g[12];
+};
+
+template <int NS>
+__global__ void __launch_bounds__(256) k_colpass_bconv(const __grid_constant__ BConvArgs a) {
+    __shared__ u64 sm[4096];
+    const long long lid = blockIdx.x >> 4;
+    const int c0 = (blockIdx.x & 15) * 16;
+    const int j = (int)(lid % a.ls.nlimb);
+    const long long t2 = lid / a.ls.nlimb;
+    const int poly = (int)(t2 % a.ls.npoly);
+    const long long item = t2 / a.ls.npoly;
+    const int li = poly * a.ls.nlimb + j;
+    const int tp = a.ls.prime_of[li];
+    const BConvSrc &S = a.g[a.ls.aux[li]];
+    u64 *__restrict__ g = a.ls.base + item * a.ls.item_stride + poly * a.ls.poly_stride + (long long)j * a.c.n;
+    const u64 *__restrict__ src = S.base + item * S.is + poly * S.ps;
+    const u64 q = a.c.q[tp], qinv = a.c.qinv_neg[tp];
+    const int ns = NS > 0 ? NS : S.nsrc;
+    const int col = threadIdx.x & 15, u = threadIdx.x >> 4;
+    u64 hat[NS > 0 ? NS : 16];
+#pragma unroll
+    for (int r = 0; r < ns; r++) hat[r] = S.hat[r * S.hat_stride + tp];
+    const u64 post = S.post ? S.post[tp] : 0;
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        const int e = ((k << 4) | u) * 256 + c0 + col;
+        acc128 s = {0, 0};
+#pragma unroll
+        for (int r = 0; r < ns; r++) {
+            const u64 pr = a.c.q[S.src_prime[r]];
+            const u64 v = add_mod(src[(long long)r * a.c.n + e], S.pre[r], pr);
+            mac(s, v, hat[r]);
+        }
+        x[k] = sub_mod(redc(s.hi, s.lo, q, qinv), post, q);
+    }
+    const ulonglong2 *tw = a.c.tw_fwd + (size_t)tp * a.c.n;
+    fwd_round<8, 4>(x, u, tw, 1, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) sm[((k << 4) | u) * 16 + col] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = sm[((u << 4) | k) * 16 + col];
+    fwd_round<8, 0>(x, u << 4, tw, 1, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) g[((u << 4) | k) * 256 + c0 + col] = x[k];
+}
+
+struct EpiArgs {
+    DevCtx c;
+    LimbSet ls;        // pass-A output (lazy values), limb index = target prime
+    const u64 *X;      // X limb i of (item, poly) at X + item*xis + poly*xps + i*N
+    long long xis, xps;
+    u64 *out;          // out limb i of (item, poly) at out + item*ois + poly*ops + i*N
+    long long ois, ops;
+    const ulonglong2 *w;  // w[target prime] Shoup pair
+    int acc0, acc1;
+};
+
+__global__ void __launch_bounds__(256) k_rowpass_epi(const __grid_constant__ EpiArgs a) {
+    __shared__ u64 sm[16 * 272];
+    const long long lid = blockIdx.x >> 4;
+    const int r0 = (blockIdx.x & 15) * 16;
+    const int j = (int)(lid % a.ls.nlimb);
+    const long long t2 = lid / a.ls.nlimb;
+    const int poly = (int)(t2 % a.ls.npoly);
+    const long long item = t2 / a.ls.npoly;
+    const int tp = a.ls.prime_of[poly * a.ls.nlimb + j];
+    const u64 *__restrict__ g =
+        a.ls.base + item * a.ls.item_stride + poly * a.ls.poly_stride + (long long)j * a.c.n + (size_t)r0 * 256;
+    const u64 q = a.c.q[tp];
+    const int u = threadIdx.x & 15, row = threadIdx.x >> 4;
+    const int base = 256 + r0 + row;
+    u64 *__restrict__ srow = sm + row * 272;
+    const ulonglong2 *tw = a.c.tw_fwd + (size_t)tp * a.c.n;
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = g[row * 256 + ((k << 4) | u)];
+    fwd_round<8, 4>(x, u, tw, base, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) srow[PADR((k << 4) | u)] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = srow[PADR((u << 4) | k)];
+    fwd_round<8, 0>(x, u << 4, tw, base, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) srow[PADR((u << 4) | k)] = reduce4(x[k], q);
+    __syncthreads();
+    const u64 *__restrict__ X = a.X + item * a.xis + poly * a.xps + (long long)j * a.c.n + (size_t)r0 * 256;
+    u64 *__restrict__ O = a.out + item * a.ois + poly * a.ops + (long long)j * a.c.n + (size_t)r0 * 256;
+    const ulonglong2 w = a.w[tp];
+    const bool acc = poly == 0 ? a.acc0 : a.acc1;
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        const int e = threadIdx.x + 256 * i;
+        const int r = e >> 8, p = e & 255;
+        const u64 v = sm[r * 272 + PADR(p)];
+        u64 res = mul_shoup(sub_mod(X[e], v, q), w.x, w.y, q);
+        if (acc) res = add_mod(res, O[e], q);
+        O[e] = res;
+    }
+}
+
+struct IpArgs {
+    DevCtx c;
+    const u64 *d;      // d limb t of item at d + item*dis + t*N (NTT form)
+    long long dis;
+    const u64 *ext;    // pass-A output: item stride eis, digit j target tt at (off_j + tt)*N
+    long long eis;
+    KsDigits dg;
+    const u64 *key;    // [dnum][2][nprimes][N] Montgomery form
+    u64 *acc;          // [item][2][nt][N]
+    int lv, nitem;
+};
+
+// grid: ((t * 16 + tile) * nitem + item): the items sharing a key tile run back to back
+__global__ void __launch_bounds__(256, 2) k_rowpass_ip(const __grid_constant__ IpArgs a) {
+    __shared__ u64 sm[16 * 272];
+    const int nt = a.lv + 1 + a.c.np_special;
+    const int item = blockIdx.x % a.nitem;
+    const int tt16 = blockIdx.x / a.nitem;
+    const int tile = tt16 & 15, t = tt16 >> 4;
+    const int r0 = tile * 16;
+    const int pt = t <= a.lv ? t : a.c.nq + (t - a.lv - 1);
+    const u64 q = a.c.q[pt], qinv = a.c.qinv_neg[pt];
+    const int u = threadIdx.x & 15, row = threadIdx.x >> 4;
+    const int base = 256 + r0 + row;
+    u64 *__restrict__ srow = sm + row * 272;
+    const ulonglong2 *tw = a.c.tw_fwd + (size_t)pt * a.c.n;
+    const long long kpoly = (long long)a.c.nprimes * a.c.n;
+    const long long tile_off = (long long)r0 * 256;
+    u64 acc0[16], acc1[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) acc0[i] = acc1[i] = 0;
+    for (int jd = 0; jd < a.dg.ndig; jd++) {
+        const int lo = a.dg.lo[jd], hi = a.dg.hi[jd];
+        const u64 *kb = a.key + (long long)jd * 2 * kpoly + (long long)pt * a.c.n + tile_off;
+        if (t >= lo && t < hi) {
+            const u64 *src = a.d + item * a.dis + (long long)t * a.c.n + tile_off;
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                const int e = threadIdx.x + 256 * i;
+                const u64 v = src[e];
+                acc0[i] = add_mod(acc0[i], redc(mulhi64(v, kb[e]), v * kb[e], q, qinv), q);
+                acc1[i] = add_mod(acc1[i], redc(mulhi64(v, kb[kpoly + e]), v * kb[kpoly + e], q, qinv), q);
+            }
+        } else {
+            const int ti = t < lo ? t : t - (hi - lo);
+            const u64 *g = a.ext + item * a.eis + (long long)(a.dg.off[jd] + ti) * a.c.n + tile_off;
+            u64 x[16];
+#pragma unroll
+            for (int k = 0; k < 16; k++) x[k] = g[row * 256 + ((k << 4) | u)];
+            fwd_round<8, 4>(x, u, tw, base, q);
+#pragma unroll
+            for (int k = 0; k < 16; k++) srow[PADR((k << 4) | u)] = x[k];
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < 16; k++) x[k] = srow[PADR((u << 4) | k)];
+            fwd_round<8, 0>(x, u << 4, tw, base, q);
+#pragma unroll
+            for (int k = 0; k < 16; k++) srow[PADR((u << 4) | k)] = reduce4(x[k], q);
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                const int e = threadIdx.x + 256 * i;
+                const int r = e >> 8, p = e & 255;
+                const u64 v = sm[r * 272 + PADR(p)];
+                acc0[i] = add_mod(acc0[i], redc(mulhi64(v, kb[e]), v * kb[e], q, qinv), q);
+                acc1[i] = add_mod(acc1[i], redc(mulhi64(v, kb[kpoly + e]), v * kb[kpoly + e], q, qinv), q);
+            }
+            __syncthreads();
+        }
+    }
+    u64 *o = a.acc + (long long)item * 2 * nt * a.c.n + (long long)t * a.c.n + tile_off;
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        const int e = threadIdx.x + 256 * i;
+        o[e] = acc0[i];
+        o[(long long)nt * a.c.n + e] = acc1[i];
+    }
+}
+
+int launch_colpass_bconv(secpe_ctx *ctx, const BConvArgs &a) {
+    const long long nl = (long long)a.ls.nitem * a.ls.npoly * a.ls.nlimb;
+    if (nl == 0) return SECPE_OK;
+    int ns = a.g[0].nsrc;
+    for (int i = 1; i < a.ngroups; i++)
+        if (a.g[i].nsrc != ns) ns = 0;
+    const unsigned grid = (unsigned)(nl * 16);
+    KprofScope kp(ctx, "ntt16_colpass_bconv", 16.0 * ctx->n * nl);
+    switch (ns) {
+        case 1: SECPE_LAUNCH(ctx, k_colpass_bconv<1>, grid, 256, 0, a); break;
+        case 2: SECPE_LAUNCH(ctx, k_colpass_bconv<2>, grid, 256, 0, a); break;
+        case 3: SECPE_LAUNCH(ctx, k_colpass_bconv<3>, grid, 256, 0, a); break;
+        case 4: SECPE_LAUNCH(ctx, k_colpass_bconv<4>, grid, 256, 0, a); break;
+        case 8: SECPE_LAUNCH(ctx, k_colpass_bconv<8>, grid, 256, 0, a); break;
+        default: SECPE_LAUNCH(ctx, k_colpass_bconv<0>, grid, 256, 0, a);
+    }
+    return SECPE_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+bool fused_path(const secpe_ctx *ctx) { return ctx->log_n == 16; }
+
+// ModUp + inner product for N = 2^16: pass A with the digit's base
+// conversion as prologue into ext, then pass B of every digit fused with the
+// key inner product into acc [B][2][nt][N].
+int modup_ip_fused(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const u64 *dcoef, int B, int lv,
+                   const KsDigits &dg, int tot, const u64 *key, u64 *ext, u64 *acc) {
+    const int n = ctx->n, nt = lv + 1 + ctx->npsp;
+    if (dg.ndig > 12) return SECPE_EINVAL;
+    BConvArgs a;
+    a.c = ctx->dev;
+    a.ngroups = dg.ndig;
+    a.ls.base = ext;
+    a.ls.nitem = B;
+    a.ls.item_stride = (long long)tot * n;
+    a.ls.npoly = 1;
+    a.ls.poly_stride = 0;
+    a.ls.nlimb = tot;
+    int e = 0;
+    for (int j = 0; j < dg.ndig; j++) {
+        BConvSrc &S = a.g[j];
+        const int lo = dg.lo[j], hi = dg.hi[j];
+        S.base = dcoef + (size_t)lo * n;
+        S.is = (long long)(lv + 1) * n;
+        S.ps = 0;
+        S.nsrc = hi - lo;
+        const size_t tb = ((size_t)lv * ctx->dnum + j) * ctx->alpha;
+        for (int r = 0; r < S.nsrc; r++) {
+            S.src_prime[r] = lo + r;
+            S.pre[r] = 0;
+        }
+        S.hat = ctx->dev.mu_hat + tb * ctx->nprimes;
+        S.hat_stride = ctx->nprimes;
+        S.post = nullptr;
+        for (int t = 0; t < nt; t++) {
+            if (t >= lo && t < hi) continue;
+            a.ls.prime_of[e] = (int8_t)(t <= lv ? t : ctx->nq + (t - lv - 1));
+            a.ls.aux[e] = (int8_t)j;
+            e++;
+        }
+    }
+    const int last = dg.ndig - 1;
+    if (dg.ndig > 1 && a.g[last].nsrc != a.g[0].nsrc) {
+        // the partial last digit gets its own launch so both use a
+        // compile-time source count
+        BConvArgs b = a;
+        b.ngroups = 1;
+        b.g[0] = a.g[last];
+        b.ls.base = ext + (size_t)dg.off[last] * n;
+        b.ls.nlimb = tot - dg.off[last];
+        for (int i = 0; i < b.ls.nlimb; i++) {
+            b.ls.prime_of[i] = a.ls.prime_of[dg.off[last] + i];
+            b.ls.aux[i] = 0;
+        }
+        a.ngroups = last;
+        a.ls.nlimb = dg.off[last];
+        SECPE_CHECK(launch_colpass_bconv(ctx, a));
+        SECPE_CHECK(launch_colpass_bconv(ctx, b));
+    } else {
+        SECPE_CHECK(launch_colpass_bconv(ctx, a));
+    }
+    IpArgs ip;
+    ip.c = ctx->dev;
+    ip.d = d;
+    ip.dis = d_item_stride;
+    ip.ext = ext;
+    ip.eis = (long long)tot * n;
+    ip.dg = dg;
+    ip.key = key;
+    ip.acc = acc;
+    ip.lv = lv;
+    ip.nitem = B;
+    KprofScope kp(ctx, "ntt16_rowpass_ip", 8.0 * n * ((double)B * (tot + lv + 1) + 2.0 * dg.ndig * nt + 2.0 * B * nt));
+    SECPE_LAUNCH(ctx, k_rowpass_ip, (unsigned)((long long)nt * 16 * B), 256, 0, ip);
+    return SECPE_OK;
+}
+
+// out (+)= (X - NTT(FastBConv(src))) * w over limbs 0..nl-1 of B items x 2 polys.
+int bconv_ntt_epi(secpe_ctx *ctx, const BConvSrc &S, int B, int nl, u64 *tmp, const u64 *X, long long xis,
+                  long long xps, const CtB &out, const ulonglong2 *w, bool acc0, bool acc1) {
+    const int n = ctx->n;
+    BConvArgs a;
+    a.c = ctx->dev;
+    a.ngroups = 1;
+    a.g[0] = S;
+    a.ls = make_limbset(tmp, B, 2ll * nl * n, 2, (long long)nl * n, nl, 0);
+    SECPE_CHECK(launch_colpass_bconv(ctx, a));
+    EpiArgs ep;
+    ep.c = ctx->dev;
+    ep.ls = a.ls;
+    ep.X = X;
+    ep.xis = xis;
+    ep.xps = xps;
+    ep.out = out.data;
+    ep.ois = out.stride;
+    ep.ops = out.pstride();
+    ep.w = w;
+    ep.acc0 = acc0 ? 1 : 0;
+    ep.acc1 = acc1 ? 1 : 0;
+    const long long nlimbs = (long long)B * 2 * nl;
+    KprofScope kp(ctx, "ntt16_rowpass_epi", 8.0 * n * nlimbs * (acc0 || acc1 ? 4.0 : 3.0));
+    SECPE_LAUNCH(ctx, k_rowpass_epi, (unsigned)(nlimbs * 16), 256, 0, ep);
+    return SECPE_OK;
+}
+
+// ModDown of acc [B][2][nt][N] (special limbs already INTT'd) into out.
+int moddown_fused(secpe_ctx *ctx, const u64 *acc, int B, int lv, const CtB &out, bool acc0, bool acc1, u64 *tmp) {
+    const int n = ctx->n, nt = lv + 1 + ctx->npsp, k = ctx->npsp;
+    BConvSrc S;
+    S.base = acc + (size_t)(lv + 1) * n;
+    S.is = 2ll * nt * n;
+    S.ps = (long long)nt * n;
+    S.nsrc = k;
+    for (int j = 0; j < k; j++) {
+        const u64 pj = ctx->primes[ctx->nq + j];
+        u64 prod = 1;
+        for (int j2 = 0; j2 < k; j2++)
+            if (j2 != j) prod = hm::mulmod(prod, ctx->primes[ctx->nq + j2] % pj, pj);
+        const u64 inv = hm::invmod(prod, pj);
+        S.src_prime[j] = ctx->nq + j;
+        // [floor(P/2) * inv]_{p_j}: the source limbs already carry the factor inv
+        u64 pm = 1;
+        for (int j2 = 0; j2 < k; j2++) pm = hm::mulmod(pm, ctx->primes[ctx->nq + j2] % pj, pj);
+        S.pre[j] = hm::mulmod(hm::mulmod((pm + pj - 1) % pj, hm::invmod(2, pj), pj), inv, pj);
+    }
+    S.hat = ctx->dev.md_hat;
+    S.hat_stride = ctx->nq;
+    S.post = ctx->dev.md_hP;
+    return bconv_ntt_epi(ctx, S, B, lv + 1, tmp, acc, 2ll * nt * n, (long long)nt * n, out, ctx->dev.md_pinv, acc0,
+                         acc1);
+}
+
+// Rescale of `in` by q_l into out, y = INTT of the last limb [B][2][N].
+int rescale_fused(secpe_ctx *ctx, const CtB &in, const u64 *y, const CtB &out, u64 *tmp) {
+    const int n = ctx->n, lv = in.level;
+    BConvSrc S;
+    S.base = y;
+    S.is = 2ll * n;
+    S.ps = n;
+    S.nsrc = 1;
+    S.src_prime[0] = lv;
+    S.pre[0] = ctx->primes[lv] / 2;
+    S.hat = ctx->dev.mont_one;
+    S.hat_stride = 0;
+    S.post = ctx->dev.rs_hmod + (size_t)lv * ctx->nq;
+    return bconv_ntt_epi(ctx, S, in.B, lv, tmp, in.data, in.stride, in.pstride(), out,
+                         ctx->dev.rs_qinv + (size_t)lv * ctx->nq, false, false);
+}

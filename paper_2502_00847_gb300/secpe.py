@@ -23,6 +23,7 @@ EXPORTS = [
     "secpe_rescale", "secpe_rotate", "secpe_keyswitch", "secpe_refresh_testonly", "secpe_sign", "secpe_max",
     "secpe_ensemble_aggregate", "secpe_encrypted_argmax", "secpe_argmax_batch", "secpe_get_counters",
     "secpe_reset_counters", "secpe_select_primes", "secpe_kprof_begin", "secpe_kprof_end",
+    "secpe_keyswitch_batch", "secpe_mul_relin_batch", "secpe_rotate_batch", "secpe_rescale_batch",
 ]
 
 
@@ -41,6 +42,11 @@ class QueryC(ctypes.Structure):
     _fields_ = [("cts", ctypes.POINTER(CtC)), ("K", ctypes.c_int32), ("C", ctypes.c_int32),
                 ("d_min", ctypes.c_double), ("d_max", ctypes.c_double), ("qseed", ctypes.c_uint64),
                 ("z_out", ctypes.POINTER(CtC))]
+
+
+class CtBatchC(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("batch", ctypes.c_int32), ("cap", ctypes.c_int32),
+                ("level", ctypes.c_int32), ("scale", ctypes.c_double), ("stride", ctypes.c_uint64)]
 
 
 class CountersC(ctypes.Structure):
@@ -101,6 +107,10 @@ def lib():
         "secpe_select_primes": (i32, [P(ParamsC), P(u64), i32]),
         "secpe_kprof_begin": (i32, [vp, ctypes.c_char_p, i32]),
         "secpe_kprof_end": (i32, [vp, P(KprofC)]),
+        "secpe_keyswitch_batch": (i32, [vp, vp, i32, P(CtBatchC), P(CtBatchC), vp]),
+        "secpe_mul_relin_batch": (i32, [vp, vp, P(CtBatchC), P(CtBatchC), P(CtBatchC), vp]),
+        "secpe_rotate_batch": (i32, [vp, vp, P(CtBatchC), i32, P(CtBatchC), vp]),
+        "secpe_rescale_batch": (i32, [vp, P(CtBatchC), P(CtBatchC), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -466,3 +476,56 @@ def argmax_batch(ctx, keys, queries):
     _check(lib().secpe_argmax_batch(ctx.h, keys.h, qarr, len(queries), _stream()), "secpe_argmax_batch")
     for q, (_, z) in zip(queries, keep):
         q["z_out"].update(z)
+
+
+# ------------------------------------------------------------ batched primitives
+class CtBatch:
+    """`batch` ciphertexts in one tensor [batch][2][cap][N] at a common level/scale."""
+
+    def __init__(self, data, level, scale):
+        self.data = data
+        self.level = level
+        self.scale = scale
+
+    @property
+    def batch(self):
+        return int(self.data.shape[0])
+
+    def struct(self):
+        cap, n = int(self.data.shape[2]), int(self.data.shape[3])
+        return CtBatchC(ctypes.c_void_p(self.data.data_ptr()), self.batch, cap, self.level, self.scale, 2 * cap * n)
+
+    def update(self, c):
+        self.level = int(c.level)
+        self.scale = float(c.scale)
+
+
+def keyswitch_batch(ctx, keys, galois_step, d, out):
+    cd, co = d.struct(), out.struct()
+    _check(lib().secpe_keyswitch_batch(ctx.h, keys.h, galois_step, ctypes.byref(cd), ctypes.byref(co), _stream()),
+           "secpe_keyswitch_batch")
+    out.update(co)
+    return out
+
+
+def mul_relin_batch(ctx, keys, a, b, out):
+    ca, cb, co = a.struct(), b.struct(), out.struct()
+    _check(lib().secpe_mul_relin_batch(ctx.h, keys.h, ctypes.byref(ca), ctypes.byref(cb), ctypes.byref(co),
+                                       _stream()), "secpe_mul_relin_batch")
+    out.update(co)
+    return out
+
+
+def rotate_batch(ctx, keys, a, steps, out):
+    ca, co = a.struct(), out.struct()
+    _check(lib().secpe_rotate_batch(ctx.h, keys.h, ctypes.byref(ca), steps, ctypes.byref(co), _stream()),
+           "secpe_rotate_batch")
+    out.update(co)
+    return out
+
+
+def rescale_batch(ctx, a, out):
+    ca, co = a.struct(), out.struct()
+    _check(lib().secpe_rescale_batch(ctx.h, ctypes.byref(ca), ctypes.byref(co), _stream()), "secpe_rescale_batch")
+    out.update(co)
+    return out
