@@ -155,6 +155,19 @@ int secpe_mul_relin(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *a, c
                     secpe_ct *out, void *stream);
 /* Rounded division by the last prime; out may alias in. */
 int secpe_rescale(secpe_ctx *ctx, const secpe_ct *in, secpe_ct *out, void *stream);
+/* Same result as secpe_rescale (bit for bit), for callers that may not
+ * allocate device memory during a call (graph capture that forbids
+ * allocation calls, fixed-footprint serving loops, hosts that own all
+ * device memory).  The paper has no counterpart: this is a deployment
+ * variant.  Its scratch is a fixed file-scope device array of
+ * 2 * 65536 * 24 words (24 MiB) that every GPU loading the library keeps
+ * until exit; a call needs 2 * N * (level + 1) words and returns
+ * SECPE_EINVAL beyond that (N = 2^16: level <= 23).  The first call on a
+ * device looks up the array's device address (make it before any stream
+ * capture).  All calls share the array: calls that may overlap on the GPU
+ * race and must not be issued.  No cudaMalloc/cudaFree or other allocating
+ * call is made.  out may alias in. */
+int secpe_rescale_noalloc(secpe_ctx *ctx, const secpe_ct *in, secpe_ct *out, void *stream);
 /* RotL(in, steps) for steps > 0, RotR(in, -steps) for steps < 0. */
 int secpe_rotate(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *in, int steps,
                  secpe_ct *out, void *stream);

@@ -24,6 +24,7 @@ EXPORTS = [
     "secpe_ensemble_aggregate", "secpe_encrypted_argmax", "secpe_argmax_batch", "secpe_get_counters",
     "secpe_reset_counters", "secpe_select_primes", "secpe_kprof_begin", "secpe_kprof_end",
     "secpe_keyswitch_batch", "secpe_mul_relin_batch", "secpe_rotate_batch", "secpe_rescale_batch",
+    "secpe_rescale_noalloc",
 ]
 
 
@@ -111,6 +112,7 @@ def lib():
         "secpe_mul_relin_batch": (i32, [vp, vp, P(CtBatchC), P(CtBatchC), P(CtBatchC), vp]),
         "secpe_rotate_batch": (i32, [vp, vp, P(CtBatchC), i32, P(CtBatchC), vp]),
         "secpe_rescale_batch": (i32, [vp, P(CtBatchC), P(CtBatchC), vp]),
+        "secpe_rescale_noalloc": (i32, [vp, P(CtC), P(CtC), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -390,6 +392,16 @@ def rescale(ctx, a, out=None):
     out = ctx.new_ct() if out is None else out
     ca, co = a.struct(), out.struct()
     _check(lib().secpe_rescale(ctx.h, ctypes.byref(ca), ctypes.byref(co), _stream()), "secpe_rescale")
+    out.update(co)
+    return out
+
+
+def rescale_noalloc(ctx, a, out):
+    """secpe_rescale_noalloc: the rescale with no device allocation (scratch is
+    a fixed array inside the library); `out` must be preallocated."""
+    ca, co = a.struct(), out.struct()
+    _check(lib().secpe_rescale_noalloc(ctx.h, ctypes.byref(ca), ctypes.byref(co), _stream()),
+           "secpe_rescale_noalloc")
     out.update(co)
     return out
 
