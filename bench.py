@@ -35,6 +35,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--queries", type=int, default=256)
+    ap.add_argument("--classes", default="2,3,4,6,14,64",
+                    help="class counts C drawn uniformly per query (the default is the mix)")
     ap.add_argument("--plain-queries", type=int, default=16,
                     help="queries timed on the one-query-per-launch path")
     ap.add_argument("--no-e2e", action="store_true")
@@ -228,7 +230,8 @@ def run_ours(args, world, rank, local):
     n, cap = ctx.n, ctx.L + 1
     ct_words = 2 * cap * n
 
-    qs = workloads.argmax_queries(args.queries, seed=4 + 1000 * rank)
+    c_choices = tuple(int(c) for c in args.classes.split(","))
+    qs = workloads.argmax_queries(args.queries, seed=4 + 1000 * rank, C_choices=c_choices)
     n_cts = sum(q.K for q in qs)
     # inputs: one big device tensor of ciphertexts, encrypted on the device
     inputs = torch.empty((n_cts, 2, cap, n), dtype=torch.int64, device=dev)
