@@ -47,6 +47,11 @@ def parse():
                     help="primitive micro-benchmark (N=2^16, 24+4 primes, dnum=3) instead of the Argmax step")
     ap.add_argument("--micro-ops", default="ntt,keyswitch,hmult,rescale,rotate")
     ap.add_argument("--micro-batch", default="1,8,64")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving loop: Poisson arrivals, continuous batching, p50/p99 latency")
+    ap.add_argument("--rates", default="50,200,500,1000,2000")
+    ap.add_argument("--serve-queries", type=int, default=384, help="queries submitted per arrival rate")
+    ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--micro-params", default="micro", choices=["micro", "argmax"],
                     help="micro: 24+4 primes, dnum=3 (primitive config); argmax: the Argmax set (dnum=6)")
     return ap.parse_args()
@@ -447,10 +452,115 @@ def run_micro(args, rank):
                           "steps": args.steps, "warmup": args.warmup, "results": res}))
 
 
+def run_serve(args, rank):
+    """Serving loop (Poisson arrivals at each rate, continuous batching by
+    secpe_server_*, admission by an HBM budget) against the plain path: the
+    same queries served one at a time in arrival order (FIFO queue with the
+    measured one-query service times)."""
+    import numpy as np
+    import torch
+
+    from oracle.params import ARGMAX
+    from paper_2502_00847_gb300 import build as pkg_build
+    from paper_2502_00847_gb300 import secpe, workloads
+
+    pkg_build.build()
+    ctx = secpe.Context.from_params(ARGMAX)
+    keys = secpe.Keys(ctx, 1000 + rank, ROT_STEPS)
+    n, cap = ctx.n, ctx.L + 1
+    pool = workloads.argmax_queries(64, seed=5)
+    n_cts = sum(q.K for q in pool)
+    inputs = torch.empty((n_cts, 2, cap, n), dtype=torch.int64, device="cuda")
+    views, off = [], 0
+    for q in pool:
+        cts = []
+        for i in range(q.K):
+            c = secpe.Ciphertext(inputs[off], 0, ctx.scale)
+            secpe.encrypt_logits(ctx, keys, q.logits[i], q.d_min, q.enc_seeds[i], out=c)
+            cts.append(c)
+            off += 1
+        views.append(cts)
+    # plain service time per pool query (one query per call)
+    zt = ctx.new_ct()
+    svc = []
+    for i, q in enumerate(pool):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        y = secpe.ensemble_aggregate(ctx, views[i], q.d_min, q.d_max)
+        secpe.encrypted_argmax(ctx, keys, y, q.C, q.qseed, out=zt)
+        torch.cuda.synchronize()
+        svc.append(time.perf_counter() - t)
+    results = []
+    rng = np.random.default_rng(5)
+    for lam in [float(x) for x in args.rates.split(",")]:
+        nq = args.serve_queries
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, nq))
+        pick = rng.integers(0, len(pool), nq)
+        srv = secpe.Server(ctx, keys, hbm_budget_bytes=int(args.budget_gb * 1e9), max_batch=64)
+        zbufs = {}
+        pending = {}
+        lat = []
+        t0 = time.perf_counter()
+        nxt = 0
+        batch_sizes = []
+        inflight = []  # one event per enqueued phase: bounds how far the host runs ahead of the GPU
+        while nxt < nq or pending:
+            now = time.perf_counter() - t0
+            while nxt < nq and arrivals[nxt] <= now:
+                i = int(pick[nxt])
+                z = ctx.new_ct()
+                tk = srv.submit(views[i], pool[i].C, pool[i].d_min, pool[i].d_max, pool[i].qseed + nxt, z)
+                pending[tk] = arrivals[nxt]
+                zbufs[tk] = z
+                nxt += 1
+            launched = srv.step()
+            if launched:
+                batch_sizes.append(launched)
+                ev = torch.cuda.Event()
+                ev.record()
+                inflight.append(ev)
+                if len(inflight) > 4:
+                    inflight.pop(0).synchronize()
+            done = [tk for tk in pending if srv.poll(tk) == 1]
+            now = time.perf_counter() - t0
+            for tk in done:
+                lat.append(now - pending.pop(tk))
+                srv.forget(tk)
+                zbufs.pop(tk)
+            if not launched and not done and nxt < nq:
+                time.sleep(max(0.0, min(0.002, arrivals[nxt] - now)))
+            elif not launched and not done:
+                torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        srv.close()
+        # plain path: FIFO single server with the measured service times
+        finish, plat = 0.0, []
+        for a, i in zip(arrivals, pick):
+            finish = max(finish, a) + svc[int(i)]
+            plat.append(finish - a)
+        lat = np.array(lat)
+        plat = np.array(plat)
+        results.append({"rate_qps": lam, "queries": nq,
+                        "served": {"throughput_qps": nq / (wall - arrivals[0]), "p50_ms": 1e3 * np.median(lat),
+                                   "p99_ms": 1e3 * np.percentile(lat, 99),
+                                   "mean_batch": float(np.mean(batch_sizes)) if batch_sizes else 0},
+                        "plain": {"throughput_qps": nq / (finish - arrivals[0]), "p50_ms": 1e3 * np.median(plat),
+                                  "p99_ms": 1e3 * np.percentile(plat, 99)}})
+    if rank == 0:
+        print(json.dumps({"mode": "serve", "metric": METRIC,
+                          "config": {"workload": "serving loop: Poisson arrivals, %d queries per rate from a pool of "
+                                                 "64 (K~U{4,8,16}, C~U{2,3,4,6,14,64}, seed 5), N=2^16, HBM "
+                                                 "budget %.0f GB, max batch 64" % (args.serve_queries,
+                                                                                   args.budget_gb)},
+                          "plain_service_ms_mean": 1e3 * float(np.mean(svc)), "rates": results}))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
-    if args.micro:
+    if args.serve:
+        run_serve(args, rank)
+    elif args.micro:
         run_micro(args, rank)
     elif args.impl == "reference":
         run_reference(args, world, rank)

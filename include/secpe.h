@@ -239,6 +239,42 @@ typedef struct {
 int secpe_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q,
                        int n_queries, void *stream);
 
+/* ---- continuous-batching server ---------------------------------------- */
+/* A server keeps the state of admitted queries on the device and advances
+ * them phase by phase (aggregation + duplication, QuickMax rounds, final
+ * Sign); each secpe_server_step runs one phase, batched over every query at
+ * the same point of the circuit as the oldest admitted query (up to
+ * max_batch), so queries submitted while others run join at the next phase
+ * boundary.  A query is admitted when keys + in-flight states + one step's
+ * scratch + its state fit hbm_budget_bytes; until then it waits.  Results
+ * are bit-identical to secpe_encrypted_argmax on the aggregated input.
+ * The query's cts and z_out must stay valid until it completes. */
+typedef struct secpe_server secpe_server;
+typedef struct {
+    int32_t waiting, active, done;
+    uint64_t in_flight_bytes, keys_bytes, scratch_bytes;
+} secpe_server_stats_t;
+/* SECPE_EADMIT if the budget cannot hold even one query. */
+int secpe_server_create(secpe_ctx *ctx, const secpe_keys *keys, uint64_t hbm_budget_bytes, int max_batch,
+                        secpe_server **out);
+void secpe_server_destroy(secpe_server *srv);
+/* Validates the query (levels, scales, keys: SECPE_EKEY if a needed Galois
+ * key is missing) and queues it; returns its ticket. */
+int secpe_server_submit(secpe_server *srv, const secpe_query *q, int64_t *ticket);
+/* Drops a query that has not completed (its state is released). */
+int secpe_server_cancel(secpe_server *srv, int64_t ticket);
+/* Admits what fits, then enqueues one batched phase on `stream`; *launched
+ * = number of queries in that phase (0 when idle). */
+int secpe_server_step(secpe_server *srv, void *stream, int *launched);
+/* *done = 1 when the query's result is ready on the device, 0 if not yet,
+ * -1 if cancelled. */
+int secpe_server_poll(secpe_server *srv, int64_t ticket, int *done);
+/* Steps until the query completes; SECPE_ETIMEOUT after timeout_s seconds. */
+int secpe_server_wait(secpe_server *srv, int64_t ticket, double timeout_s);
+/* Releases the bookkeeping of a completed or cancelled query. */
+int secpe_server_forget(secpe_server *srv, int64_t ticket);
+int secpe_server_stats(const secpe_server *srv, secpe_server_stats_t *out);
+
 /* Counters of the last circuit call on this context (rotations, Sign
  * calls, relinearisations, refreshes, key switches, kernel launches). */
 typedef struct {

@@ -24,7 +24,9 @@ EXPORTS = [
     "secpe_ensemble_aggregate", "secpe_encrypted_argmax", "secpe_argmax_batch", "secpe_get_counters",
     "secpe_reset_counters", "secpe_select_primes", "secpe_kprof_begin", "secpe_kprof_end",
     "secpe_keyswitch_batch", "secpe_mul_relin_batch", "secpe_rotate_batch", "secpe_rescale_batch",
-    "secpe_rescale_noalloc",
+    "secpe_rescale_noalloc", "secpe_server_create", "secpe_server_destroy", "secpe_server_submit",
+    "secpe_server_cancel", "secpe_server_step", "secpe_server_poll", "secpe_server_wait", "secpe_server_forget",
+    "secpe_server_stats",
 ]
 
 
@@ -48,6 +50,12 @@ class QueryC(ctypes.Structure):
 class CtBatchC(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("batch", ctypes.c_int32), ("cap", ctypes.c_int32),
                 ("level", ctypes.c_int32), ("scale", ctypes.c_double), ("stride", ctypes.c_uint64)]
+
+
+class ServerStatsC(ctypes.Structure):
+    _fields_ = [("waiting", ctypes.c_int32), ("active", ctypes.c_int32), ("done", ctypes.c_int32),
+                ("in_flight_bytes", ctypes.c_uint64), ("keys_bytes", ctypes.c_uint64),
+                ("scratch_bytes", ctypes.c_uint64)]
 
 
 class CountersC(ctypes.Structure):
@@ -113,6 +121,15 @@ def lib():
         "secpe_rotate_batch": (i32, [vp, vp, P(CtBatchC), i32, P(CtBatchC), vp]),
         "secpe_rescale_batch": (i32, [vp, P(CtBatchC), P(CtBatchC), vp]),
         "secpe_rescale_noalloc": (i32, [vp, P(CtC), P(CtC), vp]),
+        "secpe_server_create": (i32, [vp, vp, u64, i32, P(vp)]),
+        "secpe_server_destroy": (None, [vp]),
+        "secpe_server_submit": (i32, [vp, P(QueryC), P(ctypes.c_int64)]),
+        "secpe_server_cancel": (i32, [vp, ctypes.c_int64]),
+        "secpe_server_step": (i32, [vp, vp, P(i32)]),
+        "secpe_server_poll": (i32, [vp, ctypes.c_int64, P(i32)]),
+        "secpe_server_wait": (i32, [vp, ctypes.c_int64, dbl]),
+        "secpe_server_forget": (i32, [vp, ctypes.c_int64]),
+        "secpe_server_stats": (i32, [vp, P(ServerStatsC)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -541,3 +558,65 @@ def rescale_batch(ctx, a, out):
     _check(lib().secpe_rescale_batch(ctx.h, ctypes.byref(ca), ctypes.byref(co), _stream()), "secpe_rescale_batch")
     out.update(co)
     return out
+
+
+# ------------------------------------------------------------------ server
+class Server:
+    """Continuous-batching server (secpe_server_*).  Keeps the ctypes query
+    structs of submitted queries alive until they are forgotten."""
+
+    def __init__(self, ctx, keys, hbm_budget_bytes, max_batch=64):
+        h = ctypes.c_void_p()
+        _check(lib().secpe_server_create(ctx.h, keys.h, int(hbm_budget_bytes), max_batch, ctypes.byref(h)),
+               "secpe_server_create")
+        self.h, self.ctx, self.keys = h, ctx, keys
+        self._keep = {}
+
+    def submit(self, cts, C, d_min, d_max, qseed, z_out):
+        arr = (CtC * len(cts))(*[c.struct() for c in cts])
+        z = z_out.struct()
+        qc = QueryC(arr, len(cts), C, d_min, d_max, qseed, ctypes.pointer(z))
+        t = ctypes.c_int64()
+        _check(lib().secpe_server_submit(self.h, ctypes.byref(qc), ctypes.byref(t)), "secpe_server_submit")
+        self._keep[t.value] = (arr, z, qc, z_out, cts)
+        return t.value
+
+    def step(self):
+        n = ctypes.c_int32()
+        _check(lib().secpe_server_step(self.h, _stream(), ctypes.byref(n)), "secpe_server_step")
+        return n.value
+
+    def poll(self, ticket):
+        d = ctypes.c_int32()
+        _check(lib().secpe_server_poll(self.h, ticket, ctypes.byref(d)), "secpe_server_poll")
+        if d.value == 1:
+            arr, z, qc, z_out, cts = self._keep[ticket]
+            z_out.update(z)
+        return d.value
+
+    def wait(self, ticket, timeout_s=600.0):
+        _check(lib().secpe_server_wait(self.h, ticket, timeout_s), "secpe_server_wait")
+        return self.poll(ticket)
+
+    def cancel(self, ticket):
+        _check(lib().secpe_server_cancel(self.h, ticket), "secpe_server_cancel")
+
+    def forget(self, ticket):
+        _check(lib().secpe_server_forget(self.h, ticket), "secpe_server_forget")
+        self._keep.pop(ticket, None)
+
+    def stats(self):
+        st = ServerStatsC()
+        _check(lib().secpe_server_stats(self.h, ctypes.byref(st)), "secpe_server_stats")
+        return {f[0]: int(getattr(st, f[0])) for f in ServerStatsC._fields_}
+
+    def close(self):
+        if self.h:
+            lib().secpe_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

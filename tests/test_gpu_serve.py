@@ -1,0 +1,119 @@
+"""Continuous-batching server (secpe_server_*): queries submitted while others
+are in flight join at phase boundaries; each result is bit-identical alone
+and in the mix, and equal to the one-query path; admission by HBM budget,
+missing keys, cancellation and bounded waits are host-side failure paths
+(no GPU fault)."""
+import numpy as np
+import pytest
+
+from oracle import TOY
+from paper_2502_00847_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+ROT = [1, 2, -2, -4]
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_2502_00847_gb300 import build as pkg_build
+    from paper_2502_00847_gb300 import secpe
+    pkg_build.build()
+    torch.cuda.set_device(0)
+    ctx = secpe.Context.from_params(TOY)
+    keys = secpe.Keys(ctx, 31, ROT)
+    qs = [workloads.toy_query(seed=s, K=k, C=c) for s, k, c in
+          ((21, 3, 2), (22, 2, 4), (23, 4, 3), (24, 2, 2), (25, 3, 4))]
+    inputs = [[secpe.encrypt_logits(ctx, keys, q.logits[i], q.d_min, q.enc_seeds[i]) for i in range(q.K)]
+              for q in qs]
+    ref = []
+    for q, cts in zip(qs, inputs):
+        y = secpe.ensemble_aggregate(ctx, cts, q.d_min, q.d_max)
+        ref.append(secpe.encrypted_argmax(ctx, keys, y, q.C, q.qseed).residues())
+    return ctx, keys, qs, inputs, ref, secpe
+
+
+def submit(srv, ctx, q, cts):
+    z = ctx.new_ct()
+    return srv.submit(cts, q.C, q.d_min, q.d_max, q.qseed, z), z
+
+
+def test_interleaved_submissions_match_single_query_path(env):
+    ctx, keys, qs, inputs, ref, secpe = env
+    srv = secpe.Server(ctx, keys, hbm_budget_bytes=8 << 30, max_batch=8)
+    tickets = []
+    # two queries, a few phases, then the rest arrive while those are in flight
+    for i in (0, 1):
+        tickets.append(submit(srv, ctx, qs[i], inputs[i]))
+    assert srv.step() == 1          # oldest first: query 0's aggregation
+    assert srv.step() >= 1
+    for i in (2, 3, 4):
+        tickets.append(submit(srv, ctx, qs[i], inputs[i]))
+    batched = 0
+    for _ in range(200):
+        n = srv.step()
+        batched = max(batched, n)
+        if n == 0:
+            break
+    assert batched >= 2, "later arrivals were never batched with earlier ones"
+    for i, (t, z) in enumerate(tickets):
+        assert srv.wait(t, 60.0) == 1
+        assert np.array_equal(z.residues(), ref[i]), i
+        d = secpe.decrypt(ctx, keys, z, qs[i].C)
+        assert int(np.argmax(d)) == int(np.argmax(qs[i].logits.mean(0)))
+        srv.forget(t)
+    st = srv.stats()
+    assert st["active"] == 0 and st["waiting"] == 0 and st["in_flight_bytes"] == 0
+
+
+def test_alone_equals_in_mix(env):
+    ctx, keys, qs, inputs, ref, secpe = env
+    alone = secpe.Server(ctx, keys, hbm_budget_bytes=8 << 30, max_batch=8)
+    t, z = submit(alone, ctx, qs[2], inputs[2])
+    alone.wait(t, 60.0)
+    mixed = secpe.Server(ctx, keys, hbm_budget_bytes=8 << 30, max_batch=8)
+    subs = [submit(mixed, ctx, qs[i], inputs[i]) for i in (4, 2, 0, 3)]
+    for tk, _ in subs:
+        mixed.wait(tk, 60.0)
+    assert np.array_equal(z.residues(), subs[1][1].residues())
+
+
+def test_admission_by_budget(env):
+    ctx, keys, qs, inputs, ref, secpe = env
+    with pytest.raises(secpe.SecpeError) as e:
+        secpe.Server(ctx, keys, hbm_budget_bytes=1 << 20, max_batch=8)
+    assert e.value.code == -8
+    # room for one query in flight: the second waits until the first is done
+    probe = secpe.Server(ctx, keys, hbm_budget_bytes=8 << 30, max_batch=1)
+    s0 = probe.stats()
+    one = s0["keys_bytes"] + s0["scratch_bytes"] + 3 * 2 * ctx.n * (ctx.L + 1) * 8
+    srv = secpe.Server(ctx, keys, hbm_budget_bytes=one + 1, max_batch=1)
+    (t0, z0), (t1, z1) = submit(srv, ctx, qs[0], inputs[0]), submit(srv, ctx, qs[3], inputs[3])
+    srv.step()
+    st = srv.stats()
+    assert st["active"] == 1 and st["waiting"] == 1
+    srv.wait(t0, 60.0)
+    srv.wait(t1, 60.0)
+    assert np.array_equal(z0.residues(), ref[0]) and np.array_equal(z1.residues(), ref[3])
+
+
+def test_missing_key_cancel_and_timeout(env):
+    ctx, keys, qs, inputs, ref, secpe = env
+    srv = secpe.Server(ctx, keys, hbm_budget_bytes=8 << 30, max_batch=8)
+    q = workloads.toy_query(seed=40, K=2, C=6)      # needs RotR(8) and RotL(4): not generated
+    cts = [secpe.encrypt_logits(ctx, keys, q.logits[i], q.d_min, q.enc_seeds[i]) for i in range(q.K)]
+    with pytest.raises(secpe.SecpeError) as e:
+        submit(srv, ctx, q, cts)
+    assert e.value.code == -5
+    t0, z0 = submit(srv, ctx, qs[1], inputs[1])
+    t1, z1 = submit(srv, ctx, qs[0], inputs[0])
+    srv.step()
+    srv.cancel(t0)
+    assert srv.poll(t0) == -1
+    with pytest.raises(secpe.SecpeError) as e:
+        srv.wait(t1, 0.0)
+    assert e.value.code == -7
+    assert srv.wait(t1, 60.0) == 1
+    assert np.array_equal(z1.residues(), ref[0])
+    assert ctx.stream_status() == 0
