@@ -427,6 +427,10 @@ def run_micro(args, rank):
         a = secpe.CtBatch(x, L, ctx.scale)
         b = secpe.CtBatch(y, L, ctx.scale)
         o = secpe.CtBatch(out, 0, ctx.scale)
+        if "ntt_tc" in ops:
+            ms = timed(lambda: secpe.ntt_cts_tc(ctx, x, B, 2 * cap * n, cap, L))
+            res["ntt_tc_B%d" % B] = {"ms": ms, "us_per_limb": ms * 1e3 / (B * 2 * cap),
+                                     "GBps_alg": B * 2 * cap * limb * 4 / (ms / 1e3) / 1e9}
         if "keyswitch" in ops:
             ms = timed(lambda: secpe.keyswitch_batch(ctx, keys, 0, a, o))
             alg = B * (cap * limb + 2 * cap * limb) + ksk_bytes
@@ -444,6 +448,33 @@ def run_micro(args, rank):
             res["rotate_B%d" % B] = {"ms_mean": sum(per) / len(per), "ms_by_log2_step": per}
         del x, y, out
         torch.cuda.empty_cache()
+    if "ntt_tc_identity" in ops:
+        # precision variant: bit identity with the CUDA-core NTT over 10^4 seeded random ciphertexts
+        total, chunk, mism = 10000, 50, 0
+        t_tc = t_cc = 0.0
+        for s0 in range(0, total, chunk):
+            g2 = torch.Generator(device="cpu").manual_seed(30000 + s0)
+            t = torch.empty((chunk, 2, cap, n), dtype=torch.int64)
+            for i in range(cap):
+                t[:, :, i] = torch.randint(0, primes[i], (chunk, 2, n), generator=g2, dtype=torch.int64)
+            u = t.cuda()
+            v = u.clone()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            secpe.ntt_cts(ctx, u, chunk, 2 * cap * n, cap, L)
+            e[1].record()
+            secpe.ntt_cts_tc(ctx, v, chunk, 2 * cap * n, cap, L)
+            e[2].record()
+            torch.cuda.synchronize()
+            t_cc += e[0].elapsed_time(e[1])
+            t_tc += e[1].elapsed_time(e[2])
+            mism += int((u != v).any(dim=(1, 2, 3)).sum().item())
+            secpe.ntt_cts(ctx, u, chunk, 2 * cap * n, cap, L, inverse=True)
+            secpe.ntt_cts_tc(ctx, v, chunk, 2 * cap * n, cap, L, inverse=True)
+            torch.cuda.synchronize()
+            mism += int((u != v).any(dim=(1, 2, 3)).sum().item())
+        res["ntt_tc_identity"] = {"ciphertexts": total, "mismatching_ciphertexts": mism,
+                                  "forward_ms_cuda_cores": t_cc, "forward_ms_tensor_pipe": t_tc}
     if rank == 0:
         desc = ("24x50-bit + 4x60-bit special primes, dnum=3" if args.micro_params == "micro" else
                 "q0 60-bit + 23x50-bit + 4x60-bit special primes, dnum=6")

@@ -143,6 +143,16 @@ int secpe_ntt(secpe_ctx *ctx, uint64_t *limbs, const int32_t *prime_idx, int cou
  * of `ct_stride` words: both polynomials, limbs 0..level. */
 int secpe_ntt_cts(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, int cap, int level,
                   int inverse, void *stream);
+/* Precision variant (N = 2^16 only): the same transforms, bit-identical,
+ * with the column pass (a fixed 256 x 256 matrix per prime applied to every
+ * column) computed as an exact contraction on the tensor pipe: residues and
+ * matrix entries split into 8-bit limbs, u8 x u8 -> s32 products, diagonal
+ * sums recombined modulo q.  The row pass stays on CUDA cores.  The first
+ * call on a context builds the matrices (28 MiB for 28 primes). */
+int secpe_ntt_tc(secpe_ctx *ctx, uint64_t *limbs, const int32_t *prime_idx, int count, int inverse,
+                 void *stream);
+int secpe_ntt_cts_tc(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, int cap, int level,
+                     int inverse, void *stream);
 int secpe_add(secpe_ctx *ctx, const secpe_ct *a, const secpe_ct *b, secpe_ct *out, void *stream);
 int secpe_sub(secpe_ctx *ctx, const secpe_ct *a, const secpe_ct *b, secpe_ct *out, void *stream);
 /* out = a * c landing at out_level with scale exactly `target_scale`

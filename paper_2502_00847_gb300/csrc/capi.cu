@@ -614,3 +614,30 @@ extern "C" int secpe_rescale_batch(secpe_ctx *ctx, const secpe_ctbatch *in, secp
     SECPE_CHECK(E.rescale(bview(ctx, in), r));
     return finish(ctx, copy_batch_out(ctx, r, out));
 }
+
+// ---------------------------------------------------------------- precision variant
+extern "C" int secpe_ntt_tc(secpe_ctx *ctx, uint64_t *limbs, const int32_t *prime_idx, int count, int inverse,
+                            void *stream) {
+    if (!ctx || !limbs || !prime_idx || count < 0 || ctx->log_n != 16) return SECPE_EINVAL;
+    CallScope cs(ctx, stream);
+    for (int s = 0; s < count; s += SECPE_MAX_LIMBSET) {
+        const int c = std::min(SECPE_MAX_LIMBSET, count - s);
+        LimbSet ls = make_limbset((u64 *)limbs + (size_t)s * ctx->n, 1, 0, 1, 0, c, 0);
+        for (int j = 0; j < c; j++) {
+            if (prime_idx[s + j] < 0 || prime_idx[s + j] >= ctx->nprimes) return SECPE_EINVAL;
+            ls.prime_of[j] = (int8_t)prime_idx[s + j];
+        }
+        SECPE_CHECK(ntt_limbset_tc(ctx, ls, inverse != 0));
+    }
+    return finish(ctx, SECPE_OK);
+}
+
+extern "C" int secpe_ntt_cts_tc(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, int cap, int level,
+                                int inverse, void *stream) {
+    if (!ctx || !base || batch < 0 || level < 0 || level >= cap || level > ctx->L || ctx->log_n != 16 ||
+        ct_stride < 2ull * cap * ctx->n)
+        return SECPE_EINVAL;
+    CallScope cs(ctx, stream);
+    LimbSet ls = make_limbset((u64 *)base, batch, (long long)ct_stride, 2, (long long)cap * ctx->n, level + 1, 0);
+    return finish(ctx, ntt_limbset_tc(ctx, ls, inverse != 0));
+}

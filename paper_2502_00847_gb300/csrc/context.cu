@@ -270,6 +270,7 @@ extern "C" int secpe_ctx_create(const secpe_params *p, secpe_ctx **out) {
 extern "C" void secpe_ctx_destroy(secpe_ctx *ctx) {
     if (!ctx) return;
     cudaDeviceSynchronize();
+    tc_forget_ctx(ctx);
     for (void *p : ctx->allocations) cudaFree(p);
     delete ctx;
 }

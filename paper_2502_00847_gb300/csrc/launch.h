@@ -56,6 +56,13 @@ static inline unsigned grid1d(long long work, int block) {
 int ntt_limbset(secpe_ctx *ctx, const LimbSet &ls, bool inverse, const LimbSet *src = nullptr,
                 const ulonglong2 *scale_tab = nullptr, int scale_off = 0);
 
+// N = 2^16 only: the row pass (last 8 stages of the forward NTT, first 8 of
+// the inverse) alone, in place.
+int ntt_rowpass_only(secpe_ctx *ctx, const LimbSet &ls, bool inverse);
+// Precision variant (ntt_tc.cu): NTT/INTT with the column pass on the tensor pipe.
+int ntt_limbset_tc(secpe_ctx *ctx, const LimbSet &ls, bool inverse);
+void tc_forget_ctx(const secpe_ctx *ctx);
+
 // Convenience: LimbSet for `nitem` ciphertext-like objects of `npoly`
 // polynomials, limbs [l0, l0 + nlimb) mapped to primes [p0, p0 + nlimb).
 LimbSet make_limbset(u64 *base, int nitem, long long item_stride, int npoly,

@@ -258,6 +258,25 @@ __global__ void k_scale_ninv(const __grid_constant__ NttArgs a, long long total)
 
 }  // namespace
 
+int ntt_rowpass_only(secpe_ctx *ctx, const LimbSet &ls, bool inverse) {
+    const long long nl = (long long)ls.nitem * ls.npoly * ls.nlimb;
+    if (nl == 0) return SECPE_OK;
+    if (ctx->log_n != 16 || ls.npoly * ls.nlimb > SECPE_MAX_LIMBSET) return SECPE_EINVAL;
+    NttArgs a;
+    a.c = ctx->dev;
+    a.ls = ls;
+    a.src = ls;
+    a.has_src = 0;
+    a.tiles = 16;
+    a.scale_tab = nullptr;
+    a.scale_off = 0;
+    if (!inverse)
+        SECPE_LAUNCH(ctx, k_ntt16_rowpass<false>, (unsigned)(nl * 16), 256, 0, a);
+    else
+        SECPE_LAUNCH(ctx, k_ntt16_rowpass<true>, (unsigned)(nl * 16), 256, 0, a);
+    return SECPE_OK;
+}
+
 LimbSet make_limbset(u64 *base, int nitem, long long item_stride, int npoly, long long poly_stride,
                      int nlimb, int prime0) {
     LimbSet ls;

@@ -26,7 +26,7 @@ EXPORTS = [
     "secpe_keyswitch_batch", "secpe_mul_relin_batch", "secpe_rotate_batch", "secpe_rescale_batch",
     "secpe_rescale_noalloc", "secpe_server_create", "secpe_server_destroy", "secpe_server_submit",
     "secpe_server_cancel", "secpe_server_step", "secpe_server_poll", "secpe_server_wait", "secpe_server_forget",
-    "secpe_server_stats",
+    "secpe_server_stats", "secpe_ntt_tc", "secpe_ntt_cts_tc",
 ]
 
 
@@ -130,6 +130,8 @@ def lib():
         "secpe_server_wait": (i32, [vp, ctypes.c_int64, dbl]),
         "secpe_server_forget": (i32, [vp, ctypes.c_int64]),
         "secpe_server_stats": (i32, [vp, P(ServerStatsC)]),
+        "secpe_ntt_tc": (i32, [vp, vp, P(i32), i32, i32, vp]),
+        "secpe_ntt_cts_tc": (i32, [vp, vp, i32, ctypes.c_size_t, i32, i32, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -356,6 +358,19 @@ def ntt(ctx, limbs, prime_idx, inverse=False):
     _check(lib().secpe_ntt(ctx.h, ctypes.c_void_p(limbs.data_ptr()), pi, len(prime_idx), 1 if inverse else 0,
                            _stream()), "secpe_ntt")
     return limbs
+
+
+def ntt_tc(ctx, limbs, prime_idx, inverse=False):
+    """Precision variant of ntt(): column pass on the tensor pipe (N = 2^16)."""
+    pi = (ctypes.c_int32 * len(prime_idx))(*prime_idx)
+    _check(lib().secpe_ntt_tc(ctx.h, ctypes.c_void_p(limbs.data_ptr()), pi, len(prime_idx), 1 if inverse else 0,
+                              _stream()), "secpe_ntt_tc")
+    return limbs
+
+
+def ntt_cts_tc(ctx, base, batch, ct_stride, cap, level, inverse=False):
+    _check(lib().secpe_ntt_cts_tc(ctx.h, ctypes.c_void_p(base.data_ptr()), batch, ct_stride, cap, level,
+                                  1 if inverse else 0, _stream()), "secpe_ntt_cts_tc")
 
 
 def ntt_cts(ctx, base, batch, ct_stride, cap, level, inverse=False):

@@ -125,3 +125,35 @@ def test_batched_argmax_mix(env):
     o2.keygen(99)
     zo = o2.decrypt(Ct(z.residues(), z.level, z.scale), qs[0].C)
     assert np.max(np.abs(zo - secpe.decrypt(ctx, k2, z, qs[0].C))) < 2.0 ** -30
+
+
+def test_tensor_pipe_ntt_bit_identical(env):
+    """Precision variant: column pass as an exact 8-bit-limb contraction on the
+    tensor pipe; forward and inverse bit-identical to the CUDA-core NTT."""
+    import torch
+    o, ctx, keys, secpe = env
+    rng = np.random.default_rng(33)
+    pidx = [(3 * i) % 28 for i in range(29)]
+    x = np.stack([rng.integers(0, o.primes[i], o.n, dtype=np.uint64) for i in pidx])
+    # extremes: zeros and q - 1 everywhere in two limbs
+    x[0] = 0
+    x[1] = o.primes[pidx[1]] - 1
+    a = torch.from_numpy(x.view(np.int64)).cuda()
+    b = a.clone()
+    secpe.ntt(ctx, a, pidx)
+    secpe.ntt_tc(ctx, b, pidx)
+    assert torch.equal(a, b)
+    exp = x[5].copy()
+    o.ntt(exp, pidx[5])
+    assert np.array_equal(b[5].cpu().numpy().view(np.uint64), exp)
+    secpe.ntt(ctx, a, pidx, inverse=True)
+    secpe.ntt_tc(ctx, b, pidx, inverse=True)
+    assert torch.equal(a, b)
+    assert np.array_equal(b.cpu().numpy().view(np.uint64), x)
+    # ciphertext layout entry point
+    B, cap = 3, ctx.L + 1
+    c = torch.from_numpy(workloads.residues((B, 2, cap, ctx.n), o.primes[:cap], seed=7).view(np.int64)).cuda()
+    d = c.clone()
+    secpe.ntt_cts(ctx, c, B, 2 * cap * ctx.n, cap, ctx.L)
+    secpe.ntt_cts_tc(ctx, d, B, 2 * cap * ctx.n, cap, ctx.L)
+    assert torch.equal(c, d)
