@@ -326,11 +326,10 @@ class Oracle:
         return self.decode_coeffs(self.decrypt_coeffs(ct), ct.scale, n_slots)
 
     # ------------------------------------------------------ key switching
-    def keyswitch(self, d, level, ksk):
-        """Hybrid key switching of d (NTT form, limbs 0..level) with key ksk:
-        ModUp per digit (INTT, FastBConv to the other primes, NTT), inner
-        product with the key over Q_l u P, then ModDown (INTT of the special
-        limbs, FastBConv to q_i, NTT, (x - conv) * P^-1)."""
+    def keyswitch_acc(self, d, level, ksk):
+        """ModUp and key inner product of hybrid key switching (before the
+        division by P): d (NTT form, limbs 0..level) -> (acc0, acc1) over
+        Q_l u P.  ModUp per digit: INTT, FastBConv to the other primes, NTT."""
         self.counters["keyswitches"] += 1
         q_idx = list(range(level + 1))
         sp_idx = self.ctx.special_idx()
@@ -353,7 +352,39 @@ class Oracle:
             for t in tgt:
                 acc0[t] = self.vadd(acc0[t], self.vmul(ext[t], ksk[j, 0, t], t), t)
                 acc1[t] = self.vadd(acc1[t], self.vmul(ext[t], ksk[j, 1, t], t), t)
+        return acc0, acc1
+
+    def keyswitch(self, d, level, ksk):
+        """Hybrid key switching of d with key ksk: ModUp, inner product, then
+        ModDown (rounded division by P)."""
+        acc0, acc1 = self.keyswitch_acc(d, level, ksk)
         return self.moddown(acc0, level), self.moddown(acc1, level)
+
+    def moddown_rescale(self, acc, dk, level):
+        """Relinearisation's ModDown fused with the rescale (READING: one
+        rounded division instead of two): x = P*dk + acc over Q_l u P,
+        out = round(x / (P q_l)) over q_0..q_{l-1}, computed as
+        (x - (FastBConv([x + h]_M) - h)) * M^-1 with M = P q_l, h = floor(M/2),
+        the FastBConv from the primes of M (the special primes and q_l)."""
+        sp_idx = self.ctx.special_idx()
+        ql = self.primes[level]
+        M = self.ctx.P * ql
+        h = M // 2
+        src = sp_idx + [level]
+        xs = np.stack([acc[t].copy() for t in sp_idx] +
+                      [self.vadd(self.vscale(dk[level], self.ctx.P % ql, level), acc[level], level)])
+        for r, t in enumerate(src):
+            self.intt(xs[r], t)
+            xs[r] = self.vaddc(xs[r], h % self.primes[t], t)
+        conv = self.fast_bconv(xs, src, list(range(level)))
+        out = np.empty((level, self.n), dtype=U64)
+        for pi in range(level):
+            q = self.primes[pi]
+            c = self.vaddc(conv[pi], -h % q, pi)
+            self.ntt(c, pi)
+            x = self.vadd(self.vscale(dk[pi], self.ctx.P % q, pi), acc[pi], pi)
+            out[pi] = self.vscale(self.vsub(x, c, pi), pow(M % q, -1, q), pi)
+        return out
 
     def moddown(self, acc, level):
         """Rounded division by P of x given over Q_l u P (READING: rounding,
@@ -426,27 +457,47 @@ class Oracle:
                 out[k, pi] = self.vscale(t, pow(ql % self.primes[pi], -1, self.primes[pi]), pi)
         return Ct(out, lv - 1, ct.scale / float(ql))
 
+    def tensor(self, a, b):
+        """(a0 b0, a0 b1 + a1 b0, a1 b1) at the lower level, scale s_a s_b:
+        a 3-component ciphertext (decrypts with (1, s, s^2))."""
+        lv = min(a.level, b.level)
+        a, b = self.drop(a, lv), self.drop(b, lv)
+        d = np.empty((3, lv + 1, self.n), dtype=U64)
+        for pi in range(lv + 1):
+            d[0, pi] = self.vmul(a.c[0, pi], b.c[0, pi], pi)
+            d[1, pi] = self.vadd(self.vmul(a.c[0, pi], b.c[1, pi], pi),
+                                 self.vmul(a.c[1, pi], b.c[0, pi], pi), pi)
+            d[2, pi] = self.vmul(a.c[1, pi], b.c[1, pi], pi)
+        return Ct(d, lv, a.scale * b.scale)
+
+    def relin_rescale(self, d):
+        """Relinearise a 3-component ciphertext and divide by its last prime:
+        key switching of d2 (ModUp, inner product) and one rounded division of
+        (P d_k + acc_k) by P q_l for k = 0, 1."""
+        lv = d.level
+        if lv < 1 + self.p.reserve:
+            raise ValueError("not enough levels")
+        self.counters["relins"] += 1
+        acc0, acc1 = self.keyswitch_acc(d.c[2], lv, self.rlk)
+        c = np.stack([self.moddown_rescale(acc0, d.c[0], lv), self.moddown_rescale(acc1, d.c[1], lv)])
+        return Ct(c, lv - 1, d.scale / float(self.primes[lv]))
+
+    def add3(self, a, b):
+        """Sum of two 3-component ciphertexts at the same level and scale."""
+        assert a.level == b.level
+        self._check_scales(a, b)
+        c = np.empty_like(a.c)
+        for k in range(3):
+            for pi in range(a.level + 1):
+                c[k, pi] = self.vadd(a.c[k, pi], b.c[k, pi], pi)
+        return Ct(c, a.level, a.scale)
+
     def mul(self, a, b):
-        """Tensor, relinearise, rescale (SecPE Sec. 2.2 slot-wise product)."""
+        """Slot-wise product (SecPE Sec. 2.2): tensor, relinearise, rescale."""
         lv = min(a.level, b.level)
         if lv < 1 + self.p.reserve:
             raise ValueError("not enough levels")
-        a, b = self.drop(a, lv), self.drop(b, lv)
-        d0 = np.empty((lv + 1, self.n), dtype=U64)
-        d1 = np.empty_like(d0)
-        d2 = np.empty_like(d0)
-        for pi in range(lv + 1):
-            d0[pi] = self.vmul(a.c[0, pi], b.c[0, pi], pi)
-            d1[pi] = self.vadd(self.vmul(a.c[0, pi], b.c[1, pi], pi),
-                               self.vmul(a.c[1, pi], b.c[0, pi], pi), pi)
-            d2[pi] = self.vmul(a.c[1, pi], b.c[1, pi], pi)
-        self.counters["relins"] += 1
-        k0, k1 = self.keyswitch(d2, lv, self.rlk)
-        c = np.empty((2, lv + 1, self.n), dtype=U64)
-        for pi in range(lv + 1):
-            c[0, pi] = self.vadd(d0[pi], k0[pi], pi)
-            c[1, pi] = self.vadd(d1[pi], k1[pi], pi)
-        return self.rescale(Ct(c, lv, a.scale * b.scale))
+        return self.relin_rescale(self.tensor(a, b))
 
     def mul_const(self, x, c, target, out_level):
         """x * c landing at out_level with scale exactly `target`: drop x to
@@ -517,9 +568,10 @@ class Oracle:
         fixed depth-4 baby-step giant-step DAG:
           x2 = x*x, x3 = x*x2, x4 = x2*x2, x8 = x4*x4,
           B = c5 x + c7 x3, T = x4 * B, U = x8 * (c9 x), A = c1 x + c3 x3,
-          p = A + T + U,
-        the constant multiplies landing at the scales that make the three
-        addends' scales equal to s_out."""
+          p = A + (T + U),
+        the constant multiplies landing at the scales that make the addends'
+        scales equal to s_out; T and U are added before their single
+        relinearisation (5 key switches per polynomial)."""
         c1, c3, c5, c7, c9 = c
         lv = x.level
         q3 = float(self.primes[lv - 3])
@@ -529,11 +581,13 @@ class Oracle:
         x8 = self.mul(x4, x4)
         sB = s_out * q3 / x4.scale
         B = self.add(self.mul_const(x, c5, sB, lv - 3), self.mul_const(x3, c7, sB, lv - 3))
-        T = self.mul(x4, B)
         s9 = s_out * q3 / x8.scale
-        U = self.mul(x8, self.mul_const(x, c9, s9, lv - 3))
+        X9 = self.mul_const(x, c9, s9, lv - 3)
+        # T = x4 * B and U = x8 * (c9 x) share one relinearisation (READING:
+        # lazy relinearisation, the 3-component products are added first)
+        TU = self.relin_rescale(self.add3(self.tensor(x4, B), self.tensor(x8, X9)))
         A = self.add(self.mul_const(x, c1, s_out, lv - 4), self.mul_const(x3, c3, s_out, lv - 4))
-        return self.add(self.add(A, T), U)
+        return self.add(A, TU)
 
     def sign(self, x, out_levels):
         """Sign(x) = f^df(g^dg(x)) (SecPE Eq. comp); before each polynomial,

@@ -22,7 +22,7 @@ def poly9(x, c):
     T = x4 * B
     U = x8 * (c9 * x)
     A = c1 * x + c3 * x3
-    return (A + T) + U
+    return A + (T + U)
 
 
 def sign(x, dg=2, df=2):

@@ -168,6 +168,55 @@ extern "C" int secpe_ctx_create(const secpe_params *p, secpe_ctx **out) {
         md_hP[t] = hm::mulmod(pm1, hm::invmod(2, P[t]), P[t]);
     }
 
+    // Relinearisation ModDown + rescale tables (per level l >= 1)
+    const int ks = k + 1;
+    std::vector<ulonglong2> mdr_ninv((size_t)2 * nq * ks, make_ulonglong2(0, 0)), mdr_inv((size_t)nq * ks,
+                                                                                         make_ulonglong2(0, 0));
+    std::vector<ulonglong2> mdr_w((size_t)nq * nq, make_ulonglong2(0, 0));
+    std::vector<u64> mdr_pre((size_t)nq * ks, 0), mdr_hat((size_t)nq * ks * nq, 0), mdr_post((size_t)nq * nq, 0);
+    std::vector<u64> mdr_pre_scaled((size_t)nq * ks, 0), pmod(np);
+    for (int t = 0; t < np; t++) {
+        u64 pm = 1;
+        for (int j = 0; j < k; j++) pm = hm::mulmod(pm, P[nq + j] % P[t], P[t]);
+        pmod[t] = pm;
+    }
+    for (int lv = 1; lv < nq; lv++) {
+        std::vector<int> src(ks);
+        src[0] = lv;
+        for (int j = 0; j < k; j++) src[1 + j] = nq + j;
+        for (int j = 0; j < ks; j++) {
+            const u64 s_ = P[src[j]];
+            u64 mh = 1;  // M / s_j mod s_j
+            for (int j2 = 0; j2 < ks; j2++)
+                if (j2 != j) mh = hm::mulmod(mh, P[src[j2]] % s_, s_);
+            const u64 inv = hm::invmod(mh, s_);
+            mdr_inv[(size_t)lv * ks + j] = sh(inv, s_);
+            u64 mm = 1;  // M mod s_j
+            for (int j2 = 0; j2 < ks; j2++) mm = hm::mulmod(mm, P[src[j2]] % s_, s_);
+            const u64 hmod = hm::mulmod((mm + s_ - 1) % s_, hm::invmod(2, s_), s_);
+            mdr_pre[(size_t)lv * ks + j] = hmod;
+            mdr_pre_scaled[(size_t)lv * ks + j] = hm::mulmod(hmod, inv, s_);
+            const u64 ni = hm::invmod((u64)n, s_);
+            const u64 s0 = hm::mulmod(ni, inv, s_);
+            const u64 w1 = hm::invmod(hm::powmod(ctx->psi[src[j]], hm::bitrev(1, ctx->log_n), s_), s_);
+            mdr_ninv[2 * ((size_t)lv * ks + j)] = sh(s0, s_);
+            mdr_ninv[2 * ((size_t)lv * ks + j) + 1] = sh(hm::mulmod(s0, w1, s_), s_);
+            for (int i = 0; i < nq; i++) {
+                u64 hq = 1;
+                for (int j2 = 0; j2 < ks; j2++)
+                    if (j2 != j) hq = hm::mulmod(hq, P[src[j2]] % P[i], P[i]);
+                mdr_hat[((size_t)lv * ks + j) * nq + i] = mont(hq, P[i]);
+            }
+        }
+        for (int i = 0; i < nq; i++) {
+            u64 mm = 1;
+            for (int j2 = 0; j2 < ks; j2++) mm = hm::mulmod(mm, P[src[j2]] % P[i], P[i]);
+            mdr_post[(size_t)lv * nq + i] = hm::mulmod((mm + P[i] - 1) % P[i], hm::invmod(2, P[i]), P[i]);
+            if (i < lv) mdr_w[(size_t)lv * nq + i] = sh(hm::invmod(mm, P[i]), P[i]);
+        }
+    }
+    ctx->h_mdr_pre_scaled = mdr_pre_scaled;
+
     // Rescale tables
     std::vector<ulonglong2> rs_qinv((size_t)nq * nq, make_ulonglong2(0, 0));
     std::vector<u64> rs_hmod((size_t)nq * nq, 0);
@@ -240,6 +289,13 @@ extern "C" int secpe_ctx_create(const secpe_params *p, secpe_ctx **out) {
     UP(md_hat, md_hat);
     UP(md_pinv, md_pinv);
     UP(md_hP, md_hP);
+    UP(mdr_ninv, mdr_ninv);
+    UP(mdr_inv, mdr_inv);
+    UP(mdr_pre, mdr_pre);
+    UP(mdr_hat, mdr_hat);
+    UP(mdr_post, mdr_post);
+    UP(mdr_w, mdr_w);
+    UP(pmod, pmod);
     UP(rs_qinv, rs_qinv);
     UP(rs_hmod, rs_hmod);
     UP(mr_inv, mr_inv);

@@ -102,13 +102,11 @@ int Eval::rescale(const Ct &in, Ct &out) {
     return SECPE_OK;
 }
 
-int Eval::mul(const Ct &a, const Ct &b, Ct &out) {
+int Eval::tensor(const Ct &a, const Ct &b, Ct &out3) {
     if (a.B() != b.B()) return SECPE_EINVAL;
     const int lv = std::min(a.level(), b.level());
-    if (lv < 1 + ctx->p.reserve) return SECPE_ELEVEL;
-    if (!keys || !keys->rlk) return SECPE_EKEY;
     const int B = a.B(), n = ctx->n;
-    Ct d;  // (d0, d1, d2) per item, viewed as a 2-poly batch with stride 3 limb stacks
+    Ct d;
     d.buf = std::make_shared<DevBuf>();
     SECPE_CHECK(d.buf->alloc(ctx, sizeof(u64) * (size_t)B * 3 * (lv + 1) * n));
     SECPE_CHECK(launch_tensor(ctx, a.v, b.v, d.buf->u(), lv + 1));
@@ -119,9 +117,47 @@ int Eval::mul(const Ct &a, const Ct &b, Ct &out) {
     d.v.level = lv;
     d.v.scale = a.scale() * b.scale();
     d.v.n = n;
-    ctx->counters.relins += B;
-    SECPE_CHECK(keyswitch(ctx, d.v.data + 2ll * (lv + 1) * n, d.v.stride, B, lv, keys->rlk, d.v, true, true));
-    return rescale(d, out);
+    out3 = d;
+    return SECPE_OK;
+}
+
+int Eval::add3(const Ct &a3, const Ct &b3, Ct &out3) {
+    if (a3.B() != b3.B() || a3.level() != b3.level()) return SECPE_EINVAL;
+    if (!scales_match(a3.scale(), b3.scale())) return SECPE_ESCALE;
+    const int lv = a3.level(), B = a3.B(), n = ctx->n;
+    Ct o;
+    o.buf = std::make_shared<DevBuf>();
+    SECPE_CHECK(o.buf->alloc(ctx, sizeof(u64) * (size_t)B * 3 * (lv + 1) * n));
+    o.v = a3.v;
+    o.v.data = o.buf->u();
+    o.v.cap = lv + 1;
+    o.v.stride = 3ll * (lv + 1) * n;
+    SECPE_CHECK(launch_addsub(ctx, a3.v, b3.v, o.v, lv + 1, false, 3));
+    out3 = o;
+    return SECPE_OK;
+}
+
+int Eval::relin_rescale(const Ct &d3, Ct &out) {
+    const int lv = d3.level();
+    if (lv < 1 + ctx->p.reserve) return SECPE_ELEVEL;
+    if (!keys || !keys->rlk) return SECPE_EKEY;
+    if (d3.v.cap != lv + 1 || d3.v.stride != 3ll * (lv + 1) * ctx->n) return SECPE_EINVAL;
+    Ct o;
+    SECPE_CHECK(ct_alloc(ctx, d3.B(), lv - 1, d3.scale() / (double)ctx->primes[lv], o));
+    ctx->counters.relins += d3.B();
+    SECPE_CHECK(relin_rescale_batch(ctx, d3.v.data, d3.B(), lv, keys->rlk, o.v));
+    out = o;
+    return SECPE_OK;
+}
+
+int Eval::mul(const Ct &a, const Ct &b, Ct &out) {
+    if (a.B() != b.B()) return SECPE_EINVAL;
+    const int lv = std::min(a.level(), b.level());
+    if (lv < 1 + ctx->p.reserve) return SECPE_ELEVEL;
+    if (!keys || !keys->rlk) return SECPE_EKEY;
+    Ct d;
+    SECPE_CHECK(tensor(a, b, d));
+    return relin_rescale(d, out);
 }
 
 int Eval::mul_const(const Ct &x, const std::vector<double> &c, double target, int out_level, Ct &out) {
@@ -216,7 +252,7 @@ int Eval::poly9(const Ct &x, const double *c, double s_out, Ct &out) {
     if (lv < 4 + ctx->p.reserve) return SECPE_ELEVEL;
     const double q3 = (double)ctx->primes[lv - 3];
     // temporaries are released as soon as they are dead (Ct() frees them)
-    Ct x2, x3, x4, x8, t1, t2, Bv, T, t3, U, t4, t5, A, AT;
+    Ct x2, x3, x4, x8, t1, t2, Bv, X9, T3, U3, TU3, TU, t4, t5, A;
     SECPE_CHECK(mul(x, x, x2));
     SECPE_CHECK(mul(x, x2, x3));
     SECPE_CHECK(mul(x2, x2, x4));
@@ -228,24 +264,28 @@ int Eval::poly9(const Ct &x, const double *c, double s_out, Ct &out) {
     SECPE_CHECK(add(t1, t2, Bv));
     t1 = Ct();
     t2 = Ct();
-    SECPE_CHECK(mul(x4, Bv, T));
+    const double s9 = s_out * q3 / x8.scale();
+    SECPE_CHECK(mul_const(x, {c[4]}, s9, lv - 3, X9));
+    // T = x4 * B and U = x8 * (c9 x) are added as 3-component ciphertexts and
+    // relinearised once
+    SECPE_CHECK(tensor(x4, Bv, T3));
     x4 = Ct();
     Bv = Ct();
-    const double s9 = s_out * q3 / x8.scale();
-    SECPE_CHECK(mul_const(x, {c[4]}, s9, lv - 3, t3));
-    SECPE_CHECK(mul(x8, t3, U));
+    SECPE_CHECK(tensor(x8, X9, U3));
     x8 = Ct();
-    t3 = Ct();
+    X9 = Ct();
+    SECPE_CHECK(add3(T3, U3, TU3));
+    T3 = Ct();
+    U3 = Ct();
+    SECPE_CHECK(relin_rescale(TU3, TU));
+    TU3 = Ct();
     SECPE_CHECK(mul_const(x, {c[0]}, s_out, lv - 4, t4));
     SECPE_CHECK(mul_const(x3, {c[1]}, s_out, lv - 4, t5));
     x3 = Ct();
     SECPE_CHECK(add(t4, t5, A));
     t4 = Ct();
     t5 = Ct();
-    SECPE_CHECK(add(A, T, AT));
-    A = Ct();
-    T = Ct();
-    return add(AT, U, out);
+    return add(A, TU, out);
 }
 
 int Eval::sign(const Ct &x, int out_levels, Ct &out) {

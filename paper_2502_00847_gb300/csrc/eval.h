@@ -60,6 +60,10 @@ struct Eval {
     int add(const Ct &a, const Ct &b, Ct &out);
     int sub(const Ct &a, const Ct &b, Ct &out);
     int mul(const Ct &a, const Ct &b, Ct &out);
+    // 3-component ciphertexts (stride 3 (level+1) N, scale tracked)
+    int tensor(const Ct &a, const Ct &b, Ct &out3);
+    int add3(const Ct &a3, const Ct &b3, Ct &out3);
+    int relin_rescale(const Ct &d3, Ct &out);
     int mul_const(const Ct &x, const std::vector<double> &c, double target, int out_level, Ct &out);
     int add_const(const Ct &x, double c, Ct &out);
     int rescale(const Ct &in, Ct &out);
@@ -77,6 +81,10 @@ struct Eval {
 // result into polys 0 and 1 of `out` (B items, level lv).
 int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int lv, const u64 *key,
               const CtB &out, bool acc0, bool acc1);
+// ModUp + key inner product only: acc [B][2][lv+1+k][N] (allocated here).
+int keyswitch_acc(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int lv, const u64 *key, DevBuf &acc);
+// Relinearise the 3-component tensor d [B][3][lv+1][N] and rescale: out at lv-1.
+int relin_rescale_batch(secpe_ctx *ctx, const u64 *d, int B, int lv, const u64 *key, const CtB &out);
 int rescale_batch(secpe_ctx *ctx, const CtB &in, const CtB &out);
 unsigned galois_elt(const secpe_ctx *ctx, int steps);
 const u64 *galois_key(const secpe_keys *keys, unsigned g);
@@ -87,4 +95,5 @@ bool fused_path(const secpe_ctx *ctx);
 int modup_ip_fused(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const u64 *dcoef, int B, int lv,
                    const KsDigits &dg, int tot, const u64 *key, u64 *ext, u64 *acc);
 int moddown_fused(secpe_ctx *ctx, const u64 *acc, int B, int lv, const CtB &out, bool acc0, bool acc1, u64 *tmp);
+int moddown_rescale_fused(secpe_ctx *ctx, u64 *acc, const u64 *d, int B, int lv, const CtB &out, u64 *tmp);
 int rescale_fused(secpe_ctx *ctx, const CtB &in, const u64 *y, const CtB &out, u64 *tmp);

@@ -42,6 +42,15 @@ struct DevCtx {
     const u64 *md_hat;         // [np_special*nq] Montgomery form of Phat_j mod q_i
     const ulonglong2 *md_pinv; // [nq] P^-1 mod q_i (shoup)
     const u64 *md_hP;          // [nprimes] floor(P/2) mod t
+    // Relinearisation's ModDown fused with the rescale at level l: division by
+    // M = P q_l from the sources s = (q_l, p_0, .., p_{k-1}), per level l:
+    const ulonglong2 *mdr_ninv;  // [(l*(k+1) + j)*2 + {0,1}] INTT scaling N^-1 [(M/s_j)^-1]_{s_j} (and * psi^-brv(1))
+    const ulonglong2 *mdr_inv;   // [l*(k+1) + j] [(M/s_j)^-1]_{s_j} (shoup)
+    const u64 *mdr_pre;          // [l*(k+1) + j] floor(M/2) mod s_j
+    const u64 *mdr_hat;          // [(l*(k+1) + j)*nq + i] Montgomery form of (M/s_j) mod q_i
+    const u64 *mdr_post;         // [l*nq + i] floor(M/2) mod q_i
+    const ulonglong2 *mdr_w;     // [l*nq + i] M^-1 mod q_i (shoup)
+    const u64 *pmod;             // [nprimes] P mod prime t
     // Rescale by q_l, per level l: [l*nq + i]
     const ulonglong2 *rs_qinv; // q_l^-1 mod q_i (shoup)
     const u64 *rs_hmod;        // floor(q_l/2) mod q_i
@@ -104,6 +113,7 @@ struct secpe_ctx {
     // host copies used by host-side constant encoding
     std::vector<u64> h_qinv_neg, h_r2, h_mu;
     std::vector<ulonglong2> h_mu_inv;  // host mirror of DevCtx::mu_inv
+    std::vector<u64> h_mdr_pre_scaled; // [l*(k+1) + j] floor(M/2) * [(M/s_j)^-1] mod s_j
 };
 
 struct secpe_keys {

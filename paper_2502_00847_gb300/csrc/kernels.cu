@@ -23,9 +23,9 @@ __device__ __forceinline__ u64 signed_mod(long long k, u64 q, u64 mu) {
 
 // ------------------------------------------------------------ add / sub
 __global__ void k_addsub(DevCtx c, const u64 *a, long long as, const u64 *b, long long bs,
-                         u64 *o, long long os, int cap_a, int cap_b, int cap_o, int nl, int sub) {
+                         u64 *o, long long os, int cap_a, int cap_b, int cap_o, int nl, int sub, int npoly) {
     const int li = blockIdx.y;
-    const int i = li % nl, k = (li / nl) & 1, item = li / (2 * nl);
+    const int i = li % nl, k = (li / nl) % npoly, item = li / (npoly * nl);
     const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (e >= c.n) return;
     const u64 q = c.q[i];
@@ -492,6 +492,68 @@ __global__ void k_limb_automorph(DevCtx c, const u64 *in, u64 *o, unsigned g) {
     o[(long long)t * c.n + j] = in[(long long)t * c.n + src];
 }
 
+// ------------------------------------------------------------ relin ModDown + rescale
+// acc[item][poly][lv] <- P * d[item][poly][lv] + acc[item][poly][lv] (NTT form):
+// the q_l limb of x = P d + acc, next to the special limbs in acc.
+__global__ void k_mdr_prep(DevCtx c, const u64 *d, long long dis, long long dps, u64 *acc, int lv) {
+    const int nt = lv + 1 + c.np_special;
+    const int kp = blockIdx.y;  // item*2 + poly
+    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= c.n) return;
+    const int item = kp >> 1, poly = kp & 1;
+    const u64 q = c.q[lv], qi = c.qinv_neg[lv], r2 = c.r2[lv], pm = c.pmod[lv];
+    const ulonglong2 dv = ld2(d + item * dis + poly * dps + (long long)lv * c.n + e);
+    u64 *ap = acc + ((long long)kp * nt + lv) * c.n + e;
+    ulonglong2 av = ld2(ap);
+    av.x = add_mod(av.x, mul_mod(dv.x, pm, q, qi, r2), q);
+    av.y = add_mod(av.y, mul_mod(dv.y, pm, q, qi, r2), q);
+    st2(ap, av);
+}
+
+// generic path: sources = acc limbs lv..lv+k (coefficient form) of (item, poly);
+// conv[item][poly][i] = FastBConv([x + h]_M -> q_i) - h, i < lv
+__global__ void k_mdr_bconv(DevCtx c, const u64 *acc, u64 *conv, int lv) {
+    const int nt = lv + 1 + c.np_special, ks = c.np_special + 1;
+    const int kp = blockIdx.y;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= c.n) return;
+    u64 y[9];
+    for (int j = 0; j < ks; j++) {
+        const int sp = j == 0 ? lv : c.nq + j - 1;
+        const u64 q = c.q[sp];
+        u64 v = acc[((long long)kp * nt + lv + j) * c.n + e];
+        v = add_mod(v, c.mdr_pre[(size_t)lv * ks + j], q);
+        const ulonglong2 w = c.mdr_inv[(size_t)lv * ks + j];
+        y[j] = mul_shoup(v, w.x, w.y, q);
+    }
+    for (int i = 0; i < lv; i++) {
+        acc128 s = {0, 0};
+        for (int j = 0; j < ks; j++) mac(s, y[j], c.mdr_hat[((size_t)lv * ks + j) * c.nq + i]);
+        const u64 q = c.q[i];
+        const u64 r = redc(s.hi, s.lo, q, c.qinv_neg[i]);
+        conv[((long long)kp * lv + i) * c.n + e] = sub_mod(r, c.mdr_post[(size_t)lv * c.nq + i], q);
+    }
+}
+
+// out_i = (acc_i - conv_i) * M^-1 + d_i * q_l^-1, i < lv
+__global__ void k_mdr_fin(DevCtx c, const u64 *acc, const u64 *conv, const u64 *d, long long dis, long long dps,
+                          u64 *o, long long os, int cap_o, int lv) {
+    const int nt = lv + 1 + c.np_special;
+    const int li = blockIdx.y;
+    const int i = li % lv, kp = li / lv, item = kp >> 1, poly = kp & 1;
+    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= c.n) return;
+    const u64 q = c.q[i];
+    const ulonglong2 w = c.mdr_w[(size_t)lv * c.nq + i], w2 = c.rs_qinv[(size_t)lv * c.nq + i];
+    const ulonglong2 a = ld2(acc + ((long long)kp * nt + i) * c.n + e);
+    const ulonglong2 b = ld2(conv + ((long long)kp * lv + i) * c.n + e);
+    const ulonglong2 dv = ld2(d + item * dis + poly * dps + (long long)i * c.n + e);
+    ulonglong2 r;
+    r.x = add_mod(mul_shoup(sub_mod(a.x, b.x, q), w.x, w.y, q), mul_shoup(dv.x, w2.x, w2.y, q), q);
+    r.y = add_mod(mul_shoup(sub_mod(a.y, b.y, q), w.x, w.y, q), mul_shoup(dv.y, w2.x, w2.y, q), q);
+    st2(o + item * os + ((long long)poly * cap_o + i) * c.n + e, r);
+}
+
 }  // namespace
 
 // ======================================================================
@@ -501,10 +563,10 @@ static dim3 limb_grid(int n, int per_thread, long long nlimbs) {
     return dim3((unsigned)((n / per_thread + 255) / 256), (unsigned)nlimbs);
 }
 
-int launch_addsub(secpe_ctx *ctx, const CtB &a, const CtB &b, const CtB &o, int nl, bool sub) {
+int launch_addsub(secpe_ctx *ctx, const CtB &a, const CtB &b, const CtB &o, int nl, bool sub, int npoly) {
     if (nl <= 0 || a.B == 0) return SECPE_OK;
-    SECPE_LAUNCH(ctx, k_addsub, limb_grid(ctx->n, 2, (long long)a.B * 2 * nl), 256, 0, ctx->dev, a.data,
-                 a.stride, b.data, b.stride, o.data, o.stride, a.cap, b.cap, o.cap, nl, sub ? 1 : 0);
+    SECPE_LAUNCH(ctx, k_addsub, limb_grid(ctx->n, 2, (long long)a.B * npoly * nl), 256, 0, ctx->dev, a.data,
+                 a.stride, b.data, b.stride, o.data, o.stride, a.cap, b.cap, o.cap, nl, sub ? 1 : 0, npoly);
     return SECPE_OK;
 }
 
@@ -688,5 +750,23 @@ int launch_limb_mul(secpe_ctx *ctx, const u64 *a, const u64 *b, u64 *o) {
 
 int launch_limb_automorph(secpe_ctx *ctx, const u64 *in, u64 *o, unsigned g) {
     SECPE_LAUNCH(ctx, k_limb_automorph, limb_grid(ctx->n, 1, ctx->nprimes), 256, 0, ctx->dev, in, o, g);
+    return SECPE_OK;
+}
+
+int launch_mdr_prep(secpe_ctx *ctx, const u64 *d, long long dis, long long dps, u64 *acc, int B, int lv) {
+    SECPE_LAUNCH(ctx, k_mdr_prep, limb_grid(ctx->n, 2, (long long)B * 2), 256, 0, ctx->dev, d, dis, dps, acc, lv);
+    return SECPE_OK;
+}
+
+int launch_mdr_bconv(secpe_ctx *ctx, const u64 *acc, u64 *conv, int B, int lv) {
+    if (ctx->npsp + 1 > 9) return SECPE_EINVAL;
+    SECPE_LAUNCH(ctx, k_mdr_bconv, limb_grid(ctx->n, 1, (long long)B * 2), 256, 0, ctx->dev, acc, conv, lv);
+    return SECPE_OK;
+}
+
+int launch_mdr_fin(secpe_ctx *ctx, const u64 *acc, const u64 *conv, const u64 *d, long long dis, long long dps,
+                   const CtB &o, int lv) {
+    SECPE_LAUNCH(ctx, k_mdr_fin, limb_grid(ctx->n, 2, (long long)o.B * 2 * lv), 256, 0, ctx->dev, acc, conv, d,
+                 dis, dps, o.data, o.stride, o.cap, lv);
     return SECPE_OK;
 }

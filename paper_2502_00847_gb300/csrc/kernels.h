@@ -19,7 +19,7 @@ struct PrimeList {
     int p[SECPE_MAX_PRIMES];
 };
 
-int launch_addsub(secpe_ctx *ctx, const CtB &a, const CtB &b, const CtB &o, int nl, bool sub);
+int launch_addsub(secpe_ctx *ctx, const CtB &a, const CtB &b, const CtB &o, int nl, bool sub, int npoly = 2);
 int launch_tensor(secpe_ctx *ctx, const CtB &a, const CtB &b, u64 *d, int nl);
 int launch_mulconst(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, const std::vector<long long> &k);
 int launch_addconst(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, const std::vector<long long> &k);
@@ -49,3 +49,7 @@ int launch_ksk_gen(secpe_ctx *ctx, const u64 *a, const u64 *e_ntt, const u64 *s,
 int launch_from_mont(secpe_ctx *ctx, const u64 *in, u64 *out, int nlimb_total);
 int launch_limb_mul(secpe_ctx *ctx, const u64 *a, const u64 *b, u64 *o);
 int launch_limb_automorph(secpe_ctx *ctx, const u64 *in, u64 *o, unsigned g);
+int launch_mdr_prep(secpe_ctx *ctx, const u64 *d, long long dis, long long dps, u64 *acc, int B, int lv);
+int launch_mdr_bconv(secpe_ctx *ctx, const u64 *acc, u64 *conv, int B, int lv);
+int launch_mdr_fin(secpe_ctx *ctx, const u64 *acc, const u64 *conv, const u64 *d, long long dis, long long dps,
+                   const CtB &o, int lv);

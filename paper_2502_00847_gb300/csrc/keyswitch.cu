@@ -15,9 +15,7 @@
 // q_i, NTT, (x_i - z_i) * q_l^-1.
 #include "eval.h"
 
-int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int lv, const u64 *key,
-              const CtB &out, bool acc0, bool acc1) {
-    if (B == 0) return SECPE_OK;
+int keyswitch_acc(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int lv, const u64 *key, DevBuf &acc) {
     const int n = ctx->n, k = ctx->npsp, alpha = ctx->alpha;
     const int nt = lv + 1 + k;
     KsDigits dg;
@@ -33,11 +31,14 @@ int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int 
         for (int t = 0; t < nt; t++) {
             if (t >= lo && t < hi) continue;
             if (tot >= SECPE_MAX_LIMBSET) return SECPE_EINVAL;
-            ext_ls.prime_of[tot++] = (int8_t)(t <= lv ? t : ctx->nq + (t - lv - 1));
+            ext_ls.prime_of[tot] = (int8_t)(t <= lv ? t : ctx->nq + (t - lv - 1));
+            ext_ls.aux[tot] = 0;
+            tot++;
         }
         dg.ndig++;
     }
     ctx->counters.keyswitches++;
+    SECPE_CHECK(acc.alloc(ctx, sizeof(u64) * (size_t)B * 2 * nt * n));
 
     // 1. INTT of d into dcoef [B][lv+1][N] (on the fused path the INTT also
     //    applies the ModUp pre-multiplier [Qhat_i^-1]_{q_i})
@@ -48,24 +49,12 @@ int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int 
     const bool fused = fused_path(ctx);
     SECPE_CHECK(ntt_limbset(ctx, dst, true, &src, fused ? ctx->dev.ninv_modup : nullptr, lv * ctx->nq));
 
-    if (fused) {
-        DevBuf ext, acc, tmp;
-        SECPE_CHECK(ext.alloc(ctx, sizeof(u64) * (size_t)B * tot * n));
-        SECPE_CHECK(acc.alloc(ctx, sizeof(u64) * (size_t)B * 2 * nt * n));
-        SECPE_CHECK(modup_ip_fused(ctx, d, d_item_stride, dcoef.u(), B, lv, dg, tot, key, ext.u(), acc.u()));
-        ext.release();
-        dcoef.release();
-        LimbSet pls = make_limbset(acc.u() + (size_t)(lv + 1) * n, B, 2ll * nt * n, 2, (long long)nt * n, k,
-                                   ctx->nq);
-        SECPE_CHECK(ntt_limbset(ctx, pls, true, nullptr, ctx->dev.ninv_moddown, 0));
-        SECPE_CHECK(tmp.alloc(ctx, sizeof(u64) * (size_t)B * 2 * (lv + 1) * n));
-        return moddown_fused(ctx, acc.u(), B, lv, out, acc0, acc1, tmp.u());
-    }
-
-    // 2. ModUp
     DevBuf ext;
-    const long long ext_stride = (long long)tot * n;
     SECPE_CHECK(ext.alloc(ctx, sizeof(u64) * (size_t)B * tot * n));
+    if (fused) return modup_ip_fused(ctx, d, d_item_stride, dcoef.u(), B, lv, dg, tot, key, ext.u(), acc.u());
+
+    // 2. ModUp: FastBConv per digit, NTT of the extended limbs
+    const long long ext_stride = (long long)tot * n;
     for (int j = 0; j < dg.ndig; j++) {
         const int ntgt = nt - (dg.hi[j] - dg.lo[j]);
         SECPE_CHECK(launch_modup_bconv(ctx, dcoef.u(), ext.u(), ext_stride, dg.off[j], B, lv, j, dg.lo[j],
@@ -78,24 +67,47 @@ int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int 
     ext_ls.poly_stride = 0;
     ext_ls.nlimb = tot;
     SECPE_CHECK(ntt_limbset(ctx, ext_ls, false));
-
     // 3. inner product -> acc [B][2][nt][N]
-    DevBuf acc;
-    SECPE_CHECK(acc.alloc(ctx, sizeof(u64) * (size_t)B * 2 * nt * n));
-    SECPE_CHECK(launch_ksk_ip(ctx, d, d_item_stride, ext.u(), ext_stride, dg, key, acc.u(), B, lv));
-    ext.release();
+    return launch_ksk_ip(ctx, d, d_item_stride, ext.u(), ext_stride, dg, key, acc.u(), B, lv);
+}
 
+int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int lv, const u64 *key,
+              const CtB &out, bool acc0, bool acc1) {
+    if (B == 0) return SECPE_OK;
+    const int n = ctx->n, k = ctx->npsp, nt = lv + 1 + k;
+    DevBuf acc, tmp;
+    SECPE_CHECK(keyswitch_acc(ctx, d, d_item_stride, B, lv, key, acc));
     // 4. ModDown
-    LimbSet pls = make_limbset(acc.u() + (size_t)(lv + 1) * n, B, 2ll * nt * n, 2, (long long)nt * n, k,
-                               ctx->nq);
+    LimbSet pls = make_limbset(acc.u() + (size_t)(lv + 1) * n, B, 2ll * nt * n, 2, (long long)nt * n, k, ctx->nq);
+    SECPE_CHECK(tmp.alloc(ctx, sizeof(u64) * (size_t)B * 2 * (lv + 1) * n));
+    if (fused_path(ctx)) {
+        SECPE_CHECK(ntt_limbset(ctx, pls, true, nullptr, ctx->dev.ninv_moddown, 0));
+        return moddown_fused(ctx, acc.u(), B, lv, out, acc0, acc1, tmp.u());
+    }
     SECPE_CHECK(ntt_limbset(ctx, pls, true));
-    DevBuf conv;
-    SECPE_CHECK(conv.alloc(ctx, sizeof(u64) * (size_t)B * 2 * (lv + 1) * n));
-    SECPE_CHECK(launch_moddown_bconv(ctx, acc.u(), conv.u(), B, lv));
-    LimbSet cls = make_limbset(conv.u(), B, 2ll * (lv + 1) * n, 2, (long long)(lv + 1) * n, lv + 1, 0);
+    SECPE_CHECK(launch_moddown_bconv(ctx, acc.u(), tmp.u(), B, lv));
+    LimbSet cls = make_limbset(tmp.u(), B, 2ll * (lv + 1) * n, 2, (long long)(lv + 1) * n, lv + 1, 0);
     SECPE_CHECK(ntt_limbset(ctx, cls, false));
-    SECPE_CHECK(launch_moddown_fin(ctx, acc.u(), conv.u(), out, lv, acc0, acc1));
-    return SECPE_OK;
+    return launch_moddown_fin(ctx, acc.u(), tmp.u(), out, lv, acc0, acc1);
+}
+
+int relin_rescale_batch(secpe_ctx *ctx, const u64 *d, int B, int lv, const u64 *key, const CtB &out) {
+    if (B == 0) return SECPE_OK;
+    const int n = ctx->n, k = ctx->npsp, nt = lv + 1 + k;
+    const long long dis = 3ll * (lv + 1) * n, dps = (long long)(lv + 1) * n;
+    DevBuf acc, tmp;
+    SECPE_CHECK(keyswitch_acc(ctx, d + 2 * dps, dis, B, lv, key, acc));
+    SECPE_CHECK(tmp.alloc(ctx, sizeof(u64) * (size_t)B * 2 * lv * n));
+    if (fused_path(ctx)) return moddown_rescale_fused(ctx, acc.u(), d, B, lv, out, tmp.u());
+    SECPE_CHECK(launch_mdr_prep(ctx, d, dis, dps, acc.u(), B, lv));
+    LimbSet src = make_limbset(acc.u() + (size_t)lv * n, B, 2ll * nt * n, 2, (long long)nt * n, k + 1, 0);
+    for (int p = 0; p < 2; p++)
+        for (int j = 0; j <= k; j++) src.prime_of[p * (k + 1) + j] = (int8_t)(j == 0 ? lv : ctx->nq + j - 1);
+    SECPE_CHECK(ntt_limbset(ctx, src, true));
+    SECPE_CHECK(launch_mdr_bconv(ctx, acc.u(), tmp.u(), B, lv));
+    LimbSet cls = make_limbset(tmp.u(), B, 2ll * lv * n, 2, (long long)lv * n, lv, 0);
+    SECPE_CHECK(ntt_limbset(ctx, cls, false));
+    return launch_mdr_fin(ctx, acc.u(), tmp.u(), d, dis, dps, out, lv);
 }
 
 int rescale_batch(secpe_ctx *ctx, const CtB &in, const CtB &out) {

@@ -96,6 +96,9 @@ struct EpiArgs {
     long long ois, ops;
     const ulonglong2 *w;  // w[target prime] Shoup pair
     int acc0, acc1;
+    const u64 *Y;         // optional: + Y * w2 (Y limb i at Y + item*yis + poly*yps + i*N)
+    long long yis, yps;
+    const ulonglong2 *w2;
 };
 
 __global__ void __launch_bounds__(256) k_rowpass_epi(const __grid_constant__ EpiArgs a) {
@@ -131,6 +134,18 @@ __global__ void __launch_bounds__(256) k_rowpass_epi(const __grid_constant__ Epi
     u64 *__restrict__ O = a.out + item * a.ois + poly * a.ops + (long long)j * a.c.n + (size_t)r0 * 256;
     const ulonglong2 w = a.w[tp];
     const bool acc = poly == 0 ? a.acc0 : a.acc1;
+    if (a.Y) {
+        const u64 *__restrict__ Y = a.Y + item * a.yis + poly * a.yps + (long long)j * a.c.n + (size_t)r0 * 256;
+        const ulonglong2 w2 = a.w2[tp];
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const int e = threadIdx.x + 256 * i;
+            const int r = e >> 8, p = e & 255;
+            const u64 v = sm[r * 272 + PADR(p)];
+            O[e] = add_mod(mul_shoup(sub_mod(X[e], v, q), w.x, w.y, q), mul_shoup(Y[e], w2.x, w2.y, q), q);
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 16; i++) {
         const int e = threadIdx.x + 256 * i;
@@ -234,6 +249,7 @@ int launch_colpass_bconv(secpe_ctx *ctx, const BConvArgs &a) {
         case 2: SECPE_LAUNCH(ctx, k_colpass_bconv<2>, grid, 256, 0, a); break;
         case 3: SECPE_LAUNCH(ctx, k_colpass_bconv<3>, grid, 256, 0, a); break;
         case 4: SECPE_LAUNCH(ctx, k_colpass_bconv<4>, grid, 256, 0, a); break;
+        case 5: SECPE_LAUNCH(ctx, k_colpass_bconv<5>, grid, 256, 0, a); break;
         case 8: SECPE_LAUNCH(ctx, k_colpass_bconv<8>, grid, 256, 0, a); break;
         default: SECPE_LAUNCH(ctx, k_colpass_bconv<0>, grid, 256, 0, a);
     }
@@ -320,9 +336,10 @@ int modup_ip_fused(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const 
     return SECPE_OK;
 }
 
-// out (+)= (X - NTT(FastBConv(src))) * w over limbs 0..nl-1 of B items x 2 polys.
+// out (+)= (X - NTT(FastBConv(src))) * w [+ Y * w2] over limbs 0..nl-1 of B items x 2 polys.
 int bconv_ntt_epi(secpe_ctx *ctx, const BConvSrc &S, int B, int nl, u64 *tmp, const u64 *X, long long xis,
-                  long long xps, const CtB &out, const ulonglong2 *w, bool acc0, bool acc1) {
+                  long long xps, const CtB &out, const ulonglong2 *w, bool acc0, bool acc1, const u64 *Y = nullptr,
+                  long long yis = 0, long long yps = 0, const ulonglong2 *w2 = nullptr) {
     const int n = ctx->n;
     BConvArgs a;
     a.c = ctx->dev;
@@ -342,6 +359,10 @@ int bconv_ntt_epi(secpe_ctx *ctx, const BConvSrc &S, int B, int nl, u64 *tmp, co
     ep.w = w;
     ep.acc0 = acc0 ? 1 : 0;
     ep.acc1 = acc1 ? 1 : 0;
+    ep.Y = Y;
+    ep.yis = yis;
+    ep.yps = yps;
+    ep.w2 = w2;
     const long long nlimbs = (long long)B * 2 * nl;
     KprofScope kp(ctx, "ntt16_rowpass_epi", 8.0 * n * nlimbs * (acc0 || acc1 ? 4.0 : 3.0));
     SECPE_LAUNCH(ctx, k_rowpass_epi, (unsigned)(nlimbs * 16), 256, 0, ep);
@@ -390,4 +411,33 @@ int rescale_fused(secpe_ctx *ctx, const CtB &in, const u64 *y, const CtB &out, u
     S.post = ctx->dev.rs_hmod + (size_t)lv * ctx->nq;
     return bconv_ntt_epi(ctx, S, in.B, lv, tmp, in.data, in.stride, in.pstride(), out,
                          ctx->dev.rs_qinv + (size_t)lv * ctx->nq, false, false);
+}
+
+// Relinearisation's ModDown fused with the rescale: acc [B][2][nt][N] from
+// the key inner product, d = the 3-component tensor [B][3][lv+1][N]; acc's
+// limbs lv..lv+k are the sources (q_l limb replaced by P d_l + acc_l, the
+// INTT applies the FastBConv pre-multipliers); out at level lv-1.
+int moddown_rescale_fused(secpe_ctx *ctx, u64 *acc, const u64 *d, int B, int lv, const CtB &out, u64 *tmp) {
+    const int n = ctx->n, nt = lv + 1 + ctx->npsp, k = ctx->npsp, ks = k + 1;
+    const long long dis = 3ll * (lv + 1) * n, dps = (long long)(lv + 1) * n;
+    SECPE_CHECK(launch_mdr_prep(ctx, d, dis, dps, acc, B, lv));
+    LimbSet src = make_limbset(acc + (size_t)lv * n, B, 2ll * nt * n, 2, (long long)nt * n, ks, 0);
+    for (int p = 0; p < 2; p++)
+        for (int j = 0; j < ks; j++) src.prime_of[p * ks + j] = (int8_t)(j == 0 ? lv : ctx->nq + j - 1);
+    SECPE_CHECK(ntt_limbset(ctx, src, true, nullptr, ctx->dev.mdr_ninv, lv * ks));
+    BConvSrc S;
+    S.base = acc + (size_t)lv * n;
+    S.is = 2ll * nt * n;
+    S.ps = (long long)nt * n;
+    S.nsrc = ks;
+    for (int j = 0; j < ks; j++) {
+        S.src_prime[j] = j == 0 ? lv : ctx->nq + j - 1;
+        S.pre[j] = ctx->h_mdr_pre_scaled[(size_t)lv * ks + j];
+    }
+    S.hat = ctx->dev.mdr_hat + (size_t)lv * ks * ctx->nq;
+    S.hat_stride = ctx->nq;
+    S.post = ctx->dev.mdr_post + (size_t)lv * ctx->nq;
+    return bconv_ntt_epi(ctx, S, B, lv, tmp, acc, 2ll * nt * n, (long long)nt * n, out,
+                         ctx->dev.mdr_w + (size_t)lv * ctx->nq, false, false, d, dis, dps,
+                         ctx->dev.rs_qinv + (size_t)lv * ctx->nq);
 }

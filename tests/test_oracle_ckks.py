@@ -225,3 +225,65 @@ def test_plainsim_argmax_exact_on_margins():
             full[: len(yp)] = yp
             z = plainsim.argmax_slots(full, C)[:C]
             assert int(np.argmax(z)) == int(np.argmax(y))
+
+
+def test_moddown_rescale_is_exact_division_definition(toy_oracle):
+    """Relinearisation's fused ModDown + rescale against its big-integer
+    definition: out = (x + h - FastBConv([x + h]_M)) / M, M = P q_l,
+    x = P d + acc (CRT value over Q_l P), FastBConv from the primes of M."""
+    o = toy_oracle
+    rng = np.random.default_rng(12)
+    lv = 4
+    P = o.ctx.P
+    ql = o.primes[lv]
+    M = P * ql
+    h = M // 2
+    q_idx = list(range(lv + 1))
+    tgt = q_idx + o.ctx.special_idx()
+    QP = P
+    for i in q_idx:
+        QP *= o.primes[i]
+    d_big = [int(rng.integers(0, 2**62)) ** 2 % (QP // P) for _ in range(o.n)]
+    a_big = [int(rng.integers(0, 2**62)) ** 3 % QP for _ in range(o.n)]
+    dk = np.empty((lv + 1, o.n), dtype=np.uint64)
+    for i in q_idx:
+        dk[i] = np.array([v % o.primes[i] for v in d_big], dtype=np.uint64)
+        o.ntt(dk[i], i)
+    acc = {}
+    for t in tgt:
+        limb = np.array([v % o.primes[t] for v in a_big], dtype=np.uint64)
+        o.ntt(limb, t)
+        acc[t] = limb
+    out = o.moddown_rescale(acc, dk, lv)
+    res = []
+    for i in range(lv):
+        x = out[i].copy()
+        o.intt(x, i)
+        res.append(x)
+    src = o.ctx.special_idx() + [lv]
+    Qo = QP // P // ql
+    for c in range(0, o.n, 61):
+        x = (P * d_big[c] + a_big[c]) % QP
+        conv = 0
+        for t in src:
+            s = o.primes[t]
+            mh = M // s
+            conv += ((x + h) % s) * pow(mh % s, -1, s) % s * mh
+        assert (x + h - conv) % M == 0
+        exact = (x + h - conv) // M
+        for i in range(lv):
+            assert int(res[i][c]) == exact % o.primes[i]
+        assert 0 <= exact < Qo * (P + 1)
+
+
+def test_lazy_relinearisation_counts(toy_oracle):
+    """5 relinearisations per degree-9 polynomial: 20 per Sign with (2, 2)."""
+    o = toy_oracle
+    x = o.encrypt(np.linspace(-0.4, 0.4, 8), seed=60)
+    o.reset_counters()
+    o.qseed, o.ridx = 3, 0
+    s = o.sign(x, 0)
+    assert o.counters["relins"] == 20 and s.level >= o.p.reserve
+    from oracle import plainsim
+    ref = plainsim.sign(np.linspace(-0.4, 0.4, 8))
+    assert np.max(np.abs(o.decrypt(s, 8) - ref)) < 2.0 ** -12
