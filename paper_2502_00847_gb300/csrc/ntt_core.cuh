@@ -93,3 +93,14 @@ static __device__ __forceinline__ u64 reduce4(u64 v, u64 q) {
 // [0, 2q) -> [0, q)
 static __device__ __forceinline__ u64 reduce2(u64 v, u64 q) { return v >= q ? v - q : v; }
 
+
+// Asks L2 to fetch the 128-byte line holding p (no register result).
+static __device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Prefetches a contiguous 32 KiB tile (16 rows of 256 words) to L2: 256
+// lines, one per thread of a 256-thread block.
+static __device__ __forceinline__ void prefetch_tile_l2(const u64 *tile) {
+    prefetch_l2(tile + 16 * threadIdx.x);
+}

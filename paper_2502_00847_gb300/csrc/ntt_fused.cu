@@ -42,7 +42,7 @@ struct BConvArgs {
 };
 
 template <int NS>
-__global__ void __launch_bounds__(256) k_colpass_bconv(const __grid_constant__ BConvArgs a) {
+__global__ void __launch_bounds__(256, 3) k_colpass_bconv(const __grid_constant__ BConvArgs a) {
     __shared__ u64 sm[4096];
     const long long lid = blockIdx.x >> 4;
     const int c0 = (blockIdx.x & 15) * 16;
@@ -117,6 +117,12 @@ __global__ void __launch_bounds__(256) k_rowpass_epi(const __grid_constant__ Epi
     const int base = 256 + r0 + row;
     u64 *__restrict__ srow = sm + row * 272;
     const ulonglong2 *tw = a.c.tw_fwd + (size_t)tp * a.c.n;
+    // the epilogue's operands are fetched to L2 while the tile is transformed
+    prefetch_tile_l2(a.X + item * a.xis + poly * a.xps + (long long)j * a.c.n + (size_t)r0 * 256);
+    if (a.Y)
+        prefetch_tile_l2(a.Y + item * a.yis + poly * a.yps + (long long)j * a.c.n + (size_t)r0 * 256);
+    else if (poly == 0 ? a.acc0 : a.acc1)
+        prefetch_tile_l2(a.out + item * a.ois + poly * a.ops + (long long)j * a.c.n + (size_t)r0 * 256);
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = g[row * 256 + ((k << 4) | u)];
@@ -191,6 +197,8 @@ __global__ void __launch_bounds__(256, 2) k_rowpass_ip(const __grid_constant__ I
     for (int jd = 0; jd < a.dg.ndig; jd++) {
         const int lo = a.dg.lo[jd], hi = a.dg.hi[jd];
         const u64 *kb = a.key + (long long)jd * 2 * kpoly + (long long)pt * a.c.n + tile_off;
+        prefetch_tile_l2(kb);
+        prefetch_tile_l2(kb + kpoly);
         if (t >= lo && t < hi) {
             const u64 *src = a.d + item * a.dis + (long long)t * a.c.n + tile_off;
 #pragma unroll
