@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--rates", default="50,200,500,1000,2000")
     ap.add_argument("--serve-queries", type=int, default=384, help="queries submitted per arrival rate")
     ap.add_argument("--budget-gb", type=float, default=120.0)
-    ap.add_argument("--micro-params", default="micro", choices=["micro", "argmax"],
+    ap.add_argument("--params", default="argmax", choices=["argmax", "argmax8"],
+                    help="Argmax parameter set: argmax (4 special primes, dnum=6) or argmax8 (8 special, dnum=3)")
+    ap.add_argument("--micro-params", default="micro", choices=["micro", "argmax", "argmax8"],
                     help="micro: 24+4 primes, dnum=3 (primitive config); argmax: the Argmax set (dnum=6)")
     return ap.parse_args()
 
@@ -225,13 +227,14 @@ def run_ours(args, world, rank, local):
     import numpy as np
     import torch
 
-    from oracle.params import ARGMAX
+    from oracle.params import PRESETS
     from paper_2502_00847_gb300 import build as pkg_build
     from paper_2502_00847_gb300 import secpe, workloads
 
     pkg_build.build()
     dev = torch.device("cuda", torch.cuda.current_device())
-    ctx = secpe.Context.from_params(ARGMAX)
+    P = PRESETS[args.params]
+    ctx = secpe.Context.from_params(P)
     keys = secpe.Keys(ctx, 1000 + rank, ROT_STEPS)
     n, cap = ctx.n, ctx.L + 1
     ct_words = 2 * cap * n
@@ -360,7 +363,7 @@ def run_ours(args, world, rank, local):
             "config": {"workload": "batched encrypted ensemble Argmax, N=2^16, %d queries per GPU, "
                                    "K~U{4,8,16}, C~U{2,3,4,6,14,64}, seed 4" % len(qs),
                        "queries_per_gpu": len(qs), "input_ciphertexts": n_cts,
-                       "params": "q0 60-bit + 23x50-bit, 4 special 60-bit, dnum=6, Delta=2^50",
+                       "params": "q0 60-bit + 23x50-bit, %d special 60-bit, dnum=%d, Delta=2^50" % (P.n_p, P.dnum),
                        "l2": "inputs (%.1f GB) larger than L2" % (n_cts * ct_words * 8 / 1e9),
                        "parallelism": "dp%d (independent queries per GPU)" % world},
             "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
@@ -378,14 +381,14 @@ def run_micro(args, rank):
     import numpy as np
     import torch
 
-    from oracle.params import ARGMAX, MICRO
+    from oracle.params import PRESETS
     from paper_2502_00847_gb300 import build as pkg_build
     from paper_2502_00847_gb300 import secpe
 
     pkg_build.build()
     ops = args.micro_ops.split(",")
     batches = [int(b) for b in args.micro_batch.split(",")]
-    P = MICRO if args.micro_params == "micro" else ARGMAX
+    P = PRESETS[args.micro_params]
     ctx = secpe.Context.from_params(P)
     rot = [1 << j for j in range(16)] if "rotate" in ops else []
     keys = secpe.Keys(ctx, 2, rot)
@@ -478,7 +481,7 @@ def run_micro(args, rank):
                                   "forward_ms_cuda_cores": t_cc, "forward_ms_tensor_pipe": t_tc}
     if rank == 0:
         desc = ("24x50-bit + 4x60-bit special primes, dnum=3" if args.micro_params == "micro" else
-                "q0 60-bit + 23x50-bit + 4x60-bit special primes, dnum=6")
+                "q0 60-bit + 23x50-bit + %dx60-bit special primes, dnum=%d" % (P.n_p, P.dnum))
         print(json.dumps({"mode": "micro", "config": {"workload": "primitive micro-benchmark N=2^16, %s, random "
                                                                   "residues seed 2" % desc},
                           "steps": args.steps, "warmup": args.warmup, "results": res}))

@@ -161,7 +161,12 @@ MICRO = Params(log_n=16, q0_bits=50, q_bits=50, n_q=24, p_bits=60, n_p=4,
                dnum=3, log_scale=50)
 ARGMAX = Params(log_n=16, q0_bits=60, q_bits=50, n_q=24, p_bits=60, n_p=4,
                 dnum=6, log_scale=50)
-PRESETS = {"toy": TOY, "micro": MICRO, "argmax": ARGMAX}
+# ARGMAX8: the same ciphertext primes with 8 special primes and dnum = 3
+# (alpha = 8 = n_p, P > every digit; log2(QP) = 1690 <= 1763, the paper's
+# 128-bit budget at N = 2^16): half the extended limbs of ARGMAX's ModUp.
+ARGMAX8 = Params(log_n=16, q0_bits=60, q_bits=50, n_q=24, p_bits=60, n_p=8,
+                 dnum=3, log_scale=50)
+PRESETS = {"toy": TOY, "micro": MICRO, "argmax": ARGMAX, "argmax8": ARGMAX8}
 
 
 class Context:

@@ -157,3 +157,34 @@ def test_tensor_pipe_ntt_bit_identical(env):
     secpe.ntt_cts(ctx, c, B, 2 * cap * ctx.n, cap, ctx.L)
     secpe.ntt_cts_tc(ctx, d, B, 2 * cap * ctx.n, cap, ctx.L)
     assert torch.equal(c, d)
+
+
+def test_argmax8_parameter_set_bit_exact():
+    """8 special primes, dnum = 3: HMult, rotation and a two-query batched
+    Argmax, bit-exact / decoded against the oracle and the plaintext argmax."""
+    from oracle import ARGMAX8
+    from paper_2502_00847_gb300 import secpe
+    o = Oracle(ARGMAX8)
+    o.keygen(808, rot_steps=[1, -4])
+    ctx = secpe.Context.from_params(ARGMAX8)
+    keys = secpe.Keys(ctx, 808, [1, -4])
+    assert ctx.primes() == o.primes
+    rng = np.random.default_rng(88)
+    a_o = o.encrypt(rng.uniform(-1, 1, 8), seed=5)
+    b_o = o.drop(o.encrypt(rng.uniform(-1, 1, 8), seed=6), 17)
+    a, b = to_gpu(secpe, ctx, a_o), to_gpu(secpe, ctx, b_o)
+    same(secpe.mul_relin(ctx, keys, a, b), o.mul(a_o, b_o))
+    same(secpe.rotate(ctx, keys, b, -4), o.rotate(b_o, -4))
+    qs = workloads.argmax_queries(2, seed=8, K_choices=(4,), C_choices=(2, 4))
+    rot = sorted({-(1 << (q.C - 1).bit_length()) for q in qs} | {1, 2})
+    k2 = secpe.Keys(ctx, 5, rot)
+    batch = []
+    for q in qs:
+        cts = [secpe.encrypt_logits(ctx, k2, q.logits[i], q.d_min, q.enc_seeds[i]) for i in range(q.K)]
+        batch.append(dict(cts=cts, C=q.C, d_min=q.d_min, d_max=q.d_max, qseed=q.qseed, z_out=ctx.new_ct()))
+    secpe.argmax_batch(ctx, k2, batch)
+    for q, b in zip(qs, batch):
+        zd = secpe.decrypt(ctx, k2, b["z_out"], q.C)
+        zp = plainsim.ensemble_argmax(q.logits, q.d_min, q.d_max, ctx.n // 2)
+        assert np.max(np.abs(zd - zp)) < 2.0 ** -12
+        assert int(np.argmax(zd)) == int(np.argmax(q.logits.mean(0)))
