@@ -125,6 +125,14 @@ int secpe_encrypt(secpe_ctx *ctx, const secpe_keys *keys, const double *v, int n
  * beyond. */
 int secpe_encrypt_logits(secpe_ctx *ctx, const secpe_keys *keys, const double *v, int C,
                          double d_min, uint64_t seed, secpe_ct *out, void *stream);
+/* Seeded ciphertexts: c1 of a fresh encryption is the uniform polynomial
+ * drawn from the stream of its encryption seed, so a client can send c0 and
+ * the 8-byte seed only.  This regenerates c1 (limbs 0..level) on the device
+ * for `batch` ciphertexts at base + i*ct_stride words ([2][cap][N] each),
+ * seeds[i] being ciphertext i's encryption seed; the result is bit-identical
+ * to the ciphertext secpe_encrypt* produced. */
+int secpe_expand_seeded(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, int cap, int level,
+                        const uint64_t *seeds, void *stream);
 /* Decrypts and decodes slots 0..n-1 to host doubles.  Synchronous. */
 int secpe_decrypt(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *ct, double *v_out,
                   int n, void *stream);

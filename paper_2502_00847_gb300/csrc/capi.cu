@@ -641,3 +641,22 @@ extern "C" int secpe_ntt_cts_tc(secpe_ctx *ctx, uint64_t *base, int batch, size_
     LimbSet ls = make_limbset((u64 *)base, batch, (long long)ct_stride, 2, (long long)cap * ctx->n, level + 1, 0);
     return finish(ctx, ntt_limbset_tc(ctx, ls, inverse != 0));
 }
+
+extern "C" int secpe_expand_seeded(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, int cap, int level,
+                                   const uint64_t *seeds, void *stream) {
+    if (!ctx || !base || !seeds || batch < 0 || level < 0 || level > ctx->L || cap < level + 1 ||
+        ct_stride < 2ull * cap * ctx->n)
+        return SECPE_EINVAL;
+    CallScope cs(ctx, stream);
+    PrimeList pl;
+    pl.n = level + 1;
+    for (int i = 0; i <= level; i++) pl.p[i] = i;
+    for (int s0 = 0; s0 < batch; s0 += SECPE_MAX_BATCH_CONST) {
+        const int c = std::min(SECPE_MAX_BATCH_CONST, batch - s0);
+        std::vector<u64> keys(c);
+        for (int i = 0; i < c; i++) keys[i] = hm::sm_stream(seeds[s0 + i], DOM_ENC_A, 0);
+        u64 *c1 = (u64 *)base + (size_t)s0 * ct_stride + (size_t)cap * ctx->n;
+        SECPE_CHECK(launch_sample_uniform(ctx, keys, c1, (long long)ct_stride, pl));
+    }
+    return finish(ctx, SECPE_OK);
+}

@@ -26,7 +26,7 @@ EXPORTS = [
     "secpe_keyswitch_batch", "secpe_mul_relin_batch", "secpe_rotate_batch", "secpe_rescale_batch",
     "secpe_rescale_noalloc", "secpe_server_create", "secpe_server_destroy", "secpe_server_submit",
     "secpe_server_cancel", "secpe_server_step", "secpe_server_poll", "secpe_server_wait", "secpe_server_forget",
-    "secpe_server_stats", "secpe_ntt_tc", "secpe_ntt_cts_tc",
+    "secpe_server_stats", "secpe_ntt_tc", "secpe_ntt_cts_tc", "secpe_expand_seeded",
 ]
 
 
@@ -132,6 +132,7 @@ def lib():
         "secpe_server_stats": (i32, [vp, P(ServerStatsC)]),
         "secpe_ntt_tc": (i32, [vp, vp, P(i32), i32, i32, vp]),
         "secpe_ntt_cts_tc": (i32, [vp, vp, i32, ctypes.c_size_t, i32, i32, i32, vp]),
+        "secpe_expand_seeded": (i32, [vp, vp, i32, ctypes.c_size_t, i32, i32, P(u64), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -332,6 +333,14 @@ def encrypt_logits(ctx, keys, v, d_min, seed, out=None):
            "secpe_encrypt_logits")
     out.update(c)
     return out
+
+
+def expand_seeded(ctx, cts_tensor, level, seeds):
+    """Regenerate c1 of `cts_tensor` ([batch][2][cap][N]) from the encryption seeds."""
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+    batch, cap, n = int(cts_tensor.shape[0]), int(cts_tensor.shape[2]), int(cts_tensor.shape[3])
+    _check(lib().secpe_expand_seeded(ctx.h, ctypes.c_void_p(cts_tensor.data_ptr()), batch, 2 * cap * n, cap, level,
+                                     _u64p(seeds), _stream()), "secpe_expand_seeded")
 
 
 def decrypt(ctx, keys, ct, n):

@@ -222,3 +222,18 @@ def test_error_paths(env):
         secpe.add(ctx, ct, other)
     assert e.value.code == -4
     assert ctx.stream_status() == 0
+
+
+def test_seeded_ciphertext_expansion(env):
+    import torch
+    o, ctx, keys, secpe = env
+    rng = np.random.default_rng(9)
+    cts = torch.zeros((3, 2, ctx.L + 1, ctx.n), dtype=torch.int64, device="cuda")
+    seeds = [901, 902, 903]
+    for i in range(3):
+        secpe.encrypt_logits(ctx, keys, rng.uniform(-1, 1, 3), -1.0, seeds[i],
+                             out=secpe.Ciphertext(cts[i], 0, ctx.scale))
+    ref = cts.clone()
+    cts[:, 1] = 0
+    secpe.expand_seeded(ctx, cts, ctx.L, seeds)
+    assert torch.equal(cts, ref)
