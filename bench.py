@@ -135,14 +135,22 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(world, x):
+def max_over_ranks(world, x, device="cuda"):
+    """Max of a per-rank scalar (timing): the only collective, off the data path."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_queries(n_queries, rank, c_choices=(2, 3, 4, 6, 14, 64)):
+    """Each rank serves its own independent query mix (weak scaling: the work
+    per GPU is fixed as ranks are added; no data crosses ranks)."""
+    from paper_2502_00847_gb300 import workloads
+    return workloads.argmax_queries(n_queries, seed=4 + 1000 * rank, C_choices=tuple(c_choices))
 
 
 def hbm_peak():
@@ -240,7 +248,7 @@ def run_ours(args, world, rank, local):
     ct_words = 2 * cap * n
 
     c_choices = tuple(int(c) for c in args.classes.split(","))
-    qs = workloads.argmax_queries(args.queries, seed=4 + 1000 * rank, C_choices=c_choices)
+    qs = rank_queries(args.queries, rank, c_choices)
     n_cts = sum(q.K for q in qs)
     # inputs: one big device tensor of ciphertexts, encrypted on the device
     inputs = torch.empty((n_cts, 2, cap, n), dtype=torch.int64, device=dev)

@@ -1,0 +1,58 @@
+"""The multi-GPU path shards independent queries across ranks (weak
+scaling, no collective on the data path): with two gloo ranks on the CPU,
+each rank gets its own query mix, the barrier works and the step time is the
+max over ranks; the oracle reference arm runs on rank 0 only."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    qs = bench.rank_queries(8, rank)
+    sig = [(q.K, q.C, round(float(q.logits[0, 0]), 6)) for q in qs]
+    bench.barrier(world)
+    t = bench.max_over_ranks(world, 10.0 + rank, device="cpu")
+    out[rank] = (sig, t)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_shard_queries_and_take_max_time():
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
+        r0, r1 = out[0], out[1]
+    assert r0[0] != r1[0], "ranks must get different query mixes"
+    assert r0[1] == r1[1] == 11.0
+
+
+def test_reference_arm_prints_on_rank0_only(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class A:
+        queries, steps, warmup, gpus = 4, 1, 0, 2
+    called = []
+    monkeypatch.setattr(bench, "oracle_sample", lambda seconds_budget=0: called.append(1) or (1.0, 1.0, 0.0))
+    bench.run_reference(A, 2, 1)
+    assert capsys.readouterr().out == "" and not called
+    bench.run_reference(A, 2, 0)
+    line = capsys.readouterr().out.strip()
+    assert '"impl": "reference"' in line and called
