@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--kprof", default="ntt16",
                     help="kernel class timed live for the roofline")
+    ap.add_argument("--breakdown", action="store_true",
+                    help="after the timed steps, one more step with every launch timed by kernel name")
     ap.add_argument("--micro", action="store_true",
                     help="primitive micro-benchmark (N=2^16, 24+4 primes, dnum=3) instead of the Argmax step")
     ap.add_argument("--micro-ops", default="ntt,keyswitch,hmult,rescale,rotate")
@@ -298,6 +300,21 @@ def run_ours(args, world, rank, local):
     ms_per_step = ms / args.steps
     value = world * len(qs) * args.steps / (ms / 1e3)
 
+    # per-kernel breakdown of one extra step (not part of the timed region)
+    breakdown = None
+    if args.breakdown:
+        ctx.kprof_begin("*", max_launches=1 << 20)
+        bev0, bev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        bev0.record()
+        step()
+        bev1.record()
+        ctx.kprof_end()
+        step_ms = bev0.elapsed_time(bev1)
+        rows = ctx.kprof_report()
+        breakdown = {"step_ms": step_ms, "kernel_ms": sum(r[2] for r in rows),
+                     "kernels": [{"kernel": r[0], "launches": r[1], "ms": r[2], "share": r[2] / step_ms}
+                                 for r in rows]}
+
     # plain path: the same kernels, one query per call, sequentially
     plain = None
     if args.plain_queries > 0 and rank == 0:
@@ -381,6 +398,7 @@ def run_ours(args, world, rank, local):
                        "parallelism": "dp%d (independent queries per GPU)" % world},
             "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk, "gpu_launches": cnt["launches"],
+            **({"breakdown": breakdown} if breakdown else {}),
             "per_step_ops": {k: cnt[k] / args.steps for k in ("rotations", "signs", "relins", "refreshes",
                                                                "keyswitches")},
         }

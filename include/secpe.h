@@ -316,6 +316,13 @@ typedef struct {
 int secpe_kprof_begin(secpe_ctx *ctx, const char *name_filter, int max_launches);
 /* Synchronises the device, sums the recorded durations, stops recording. */
 int secpe_kprof_end(secpe_ctx *ctx, secpe_kprof *out);
+/* With name_filter "*", every launch is recorded under its kernel's name
+ * (and no operation-level range is).  After secpe_kprof_end, writes one
+ * line per kernel, "name<TAB>launches<TAB>total ms", sorted by time, into
+ * buf (host, len bytes, truncated and NUL-terminated; len may be 0 with buf
+ * null) and the full text's size + 1 into *needed.  SECPE_EINVAL while the
+ * profiler is still recording. */
+int secpe_kprof_report(const secpe_ctx *ctx, char *buf, size_t len, size_t *needed);
 
 #ifdef __cplusplus
 }

@@ -1,6 +1,9 @@
 // extern "C" entry points declared in include/secpe.h.
 #include <cmath>
 #include <cstring>
+#include <algorithm>
+#include <map>
+#include <string>
 
 #include "eval.h"
 
@@ -512,6 +515,7 @@ extern "C" int secpe_kprof_begin(secpe_ctx *ctx, const char *name_filter, int ma
         k.ev.push_back(e);
     }
     k.filter = name_filter;
+    k.all = k.filter == "*";
     k.used = 0;
     k.launches = 0;
     k.bytes = 0.0;
@@ -525,14 +529,45 @@ extern "C" int secpe_kprof_end(secpe_ctx *ctx, secpe_kprof *out) {
     k.active = false;
     SECPE_CUDA(cudaDeviceSynchronize());
     double ms = 0.0;
+    k.ms.assign(k.used, 0.f);
     for (int i = 0; i < k.used; i++) {
         float t = 0.f;
         SECPE_CUDA(cudaEventElapsedTime(&t, k.ev[2 * i], k.ev[2 * i + 1]));
+        k.ms[i] = t;
         ms += t;
     }
     out->launches = k.used;
     out->total_ms = ms;
     out->bytes = k.bytes;
+    return SECPE_OK;
+}
+
+extern "C" int secpe_kprof_report(const secpe_ctx *ctx, char *buf, size_t len, size_t *needed) {
+    if (!ctx || (!buf && len) || !needed) return SECPE_EINVAL;
+    const KProf &k = ctx->kprof;
+    if (k.active) return SECPE_EINVAL;
+    std::map<std::string, std::pair<int64_t, double>> agg;
+    for (int i = 0; i < (int)k.ms.size() && i < (int)k.names.size(); i++) {
+        if (!k.names[i]) continue;
+        auto &a = agg[k.names[i]];
+        a.first++;
+        a.second += k.ms[i];
+    }
+    std::vector<std::pair<double, std::string>> rows;
+    for (auto &kv : agg) {
+        char line[512];
+        snprintf(line, sizeof line, "%s\t%lld\t%.6f\n", kv.first.c_str(), (long long)kv.second.first, kv.second.second);
+        rows.push_back({kv.second.second, line});
+    }
+    std::sort(rows.begin(), rows.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::string text;
+    for (auto &r : rows) text += r.second;
+    *needed = text.size() + 1;
+    if (len) {
+        const size_t m = std::min(len - 1, text.size());
+        memcpy(buf, text.data(), m);
+        buf[m] = 0;
+    }
     return SECPE_OK;
 }
 

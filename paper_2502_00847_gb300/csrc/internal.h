@@ -91,8 +91,11 @@ struct CtB {
 // event-based timing of selected kernel launches (secpe_kprof_*)
 struct KProf {
     bool active = false;
+    bool all = false;             // filter "*": every launch, by kernel name
     std::string filter;
     std::vector<cudaEvent_t> ev;  // pairs
+    std::vector<const char *> names;  // kernel name of pair i (filter "*")
+    std::vector<float> ms;        // duration of pair i, filled by secpe_kprof_end
     int used = 0;                 // pairs recorded
     int64_t launches = 0;
     double bytes = 0.0;

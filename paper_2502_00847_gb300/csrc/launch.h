@@ -2,9 +2,29 @@
 #pragma once
 #include "internal.h"
 
+// Records a CUDA event pair around one launch, under the kernel's name, when
+// the context's kernel profiler runs with the filter "*".
+struct KprofLaunch {
+    secpe_ctx *ctx;
+    int idx = -1;
+    KprofLaunch(secpe_ctx *c, const char *name) : ctx(c) {
+        KProf &k = c->kprof;
+        if (!k.active || !k.all || 2 * (k.used + 1) > (int)k.ev.size()) return;
+        idx = k.used++;
+        k.launches++;
+        if ((int)k.names.size() <= idx) k.names.resize(idx + 1);
+        k.names[idx] = name;
+        cudaEventRecord(k.ev[2 * idx], c->stream);
+    }
+    ~KprofLaunch() {
+        if (idx >= 0) cudaEventRecord(ctx->kprof.ev[2 * idx + 1], ctx->stream);
+    }
+};
+
 // Launch on ctx->stream, count it, and turn a launch error into SECPE_ECUDA.
 #define SECPE_LAUNCH(ctx, kernel, grid, block, smem, ...)                               \
     do {                                                                                  \
+        KprofLaunch _kpl((ctx), #kernel);                                                 \
         kernel<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);                  \
         (ctx)->counters.launches++;                                                       \
         cudaError_t _e = cudaGetLastError();                                              \
@@ -29,7 +49,7 @@ struct KprofScope {
     int idx = -1;
     KprofScope(secpe_ctx *c, const char *name, double bytes) : ctx(c) {
         KProf &k = c->kprof;
-        if (!k.active || std::string(name).find(k.filter) == std::string::npos) return;
+        if (!k.active || k.all || std::string(name).find(k.filter) == std::string::npos) return;
         if (2 * (k.used + 1) > (int)k.ev.size()) return;
         idx = k.used++;
         k.launches++;

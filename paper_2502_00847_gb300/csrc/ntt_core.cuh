@@ -104,3 +104,46 @@ static __device__ __forceinline__ void prefetch_l2(const void *p) {
 static __device__ __forceinline__ void prefetch_tile_l2(const u64 *tile) {
     prefetch_l2(tile + 16 * threadIdx.x);
 }
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, cp.async.bulk) from global to shared memory,
+// completed on a shared-memory mbarrier.  Every wait is bounded: a wait that
+// gives up records SECPE_ETIMEOUT in the context's status word.
+#define SECPE_WAIT_LIMIT (1L << 22)
+
+static __device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+static __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Arms the barrier for `bytes` of incoming copies (one arrival).
+static __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// Copies `bytes` (a multiple of 16; both addresses 16-byte aligned).
+static __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+static __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for phase `parity` of the barrier; false after SECPE_WAIT_LIMIT polls.
+static __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (long i = 0; i < SECPE_WAIT_LIMIT; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}

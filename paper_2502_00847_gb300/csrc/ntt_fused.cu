@@ -101,8 +101,16 @@ struct EpiArgs {
     const ulonglong2 *w2;
 };
 
-__global__ void __launch_bounds__(256) k_rowpass_epi(const __grid_constant__ EpiArgs a) {
-    __shared__ u64 sm[16 * 272];
+// Dynamic shared memory: the padded transform tile (16 x 272 words), the
+// X tile (4096 words, fetched by one bulk copy while the tile is
+// transformed) and the copy's mbarrier.
+constexpr int EPI_SMEM = (16 * 272 + 4096) * 8 + 16;
+
+__global__ void __launch_bounds__(256, 3) k_rowpass_epi(const __grid_constant__ EpiArgs a) {
+    extern __shared__ __align__(16) u64 dsm[];
+    u64 *sm = dsm;
+    u64 *xs = dsm + 16 * 272;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(xs + 4096);
     const long long lid = blockIdx.x >> 4;
     const int r0 = (blockIdx.x & 15) * 16;
     const int j = (int)(lid % a.ls.nlimb);
@@ -117,8 +125,15 @@ __global__ void __launch_bounds__(256) k_rowpass_epi(const __grid_constant__ Epi
     const int base = 256 + r0 + row;
     u64 *__restrict__ srow = sm + row * 272;
     const ulonglong2 *tw = a.c.tw_fwd + (size_t)tp * a.c.n;
-    // the epilogue's operands are fetched to L2 while the tile is transformed
-    prefetch_tile_l2(a.X + item * a.xis + poly * a.xps + (long long)j * a.c.n + (size_t)r0 * 256);
+    const u64 *__restrict__ X = a.X + item * a.xis + poly * a.xps + (long long)j * a.c.n + (size_t)r0 * 256;
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    // the X tile (32 KiB, contiguous) streams into shared memory while the
+    // tile is transformed; the other epilogue operand is fetched to L2
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, 4096 * 8);
+        bulk_g2s(xs, X, 4096 * 8, bar);
+    }
     if (a.Y)
         prefetch_tile_l2(a.Y + item * a.yis + poly * a.yps + (long long)j * a.c.n + (size_t)r0 * 256);
     else if (poly == 0 ? a.acc0 : a.acc1)
@@ -136,7 +151,11 @@ __global__ void __launch_bounds__(256) k_rowpass_epi(const __grid_constant__ Epi
 #pragma unroll
     for (int k = 0; k < 16; k++) srow[PADR((u << 4) | k)] = reduce4(x[k], q);
     __syncthreads();
-    const u64 *__restrict__ X = a.X + item * a.xis + poly * a.xps + (long long)j * a.c.n + (size_t)r0 * 256;
+    if (!mbar_wait(bar, 0)) {
+        if (threadIdx.x == 0) atomicCAS(a.c.status, 0, SECPE_ETIMEOUT);
+        mbar_wait(bar, 0);  // the copy may still be landing in this CTA's shared memory
+        return;
+    }
     u64 *__restrict__ O = a.out + item * a.ois + poly * a.ops + (long long)j * a.c.n + (size_t)r0 * 256;
     const ulonglong2 w = a.w[tp];
     const bool acc = poly == 0 ? a.acc0 : a.acc1;
@@ -148,7 +167,7 @@ __global__ void __launch_bounds__(256) k_rowpass_epi(const __grid_constant__ Epi
             const int e = threadIdx.x + 256 * i;
             const int r = e >> 8, p = e & 255;
             const u64 v = sm[r * 272 + PADR(p)];
-            O[e] = add_mod(mul_shoup(sub_mod(X[e], v, q), w.x, w.y, q), mul_shoup(Y[e], w2.x, w2.y, q), q);
+            O[e] = add_mod(mul_shoup(sub_mod(xs[e], v, q), w.x, w.y, q), mul_shoup(Y[e], w2.x, w2.y, q), q);
         }
         return;
     }
@@ -157,7 +176,7 @@ __global__ void __launch_bounds__(256) k_rowpass_epi(const __grid_constant__ Epi
         const int e = threadIdx.x + 256 * i;
         const int r = e >> 8, p = e & 255;
         const u64 v = sm[r * 272 + PADR(p)];
-        u64 res = mul_shoup(sub_mod(X[e], v, q), w.x, w.y, q);
+        u64 res = mul_shoup(sub_mod(xs[e], v, q), w.x, w.y, q);
         if (acc) res = add_mod(res, O[e], q);
         O[e] = res;
     }
@@ -175,8 +194,12 @@ struct IpArgs {
     int lv, nitem;
 };
 
-// grid: ((t * 16 + tile) * nitem + item): the items sharing a key tile run back to back
-__global__ void __launch_bounds__(256, 2) k_rowpass_ip(const __grid_constant__ IpArgs a) {
+// grid: ((t * 16 + tile) * nitem + item): the items sharing a key tile run back to back.
+// The two accumulators live in the output tile itself (the first digit
+// writes it, later digits read, add and write it back): the CTA touches its
+// 64 KiB of output repeatedly within its lifetime, so it stays in L2, and the
+// registers stay free for the transform (3 CTAs per SM, no spills).
+__global__ void __launch_bounds__(256, 3) k_rowpass_ip(const __grid_constant__ IpArgs a) {
     __shared__ u64 sm[16 * 272];
     const int nt = a.lv + 1 + a.c.np_special;
     const int item = blockIdx.x % a.nitem;
@@ -191,24 +214,15 @@ __global__ void __launch_bounds__(256, 2) k_rowpass_ip(const __grid_constant__ I
     const ulonglong2 *tw = a.c.tw_fwd + (size_t)pt * a.c.n;
     const long long kpoly = (long long)a.c.nprimes * a.c.n;
     const long long tile_off = (long long)r0 * 256;
-    u64 acc0[16], acc1[16];
-#pragma unroll
-    for (int i = 0; i < 16; i++) acc0[i] = acc1[i] = 0;
+    u64 *__restrict__ o0 = a.acc + (long long)item * 2 * nt * a.c.n + (long long)t * a.c.n + tile_off;
+    u64 *__restrict__ o1 = o0 + (long long)nt * a.c.n;
     for (int jd = 0; jd < a.dg.ndig; jd++) {
         const int lo = a.dg.lo[jd], hi = a.dg.hi[jd];
         const u64 *kb = a.key + (long long)jd * 2 * kpoly + (long long)pt * a.c.n + tile_off;
         prefetch_tile_l2(kb);
         prefetch_tile_l2(kb + kpoly);
-        if (t >= lo && t < hi) {
-            const u64 *src = a.d + item * a.dis + (long long)t * a.c.n + tile_off;
-#pragma unroll
-            for (int i = 0; i < 16; i++) {
-                const int e = threadIdx.x + 256 * i;
-                const u64 v = src[e];
-                acc0[i] = add_mod(acc0[i], redc(mulhi64(v, kb[e]), v * kb[e], q, qinv), q);
-                acc1[i] = add_mod(acc1[i], redc(mulhi64(v, kb[kpoly + e]), v * kb[kpoly + e], q, qinv), q);
-            }
-        } else {
+        const bool own = t >= lo && t < hi;
+        if (!own) {
             const int ti = t < lo ? t : t - (hi - lo);
             const u64 *g = a.ext + item * a.eis + (long long)(a.dg.off[jd] + ti) * a.c.n + tile_off;
             u64 x[16];
@@ -224,23 +238,23 @@ __global__ void __launch_bounds__(256, 2) k_rowpass_ip(const __grid_constant__ I
 #pragma unroll
             for (int k = 0; k < 16; k++) srow[PADR((u << 4) | k)] = reduce4(x[k], q);
             __syncthreads();
-#pragma unroll
-            for (int i = 0; i < 16; i++) {
-                const int e = threadIdx.x + 256 * i;
-                const int r = e >> 8, p = e & 255;
-                const u64 v = sm[r * 272 + PADR(p)];
-                acc0[i] = add_mod(acc0[i], redc(mulhi64(v, kb[e]), v * kb[e], q, qinv), q);
-                acc1[i] = add_mod(acc1[i], redc(mulhi64(v, kb[kpoly + e]), v * kb[kpoly + e], q, qinv), q);
-            }
-            __syncthreads();
         }
-    }
-    u64 *o = a.acc + (long long)item * 2 * nt * a.c.n + (long long)t * a.c.n + tile_off;
-#pragma unroll
-    for (int i = 0; i < 16; i++) {
-        const int e = threadIdx.x + 256 * i;
-        o[e] = acc0[i];
-        o[(long long)nt * a.c.n + e] = acc1[i];
+        const u64 *src = a.d + item * a.dis + (long long)t * a.c.n + tile_off;
+#pragma unroll 4
+        for (int i = 0; i < 16; i++) {
+            const int e = threadIdx.x + 256 * i;
+            const u64 v = own ? src[e] : sm[(e >> 8) * 272 + PADR(e & 255)];
+            const u64 k0 = kb[e], k1 = kb[kpoly + e];
+            u64 p0 = redc(mulhi64(v, k0), v * k0, q, qinv);
+            u64 p1 = redc(mulhi64(v, k1), v * k1, q, qinv);
+            if (jd) {
+                p0 = add_mod(p0, o0[e], q);
+                p1 = add_mod(p1, o1[e], q);
+            }
+            o0[e] = p0;
+            o1[e] = p1;
+        }
+        if (!own) __syncthreads();
     }
 }
 
@@ -373,7 +387,17 @@ int bconv_ntt_epi(secpe_ctx *ctx, const BConvSrc &S, int B, int nl, u64 *tmp, co
     ep.w2 = w2;
     const long long nlimbs = (long long)B * 2 * nl;
     KprofScope kp(ctx, "ntt16_rowpass_epi", 8.0 * n * nlimbs * (acc0 || acc1 ? 4.0 : 3.0));
-    SECPE_LAUNCH(ctx, k_rowpass_epi, (unsigned)(nlimbs * 16), 256, 0, ep);
+    // the bulk copy of the X tile needs 16-byte aligned tiles
+    if (((uintptr_t)X & 15) || (xis & 1) || (xps & 1)) return SECPE_EINVAL;
+    static bool attr_set[64];
+    int dev = 0;
+    SECPE_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return SECPE_ECUDA;
+    if (!attr_set[dev]) {
+        SECPE_CUDA(cudaFuncSetAttribute(k_rowpass_epi, cudaFuncAttributeMaxDynamicSharedMemorySize, EPI_SMEM));
+        attr_set[dev] = true;
+    }
+    SECPE_LAUNCH(ctx, k_rowpass_epi, (unsigned)(nlimbs * 16), 256, EPI_SMEM, ep);
     return SECPE_OK;
 }
 

@@ -22,7 +22,7 @@ EXPORTS = [
     "secpe_ntt_cts", "secpe_add", "secpe_sub", "secpe_mul_const", "secpe_add_const", "secpe_mul_relin",
     "secpe_rescale", "secpe_rotate", "secpe_keyswitch", "secpe_refresh_testonly", "secpe_sign", "secpe_max",
     "secpe_ensemble_aggregate", "secpe_encrypted_argmax", "secpe_argmax_batch", "secpe_get_counters",
-    "secpe_reset_counters", "secpe_select_primes", "secpe_kprof_begin", "secpe_kprof_end",
+    "secpe_reset_counters", "secpe_select_primes", "secpe_kprof_begin", "secpe_kprof_end", "secpe_kprof_report",
     "secpe_keyswitch_batch", "secpe_mul_relin_batch", "secpe_rotate_batch", "secpe_rescale_batch",
     "secpe_rescale_noalloc", "secpe_server_create", "secpe_server_destroy", "secpe_server_submit",
     "secpe_server_cancel", "secpe_server_step", "secpe_server_poll", "secpe_server_wait", "secpe_server_forget",
@@ -116,6 +116,7 @@ def lib():
         "secpe_select_primes": (i32, [P(ParamsC), P(u64), i32]),
         "secpe_kprof_begin": (i32, [vp, ctypes.c_char_p, i32]),
         "secpe_kprof_end": (i32, [vp, P(KprofC)]),
+        "secpe_kprof_report": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)]),
         "secpe_keyswitch_batch": (i32, [vp, vp, i32, P(CtBatchC), P(CtBatchC), vp]),
         "secpe_mul_relin_batch": (i32, [vp, vp, P(CtBatchC), P(CtBatchC), P(CtBatchC), vp]),
         "secpe_rotate_batch": (i32, [vp, vp, P(CtBatchC), i32, P(CtBatchC), vp]),
@@ -224,6 +225,18 @@ class Context:
         k = KprofC()
         _check(lib().secpe_kprof_end(self.h, ctypes.byref(k)), "secpe_kprof_end")
         return dict(launches=int(k.launches), total_ms=float(k.total_ms), bytes=float(k.bytes))
+
+    def kprof_report(self):
+        """Per-kernel (name, launches, ms) of the last kprof_begin("*") .. kprof_end range."""
+        need = ctypes.c_size_t()
+        _check(lib().secpe_kprof_report(self.h, None, 0, ctypes.byref(need)), "secpe_kprof_report")
+        buf = ctypes.create_string_buffer(need.value)
+        _check(lib().secpe_kprof_report(self.h, buf, need.value, ctypes.byref(need)), "secpe_kprof_report")
+        rows = []
+        for line in buf.value.decode().splitlines():
+            name, n, ms = line.split("\t")
+            rows.append((name, int(n), float(ms)))
+        return rows
 
     def stream_status(self):
         v = ctypes.c_int32()

@@ -237,3 +237,22 @@ def test_seeded_ciphertext_expansion(env):
     cts[:, 1] = 0
     secpe.expand_seeded(ctx, cts, ctx.L, seeds)
     assert torch.equal(cts, ref)
+
+
+def test_kernel_profiler_report(env):
+    """kprof "*" records every launch under its kernel name; the report's
+    launch count equals the context's launch counter for the same range."""
+    import torch
+    o, ctx, keys, secpe = env
+    rng = np.random.default_rng(6)
+    a = to_gpu(secpe, ctx, o.encrypt(rng.uniform(-1, 1, 8), seed=41))
+    torch.cuda.synchronize()
+    ctx.reset_counters()
+    ctx.kprof_begin("*", max_launches=4096)
+    secpe.mul_relin(ctx, keys, a, a)
+    secpe.rotate(ctx, keys, a, 1)
+    k = ctx.kprof_end()
+    rows = ctx.kprof_report()
+    assert rows and all(name.startswith("k_") and n > 0 and ms >= 0 for name, n, ms in rows)
+    assert sum(n for _, n, _ in rows) == k["launches"] == ctx.counters()["launches"]
+    assert [r[2] for r in rows] == sorted((r[2] for r in rows), reverse=True)
