@@ -54,8 +54,9 @@ def parse():
     ap.add_argument("--rates", default="50,200,500,1000,2000")
     ap.add_argument("--serve-queries", type=int, default=384, help="queries submitted per arrival rate")
     ap.add_argument("--budget-gb", type=float, default=120.0)
-    ap.add_argument("--params", default="argmax", choices=["argmax", "argmax8"],
-                    help="Argmax parameter set: argmax (4 special primes, dnum=6) or argmax8 (8 special, dnum=3)")
+    ap.add_argument("--params", default="argmax8", choices=["argmax", "argmax8"],
+                    help="Argmax parameter set: argmax8 (8 special 60-bit primes, dnum=3; the default) or "
+                         "argmax (4 special, dnum=6)")
     ap.add_argument("--micro-params", default="micro", choices=["micro", "argmax", "argmax8"],
                     help="micro: 24+4 primes, dnum=3 (primitive config); argmax: the Argmax set (dnum=6)")
     return ap.parse_args()
@@ -165,12 +166,12 @@ def hbm_peak():
 
 
 # ---------------------------------------------------------------- oracle
-def oracle_sample(seconds_budget=20.0):
+def oracle_sample(params_name, seconds_budget=20.0):
     """Times the CPU oracle (single thread) on full-size primitives of the
     workload and extrapolates queries/s with the per-query op mix."""
     import numpy as np
-    from oracle import ARGMAX, Oracle
-    o = Oracle(ARGMAX)
+    from oracle import PRESETS, Oracle
+    o = Oracle(PRESETS[params_name])
     t0 = time.perf_counter()
     o.keygen(11, rot_steps=[1])
     rng = np.random.default_rng(0)
@@ -203,14 +204,16 @@ def op_mix_per_query(queries, reserve_params=None):
 
 
 def run_reference(args, world, rank):
+    from oracle import PRESETS
     from paper_2502_00847_gb300 import workloads
     if rank != 0:
         return
+    P = PRESETS[args.params]
     qs = workloads.argmax_queries(args.queries, seed=4)
     relin_pq, rot_pq = op_mix_per_query(qs)
     times = []
     for i in range(args.warmup + args.steps):
-        t_mul, t_rot, _ = oracle_sample(seconds_budget=5.0)
+        t_mul, t_rot, _ = oracle_sample(args.params, seconds_budget=5.0)
         per_query = relin_pq * t_mul + rot_pq * t_rot
         if i >= args.warmup:
             times.append(per_query)
@@ -222,7 +225,7 @@ def run_reference(args, world, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": "batched encrypted ensemble Argmax, N=2^16, %d queries, K~U{4,8,16}, "
                                "C~U{2,3,4,6,14,64}" % args.queries, "queries": args.queries,
-                   "params": "q0 60-bit + 23x50-bit, 4 special, dnum=6, Delta=2^50"},
+                   "params": "q0 60-bit + 23x50-bit, %d special 60-bit, dnum=%d, Delta=2^50" % (P.n_p, P.dnum)},
         "cpu_baseline": {"value": value, "unit": "queries/s", "cores": 1, "kind": "oracle",
                          "sample": "per step: oracle HMult+relin+rescale at levels 23/15/7 and one rotation "
                                    "at level 12, N=2^16, single thread; queries/s extrapolated with the mix's "
@@ -371,7 +374,7 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if not args.no_cpu and rank == 0:
-        t_mul, t_rot, wall = oracle_sample()
+        t_mul, t_rot, wall = oracle_sample(args.params)
         relin_pq, rot_pq = op_mix_per_query(qs)
         per_query = relin_pq * t_mul + rot_pq * t_rot
         cpu = {"value": 1.0 / per_query, "unit": "queries/s", "cores": 1, "kind": "oracle",
@@ -526,12 +529,12 @@ def run_serve(args, rank):
     import numpy as np
     import torch
 
-    from oracle.params import ARGMAX
+    from oracle.params import PRESETS
     from paper_2502_00847_gb300 import build as pkg_build
     from paper_2502_00847_gb300 import secpe, workloads
 
     pkg_build.build()
-    ctx = secpe.Context.from_params(ARGMAX)
+    ctx = secpe.Context.from_params(PRESETS[args.params])
     keys = secpe.Keys(ctx, 1000 + rank, ROT_STEPS)
     n, cap = ctx.n, ctx.L + 1
     pool = workloads.argmax_queries(64, seed=5)

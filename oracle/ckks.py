@@ -503,19 +503,28 @@ class Oracle:
         """x * c landing at out_level with scale exactly `target`: drop x to
         out_level+1, multiply by the integer k = round(c * target / s_x * q),
         q = q_{out_level+1}, rescale."""
-        if x.level < out_level + 1:
-            raise ValueError("not enough levels for mul_const")
+        return self.lincomb([(x, c)], target, out_level)
+
+    def lincomb(self, terms, target, out_level):
+        """sum_i c_i x_i landing at out_level with scale exactly `target`:
+        each x_i is dropped to out_level+1 and multiplied by the integer
+        k_i = round(c_i * target / s_i * q), q = q_{out_level+1}, so that
+        every product has scale ~ target * q; the products are added and the
+        sum is rescaled once (READING: a linear combination of constant
+        multiples costs one rescale, not one per term)."""
         if out_level < self.p.reserve:
             raise ValueError("not enough levels")
-        xd = self.drop(x, out_level + 1)
         qf = float(self.primes[out_level + 1])
-        factor = target / xd.scale * qf
-        k = round_half_away(c * factor)
-        cc = np.empty_like(xd.c)
-        for kk in range(2):
-            for pi in range(out_level + 2):
-                cc[kk, pi] = self.vscale(xd.c[kk, pi], k % self.primes[pi], pi)
-        r = self.rescale(Ct(cc, out_level + 1, xd.scale))
+        cc = np.zeros((2, out_level + 2, self.n), dtype=U64)
+        for x, c in terms:
+            if x.level < out_level + 1:
+                raise ValueError("not enough levels for mul_const")
+            xd = self.drop(x, out_level + 1)
+            k = round_half_away(c * (target / xd.scale * qf))
+            for kk in range(2):
+                for pi in range(out_level + 2):
+                    cc[kk, pi] = self.vadd(cc[kk, pi], self.vscale(xd.c[kk, pi], k % self.primes[pi], pi), pi)
+        r = self.rescale(Ct(cc, out_level + 1, target * qf))
         r.scale = target
         return r
 
@@ -571,7 +580,9 @@ class Oracle:
           p = A + (T + U),
         the constant multiplies landing at the scales that make the addends'
         scales equal to s_out; T and U are added before their single
-        relinearisation (5 key switches per polynomial)."""
+        relinearisation (5 key switches per polynomial); A and B are each one
+        linear combination with a single rescale (3 constant-multiply
+        rescales per polynomial)."""
         c1, c3, c5, c7, c9 = c
         lv = x.level
         q3 = float(self.primes[lv - 3])
@@ -580,13 +591,13 @@ class Oracle:
         x4 = self.mul(x2, x2)
         x8 = self.mul(x4, x4)
         sB = s_out * q3 / x4.scale
-        B = self.add(self.mul_const(x, c5, sB, lv - 3), self.mul_const(x3, c7, sB, lv - 3))
+        B = self.lincomb([(x, c5), (x3, c7)], sB, lv - 3)
         s9 = s_out * q3 / x8.scale
         X9 = self.mul_const(x, c9, s9, lv - 3)
         # T = x4 * B and U = x8 * (c9 x) share one relinearisation (READING:
         # lazy relinearisation, the 3-component products are added first)
         TU = self.relin_rescale(self.add3(self.tensor(x4, B), self.tensor(x8, X9)))
-        A = self.add(self.mul_const(x, c1, s_out, lv - 4), self.mul_const(x3, c3, s_out, lv - 4))
+        A = self.lincomb([(x, c1), (x3, c3)], s_out, lv - 4)
         return self.add(A, TU)
 
     def sign(self, x, out_levels):

@@ -161,21 +161,38 @@ int Eval::mul(const Ct &a, const Ct &b, Ct &out) {
 }
 
 int Eval::mul_const(const Ct &x, const std::vector<double> &c, double target, int out_level, Ct &out) {
-    if (x.level() < out_level + 1 || out_level < ctx->p.reserve) return SECPE_ELEVEL;
-    if (c.size() != 1 && (int)c.size() != x.B()) return SECPE_EINVAL;
-    Ct xd = ct_drop(x, out_level + 1);
+    return lincomb({&x}, {c}, target, out_level, out);
+}
+
+// sum_t c_t x_t at out_level with scale exactly `target`: every x_t dropped
+// to out_level + 1 and multiplied by k_t = round(c_t target / s_t q),
+// q = q_{out_level+1}; the products are added and the sum rescaled once.
+int Eval::lincomb(const std::vector<const Ct *> &xs, const std::vector<std::vector<double>> &cs, double target,
+                  int out_level, Ct &out) {
+    const int nt = (int)xs.size();
+    if (nt < 1 || nt > 2 || (int)cs.size() != nt) return SECPE_EINVAL;
+    if (out_level < ctx->p.reserve || out_level < 0 || out_level + 1 > ctx->L) return SECPE_ELEVEL;
+    const int B = xs[0]->B();
     const double qf = (double)ctx->primes[out_level + 1];
-    const double factor = target / xd.scale() * qf;
-    std::vector<long long> k(c.size());
-    for (size_t i = 0; i < c.size(); i++) {
-        const double v = c[i] * factor;
-        if (!(std::fabs(v) < 4.0e18)) return SECPE_EINVAL;
-        k[i] = hm::round_half_away(v);
+    CtB v[2];
+    std::vector<long long> k[2];
+    for (int t = 0; t < nt; t++) {
+        const Ct &x = *xs[t];
+        if (x.level() < out_level + 1) return SECPE_ELEVEL;
+        if (x.B() != B || (cs[t].size() != 1 && (int)cs[t].size() != B)) return SECPE_EINVAL;
+        const Ct xd = ct_drop(x, out_level + 1);
+        const double factor = target / xd.scale() * qf;
+        for (double c : cs[t]) {
+            const double kv = c * factor;
+            if (!(std::fabs(kv) < 4.0e18)) return SECPE_EINVAL;
+            k[t].push_back(hm::round_half_away(kv));
+        }
+        v[t] = xd.v;
     }
-    Ct t;
-    SECPE_CHECK(ct_alloc(ctx, x.B(), out_level + 1, xd.scale(), t));
-    SECPE_CHECK(launch_mulconst(ctx, xd.v, t.v, out_level + 2, k));
-    SECPE_CHECK(rescale(t, out));
+    Ct tsum;
+    SECPE_CHECK(ct_alloc(ctx, B, out_level + 1, target * qf, tsum));
+    SECPE_CHECK(launch_lincomb(ctx, v, k, nt, tsum.v, out_level + 2));
+    SECPE_CHECK(rescale(tsum, out));
     out.v.scale = target;
     return SECPE_OK;
 }
@@ -252,18 +269,14 @@ int Eval::poly9(const Ct &x, const double *c, double s_out, Ct &out) {
     if (lv < 4 + ctx->p.reserve) return SECPE_ELEVEL;
     const double q3 = (double)ctx->primes[lv - 3];
     // temporaries are released as soon as they are dead (Ct() frees them)
-    Ct x2, x3, x4, x8, t1, t2, Bv, X9, T3, U3, TU3, TU, t4, t5, A;
+    Ct x2, x3, x4, x8, Bv, X9, T3, U3, TU3, TU, A;
     SECPE_CHECK(mul(x, x, x2));
     SECPE_CHECK(mul(x, x2, x3));
     SECPE_CHECK(mul(x2, x2, x4));
     x2 = Ct();
     SECPE_CHECK(mul(x4, x4, x8));
     const double sB = s_out * q3 / x4.scale();
-    SECPE_CHECK(mul_const(x, {c[2]}, sB, lv - 3, t1));
-    SECPE_CHECK(mul_const(x3, {c[3]}, sB, lv - 3, t2));
-    SECPE_CHECK(add(t1, t2, Bv));
-    t1 = Ct();
-    t2 = Ct();
+    SECPE_CHECK(lincomb({&x, &x3}, {{c[2]}, {c[3]}}, sB, lv - 3, Bv));
     const double s9 = s_out * q3 / x8.scale();
     SECPE_CHECK(mul_const(x, {c[4]}, s9, lv - 3, X9));
     // T = x4 * B and U = x8 * (c9 x) are added as 3-component ciphertexts and
@@ -279,12 +292,8 @@ int Eval::poly9(const Ct &x, const double *c, double s_out, Ct &out) {
     U3 = Ct();
     SECPE_CHECK(relin_rescale(TU3, TU));
     TU3 = Ct();
-    SECPE_CHECK(mul_const(x, {c[0]}, s_out, lv - 4, t4));
-    SECPE_CHECK(mul_const(x3, {c[1]}, s_out, lv - 4, t5));
+    SECPE_CHECK(lincomb({&x, &x3}, {{c[0]}, {c[1]}}, s_out, lv - 4, A));
     x3 = Ct();
-    SECPE_CHECK(add(t4, t5, A));
-    t4 = Ct();
-    t5 = Ct();
     return add(A, TU, out);
 }
 

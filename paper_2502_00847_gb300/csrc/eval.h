@@ -65,6 +65,8 @@ struct Eval {
     int add3(const Ct &a3, const Ct &b3, Ct &out3);
     int relin_rescale(const Ct &d3, Ct &out);
     int mul_const(const Ct &x, const std::vector<double> &c, double target, int out_level, Ct &out);
+    int lincomb(const std::vector<const Ct *> &xs, const std::vector<std::vector<double>> &cs, double target,
+                int out_level, Ct &out);
     int add_const(const Ct &x, double c, Ct &out);
     int rescale(const Ct &in, Ct &out);
     int rotate(const Ct &x, int steps, Ct &out);

@@ -81,20 +81,50 @@ struct KArr {
     long long k[SECPE_MAX_BATCH_CONST];
 };
 
-// out = x * k_item mod q_i on both polynomials, limbs 0..nl-1
-__global__ void k_mulconst(DevCtx c, const u64 *x, long long xs, int cap_x, u64 *o, long long os,
-                           int cap_o, int nl, const __grid_constant__ KArr ka, int per_item) {
+// out = sum_t x_t * k_{t,item} mod q_i on both polynomials, limbs 0..nl-1
+// (NT = 1: a constant multiple).  Each thread takes 8 residues (four
+// 16-byte accesses one block-width apart), so the per-thread Montgomery form
+// of the constants is amortised; one reduction per residue for all terms.
+struct LinArgs {
+    const u64 *x[2];
+    long long xs[2];
+    int cap[2];
+    u64 *o;
+    long long os;
+    int cap_o, nl, per_item;
+    long long k[2][SECPE_MAX_BATCH_CONST];
+};
+
+template <int NT>
+__global__ void __launch_bounds__(256) k_lincomb(DevCtx c, const __grid_constant__ LinArgs a) {
     const int li = blockIdx.y;
-    const int i = li % nl, kk = (li / nl) & 1, item = li / (2 * nl);
-    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    if (e >= c.n) return;
+    const int i = li % a.nl, kk = (li / a.nl) & 1, item = li / (2 * a.nl);
     const u64 q = c.q[i], qi = c.qinv_neg[i], r2 = c.r2[i];
-    const u64 w = signed_mod(ka.k[per_item ? item : 0], q, c.mu[i]);
-    const u64 wm = redc(mulhi64(w, r2), w * r2, q, qi);  // w * 2^64 mod q
-    ulonglong2 v = ld2(x + item * xs + ((long long)kk * cap_x + i) * c.n + e);
-    v.x = redc(mulhi64(v.x, wm), v.x * wm, q, qi);
-    v.y = redc(mulhi64(v.y, wm), v.y * wm, q, qi);
-    st2(o + item * os + ((long long)kk * cap_o + i) * c.n + e, v);
+    u64 wm[NT];
+    const u64 *xp[NT];
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+        const u64 w = signed_mod(a.k[t][a.per_item ? item : 0], q, c.mu[i]);
+        wm[t] = redc(mulhi64(w, r2), w * r2, q, qi);  // w * 2^64 mod q
+        xp[t] = a.x[t] + item * a.xs[t] + ((long long)kk * a.cap[t] + i) * c.n;
+    }
+    u64 *op = a.o + item * a.os + ((long long)kk * a.cap_o + i) * c.n;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int e = 2 * (threadIdx.x + 256 * (blockIdx.x * 4 + j));
+        if (e >= c.n) break;
+        acc128 s0 = {0, 0}, s1 = {0, 0};
+#pragma unroll
+        for (int t = 0; t < NT; t++) {
+            const ulonglong2 v = ld2(xp[t] + e);
+            mac(s0, v.x, wm[t]);
+            mac(s1, v.y, wm[t]);
+        }
+        ulonglong2 r;
+        r.x = redc(s0.hi, s0.lo, q, qi);
+        r.y = redc(s1.hi, s1.lo, q, qi);
+        st2(op + e, r);
+    }
 }
 
 // out = x with k_item added to every NTT value of c0 (the constant polynomial)
@@ -565,14 +595,46 @@ static dim3 limb_grid(int n, int per_thread, long long nlimbs) {
 
 int launch_addsub(secpe_ctx *ctx, const CtB &a, const CtB &b, const CtB &o, int nl, bool sub, int npoly) {
     if (nl <= 0 || a.B == 0) return SECPE_OK;
+    KprofScope kp(ctx, "ew_addsub", 24.0 * ctx->n * a.B * npoly * nl);
     SECPE_LAUNCH(ctx, k_addsub, limb_grid(ctx->n, 2, (long long)a.B * npoly * nl), 256, 0, ctx->dev, a.data,
                  a.stride, b.data, b.stride, o.data, o.stride, a.cap, b.cap, o.cap, nl, sub ? 1 : 0, npoly);
     return SECPE_OK;
 }
 
 int launch_tensor(secpe_ctx *ctx, const CtB &a, const CtB &b, u64 *d, int nl) {
+    KprofScope kp(ctx, "ew_tensor", 56.0 * ctx->n * a.B * nl);
     SECPE_LAUNCH(ctx, k_tensor, limb_grid(ctx->n, 2, (long long)a.B * nl), 256, 0, ctx->dev, a.data, a.stride,
                  a.cap, b.data, b.stride, b.cap, d, nl);
+    return SECPE_OK;
+}
+
+int launch_lincomb(secpe_ctx *ctx, const CtB *xs, const std::vector<long long> *ks, int nt, const CtB &o,
+                   int nl) {
+    if (nt < 1 || nt > 2 || nl <= 0) return SECPE_EINVAL;
+    const int B = o.B;
+    if (B < 1 || B > SECPE_MAX_BATCH_CONST) return SECPE_EINVAL;
+    LinArgs la;
+    la.per_item = 0;
+    for (int t = 0; t < nt; t++) {
+        if (xs[t].B != B || (ks[t].size() != 1 && (int)ks[t].size() != B)) return SECPE_EINVAL;
+        if (ks[t].size() != 1) la.per_item = 1;
+    }
+    for (int t = 0; t < nt; t++) {
+        la.x[t] = xs[t].data;
+        la.xs[t] = xs[t].stride;
+        la.cap[t] = xs[t].cap;
+        for (int b = 0; b < (la.per_item ? B : 1); b++) la.k[t][b] = ks[t][ks[t].size() == 1 ? 0 : b];
+    }
+    la.o = o.data;
+    la.os = o.stride;
+    la.cap_o = o.cap;
+    la.nl = nl;
+    const dim3 grid((unsigned)((ctx->n + 2047) / 2048), (unsigned)((long long)B * 2 * nl));
+    KprofScope kp(ctx, "ew_lincomb", 16.0 * ctx->n * B * nl * (nt + 1));
+    if (nt == 1)
+        SECPE_LAUNCH(ctx, k_lincomb<1>, grid, 256, 0, ctx->dev, la);
+    else
+        SECPE_LAUNCH(ctx, k_lincomb<2>, grid, 256, 0, ctx->dev, la);
     return SECPE_OK;
 }
 
@@ -585,15 +647,6 @@ static int fill_karr(KArr &ka, const std::vector<long long> &k, int B, int &per_
     if ((int)k.size() != B || B > SECPE_MAX_BATCH_CONST) return SECPE_EINVAL;
     per_item = 1;
     for (int i = 0; i < B; i++) ka.k[i] = k[i];
-    return SECPE_OK;
-}
-
-int launch_mulconst(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, const std::vector<long long> &k) {
-    KArr ka;
-    int per = 0;
-    SECPE_CHECK(fill_karr(ka, k, x.B, per));
-    SECPE_LAUNCH(ctx, k_mulconst, limb_grid(ctx->n, 2, (long long)x.B * 2 * nl), 256, 0, ctx->dev, x.data,
-                 x.stride, x.cap, o.data, o.stride, o.cap, nl, ka, per);
     return SECPE_OK;
 }
 

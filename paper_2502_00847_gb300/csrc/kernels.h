@@ -21,7 +21,9 @@ struct PrimeList {
 
 int launch_addsub(secpe_ctx *ctx, const CtB &a, const CtB &b, const CtB &o, int nl, bool sub, int npoly = 2);
 int launch_tensor(secpe_ctx *ctx, const CtB &a, const CtB &b, u64 *d, int nl);
-int launch_mulconst(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, const std::vector<long long> &k);
+// o = sum_t xs[t] * ks[t] (one constant per term, or one per item) over
+// limbs 0..nl-1 of both polynomials, nt in {1, 2}.
+int launch_lincomb(secpe_ctx *ctx, const CtB *xs, const std::vector<long long> *ks, int nt, const CtB &o, int nl);
 int launch_addconst(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, const std::vector<long long> &k);
 int launch_automorph(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, unsigned g);
 int launch_rescale_prep(secpe_ctx *ctx, const u64 *y, u64 *z, int B, int lv);

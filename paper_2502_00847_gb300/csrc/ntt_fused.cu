@@ -272,7 +272,10 @@ int launch_colpass_bconv(secpe_ctx *ctx, const BConvArgs &a) {
         case 3: SECPE_LAUNCH(ctx, k_colpass_bconv<3>, grid, 256, 0, a); break;
         case 4: SECPE_LAUNCH(ctx, k_colpass_bconv<4>, grid, 256, 0, a); break;
         case 5: SECPE_LAUNCH(ctx, k_colpass_bconv<5>, grid, 256, 0, a); break;
+        case 6: SECPE_LAUNCH(ctx, k_colpass_bconv<6>, grid, 256, 0, a); break;
+        case 7: SECPE_LAUNCH(ctx, k_colpass_bconv<7>, grid, 256, 0, a); break;
         case 8: SECPE_LAUNCH(ctx, k_colpass_bconv<8>, grid, 256, 0, a); break;
+        case 9: SECPE_LAUNCH(ctx, k_colpass_bconv<9>, grid, 256, 0, a); break;
         default: SECPE_LAUNCH(ctx, k_colpass_bconv<0>, grid, 256, 0, a);
     }
     return SECPE_OK;

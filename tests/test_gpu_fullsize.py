@@ -160,8 +160,9 @@ def test_tensor_pipe_ntt_bit_identical(env):
 
 
 def test_argmax8_parameter_set_bit_exact():
-    """8 special primes, dnum = 3: HMult, rotation and a two-query batched
-    Argmax, bit-exact / decoded against the oracle and the plaintext argmax."""
+    """8 special primes, dnum = 3: HMult (full and partial last digits),
+    rotation and a two-query batched Argmax, bit-exact / decoded against the
+    oracle and the plaintext argmax."""
     from oracle import ARGMAX8
     from paper_2502_00847_gb300 import secpe
     o = Oracle(ARGMAX8)
@@ -175,6 +176,11 @@ def test_argmax8_parameter_set_bit_exact():
     a, b = to_gpu(secpe, ctx, a_o), to_gpu(secpe, ctx, b_o)
     same(secpe.mul_relin(ctx, keys, a, b), o.mul(a_o, b_o))
     same(secpe.rotate(ctx, keys, b, -4), o.rotate(b_o, -4))
+    # partial last digits of 7 and 6 primes (levels 22, 21) and of 1 (level 8)
+    for lv in (22, 21, 8):
+        c_o = o.drop(a_o, lv)
+        c = to_gpu(secpe, ctx, c_o)
+        same(secpe.mul_relin(ctx, keys, c, c), o.mul(c_o, c_o))
     qs = workloads.argmax_queries(2, seed=8, K_choices=(4,), C_choices=(2, 4))
     rot = sorted({-(1 << (q.C - 1).bit_length()) for q in qs} | {1, 2})
     k2 = secpe.Keys(ctx, 5, rot)

@@ -48,9 +48,10 @@ def test_reference_arm_prints_on_rank0_only(monkeypatch, capsys):
     import bench
 
     class A:
-        queries, steps, warmup, gpus = 4, 1, 0, 2
+        queries, steps, warmup, gpus, params = 4, 1, 0, 2, "argmax8"
     called = []
-    monkeypatch.setattr(bench, "oracle_sample", lambda seconds_budget=0: called.append(1) or (1.0, 1.0, 0.0))
+    monkeypatch.setattr(bench, "oracle_sample",
+                        lambda params_name, seconds_budget=0: called.append(params_name) or (1.0, 1.0, 0.0))
     bench.run_reference(A, 2, 1)
     assert capsys.readouterr().out == "" and not called
     bench.run_reference(A, 2, 0)

@@ -80,6 +80,14 @@ def test_encrypt_decrypt_and_linear_ops(toy_oracle):
     pr = o.mul(a, b)
     assert pr.level == a.level - 1
     assert np.max(np.abs(o.decrypt(pr, 16) - v * w)) < TOL_LINEAR
+    # a linear combination of operands at different levels and scales lands
+    # at one level with the declared scale and decrypts to the combination
+    lc = o.lincomb([(a, 0.8125), (pr, -2.5)], o.p.scale, pr.level - 1)
+    assert lc.level == pr.level - 1 and lc.scale == o.p.scale
+    assert np.max(np.abs(o.decrypt(lc, 16) - (0.8125 * v - 2.5 * v * w))) < TOL_LINEAR
+    # one term is exactly the constant multiply
+    one = o.lincomb([(a, -1.7)], o.p.scale, a.level - 1)
+    assert np.array_equal(one.c, mc.c)
 
 
 def test_rotation_direction(toy_oracle):
