@@ -257,6 +257,25 @@ typedef struct {
 int secpe_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q,
                        int n_queries, void *stream);
 
+/* Graph-captured batched Argmax.  secpe_argmax_batch_capture records the
+ * whole evaluation of secpe_argmax_batch for these queries (every launch,
+ * stream-ordered allocation and copy) into one CUDA graph, on a stream of its
+ * own, without running it, and instantiates it; the z_out level/scale fields
+ * are set as a run would set them.  The graph keeps the device addresses of
+ * the queries' ciphertexts, z_out buffers and keys: the caller keeps them
+ * alive and may rewrite the input ciphertexts in place (same level, scale,
+ * layout) between launches.  secpe_graph_launch replays it on `stream` (one
+ * launch for the whole batch) and adds the captured operation and kernel
+ * counts to the context counters.  *n_nodes (if not null) receives the
+ * graph's node count.  Errors: those of secpe_argmax_batch, SECPE_ECUDA when
+ * capture or instantiation fails. */
+typedef struct secpe_graph secpe_graph;
+int secpe_argmax_batch_capture(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int n_queries,
+                               secpe_graph **out, int64_t *n_nodes);
+int secpe_graph_launch(secpe_graph *g, void *stream);
+/* Synchronises the device, destroys the graph and returns its memory. */
+void secpe_graph_destroy(secpe_graph *g);
+
 /* ---- continuous-batching server ---------------------------------------- */
 /* A server keeps the state of admitted queries on the device and advances
  * them phase by phase (aggregation + duplication, QuickMax rounds, final

@@ -506,6 +506,80 @@ extern "C" int secpe_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const 
     return finish(ctx, argmax_batch_impl(ctx, keys, q, n_queries));
 }
 
+struct secpe_graph {
+    secpe_ctx *ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    secpe_counters counts{};  // operation and kernel counts of one replay
+};
+
+extern "C" int secpe_argmax_batch_capture(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q,
+                                          int n_queries, secpe_graph **out, int64_t *n_nodes) {
+    if (!ctx || !keys || !q || n_queries < 1 || !out) return SECPE_EINVAL;
+    *out = nullptr;
+    cudaStream_t cs = nullptr;
+    SECPE_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const secpe_counters saved = ctx->counters;
+    const cudaStream_t saved_stream = ctx->stream;
+    std::memset(&ctx->counters, 0, sizeof(ctx->counters));
+    cudaGraph_t g = nullptr;
+    int st = SECPE_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        st = SECPE_ECUDA;
+    } else {
+        ctx->stream = cs;
+        st = argmax_batch_impl(ctx, keys, q, n_queries);
+        if (cudaStreamEndCapture(cs, &g) != cudaSuccess && st == SECPE_OK) st = SECPE_ECUDA;
+    }
+    const secpe_counters captured = ctx->counters;
+    ctx->counters = saved;
+    ctx->stream = saved_stream;
+    cudaGraphExec_t e = nullptr;
+    if (st == SECPE_OK && (!g || cudaGraphInstantiate(&e, g, 0) != cudaSuccess)) st = SECPE_ECUDA;
+    if (st == SECPE_OK && n_nodes) {
+        size_t nn = 0;
+        if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess) st = SECPE_ECUDA;
+        *n_nodes = (int64_t)nn;
+    }
+    cudaStreamDestroy(cs);
+    if (st != SECPE_OK) {
+        if (e) cudaGraphExecDestroy(e);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st;
+    }
+    secpe_graph *r = new secpe_graph;
+    r->ctx = ctx;
+    r->graph = g;
+    r->exec = e;
+    r->counts = captured;
+    *out = r;
+    return SECPE_OK;
+}
+
+extern "C" int secpe_graph_launch(secpe_graph *g, void *stream) {
+    if (!g || !g->exec) return SECPE_EINVAL;
+    SECPE_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    secpe_counters &c = g->ctx->counters;
+    c.rotations += g->counts.rotations;
+    c.signs += g->counts.signs;
+    c.relins += g->counts.relins;
+    c.refreshes += g->counts.refreshes;
+    c.keyswitches += g->counts.keyswitches;
+    c.launches += g->counts.launches;
+    return SECPE_OK;
+}
+
+extern "C" void secpe_graph_destroy(secpe_graph *g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    // hand the graph's allocations back to the device
+    int dev = 0;
+    if (cudaDeviceSynchronize() == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGraphMemTrim(dev);
+}
+
 extern "C" int secpe_kprof_begin(secpe_ctx *ctx, const char *name_filter, int max_launches) {
     if (!ctx || !name_filter || max_launches < 1 || max_launches > (1 << 20)) return SECPE_EINVAL;
     KProf &k = ctx->kprof;

@@ -14,10 +14,10 @@ struct KprofLaunch {
         k.launches++;
         if ((int)k.names.size() <= idx) k.names.resize(idx + 1);
         k.names[idx] = name;
-        cudaEventRecord(k.ev[2 * idx], c->stream);
+        cudaEventRecordWithFlags(k.ev[2 * idx], c->stream, cudaEventRecordExternal);
     }
     ~KprofLaunch() {
-        if (idx >= 0) cudaEventRecord(ctx->kprof.ev[2 * idx + 1], ctx->stream);
+        if (idx >= 0) cudaEventRecordWithFlags(ctx->kprof.ev[2 * idx + 1], ctx->stream, cudaEventRecordExternal);
     }
 };
 
@@ -44,6 +44,8 @@ struct KprofLaunch {
 
 // Records a CUDA event pair around the launches made in its lifetime when
 // the context's kernel profiler is active and `name` matches its filter.
+// The records are external, so that under stream capture they become event
+// record nodes of the graph (each replay re-records them).
 struct KprofScope {
     secpe_ctx *ctx;
     int idx = -1;
@@ -54,10 +56,10 @@ struct KprofScope {
         idx = k.used++;
         k.launches++;
         k.bytes += bytes;
-        cudaEventRecord(k.ev[2 * idx], c->stream);
+        cudaEventRecordWithFlags(k.ev[2 * idx], c->stream, cudaEventRecordExternal);
     }
     ~KprofScope() {
-        if (idx >= 0) cudaEventRecord(ctx->kprof.ev[2 * idx + 1], ctx->stream);
+        if (idx >= 0) cudaEventRecordWithFlags(ctx->kprof.ev[2 * idx + 1], ctx->stream, cudaEventRecordExternal);
     }
 };
 

@@ -21,7 +21,8 @@ EXPORTS = [
     "secpe_encrypt", "secpe_encrypt_logits", "secpe_decrypt", "secpe_decrypt_coeffs", "secpe_ntt",
     "secpe_ntt_cts", "secpe_add", "secpe_sub", "secpe_mul_const", "secpe_add_const", "secpe_mul_relin",
     "secpe_rescale", "secpe_rotate", "secpe_keyswitch", "secpe_refresh_testonly", "secpe_sign", "secpe_max",
-    "secpe_ensemble_aggregate", "secpe_encrypted_argmax", "secpe_argmax_batch", "secpe_get_counters",
+    "secpe_ensemble_aggregate", "secpe_encrypted_argmax", "secpe_argmax_batch", "secpe_argmax_batch_capture",
+    "secpe_graph_launch", "secpe_graph_destroy", "secpe_get_counters",
     "secpe_reset_counters", "secpe_select_primes", "secpe_kprof_begin", "secpe_kprof_end", "secpe_kprof_report",
     "secpe_keyswitch_batch", "secpe_mul_relin_batch", "secpe_rotate_batch", "secpe_rescale_batch",
     "secpe_rescale_noalloc", "secpe_server_create", "secpe_server_destroy", "secpe_server_submit",
@@ -111,6 +112,9 @@ def lib():
         "secpe_ensemble_aggregate": (i32, [vp, P(CtC), i32, dbl, dbl, P(CtC), vp]),
         "secpe_encrypted_argmax": (i32, [vp, vp, P(CtC), i32, u64, P(CtC), vp]),
         "secpe_argmax_batch": (i32, [vp, vp, P(QueryC), i32, vp]),
+        "secpe_argmax_batch_capture": (i32, [vp, vp, P(QueryC), i32, P(vp), P(ctypes.c_int64)]),
+        "secpe_graph_launch": (i32, [vp, vp]),
+        "secpe_graph_destroy": (None, [vp]),
         "secpe_get_counters": (i32, [vp, P(CountersC)]),
         "secpe_reset_counters": (i32, [vp]),
         "secpe_select_primes": (i32, [P(ParamsC), P(u64), i32]),
@@ -529,9 +533,7 @@ def encrypted_argmax(ctx, keys, y, C, qseed, out=None):
     return out
 
 
-def argmax_batch(ctx, keys, queries):
-    """queries: list of dicts with cts (list of Ciphertext), C, d_min, d_max,
-    qseed, z_out (Ciphertext).  Updates each z_out's level/scale."""
+def _query_array(queries):
     keep = []
     qarr = (QueryC * len(queries))()
     for i, q in enumerate(queries):
@@ -539,9 +541,48 @@ def argmax_batch(ctx, keys, queries):
         z = q["z_out"].struct()
         keep.append((cts, z))
         qarr[i] = QueryC(cts, len(q["cts"]), q["C"], q["d_min"], q["d_max"], q["qseed"], ctypes.pointer(z))
+    return qarr, keep
+
+
+def argmax_batch(ctx, keys, queries):
+    """queries: list of dicts with cts (list of Ciphertext), C, d_min, d_max,
+    qseed, z_out (Ciphertext).  Updates each z_out's level/scale."""
+    qarr, keep = _query_array(queries)
     _check(lib().secpe_argmax_batch(ctx.h, keys.h, qarr, len(queries), _stream()), "secpe_argmax_batch")
     for q, (_, z) in zip(queries, keep):
         q["z_out"].update(z)
+
+
+class Graph:
+    """One CUDA graph of a whole batched Argmax (secpe_argmax_batch_capture).
+    It keeps the device addresses of the queries' ciphertexts, z_out buffers
+    and keys: the caller keeps those tensors alive while the graph is used."""
+
+    def __init__(self, ctx, keys, queries):
+        qarr, keep = _query_array(queries)
+        h = ctypes.c_void_p()
+        nodes = ctypes.c_int64()
+        _check(lib().secpe_argmax_batch_capture(ctx.h, keys.h, qarr, len(queries), ctypes.byref(h),
+                                                ctypes.byref(nodes)), "secpe_argmax_batch_capture")
+        self.h = h
+        self.nodes = int(nodes.value)
+        self._refs = (ctx, keys)
+        for q, (_, z) in zip(queries, keep):
+            q["z_out"].update(z)
+
+    def launch(self):
+        _check(lib().secpe_graph_launch(self.h, _stream()), "secpe_graph_launch")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().secpe_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------ batched primitives

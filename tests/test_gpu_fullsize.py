@@ -194,3 +194,40 @@ def test_argmax8_parameter_set_bit_exact():
         zp = plainsim.ensemble_argmax(q.logits, q.d_min, q.d_max, ctx.n // 2)
         assert np.max(np.abs(zd - zp)) < 2.0 ** -12
         assert int(np.argmax(zd)) == int(np.argmax(q.logits.mean(0)))
+
+
+def test_graph_captured_batch_replays_bit_exact(env):
+    """The batched Argmax captured as one CUDA graph: a replay gives the same
+    residues as the direct call, a replay after the inputs are rewritten in
+    place gives the new inputs' results, and the counters count the replays."""
+    import torch
+    o, ctx, keys, secpe = env
+    qs = workloads.argmax_queries(3, seed=12, K_choices=(4,), C_choices=(2, 3))
+    rot = sorted({-(1 << (q.C - 1).bit_length()) for q in qs} | {1, 2})
+    k2 = secpe.Keys(ctx, 21, rot)
+    qs2 = [workloads.argmax_queries(1, seed=100 + i, K_choices=(4,), C_choices=(q.C,))[0] for i, q in enumerate(qs)]
+    cts = [[secpe.encrypt_logits(ctx, k2, q.logits[i], q.d_min, q.enc_seeds[i]) for i in range(q.K)] for q in qs]
+    batch = [dict(cts=c, C=q.C, d_min=q.d_min, d_max=q.d_max, qseed=q.qseed, z_out=ctx.new_ct())
+             for q, c in zip(qs, cts)]
+    ref = [dict(b, z_out=ctx.new_ct()) for b in batch]
+    secpe.argmax_batch(ctx, k2, ref)
+    g = secpe.Graph(ctx, k2, batch)
+    assert g.nodes > 100
+    ctx.reset_counters()
+    g.launch()
+    torch.cuda.synchronize()
+    cnt = ctx.counters()
+    assert cnt["launches"] > 100 and cnt["relins"] > 0
+    for b, r in zip(batch, ref):
+        assert b["z_out"].level == r["z_out"].level
+        assert np.array_equal(b["z_out"].residues(), r["z_out"].residues())
+    # new inputs written into the captured buffers (same classes per query)
+    for q, q2, c in zip(qs, qs2, cts):
+        for i in range(q.K):
+            secpe.encrypt_logits(ctx, k2, q2.logits[i], q2.d_min, q2.enc_seeds[i], out=c[i])
+    g.launch()
+    torch.cuda.synchronize()
+    for q, q2, b in zip(qs, qs2, batch):
+        zd = secpe.decrypt(ctx, k2, b["z_out"], q.C)
+        assert int(np.argmax(zd)) == int(np.argmax(q2.logits.mean(0)))
+    g.close()
