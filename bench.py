@@ -276,6 +276,9 @@ def run_ours(args, world, rank, local):
     def step():
         secpe.argmax_batch(ctx, keys, batch)
 
+    # launch configurations of the N = 2^16 kernels picked by the autotuner
+    tuning = ctx.autotune()
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -462,7 +465,8 @@ def run_ours(args, world, rank, local):
                        "l2": "inputs (%.1f GB) larger than L2" % (n_cts * ct_words * 8 / 1e9),
                        "parallelism": "dp%d (independent queries per GPU)" % world,
                        "launch": ("one CUDA graph per step (%d nodes)" % graph_nodes) if graph_nodes
-                                 else "direct call per step"},
+                                 else "direct call per step",
+                       "autotune": {k: v["ctas_per_sm"] for k, v in tuning.items()}},
             "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk, "gpu_launches": cnt["launches"],
             **({"breakdown": breakdown} if breakdown else {}),
@@ -488,6 +492,7 @@ def run_micro(args, rank):
     batches = [int(b) for b in args.micro_batch.split(",")]
     P = PRESETS[args.micro_params]
     ctx = secpe.Context.from_params(P)
+    ctx.autotune()
     rot = [1 << j for j in range(16)] if "rotate" in ops else []
     keys = secpe.Keys(ctx, 2, rot)
     n, cap, L = ctx.n, ctx.L + 1, ctx.L
@@ -599,6 +604,7 @@ def run_serve(args, rank):
 
     pkg_build.build()
     ctx = secpe.Context.from_params(PRESETS[args.params])
+    ctx.autotune()
     keys = secpe.Keys(ctx, 1000 + rank, ROT_STEPS)
     n, cap = ctx.n, ctx.L + 1
     pool = workloads.argmax_queries(64, seed=5)

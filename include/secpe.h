@@ -320,6 +320,26 @@ typedef struct {
 int secpe_get_counters(const secpe_ctx *ctx, secpe_counters *out);
 int secpe_reset_counters(secpe_ctx *ctx);
 
+/* ---- autotuning ---------------------------------------------------------- */
+/* Launch configurations of the N = 2^16 kernels: for each tuned kernel (the
+ * four transform passes and the base-conversion pass) the candidates are 3
+ * and 4 CTAs per SM (at most 80 or 64 registers per thread).
+ * secpe_autotune times every candidate with CUDA events on a zero-filled
+ * scratch batch of 16 x 32 limbs (the data does not change the work), keeps
+ * the fastest for this context, and reports them in *out (host, may be
+ * null).  It synchronises `stream` (it cannot be captured).  For other ring
+ * sizes there is nothing to tune and n_kernels = 0.  Untuned contexts use 3
+ * CTAs per SM.  Every configuration computes identical results. */
+typedef struct {
+    int32_t n_kernels;
+    char name[8][32];
+    int32_t ctas_per_sm[8];  /* chosen */
+    float ms[8][2];          /* per launch with 3 and with 4 CTAs per SM */
+} secpe_tuning;
+int secpe_autotune(secpe_ctx *ctx, secpe_tuning *out, void *stream);
+/* Fixes kernel `kernel` (index as in secpe_tuning) to ctas_per_sm (3 or 4). */
+int secpe_tuning_set(secpe_ctx *ctx, int kernel, int ctas_per_sm);
+
 /* ---- instrumentation --------------------------------------------------- */
 /* Times, with CUDA events recorded on the launching stream around each
  * launch, every launch of the library kernels whose name contains

@@ -506,6 +506,74 @@ extern "C" int secpe_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const 
     return finish(ctx, argmax_batch_impl(ctx, keys, q, n_queries));
 }
 
+// ---------------------------------------------------------------- autotuning
+static const char *const kTuneNames[TUNE_NSLOTS] = {"ntt16_colpass", "ntt16_rowpass", "intt16_colpass",
+                                                     "intt16_rowpass", "colpass_bconv"};
+
+extern "C" int secpe_tuning_set(secpe_ctx *ctx, int kernel, int ctas_per_sm) {
+    if (!ctx || kernel < 0 || kernel >= TUNE_NSLOTS || (ctas_per_sm != 3 && ctas_per_sm != 4)) return SECPE_EINVAL;
+    ctx->tune.ctas[kernel] = ctas_per_sm;
+    return SECPE_OK;
+}
+
+extern "C" int secpe_autotune(secpe_ctx *ctx, secpe_tuning *out, void *stream) {
+    if (!ctx) return SECPE_EINVAL;
+    if (out) std::memset(out, 0, sizeof(*out));
+    if (ctx->log_n != 16) return SECPE_OK;
+    CallScope cs(ctx, stream);
+    const int n = ctx->n, nitem = 16, nlimb = 32;
+    DevBuf buf;
+    SECPE_CHECK(buf.alloc(ctx, sizeof(u64) * (size_t)nitem * nlimb * n));
+    SECPE_CUDA(cudaMemsetAsync(buf.p, 0, buf.bytes, ctx->stream));
+    LimbSet ls = make_limbset(buf.u(), nitem, (long long)nlimb * n, 1, 0, nlimb, 0);
+    for (int j = 0; j < nlimb; j++) ls.prime_of[j] = (int8_t)(j % ctx->nprimes);
+    cudaEvent_t e0, e1;
+    SECPE_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return SECPE_ECUDA;
+    }
+    const secpe_counters saved = ctx->counters;
+    int st = SECPE_OK;
+    float ms[TUNE_NSLOTS][2] = {};
+    for (int slot = 0; slot < TUNE_NSLOTS && st == SECPE_OK; slot++) {
+        for (int v = 0; v < 2 && st == SECPE_OK; v++) {
+            ctx->tune.ctas[slot] = 3 + v;
+            auto run = [&]() {
+                return slot == TUNE_BCONV ? bconv_pass_probe(ctx, buf.u(), nitem, nlimb - ctx->alpha)
+                                          : ntt16_pass(ctx, slot, ls);
+            };
+            st = run();  // warm-up
+            if (st == SECPE_OK && cudaEventRecord(e0, ctx->stream) != cudaSuccess) st = SECPE_ECUDA;
+            for (int r = 0; r < 5 && st == SECPE_OK; r++) st = run();
+            if (st == SECPE_OK && (cudaEventRecord(e1, ctx->stream) != cudaSuccess ||
+                                   cudaEventSynchronize(e1) != cudaSuccess ||
+                                   cudaEventElapsedTime(&ms[slot][v], e0, e1) != cudaSuccess))
+                st = SECPE_ECUDA;
+            ms[slot][v] /= 5.0f;
+        }
+        ctx->tune.ctas[slot] = ms[slot][1] < ms[slot][0] ? 4 : 3;
+    }
+    ctx->counters = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SECPE_OK) {
+        for (int slot = 0; slot < TUNE_NSLOTS; slot++) ctx->tune.ctas[slot] = 3;
+        return st;
+    }
+    ctx->tune.tuned = true;
+    if (out) {
+        out->n_kernels = TUNE_NSLOTS;
+        for (int slot = 0; slot < TUNE_NSLOTS; slot++) {
+            std::snprintf(out->name[slot], sizeof out->name[slot], "%s", kTuneNames[slot]);
+            out->ctas_per_sm[slot] = ctx->tune.ctas[slot];
+            out->ms[slot][0] = ms[slot][0];
+            out->ms[slot][1] = ms[slot][1];
+        }
+    }
+    return finish(ctx, SECPE_OK);
+}
+
 struct secpe_graph {
     secpe_ctx *ctx = nullptr;
     cudaGraph_t graph = nullptr;

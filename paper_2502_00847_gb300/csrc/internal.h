@@ -101,6 +101,14 @@ struct KProf {
     double bytes = 0.0;
 };
 
+// Launch configurations chosen by secpe_autotune: CTAs per SM (3 or 4, i.e.
+// at most 80 or 64 registers per thread) of each tuned N = 2^16 kernel.
+enum TuneSlot { TUNE_COLPASS = 0, TUNE_ROWPASS, TUNE_ICOLPASS, TUNE_IROWPASS, TUNE_BCONV, TUNE_NSLOTS };
+struct Tuning {
+    int ctas[TUNE_NSLOTS] = {3, 3, 3, 3, 3};
+    bool tuned = false;
+};
+
 struct secpe_ctx {
     secpe_params p;
     int n, log_n, nq, npsp, nprimes, L, dnum, alpha;
@@ -113,6 +121,7 @@ struct secpe_ctx {
     secpe_counters counters;
     cudaStream_t stream;  // stream of the call in progress
     KProf kprof;
+    Tuning tune;
     // host copies used by host-side constant encoding
     std::vector<u64> h_qinv_neg, h_r2, h_mu;
     std::vector<ulonglong2> h_mu_inv;  // host mirror of DevCtx::mu_inv

@@ -2,6 +2,16 @@
 #pragma once
 #include "internal.h"
 
+// Records a profiler event: an external record (an event record node) while
+// the stream is being captured, a plain record otherwise.
+static inline void kprof_record(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, st);
+}
+
 // Records a CUDA event pair around one launch, under the kernel's name, when
 // the context's kernel profiler runs with the filter "*".
 struct KprofLaunch {
@@ -14,22 +24,25 @@ struct KprofLaunch {
         k.launches++;
         if ((int)k.names.size() <= idx) k.names.resize(idx + 1);
         k.names[idx] = name;
-        cudaEventRecordWithFlags(k.ev[2 * idx], c->stream, cudaEventRecordExternal);
+        kprof_record(k.ev[2 * idx], c->stream);
     }
     ~KprofLaunch() {
-        if (idx >= 0) cudaEventRecordWithFlags(ctx->kprof.ev[2 * idx + 1], ctx->stream, cudaEventRecordExternal);
+        if (idx >= 0) kprof_record(ctx->kprof.ev[2 * idx + 1], ctx->stream);
     }
 };
 
-// Launch on ctx->stream, count it, and turn a launch error into SECPE_ECUDA.
-#define SECPE_LAUNCH(ctx, kernel, grid, block, smem, ...)                               \
+// Launch on ctx->stream, count it, and turn a launch error into SECPE_ECUDA;
+// the profiler sees the launch under `name`.
+#define SECPE_LAUNCH_AS(ctx, name, kernel, grid, block, smem, ...)                      \
     do {                                                                                  \
-        KprofLaunch _kpl((ctx), #kernel);                                                 \
+        KprofLaunch _kpl((ctx), name);                                                    \
         kernel<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);                  \
         (ctx)->counters.launches++;                                                       \
         cudaError_t _e = cudaGetLastError();                                              \
         if (_e != cudaSuccess) return SECPE_ECUDA;                                        \
     } while (0)
+#define SECPE_LAUNCH(ctx, kernel, grid, block, smem, ...) \
+    SECPE_LAUNCH_AS(ctx, #kernel, kernel, grid, block, smem, __VA_ARGS__)
 
 #define SECPE_CHECK(expr)                  \
     do {                                   \
@@ -44,8 +57,8 @@ struct KprofLaunch {
 
 // Records a CUDA event pair around the launches made in its lifetime when
 // the context's kernel profiler is active and `name` matches its filter.
-// The records are external, so that under stream capture they become event
-// record nodes of the graph (each replay re-records them).
+// Under stream capture the records become event record nodes of the graph
+// (each replay re-records them).
 struct KprofScope {
     secpe_ctx *ctx;
     int idx = -1;
@@ -56,10 +69,10 @@ struct KprofScope {
         idx = k.used++;
         k.launches++;
         k.bytes += bytes;
-        cudaEventRecordWithFlags(k.ev[2 * idx], c->stream, cudaEventRecordExternal);
+        kprof_record(k.ev[2 * idx], c->stream);
     }
     ~KprofScope() {
-        if (idx >= 0) cudaEventRecordWithFlags(ctx->kprof.ev[2 * idx + 1], ctx->stream, cudaEventRecordExternal);
+        if (idx >= 0) kprof_record(ctx->kprof.ev[2 * idx + 1], ctx->stream);
     }
 };
 
@@ -81,6 +94,11 @@ int ntt_limbset(secpe_ctx *ctx, const LimbSet &ls, bool inverse, const LimbSet *
 // N = 2^16 only: the row pass (last 8 stages of the forward NTT, first 8 of
 // the inverse) alone, in place.
 int ntt_rowpass_only(secpe_ctx *ctx, const LimbSet &ls, bool inverse);
+// One N = 2^16 pass (TuneSlot TUNE_COLPASS..TUNE_IROWPASS) of every limb of
+// ls, in place, with the context's launch configuration for it.
+int ntt16_pass(secpe_ctx *ctx, int slot, const LimbSet &ls);
+// One ModUp-shaped base-conversion pass over buf (ntt_fused.cu).
+int bconv_pass_probe(secpe_ctx *ctx, u64 *buf, int nitem, int ntgt);
 // Precision variant (ntt_tc.cu): NTT/INTT with the column pass on the tensor pipe.
 int ntt_limbset_tc(secpe_ctx *ctx, const LimbSet &ls, bool inverse);
 void tc_forget_ctx(const secpe_ctx *ctx);

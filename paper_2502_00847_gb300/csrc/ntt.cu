@@ -39,8 +39,8 @@ struct NttArgs {
 // ---------------------------------------------------------------- N = 2^16
 // Pass A: columns.  Tile = 16 adjacent columns c0..c0+15, all 256 rows.
 // thread t: col = t & 15, u = t >> 4.
-template <bool INV>
-__global__ void __launch_bounds__(256) k_ntt16_colpass(const __grid_constant__ NttArgs a) {
+template <bool INV, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_ntt16_colpass(const __grid_constant__ NttArgs a) {
     __shared__ u64 sm[4096];
     const long long lid = blockIdx.x / a.tiles;
     const int c0 = (blockIdx.x % a.tiles) * 16;
@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(256) k_ntt16_colpass(const __grid_constant__ N
 // each).  thread t: u = t & 15, row = t >> 4.  Shared layout per row is
 // padded (17 words per 16) so that both register assignments are free of
 // bank conflicts.
-template <bool INV>
-__global__ void __launch_bounds__(256) k_ntt16_rowpass(const __grid_constant__ NttArgs a) {
+template <bool INV, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_ntt16_rowpass(const __grid_constant__ NttArgs a) {
     __shared__ u64 sm[16 * 272];
     const long long lid = blockIdx.x / a.tiles;
     const int r0 = (blockIdx.x % a.tiles) * 16;
@@ -258,6 +258,49 @@ __global__ void k_scale_ninv(const __grid_constant__ NttArgs a, long long total)
 
 }  // namespace
 
+// One N = 2^16 pass with the context's tuned launch configuration.
+static int launch_pass16(secpe_ctx *ctx, int slot, const NttArgs &a, long long nl) {
+    const unsigned grid = (unsigned)(nl * 16);
+    const bool four = ctx->tune.ctas[slot] == 4;
+    void (*kf)(NttArgs) = nullptr;
+    const char *name = nullptr;
+    switch (slot) {
+        case TUNE_COLPASS:
+            kf = four ? k_ntt16_colpass<false, 4> : k_ntt16_colpass<false, 3>;
+            name = "k_ntt16_colpass<false>";
+            break;
+        case TUNE_ROWPASS:
+            kf = four ? k_ntt16_rowpass<false, 4> : k_ntt16_rowpass<false, 3>;
+            name = "k_ntt16_rowpass<false>";
+            break;
+        case TUNE_ICOLPASS:
+            kf = four ? k_ntt16_colpass<true, 4> : k_ntt16_colpass<true, 3>;
+            name = "k_ntt16_colpass<true>";
+            break;
+        case TUNE_IROWPASS:
+            kf = four ? k_ntt16_rowpass<true, 4> : k_ntt16_rowpass<true, 3>;
+            name = "k_ntt16_rowpass<true>";
+            break;
+        default: return SECPE_EINVAL;
+    }
+    SECPE_LAUNCH_AS(ctx, name, kf, grid, 256, 0, a);
+    return SECPE_OK;
+}
+
+int ntt16_pass(secpe_ctx *ctx, int slot, const LimbSet &ls) {
+    const long long nl = (long long)ls.nitem * ls.npoly * ls.nlimb;
+    if (ctx->log_n != 16 || nl == 0 || nl * 16 >= (1ll << 31)) return SECPE_EINVAL;
+    NttArgs a;
+    a.c = ctx->dev;
+    a.ls = ls;
+    a.src = ls;
+    a.has_src = 0;
+    a.tiles = 16;
+    a.scale_tab = nullptr;
+    a.scale_off = 0;
+    return launch_pass16(ctx, slot, a, nl);
+}
+
 int ntt_rowpass_only(secpe_ctx *ctx, const LimbSet &ls, bool inverse) {
     const long long nl = (long long)ls.nitem * ls.npoly * ls.nlimb;
     if (nl == 0) return SECPE_OK;
@@ -270,11 +313,7 @@ int ntt_rowpass_only(secpe_ctx *ctx, const LimbSet &ls, bool inverse) {
     a.tiles = 16;
     a.scale_tab = nullptr;
     a.scale_off = 0;
-    if (!inverse)
-        SECPE_LAUNCH(ctx, k_ntt16_rowpass<false>, (unsigned)(nl * 16), 256, 0, a);
-    else
-        SECPE_LAUNCH(ctx, k_ntt16_rowpass<true>, (unsigned)(nl * 16), 256, 0, a);
-    return SECPE_OK;
+    return launch_pass16(ctx, inverse ? TUNE_IROWPASS : TUNE_ROWPASS, a, nl);
 }
 
 LimbSet make_limbset(u64 *base, int nitem, long long item_stride, int npoly, long long poly_stride,
@@ -319,17 +358,17 @@ int ntt_limbset(secpe_ctx *ctx, const LimbSet &ls, bool inverse, const LimbSet *
         if (!inverse) {
             {
                 KprofScope kp(ctx, "ntt16_colpass", pass_bytes);
-                SECPE_LAUNCH(ctx, k_ntt16_colpass<false>, (unsigned)(nl * 16), 256, 0, a);
+                SECPE_CHECK(launch_pass16(ctx, TUNE_COLPASS, a, nl));
             }
             KprofScope kp(ctx, "ntt16_rowpass", pass_bytes);
-            SECPE_LAUNCH(ctx, k_ntt16_rowpass<false>, (unsigned)(nl * 16), 256, 0, a);
+            SECPE_CHECK(launch_pass16(ctx, TUNE_ROWPASS, a, nl));
         } else {
             {
                 KprofScope kp(ctx, "intt16_rowpass", pass_bytes);
-                SECPE_LAUNCH(ctx, k_ntt16_rowpass<true>, (unsigned)(nl * 16), 256, 0, a);
+                SECPE_CHECK(launch_pass16(ctx, TUNE_IROWPASS, a, nl));
             }
             KprofScope kp(ctx, "intt16_colpass", pass_bytes);
-            SECPE_LAUNCH(ctx, k_ntt16_colpass<true>, (unsigned)(nl * 16), 256, 0, a);
+            SECPE_CHECK(launch_pass16(ctx, TUNE_ICOLPASS, a, nl));
         }
         return SECPE_OK;
     }

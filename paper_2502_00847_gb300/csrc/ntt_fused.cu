@@ -41,8 +41,8 @@ struct BConvArgs {
     BConvSrc g[12];
 };
 
-template <int NS>
-__global__ void __launch_bounds__(256, 3) k_colpass_bconv(const __grid_constant__ BConvArgs a) {
+template <int NS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_colpass_bconv(const __grid_constant__ BConvArgs a) {
     __shared__ u64 sm[4096];
     const long long lid = blockIdx.x >> 4;
     const int c0 = (blockIdx.x & 15) * 16;
@@ -258,6 +258,29 @@ __global__ void __launch_bounds__(256, 3) k_rowpass_ip(const __grid_constant__ I
     }
 }
 
+template <int MINB>
+int launch_bconv_ns(secpe_ctx *ctx, const BConvArgs &a, int ns, unsigned grid) {
+    static const char *const names[10] = {"k_colpass_bconv<0>", "k_colpass_bconv<1>", "k_colpass_bconv<2>",
+                                          "k_colpass_bconv<3>", "k_colpass_bconv<4>", "k_colpass_bconv<5>",
+                                          "k_colpass_bconv<6>", "k_colpass_bconv<7>", "k_colpass_bconv<8>",
+                                          "k_colpass_bconv<9>"};
+    void (*kf)(BConvArgs) = nullptr;
+    switch (ns) {
+        case 1: kf = k_colpass_bconv<1, MINB>; break;
+        case 2: kf = k_colpass_bconv<2, MINB>; break;
+        case 3: kf = k_colpass_bconv<3, MINB>; break;
+        case 4: kf = k_colpass_bconv<4, MINB>; break;
+        case 5: kf = k_colpass_bconv<5, MINB>; break;
+        case 6: kf = k_colpass_bconv<6, MINB>; break;
+        case 7: kf = k_colpass_bconv<7, MINB>; break;
+        case 8: kf = k_colpass_bconv<8, MINB>; break;
+        case 9: kf = k_colpass_bconv<9, MINB>; break;
+        default: kf = k_colpass_bconv<0, MINB>; ns = 0;
+    }
+    SECPE_LAUNCH_AS(ctx, names[ns], kf, grid, 256, 0, a);
+    return SECPE_OK;
+}
+
 int launch_colpass_bconv(secpe_ctx *ctx, const BConvArgs &a) {
     const long long nl = (long long)a.ls.nitem * a.ls.npoly * a.ls.nlimb;
     if (nl == 0) return SECPE_OK;
@@ -266,25 +289,40 @@ int launch_colpass_bconv(secpe_ctx *ctx, const BConvArgs &a) {
         if (a.g[i].nsrc != ns) ns = 0;
     const unsigned grid = (unsigned)(nl * 16);
     KprofScope kp(ctx, "ntt16_colpass_bconv", 16.0 * ctx->n * nl);
-    switch (ns) {
-        case 1: SECPE_LAUNCH(ctx, k_colpass_bconv<1>, grid, 256, 0, a); break;
-        case 2: SECPE_LAUNCH(ctx, k_colpass_bconv<2>, grid, 256, 0, a); break;
-        case 3: SECPE_LAUNCH(ctx, k_colpass_bconv<3>, grid, 256, 0, a); break;
-        case 4: SECPE_LAUNCH(ctx, k_colpass_bconv<4>, grid, 256, 0, a); break;
-        case 5: SECPE_LAUNCH(ctx, k_colpass_bconv<5>, grid, 256, 0, a); break;
-        case 6: SECPE_LAUNCH(ctx, k_colpass_bconv<6>, grid, 256, 0, a); break;
-        case 7: SECPE_LAUNCH(ctx, k_colpass_bconv<7>, grid, 256, 0, a); break;
-        case 8: SECPE_LAUNCH(ctx, k_colpass_bconv<8>, grid, 256, 0, a); break;
-        case 9: SECPE_LAUNCH(ctx, k_colpass_bconv<9>, grid, 256, 0, a); break;
-        default: SECPE_LAUNCH(ctx, k_colpass_bconv<0>, grid, 256, 0, a);
-    }
-    return SECPE_OK;
+    if (ctx->tune.ctas[TUNE_BCONV] == 4) return launch_bconv_ns<4>(ctx, a, ns, grid);
+    return launch_bconv_ns<3>(ctx, a, ns, grid);
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------- host side
 bool fused_path(const secpe_ctx *ctx) { return ctx->log_n == 16; }
+
+// One base-conversion pass of the ModUp shape (alpha sources) over `nitem`
+// items of [alpha + ntgt] limbs at buf, for timing candidate launch
+// configurations (the data may be anything below the primes).
+int bconv_pass_probe(secpe_ctx *ctx, u64 *buf, int nitem, int ntgt) {
+    const int n = ctx->n, ns = ctx->alpha;
+    if (ns < 1 || ns > 16 || ntgt < 1 || ntgt > SECPE_MAX_LIMBSET) return SECPE_EINVAL;
+    BConvArgs a;
+    a.c = ctx->dev;
+    a.ngroups = 1;
+    BConvSrc &S = a.g[0];
+    S.base = buf;
+    S.is = (long long)(ns + ntgt) * n;
+    S.ps = 0;
+    S.nsrc = ns;
+    for (int r = 0; r < ns; r++) {
+        S.src_prime[r] = r;
+        S.pre[r] = 0;
+    }
+    S.hat = ctx->dev.mu_hat;
+    S.hat_stride = ctx->nprimes;
+    S.post = nullptr;
+    a.ls = make_limbset(buf + (size_t)ns * n, nitem, S.is, 1, 0, ntgt, 0);
+    for (int j = 0; j < ntgt; j++) a.ls.prime_of[j] = (int8_t)((ns + j) % ctx->nprimes);
+    return launch_colpass_bconv(ctx, a);
+}
 
 // ModUp + inner product for N = 2^16: pass A with the digit's base
 // conversion as prologue into ext, then pass B of every digit fused with the

@@ -23,7 +23,8 @@ EXPORTS = [
     "secpe_rescale", "secpe_rotate", "secpe_keyswitch", "secpe_refresh_testonly", "secpe_sign", "secpe_max",
     "secpe_ensemble_aggregate", "secpe_encrypted_argmax", "secpe_argmax_batch", "secpe_argmax_batch_capture",
     "secpe_graph_launch", "secpe_graph_destroy", "secpe_get_counters",
-    "secpe_reset_counters", "secpe_select_primes", "secpe_kprof_begin", "secpe_kprof_end", "secpe_kprof_report",
+    "secpe_reset_counters", "secpe_select_primes", "secpe_kprof_begin", "secpe_kprof_end", "secpe_kprof_report", "secpe_autotune",
+    "secpe_tuning_set",
     "secpe_keyswitch_batch", "secpe_mul_relin_batch", "secpe_rotate_batch", "secpe_rescale_batch",
     "secpe_rescale_noalloc", "secpe_server_create", "secpe_server_destroy", "secpe_server_submit",
     "secpe_server_cancel", "secpe_server_step", "secpe_server_poll", "secpe_server_wait", "secpe_server_forget",
@@ -62,6 +63,11 @@ class ServerStatsC(ctypes.Structure):
 class CountersC(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "rotations", "signs", "relins", "refreshes", "keyswitches", "launches")]
+
+
+class TuningC(ctypes.Structure):
+    _fields_ = [("n_kernels", ctypes.c_int32), ("name", (ctypes.c_char * 32) * 8),
+                ("ctas_per_sm", ctypes.c_int32 * 8), ("ms", (ctypes.c_float * 2) * 8)]
 
 
 class KprofC(ctypes.Structure):
@@ -121,6 +127,8 @@ def lib():
         "secpe_kprof_begin": (i32, [vp, ctypes.c_char_p, i32]),
         "secpe_kprof_end": (i32, [vp, P(KprofC)]),
         "secpe_kprof_report": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)]),
+        "secpe_autotune": (i32, [vp, P(TuningC), vp]),
+        "secpe_tuning_set": (i32, [vp, i32, i32]),
         "secpe_keyswitch_batch": (i32, [vp, vp, i32, P(CtBatchC), P(CtBatchC), vp]),
         "secpe_mul_relin_batch": (i32, [vp, vp, P(CtBatchC), P(CtBatchC), P(CtBatchC), vp]),
         "secpe_rotate_batch": (i32, [vp, vp, P(CtBatchC), i32, P(CtBatchC), vp]),
@@ -229,6 +237,17 @@ class Context:
         k = KprofC()
         _check(lib().secpe_kprof_end(self.h, ctypes.byref(k)), "secpe_kprof_end")
         return dict(launches=int(k.launches), total_ms=float(k.total_ms), bytes=float(k.bytes))
+
+    def autotune(self):
+        """Times the candidate launch configurations of the N = 2^16 kernels and
+        keeps the fastest; returns {kernel: {"ctas_per_sm", "ms_3", "ms_4"}}."""
+        t = TuningC()
+        _check(lib().secpe_autotune(self.h, ctypes.byref(t), _stream()), "secpe_autotune")
+        return {t.name[i].value.decode(): {"ctas_per_sm": int(t.ctas_per_sm[i]), "ms_3": float(t.ms[i][0]),
+                                           "ms_4": float(t.ms[i][1])} for i in range(t.n_kernels)}
+
+    def tuning_set(self, kernel, ctas_per_sm):
+        _check(lib().secpe_tuning_set(self.h, kernel, ctas_per_sm), "secpe_tuning_set")
 
     def kprof_report(self):
         """Per-kernel (name, launches, ms) of the last kprof_begin("*") .. kprof_end range."""

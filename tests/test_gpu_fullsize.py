@@ -231,3 +231,33 @@ def test_graph_captured_batch_replays_bit_exact(env):
         zd = secpe.decrypt(ctx, k2, b["z_out"], q.C)
         assert int(np.argmax(zd)) == int(np.argmax(q2.logits.mean(0)))
     g.close()
+
+
+def test_autotune_and_every_launch_configuration_bit_exact(env):
+    """secpe_autotune times both candidates of each tuned kernel and keeps
+    one; NTT/INTT and HMult give identical residues under 3 and 4 CTAs/SM."""
+    import torch
+    o, ctx, keys, secpe = env
+    rng = np.random.default_rng(44)
+    pidx = [(5 * i) % 28 for i in range(20)]
+    x = np.stack([rng.integers(0, o.primes[i], o.n, dtype=np.uint64) for i in pidx])
+    a_o = o.encrypt(rng.uniform(-1, 1, 8), seed=71)
+    outs = []
+    for v in (3, 4):
+        for k in range(5):
+            ctx.tuning_set(k, v)
+        t = torch.from_numpy(x.view(np.int64)).cuda()
+        secpe.ntt(ctx, t, pidx)
+        f = t.clone()
+        secpe.ntt(ctx, t, pidx, inverse=True)
+        a = to_gpu(secpe, ctx, a_o)
+        outs.append((f.cpu(), t.cpu(), secpe.mul_relin(ctx, keys, a, a).residues()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][1].numpy().view(np.uint64), x)
+    assert np.array_equal(outs[0][2], outs[1][2])
+    res = ctx.autotune()
+    assert set(res) == {"ntt16_colpass", "ntt16_rowpass", "intt16_colpass", "intt16_rowpass", "colpass_bconv"}
+    for r in res.values():
+        assert r["ctas_per_sm"] in (3, 4) and r["ms_3"] > 0 and r["ms_4"] > 0
+        assert r["ctas_per_sm"] == (4 if r["ms_4"] < r["ms_3"] else 3)
+    same(secpe.mul_relin(ctx, keys, to_gpu(secpe, ctx, a_o), to_gpu(secpe, ctx, a_o)), o.mul(a_o, a_o))
