@@ -68,8 +68,8 @@ __global__ void k_tensor(DevCtx c, const u64 *a, long long as, int cap_a, const 
     mac(s1, a0.y, b1.y);
     mac(s1, a1.y, b0.y);
     u64 t0 = redc(s0.hi, s0.lo, q, qi), t1 = redc(s1.hi, s1.lo, q, qi);
-    r.x = redc(mulhi64(t0, r2), t0 * r2, q, qi);
-    r.y = redc(mulhi64(t1, r2), t1 * r2, q, qi);
+    r.x = mont_mul(t0, r2, q, qi);
+    r.y = mont_mul(t1, r2, q, qi);
     st2(D + ps, r);
     r.x = mul_mod(a1.x, b1.x, q, qi, r2);
     r.y = mul_mod(a1.y, b1.y, q, qi, r2);
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256) k_lincomb(DevCtx c, const __grid_constant
 #pragma unroll
     for (int t = 0; t < NT; t++) {
         const u64 w = signed_mod(a.k[t][a.per_item ? item : 0], q, c.mu[i]);
-        wm[t] = redc(mulhi64(w, r2), w * r2, q, qi);  // w * 2^64 mod q
+        wm[t] = mont_mul(w, r2, q, qi);  // w * 2^64 mod q
         xp[t] = a.x[t] + item * a.xs[t] + ((long long)kk * a.cap[t] + i) * c.n;
     }
     u64 *op = a.o + item * a.os + ((long long)kk * a.cap_o + i) * c.n;
@@ -487,8 +487,8 @@ __global__ void k_ksk_gen(DevCtx c, const u64 *a, const u64 *e_ntt, const u64 *s
     u64 b = sub_mod(e_ntt[o], mul_mod(av, s[o], q, qi, r2), q);
     if (t >= lo && t < hi) b = add_mod(b, mul_mod(pmod[t], sp[o], q, qi, r2), q);
     const long long kp = (long long)c.nprimes * c.n;
-    key[o] = redc(mulhi64(b, r2), b * r2, q, qi);
-    key[kp + o] = redc(mulhi64(av, r2), av * r2, q, qi);
+    key[o] = mont_mul(b, r2, q, qi);
+    key[kp + o] = mont_mul(av, r2, q, qi);
 }
 
 // Montgomery form -> plain residues (key export)

@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(256, 3) k_rowpass_ip(const __grid_constant__ I
             const int e = threadIdx.x + 256 * i;
             const u64 v = own ? src[e] : sm[(e >> 8) * 272 + PADR(e & 255)];
             const u64 k0 = kb[e], k1 = kb[kpoly + e];
-            u64 p0 = redc(mulhi64(v, k0), v * k0, q, qinv);
-            u64 p1 = redc(mulhi64(v, k1), v * k1, q, qinv);
+            u64 p0 = mont_mul(v, k0, q, qinv);
+            u64 p1 = mont_mul(v, k1, q, qinv);
             if (jd) {
                 p0 = add_mod(p0, o0[e], q);
                 p1 = add_mod(p1, o1[e], q);
