@@ -382,24 +382,22 @@ int argmax_batch_impl(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query 
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return rr[x] > rr[y]; });
     Eval E{ctx, keys, {}, 0};
 
-    // 1. aggregation into Y (sorted order), level L
+    // 1. aggregation into Y (sorted order), level L: one launch sums every
+    // query's K inputs
     Ct Y;
     SECPE_CHECK(ct_alloc(ctx, nq_, L, ctx->scale, Y));
-    for (int s = 0; s < nq_; s++) {
-        const secpe_query &Q = q[order[s]];
-        CtB dst = ct_slice(Y, s, s + 1).v;
-        CtB c0 = {(u64 *)Q.cts[0].data, 1, 2ll * Q.cts[0].cap * n, Q.cts[0].cap, L, ctx->scale, n};
-        if (Q.K == 1) {
-            SECPE_CUDA(cudaMemcpy2DAsync(dst.data, sizeof(u64) * dst.cap * n, c0.data, sizeof(u64) * c0.cap * n,
-                                         sizeof(u64) * (L + 1) * n, 2, cudaMemcpyDeviceToDevice, ctx->stream));
-        } else {
-            CtB c1 = {(u64 *)Q.cts[1].data, 1, 2ll * Q.cts[1].cap * n, Q.cts[1].cap, L, ctx->scale, n};
-            SECPE_CHECK(launch_addsub(ctx, c0, c1, dst, L + 1, false));
-            for (int i = 2; i < Q.K; i++) {
-                CtB ci = {(u64 *)Q.cts[i].data, 1, 2ll * Q.cts[i].cap * n, Q.cts[i].cap, L, ctx->scale, n};
-                SECPE_CHECK(launch_addsub(ctx, dst, ci, dst, L + 1, false));
+    {
+        std::vector<const u64 *> src;
+        std::vector<int> cap, qoff(1, 0);
+        for (int s = 0; s < nq_; s++) {
+            const secpe_query &Q = q[order[s]];
+            for (int i = 0; i < Q.K; i++) {
+                src.push_back((const u64 *)Q.cts[i].data);
+                cap.push_back(Q.cts[i].cap);
             }
+            qoff.push_back((int)src.size());
         }
+        SECPE_CHECK(launch_sum_cts(ctx, src, cap, qoff, Y.v, L + 1));
     }
     std::vector<double> w(nq_);
     for (int s = 0; s < nq_; s++) {

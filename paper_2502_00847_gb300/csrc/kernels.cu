@@ -43,37 +43,78 @@ __global__ void k_addsub(DevCtx c, const u64 *a, long long as, const u64 *b, lon
     st2(o + oo, x);
 }
 
+// ------------------------------------------------------------ sum of ciphertexts
+// dst[qy] = sum of the ciphertexts src[qoff[qy] .. qoff[qy+1]) over limbs
+// 0..nl-1 of both polynomials (the ensemble sum of every query of a batch in
+// one launch); 8 residues per thread.
+constexpr int SUM_MAXP = 1536;
+struct SumArgs {
+    const u64 *src[SUM_MAXP];
+    int cap[SUM_MAXP];
+    int qoff[SECPE_MAX_BATCH_CONST + 1];
+    u64 *dst;
+    long long dstride;
+    int dcap, nl;
+};
+
+__global__ void __launch_bounds__(256) k_sum_cts(DevCtx c, const __grid_constant__ SumArgs a) {
+    const int qy = blockIdx.z;
+    const int i = blockIdx.y % a.nl, k = blockIdx.y / a.nl;
+    const u64 q = c.q[i];
+    const int p0 = a.qoff[qy], p1 = a.qoff[qy + 1];
+    u64 *D = a.dst + qy * a.dstride + ((long long)k * a.dcap + i) * c.n;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int e = 2 * (threadIdx.x + 256 * (blockIdx.x * 4 + j));
+        if (e >= c.n) break;
+        ulonglong2 s = ld2(a.src[p0] + ((long long)k * a.cap[p0] + i) * c.n + e);
+        for (int p = p0 + 1; p < p1; p++) {
+            const ulonglong2 v = ld2(a.src[p] + ((long long)k * a.cap[p] + i) * c.n + e);
+            s.x = add_mod(s.x, v.x, q);
+            s.y = add_mod(s.y, v.y, q);
+        }
+        st2(D + e, s);
+    }
+}
+
 // ------------------------------------------------------------ tensor
-// d[item][0..2][i] = (a0 b0, a0 b1 + a1 b0, a1 b1), d has cap nl.
-__global__ void k_tensor(DevCtx c, const u64 *a, long long as, int cap_a, const u64 *b, long long bs,
-                         int cap_b, u64 *d, int nl) {
+// d[item][0..2][i] = (a0 b0, a0 b1 + a1 b0, a1 b1), d has cap nl.  b0, b1 are
+// first brought to Montgomery form (b R), so that each product needs one
+// reduction: a b = redc(a * bR), and a0 b1 + a1 b0 = redc(a0 b1R + a1 b0R).
+// Each thread takes 8 residues (four 16-byte accesses a block-width apart).
+__global__ void __launch_bounds__(256) k_tensor(DevCtx c, const u64 *a, long long as, int cap_a, const u64 *b,
+                                                long long bs, int cap_b, u64 *d, int nl) {
     const int li = blockIdx.y;
     const int i = li % nl, item = li / nl;
-    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    if (e >= c.n) return;
     const u64 q = c.q[i], qi = c.qinv_neg[i], r2 = c.r2[i];
-    const u64 *A = a + item * as + (long long)i * c.n + e;
-    const u64 *Bp = b + item * bs + (long long)i * c.n + e;
-    const ulonglong2 a0 = ld2(A), a1 = ld2(A + (long long)cap_a * c.n);
-    const ulonglong2 b0 = ld2(Bp), b1 = ld2(Bp + (long long)cap_b * c.n);
-    u64 *D = d + (long long)item * 3 * nl * c.n + (long long)i * c.n + e;
-    const long long ps = (long long)nl * c.n;
-    ulonglong2 r;
-    r.x = mul_mod(a0.x, b0.x, q, qi, r2);
-    r.y = mul_mod(a0.y, b0.y, q, qi, r2);
-    st2(D, r);
-    acc128 s0 = {0, 0}, s1 = {0, 0};
-    mac(s0, a0.x, b1.x);
-    mac(s0, a1.x, b0.x);
-    mac(s1, a0.y, b1.y);
-    mac(s1, a1.y, b0.y);
-    u64 t0 = redc(s0.hi, s0.lo, q, qi), t1 = redc(s1.hi, s1.lo, q, qi);
-    r.x = mont_mul(t0, r2, q, qi);
-    r.y = mont_mul(t1, r2, q, qi);
-    st2(D + ps, r);
-    r.x = mul_mod(a1.x, b1.x, q, qi, r2);
-    r.y = mul_mod(a1.y, b1.y, q, qi, r2);
-    st2(D + 2 * ps, r);
+    const u64 *A = a + item * as + (long long)i * c.n;
+    const u64 *Bp = b + item * bs + (long long)i * c.n;
+    u64 *D = d + (long long)item * 3 * nl * c.n + (long long)i * c.n;
+    const long long ps = (long long)nl * c.n, pa = (long long)cap_a * c.n, pb = (long long)cap_b * c.n;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int e = 2 * (threadIdx.x + 256 * (blockIdx.x * 4 + j));
+        if (e >= c.n) break;
+        const ulonglong2 a0 = ld2(A + e), a1 = ld2(A + pa + e);
+        const ulonglong2 b0 = ld2(Bp + e), b1 = ld2(Bp + pb + e);
+        ulonglong2 r0, r1, r2v;
+#define SECPE_TENSOR_LANE(f)                                   \
+    {                                                          \
+        const u64 b0m = mont_mul(b0.f, r2, q, qi);             \
+        const u64 b1m = mont_mul(b1.f, r2, q, qi);             \
+        r0.f = mont_mul(a0.f, b0m, q, qi);                     \
+        r2v.f = mont_mul(a1.f, b1m, q, qi);                    \
+        acc128 s = mul_full(a0.f, b1m);                        \
+        mac(s, a1.f, b0m);                                     \
+        r1.f = redc(s.hi, s.lo, q, qi);                        \
+    }
+        SECPE_TENSOR_LANE(x)
+        SECPE_TENSOR_LANE(y)
+#undef SECPE_TENSOR_LANE
+        st2(D + e, r0);
+        st2(D + ps + e, r1);
+        st2(D + 2 * ps + e, r2v);
+    }
 }
 
 // ------------------------------------------------------------ constants
@@ -601,10 +642,45 @@ int launch_addsub(secpe_ctx *ctx, const CtB &a, const CtB &b, const CtB &o, int 
     return SECPE_OK;
 }
 
+int launch_sum_cts(secpe_ctx *ctx, const std::vector<const u64 *> &src, const std::vector<int> &cap,
+                   const std::vector<int> &qoff, const CtB &dst, int nl) {
+    const int nq = (int)qoff.size() - 1;
+    if (nq < 1 || nq > dst.B || nl < 1 || nl > dst.cap || src.size() != cap.size() || qoff[0] != 0 ||
+        qoff[nq] != (int)src.size())
+        return SECPE_EINVAL;
+    int q0 = 0;
+    while (q0 < nq) {
+        // as many queries as the pointer table holds
+        int q1 = q0;
+        while (q1 < nq && q1 - q0 < SECPE_MAX_BATCH_CONST && qoff[q1 + 1] - qoff[q0] <= SUM_MAXP) q1++;
+        if (q1 == q0) return SECPE_EINVAL;  // one query with more inputs than the table
+        SumArgs sa;
+        const int base = qoff[q0];
+        for (int p = base; p < qoff[q1]; p++) {
+            if (!src[p] || cap[p] < nl) return SECPE_EINVAL;
+            sa.src[p - base] = src[p];
+            sa.cap[p - base] = cap[p];
+        }
+        for (int qq = q0; qq <= q1; qq++) {
+            if (qq < q1 && qoff[qq + 1] <= qoff[qq]) return SECPE_EINVAL;
+            sa.qoff[qq - q0] = qoff[qq] - base;
+        }
+        sa.dst = dst.data + (long long)q0 * dst.stride;
+        sa.dstride = dst.stride;
+        sa.dcap = dst.cap;
+        sa.nl = nl;
+        const dim3 grid((unsigned)((ctx->n + 2047) / 2048), (unsigned)(2 * nl), (unsigned)(q1 - q0));
+        KprofScope kp(ctx, "ew_sum", 16.0 * ctx->n * nl * (qoff[q1] - base + (q1 - q0)));
+        SECPE_LAUNCH(ctx, k_sum_cts, grid, 256, 0, ctx->dev, sa);
+        q0 = q1;
+    }
+    return SECPE_OK;
+}
+
 int launch_tensor(secpe_ctx *ctx, const CtB &a, const CtB &b, u64 *d, int nl) {
     KprofScope kp(ctx, "ew_tensor", 56.0 * ctx->n * a.B * nl);
-    SECPE_LAUNCH(ctx, k_tensor, limb_grid(ctx->n, 2, (long long)a.B * nl), 256, 0, ctx->dev, a.data, a.stride,
-                 a.cap, b.data, b.stride, b.cap, d, nl);
+    const dim3 grid((unsigned)((ctx->n + 2047) / 2048), (unsigned)((long long)a.B * nl));
+    SECPE_LAUNCH(ctx, k_tensor, grid, 256, 0, ctx->dev, a.data, a.stride, a.cap, b.data, b.stride, b.cap, d, nl);
     return SECPE_OK;
 }
 

@@ -21,6 +21,11 @@ struct PrimeList {
 
 int launch_addsub(secpe_ctx *ctx, const CtB &a, const CtB &b, const CtB &o, int nl, bool sub, int npoly = 2);
 int launch_tensor(secpe_ctx *ctx, const CtB &a, const CtB &b, u64 *d, int nl);
+// Item q of dst (limbs 0..nl-1 of both polynomials) = the sum of the
+// ciphertexts src[qoff[q] .. qoff[q+1]) (each [2][cap[p]][N]); queries are
+// launched in chunks that fit one pointer table.
+int launch_sum_cts(secpe_ctx *ctx, const std::vector<const u64 *> &src, const std::vector<int> &cap,
+                   const std::vector<int> &qoff, const CtB &dst, int nl);
 // o = sum_t xs[t] * ks[t] (one constant per term, or one per item) over
 // limbs 0..nl-1 of both polynomials, nt in {1, 2}.
 int launch_lincomb(secpe_ctx *ctx, const CtB *xs, const std::vector<long long> *ks, int nt, const CtB &o, int nl);

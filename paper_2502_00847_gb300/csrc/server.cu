@@ -137,23 +137,18 @@ int run_group(secpe_server *s, std::vector<QState *> &g) {
         Ct Y;
         SECPE_CHECK(ct_alloc(ctx, B, L, ctx->scale, Y));
         std::vector<double> w(B);
+        std::vector<const u64 *> src;
+        std::vector<int> cap, qoff(1, 0);
         for (int b = 0; b < B; b++) {
             const secpe_query &Q = g[b]->q;
-            CtB dst = ct_slice(Y, b, b + 1).v;
-            CtB c0 = {(u64 *)Q.cts[0].data, 1, 2ll * Q.cts[0].cap * n, Q.cts[0].cap, L, ctx->scale, n};
-            if (Q.K == 1) {
-                SECPE_CUDA(cudaMemcpy2DAsync(dst.data, sizeof(u64) * dst.cap * n, c0.data, sizeof(u64) * c0.cap * n,
-                                             sizeof(u64) * (L + 1) * n, 2, cudaMemcpyDeviceToDevice, ctx->stream));
-            } else {
-                CtB c1 = {(u64 *)Q.cts[1].data, 1, 2ll * Q.cts[1].cap * n, Q.cts[1].cap, L, ctx->scale, n};
-                SECPE_CHECK(launch_addsub(ctx, c0, c1, dst, L + 1, false));
-                for (int i = 2; i < Q.K; i++) {
-                    CtB ci = {(u64 *)Q.cts[i].data, 1, 2ll * Q.cts[i].cap * n, Q.cts[i].cap, L, ctx->scale, n};
-                    SECPE_CHECK(launch_addsub(ctx, dst, ci, dst, L + 1, false));
-                }
+            for (int i = 0; i < Q.K; i++) {
+                src.push_back((const u64 *)Q.cts[i].data);
+                cap.push_back(Q.cts[i].cap);
             }
+            qoff.push_back((int)src.size());
             w[b] = 1.0 / (Q.K * (Q.d_max - Q.d_min));
         }
+        SECPE_CHECK(launch_sum_cts(ctx, src, cap, qoff, Y.v, L + 1));
         Ct Yn, rot, dup;
         SECPE_CHECK(E.mul_const(Y, w, ctx->scale, L - 1, Yn));
         Y = Ct();
