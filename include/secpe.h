@@ -324,10 +324,11 @@ int secpe_reset_counters(secpe_ctx *ctx);
 /* Launch configurations of the N = 2^16 kernels: for each tuned kernel (the
  * four transform passes and the base-conversion pass) the candidates are 3
  * and 4 CTAs per SM (at most 80 or 64 registers per thread).
- * secpe_autotune times every candidate with CUDA events on a zero-filled
- * scratch batch of 16 x 32 limbs (the data does not change the work), keeps
- * the fastest for this context, and reports them in *out (host, may be
- * null).  It synchronises `stream` (it cannot be captured).  For other ring
+ * secpe_autotune times the candidates alternately with CUDA events on a
+ * zero-filled scratch batch of 64 x 32 limbs (1 GiB, larger than L2; the data
+ * does not change the work), takes the median of 5 launches each, keeps 4
+ * CTAs per SM only where it is more than 3% faster, and reports the choice in
+ * *out (host, may be null); it needs 1 GiB of free device memory.  It synchronises `stream` (it cannot be captured).  For other ring
  * sizes there is nothing to tune and n_kernels = 0.  Untuned contexts use 3
  * CTAs per SM.  Every configuration computes identical results. */
 typedef struct {

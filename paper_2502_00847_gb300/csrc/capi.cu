@@ -521,7 +521,8 @@ extern "C" int secpe_autotune(secpe_ctx *ctx, secpe_tuning *out, void *stream) {
     if (out) std::memset(out, 0, sizeof(*out));
     if (ctx->log_n != 16) return SECPE_OK;
     CallScope cs(ctx, stream);
-    const int n = ctx->n, nitem = 16, nlimb = 32;
+    // 64 items of 32 limbs (1 GiB): larger than L2, like the batched workload
+    const int n = ctx->n, nitem = 64, nlimb = 32, reps = 5;
     DevBuf buf;
     SECPE_CHECK(buf.alloc(ctx, sizeof(u64) * (size_t)nitem * nlimb * n));
     SECPE_CUDA(cudaMemsetAsync(buf.p, 0, buf.bytes, ctx->stream));
@@ -536,23 +537,32 @@ extern "C" int secpe_autotune(secpe_ctx *ctx, secpe_tuning *out, void *stream) {
     const secpe_counters saved = ctx->counters;
     int st = SECPE_OK;
     float ms[TUNE_NSLOTS][2] = {};
+    auto run = [&](int slot) {
+        return slot == TUNE_BCONV ? bconv_pass_probe(ctx, buf.u(), nitem, nlimb - ctx->alpha)
+                                  : ntt16_pass(ctx, slot, ls);
+    };
     for (int slot = 0; slot < TUNE_NSLOTS && st == SECPE_OK; slot++) {
-        for (int v = 0; v < 2 && st == SECPE_OK; v++) {
+        // the candidates alternate, so that clock and thermal drift hit both;
+        // each keeps the median of its launch times
+        std::vector<float> t[2];
+        for (int r = 0; r < 2 * reps + 2 && st == SECPE_OK; r++) {
+            const int v = r & 1;
             ctx->tune.ctas[slot] = 3 + v;
-            auto run = [&]() {
-                return slot == TUNE_BCONV ? bconv_pass_probe(ctx, buf.u(), nitem, nlimb - ctx->alpha)
-                                          : ntt16_pass(ctx, slot, ls);
-            };
-            st = run();  // warm-up
-            if (st == SECPE_OK && cudaEventRecord(e0, ctx->stream) != cudaSuccess) st = SECPE_ECUDA;
-            for (int r = 0; r < 5 && st == SECPE_OK; r++) st = run();
+            float m = 0.f;
+            if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) st = SECPE_ECUDA;
+            if (st == SECPE_OK) st = run(slot);
             if (st == SECPE_OK && (cudaEventRecord(e1, ctx->stream) != cudaSuccess ||
                                    cudaEventSynchronize(e1) != cudaSuccess ||
-                                   cudaEventElapsedTime(&ms[slot][v], e0, e1) != cudaSuccess))
+                                   cudaEventElapsedTime(&m, e0, e1) != cudaSuccess))
                 st = SECPE_ECUDA;
-            ms[slot][v] /= 5.0f;
+            if (r >= 2) t[v].push_back(m);  // the first round of each is a warm-up
         }
-        ctx->tune.ctas[slot] = ms[slot][1] < ms[slot][0] ? 4 : 3;
+        for (int v = 0; v < 2 && st == SECPE_OK; v++) {
+            std::sort(t[v].begin(), t[v].end());
+            ms[slot][v] = t[v][t[v].size() / 2];
+        }
+        // 4 CTAs per SM only for a clear win (it caps registers at 64)
+        ctx->tune.ctas[slot] = ms[slot][1] < 0.97f * ms[slot][0] ? 4 : 3;
     }
     ctx->counters = saved;
     cudaEventDestroy(e0);

@@ -259,5 +259,5 @@ def test_autotune_and_every_launch_configuration_bit_exact(env):
     assert set(res) == {"ntt16_colpass", "ntt16_rowpass", "intt16_colpass", "intt16_rowpass", "colpass_bconv"}
     for r in res.values():
         assert r["ctas_per_sm"] in (3, 4) and r["ms_3"] > 0 and r["ms_4"] > 0
-        assert r["ctas_per_sm"] == (4 if r["ms_4"] < r["ms_3"] else 3)
+        assert r["ctas_per_sm"] == (4 if r["ms_4"] < 0.97 * r["ms_3"] else 3)
     same(secpe.mul_relin(ctx, keys, to_gpu(secpe, ctx, a_o), to_gpu(secpe, ctx, a_o)), o.mul(a_o, a_o))
