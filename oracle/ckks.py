@@ -600,27 +600,31 @@ class Oracle:
         A = self.lincomb([(x, c1), (x3, c3)], s_out, lv - 4)
         return self.add(A, TU)
 
-    def sign(self, x, out_levels):
+    def sign(self, x, out_levels, last_factor=1.0):
         """Sign(x) = f^df(g^dg(x)) (SecPE Eq. comp); before each polynomial,
-        refresh if fewer than 4 (+ out_levels for the last) levels remain."""
+        refresh if fewer than 4 (+ out_levels for the last) levels remain.
+        The last polynomial's coefficients are multiplied by last_factor
+        (last_factor * Sign(x) at no extra level)."""
         self.counters["signs"] += 1
         g, f = sign_coeffs_float()
         polys = [g] * self.p.sign_dg + [f] * self.p.sign_df
         for i, c in enumerate(polys):
-            need = 4 + (out_levels if i == len(polys) - 1 else 0)
+            last = i == len(polys) - 1
+            need = 4 + (out_levels if last else 0)
             x = self.ensure(x, need)
-            x = self.poly9(x, c, self.p.scale)
+            x = self.poly9(x, [last_factor * ci for ci in c] if last else c, self.p.scale)
         return x
 
     def max(self, a, y):
-        """Max(a, y) = (a+y)/2 + (a-y)/2 * Sign(a-y) (SecPE Eq. max).
-        t = d * Sign(d) with d = a - y encodes d*s at scale S; declaring its
-        scale 2S makes it encode d*s/2 at no cost.  u = (a+y) * 1/2 is then
-        brought to t's level with scale exactly 2S, and max = t + u."""
+        """Max(a, y) = (a+y)/2 + (a-y)/2 * Sign(a-y) (SecPE Eq. max),
+        computed as (a+y)*1/2 + d * (Sign(d)/2) with d = a - y: the 1/2 of the
+        second term is folded into the coefficients of Sign's last
+        polynomial, so t = d * (Sign(d)/2) keeps d's scale (READING: no level
+        is spent on it, and the scale does not grow from round to round);
+        u = (a+y) * 1/2 is brought to t's level and scale, max = t + u."""
         d = self.sub(a, y)
-        s = self.sign(d, 1)
+        s = self.sign(d, 1, last_factor=0.5)
         t = self.mul(d, s)
-        t.scale = 2.0 * t.scale
         u = self.mul_const(self.add(a, y), 0.5, t.scale, t.level)
         return self.add(t, u)
 

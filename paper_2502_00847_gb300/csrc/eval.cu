@@ -297,29 +297,36 @@ int Eval::poly9(const Ct &x, const double *c, double s_out, Ct &out) {
     return add(A, TU, out);
 }
 
-int Eval::sign(const Ct &x, int out_levels, Ct &out) {
+// The last polynomial's coefficients are multiplied by last_factor, so the
+// result is last_factor * Sign(x) at no extra level.
+int Eval::sign(const Ct &x, int out_levels, Ct &out, double last_factor) {
     double g[5], f[5];
     sign_coeffs(g, f);
     ctx->counters.signs += x.B();
     const int np = ctx->p.sign_dg + ctx->p.sign_df;
     Ct cur = x;
     for (int i = 0; i < np; i++) {
-        const int need = 4 + (i == np - 1 ? out_levels : 0);
+        const bool last = i == np - 1;
+        const int need = 4 + (last ? out_levels : 0);
+        double c[5];
+        for (int k = 0; k < 5; k++) c[k] = (i < ctx->p.sign_dg ? g[k] : f[k]) * (last ? last_factor : 1.0);
         Ct e, p;
         SECPE_CHECK(ensure(cur, need, e));
-        SECPE_CHECK(poly9(e, i < ctx->p.sign_dg ? g : f, ctx->scale, p));
+        SECPE_CHECK(poly9(e, c, ctx->scale, p));
         cur = p;
     }
     out = cur;
     return SECPE_OK;
 }
 
+// Max(a, y) = (a+y)/2 + d * (Sign(d)/2), d = a - y: the 1/2 of the second
+// term is folded into Sign's last polynomial, so t = d * (Sign(d)/2) keeps
+// d's scale; (a+y) * 1/2 is brought to t's level and scale.
 int Eval::max(const Ct &a, const Ct &y, Ct &out) {
     Ct d, s, t, apy, u;
     SECPE_CHECK(sub(a, y, d));
-    SECPE_CHECK(sign(d, 1, s));
+    SECPE_CHECK(sign(d, 1, s, 0.5));
     SECPE_CHECK(mul(d, s, t));
-    t.v.scale = 2.0 * t.v.scale;
     SECPE_CHECK(add(a, y, apy));
     SECPE_CHECK(mul_const(apy, {0.5}, t.scale(), t.level(), u));
     return add(t, u, out);

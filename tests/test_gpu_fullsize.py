@@ -102,7 +102,9 @@ def test_micro_keyswitch_dnum3_bit_exact():
 def test_batched_argmax_mix(env):
     o, ctx, keys, secpe = env
     qs = workloads.argmax_queries(5, seed=4, K_choices=(4, 8), C_choices=(2, 3, 6, 14))
-    rot = sorted({-(1 << (q.C - 1).bit_length()) for q in qs} | {1 << i for i in range(4)})
+    # and two queries with the largest class count of the mix (6 QuickMax rounds)
+    qs += workloads.argmax_queries(2, seed=9, K_choices=(4,), C_choices=(64,))
+    rot = sorted({-(1 << (q.C - 1).bit_length()) for q in qs} | {1 << i for i in range(6)})
     k2 = secpe.Keys(ctx, 99, rot)
     inputs = [[secpe.encrypt_logits(ctx, k2, q.logits[i], q.d_min, q.enc_seeds[i]) for i in range(q.K)]
               for q in qs]

@@ -10,7 +10,7 @@ from paper_2502_00847_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
 
-ROT = [1, 2, 4, -2, -4, -8, 3]
+ROT = [1, 2, 4, -2, -4, -8, 3, 8, 16, 32, -64]
 TOL_Z = 2.0 ** -12
 
 
@@ -160,7 +160,7 @@ def test_sign_and_max_bit_exact(env):
     assert ridx == o.ridx
 
 
-@pytest.mark.parametrize("C,K,seed", [(2, 5, 1), (3, 4, 2), (4, 2, 3), (2, 1, 4)])
+@pytest.mark.parametrize("C,K,seed", [(2, 5, 1), (3, 4, 2), (4, 2, 3), (2, 1, 4), (33, 3, 21)])
 def test_toy_ensemble_argmax_bit_exact(env, C, K, seed):
     o, ctx, keys, secpe = env
     q = workloads.toy_query(seed=seed, K=K, C=C)

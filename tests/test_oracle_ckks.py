@@ -192,7 +192,7 @@ def test_op_counts_match_paper_formula():
                   log_scale=50).slots == sb["slots"]
 
 
-@pytest.mark.parametrize("C,seed", [(2, 1), (3, 2)])
+@pytest.mark.parametrize("C,seed", [(2, 1), (3, 2), (33, 3)])
 def test_toy_argmax_circuit(C, seed):
     from oracle import TOY
     o = Oracle(TOY)
@@ -218,6 +218,22 @@ def test_toy_argmax_circuit(C, seed):
     assert np.max(np.abs(zd - zp)) < 2.0**-12
     assert int(np.argmax(zd)) == int(np.argmax(logits.mean(0)))
     assert zd.max() > 0.5 and np.sort(zd)[-2] < 0.5
+
+
+def test_max_keeps_the_scale(toy_oracle):
+    """Max folds its 1/2 into Sign's last polynomial: the output scale stays
+    the input scale (up to the q_l / Delta drift of one rescale), so QuickMax
+    rounds do not inflate it, and the value is Max within the Sign bound."""
+    o = toy_oracle
+    rng = np.random.default_rng(12)
+    v, w = rng.uniform(-0.5, 0.5, 32), rng.uniform(-0.5, 0.5, 32)
+    a, y = o.encrypt(v, seed=51), o.encrypt(w, seed=52)
+    o.qseed, o.ridx = 5, 0
+    m = o.max(a, y)
+    assert abs(np.log2(m.scale) - np.log2(o.p.scale)) < 1e-3
+    assert np.max(np.abs(o.decrypt(m, 32) - plainsim.vmax(v, w))) < 2.0**-12
+    m2 = o.max(o.rotate(m, 1), m)
+    assert abs(np.log2(m2.scale) - np.log2(o.p.scale)) < 1e-3
 
 
 def test_plainsim_argmax_exact_on_margins():
