@@ -94,6 +94,14 @@ int secpe_ctx_n(const secpe_ctx *ctx);
 /* Device-side status word (0 = ok, else a SECPE_E* recorded by a kernel);
  * synchronises `stream` first, then clears the word. */
 int secpe_stream_status(secpe_ctx *ctx, void *stream, int *device_status);
+/* Self-test of the bounded device-side wait that the kernels with bulk
+ * copies use: a one-CTA kernel arms a shared-memory mbarrier for one arrival,
+ * performs that arrival only when `arrive` is non-zero, and waits for it with
+ * at most `polls` polls (1 .. 4194304).  Without the arrival the wait runs
+ * out, the kernel records SECPE_ETIMEOUT in the status word (read it with
+ * secpe_stream_status) and returns; the context stays usable.  Nothing
+ * faults, traps or hangs. */
+int secpe_device_wait_selftest(secpe_ctx *ctx, int arrive, int64_t polls, void *stream);
 const char *secpe_strerror(int code);
 
 /* ---- keys ------------------------------------------------------------- */

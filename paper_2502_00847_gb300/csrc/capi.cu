@@ -110,6 +110,12 @@ extern "C" const char *secpe_strerror(int code) {
     }
 }
 
+extern "C" int secpe_device_wait_selftest(secpe_ctx *ctx, int arrive, int64_t polls, void *stream) {
+    if (!ctx || polls < 1 || polls > (1 << 22)) return SECPE_EINVAL;
+    CallScope cs(ctx, stream);
+    return finish(ctx, wait_selftest(ctx, arrive, (long)polls));
+}
+
 extern "C" int secpe_stream_status(secpe_ctx *ctx, void *stream, int *device_status) {
     if (!ctx || !device_status) return SECPE_EINVAL;
     SECPE_CUDA(cudaStreamSynchronize((cudaStream_t)stream));

@@ -97,6 +97,8 @@ int ntt_rowpass_only(secpe_ctx *ctx, const LimbSet &ls, bool inverse);
 // One N = 2^16 pass (TuneSlot TUNE_COLPASS..TUNE_IROWPASS) of every limb of
 // ls, in place, with the context's launch configuration for it.
 int ntt16_pass(secpe_ctx *ctx, int slot, const LimbSet &ls);
+// Bounded-wait self-test kernel (ntt_fused.cu).
+int wait_selftest(secpe_ctx *ctx, int arrive, long polls);
 // One ModUp-shaped base-conversion pass over buf (ntt_fused.cu).
 int bconv_pass_probe(secpe_ctx *ctx, u64 *buf, int nitem, int ntgt);
 // Precision variant (ntt_tc.cu): NTT/INTT with the column pass on the tensor pipe.

@@ -141,9 +141,9 @@ static __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t par
         : "memory");
     return ok != 0;
 }
-// Waits for phase `parity` of the barrier; false after SECPE_WAIT_LIMIT polls.
-static __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (long i = 0; i < SECPE_WAIT_LIMIT; i++)
+// Waits for phase `parity` of the barrier; false after `limit` polls.
+static __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long limit = SECPE_WAIT_LIMIT) {
+    for (long i = 0; i < limit; i++)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

@@ -293,10 +293,31 @@ int launch_colpass_bconv(secpe_ctx *ctx, const BConvArgs &a) {
     return launch_bconv_ns<3>(ctx, a, ns, grid);
 }
 
+// Self-test of the bounded device wait used by the bulk-copy kernels: one
+// CTA arms an mbarrier for one arrival and, when `arrive`, performs it; every
+// thread then waits with the same bounded wait (at most `polls` polls).  A
+// wait that runs out records SECPE_ETIMEOUT in the status word and the kernel
+// returns; nothing is in flight.
+__global__ void k_wait_selftest(const __grid_constant__ DevCtx c, int arrive, long polls) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (arrive && threadIdx.x == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar)) : "memory");
+    const bool ok = mbar_wait(&bar, 0, polls);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicCAS(c.status, 0, SECPE_ETIMEOUT);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- host side
 bool fused_path(const secpe_ctx *ctx) { return ctx->log_n == 16; }
+
+int wait_selftest(secpe_ctx *ctx, int arrive, long polls) {
+    if (polls < 1 || polls > SECPE_WAIT_LIMIT) return SECPE_EINVAL;
+    SECPE_LAUNCH(ctx, k_wait_selftest, 1, 128, 0, ctx->dev, arrive ? 1 : 0, polls);
+    return SECPE_OK;
+}
 
 // One base-conversion pass of the ModUp shape (alpha sources) over `nitem`
 // items of [alpha + ntgt] limbs at buf, for timing candidate launch

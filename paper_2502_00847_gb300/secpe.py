@@ -24,7 +24,7 @@ EXPORTS = [
     "secpe_ensemble_aggregate", "secpe_encrypted_argmax", "secpe_argmax_batch", "secpe_argmax_batch_capture",
     "secpe_graph_launch", "secpe_graph_destroy", "secpe_get_counters",
     "secpe_reset_counters", "secpe_select_primes", "secpe_kprof_begin", "secpe_kprof_end", "secpe_kprof_report", "secpe_autotune",
-    "secpe_tuning_set",
+    "secpe_tuning_set", "secpe_device_wait_selftest",
     "secpe_keyswitch_batch", "secpe_mul_relin_batch", "secpe_rotate_batch", "secpe_rescale_batch",
     "secpe_rescale_noalloc", "secpe_server_create", "secpe_server_destroy", "secpe_server_submit",
     "secpe_server_cancel", "secpe_server_step", "secpe_server_poll", "secpe_server_wait", "secpe_server_forget",
@@ -129,6 +129,7 @@ def lib():
         "secpe_kprof_report": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)]),
         "secpe_autotune": (i32, [vp, P(TuningC), vp]),
         "secpe_tuning_set": (i32, [vp, i32, i32]),
+        "secpe_device_wait_selftest": (i32, [vp, i32, ctypes.c_int64, vp]),
         "secpe_keyswitch_batch": (i32, [vp, vp, i32, P(CtBatchC), P(CtBatchC), vp]),
         "secpe_mul_relin_batch": (i32, [vp, vp, P(CtBatchC), P(CtBatchC), P(CtBatchC), vp]),
         "secpe_rotate_batch": (i32, [vp, vp, P(CtBatchC), i32, P(CtBatchC), vp]),
@@ -260,6 +261,10 @@ class Context:
             name, n, ms = line.split("\t")
             rows.append((name, int(n), float(ms)))
         return rows
+
+    def device_wait_selftest(self, arrive, polls=1 << 16):
+        _check(lib().secpe_device_wait_selftest(self.h, 1 if arrive else 0, polls, _stream()),
+               "secpe_device_wait_selftest")
 
     def stream_status(self):
         v = ctypes.c_int32()

@@ -256,3 +256,22 @@ def test_kernel_profiler_report(env):
     assert rows and all(name.startswith("k_") and n > 0 and ms >= 0 for name, n, ms in rows)
     assert sum(n for _, n, _ in rows) == k["launches"] == ctx.counters()["launches"]
     assert [r[2] for r in rows] == sorted((r[2] for r in rows), reverse=True)
+
+
+def test_bounded_device_wait_reports_timeout(env):
+    """The bounded mbarrier wait of the bulk-copy kernels: with the arrival the
+    wait completes (status 0); without it the wait runs out after its poll
+    limit, the kernel records SECPE_ETIMEOUT (read and cleared by
+    secpe_stream_status) and returns, and the context keeps working."""
+    o, ctx, keys, secpe = env
+    assert ctx.stream_status() == 0
+    ctx.device_wait_selftest(True, polls=1 << 16)
+    assert ctx.stream_status() == 0
+    ctx.device_wait_selftest(False, polls=1 << 12)
+    assert ctx.stream_status() == -7
+    assert ctx.stream_status() == 0
+    with pytest.raises(secpe.SecpeError) as e:
+        ctx.device_wait_selftest(False, polls=0)
+    assert e.value.code == -1
+    a_o = o.encrypt(np.random.default_rng(9).uniform(-1, 1, 8), seed=91)
+    same(secpe.rescale(ctx, to_gpu(secpe, ctx, a_o)), o.rescale(a_o))
