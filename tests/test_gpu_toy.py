@@ -275,3 +275,23 @@ def test_bounded_device_wait_reports_timeout(env):
     assert e.value.code == -1
     a_o = o.encrypt(np.random.default_rng(9).uniform(-1, 1, 8), seed=91)
     same(secpe.rescale(ctx, to_gpu(secpe, ctx, a_o)), o.rescale(a_o))
+
+
+def test_toy_batch_many_inputs_sum_in_chunks(env):
+    """110 queries of K = 16 (1,760 input ciphertexts, more than one launch of
+    the ensemble sum holds): every index is the exact argmax, and queries in
+    both chunks equal the one-query path bit for bit."""
+    o, ctx, keys, secpe = env
+    qs = [workloads.toy_query(seed=300 + i, K=16, C=2 + i % 3) for i in range(110)]
+    inputs = [[secpe.encrypt_logits(ctx, keys, q.logits[i], q.d_min, q.enc_seeds[i]) for i in range(q.K)]
+              for q in qs]
+    batch = [dict(cts=cts, C=q.C, d_min=q.d_min, d_max=q.d_max, qseed=q.qseed, z_out=ctx.new_ct())
+             for q, cts in zip(qs, inputs)]
+    secpe.argmax_batch(ctx, keys, batch)
+    for q, b in zip(qs, batch):
+        assert int(np.argmax(secpe.decrypt(ctx, keys, b["z_out"], q.C))) == int(np.argmax(q.logits.mean(0)))
+    for i in (0, 95, 109):
+        y = secpe.ensemble_aggregate(ctx, inputs[i], qs[i].d_min, qs[i].d_max)
+        z = secpe.encrypted_argmax(ctx, keys, y, qs[i].C, qs[i].qseed)
+        assert z.level == batch[i]["z_out"].level
+        assert np.array_equal(z.residues(), batch[i]["z_out"].residues())
