@@ -226,6 +226,8 @@ int Eval::refresh(const Ct &x, Ct &out) {
     if (!keys || !keys->s_ntt) return SECPE_EKEY;
     const int B = x.B(), lv = x.level(), n = ctx->n, L = ctx->L;
     if ((int)qseeds.size() != B || B > SECPE_MAX_BATCH_CONST) return SECPE_EINVAL;
+    // the whole stand-in is one profiler range, so its share of a step can be measured
+    KprofScope kp(ctx, "refresh", 0.0);
     DevBuf m, e, M, a;
     SECPE_CHECK(m.alloc(ctx, sizeof(u64) * (size_t)B * (lv + 1) * n));
     SECPE_CHECK(launch_dec_dot(ctx, x.v, keys->s_ntt, m.u(), lv + 1));
