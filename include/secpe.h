@@ -257,11 +257,14 @@ typedef struct {
     double d_min, d_max;
     uint64_t qseed;       /* refresh randomness */
     secpe_ct *z_out;      /* output ciphertext (cap >= top level + 1) */
+    const secpe_keys *keys; /* the query's tenant key set; null = the call's (or server's) keys */
 } secpe_query;
 
 /* Aggregation + Argmax of n_queries independent queries, batched: every
  * homomorphic operation runs once for all queries that take it at that
- * point of the circuit.  Results equal the one-query calls bit for bit. */
+ * point of the circuit.  Queries of different tenants (q[i].keys) are
+ * evaluated as one batch per key set, in order of first appearance.
+ * Results equal the one-query calls with the query's keys bit for bit. */
 int secpe_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q,
                        int n_queries, void *stream);
 
@@ -290,9 +293,13 @@ void secpe_graph_destroy(secpe_graph *g);
  * Sign); each secpe_server_step runs one phase, batched over every query at
  * the same point of the circuit as the oldest admitted query (up to
  * max_batch), so queries submitted while others run join at the next phase
- * boundary.  A query is admitted when keys + in-flight states + one step's
- * scratch + its state fit hbm_budget_bytes; until then it waits.  Results
- * are bit-identical to secpe_encrypted_argmax on the aggregated input.
+ * boundary.  Queries of different tenants (secpe_query.keys; null = the
+ * server's keys) are batched only with queries of the same tenant.  Every
+ * key set seen is counted as resident; a query is admitted when those keys +
+ * in-flight states + one step's scratch + its state fit hbm_budget_bytes;
+ * until then it waits (a submit whose new key set alone cannot fit returns
+ * SECPE_EADMIT).  Results are bit-identical to secpe_encrypted_argmax with
+ * the query's keys on the aggregated input.
  * The query's cts and z_out must stay valid until it completes. */
 typedef struct secpe_server secpe_server;
 typedef struct {

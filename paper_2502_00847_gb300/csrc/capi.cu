@@ -506,7 +506,7 @@ extern "C" int secpe_encrypted_argmax(secpe_ctx *ctx, const secpe_keys *keys_, c
 
 extern "C" int secpe_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int n_queries,
                                   void *stream) {
-    if (!ctx || !keys || !q || n_queries < 0) return SECPE_EINVAL;
+    if (!ctx || !q || n_queries < 0) return SECPE_EINVAL;
     if (n_queries == 0) return SECPE_OK;
     CallScope cs(ctx, stream);
     return finish(ctx, argmax_batch_impl(ctx, keys, q, n_queries));
@@ -599,7 +599,7 @@ struct secpe_graph {
 
 extern "C" int secpe_argmax_batch_capture(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q,
                                           int n_queries, secpe_graph **out, int64_t *n_nodes) {
-    if (!ctx || !keys || !q || n_queries < 1 || !out) return SECPE_EINVAL;
+    if (!ctx || !q || n_queries < 1 || !out) return SECPE_EINVAL;
     *out = nullptr;
     cudaStream_t cs = nullptr;
     SECPE_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));

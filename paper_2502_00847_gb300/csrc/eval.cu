@@ -373,7 +373,27 @@ int Eval::argmax(const Ct &y, int C, Ct &out) {
 // finish at phase k the following contiguous range.  All queries of one
 // range share level, scale and refresh history, so each range is a single
 // batched evaluation.
+static int argmax_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_);
+
+// Queries of different tenants are evaluated as one batch per key set.
 int argmax_batch_impl(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_) {
+    std::vector<const secpe_keys *> sets;
+    for (int b = 0; b < nq_; b++) {
+        const secpe_keys *k = q[b].keys ? q[b].keys : keys;
+        if (!k) return SECPE_EINVAL;
+        if (std::find(sets.begin(), sets.end(), k) == sets.end()) sets.push_back(k);
+    }
+    if (sets.size() == 1) return argmax_batch_tenant(ctx, sets[0], q, nq_);
+    for (const secpe_keys *k : sets) {
+        std::vector<secpe_query> part;
+        for (int b = 0; b < nq_; b++)
+            if ((q[b].keys ? q[b].keys : keys) == k) part.push_back(q[b]);
+        SECPE_CHECK(argmax_batch_tenant(ctx, k, part.data(), (int)part.size()));
+    }
+    return SECPE_OK;
+}
+
+static int argmax_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_) {
     const int n = ctx->n, L = ctx->L;
     if (nq_ > SECPE_MAX_BATCH_CONST) return SECPE_EINVAL;
     std::vector<int> order(nq_), rr(nq_), cps(nq_);

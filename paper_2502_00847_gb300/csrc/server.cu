@@ -3,9 +3,9 @@
 // A query moves through the phases of SecPE Alg. 1 (as split by the batched
 // driver): phase -1 = aggregation + duplication (y + RotR(y, C')), phase
 // k = 0..r-1 = QuickMax round k, phase r = final Sign(y_dup - y_max) + 1.
-// All queries at the same phase of the same class-count power C' share
-// level, scale and refresh history, so the server runs one phase for a
-// whole group as one batched evaluation.  Each call to secpe_server_step
+// All queries of one tenant (key set) at the same phase of the same
+// class-count power C' share level, scale and refresh history, so the server
+// runs one phase for a whole group as one batched evaluation.  Each call to secpe_server_step
 // picks the group that holds the oldest admitted query, adds every other
 // query at the same point (up to max_batch), and enqueues that phase on the
 // stream; queries submitted meanwhile join at the next phase boundary.
@@ -32,6 +32,7 @@ double now_s() {
 struct QState {
     int64_t ticket = 0;
     secpe_query q;
+    const secpe_keys *keys = nullptr;  // the query's tenant key set
     int r = 0, cp = 1;
     int phase = -2;  // -2 waiting for admission, -1 aggregate+dup, 0..r-1 rounds, r final
     Ct ydup, y;
@@ -46,7 +47,8 @@ struct QState {
 
 struct secpe_server {
     secpe_ctx *ctx;
-    const secpe_keys *keys;
+    const secpe_keys *keys;            // default key set
+    std::map<const secpe_keys *, size_t> key_sets;  // every key set seen, with its device bytes
     size_t budget, keys_bytes, scratch_bytes, in_flight_bytes = 0;
     int max_batch;
     int64_t next_ticket = 1;
@@ -59,6 +61,12 @@ struct secpe_server {
 namespace {
 
 size_t ct_bytes(const secpe_ctx *ctx, int level) { return sizeof(u64) * 2ull * (level + 1) * ctx->n; }
+
+// device bytes of a key set: relinearisation + Galois keys, secret key
+size_t key_set_bytes(const secpe_ctx *ctx, const secpe_keys *keys) {
+    const size_t keyb = sizeof(u64) * (size_t)ctx->n * ctx->nprimes * 2 * ((ctx->L + ctx->alpha) / ctx->alpha);
+    return keyb * (1 + keys->gks.size()) + sizeof(u64) * (size_t)ctx->n * ctx->nprimes;
+}
 
 // device bytes a query holds while in flight: y_dup + y + z (top level bound)
 size_t query_state_bytes(const secpe_ctx *ctx) { return 3 * ct_bytes(ctx, ctx->L); }
@@ -129,7 +137,7 @@ int gather(secpe_ctx *ctx, const std::vector<QState *> &g, bool dup, Ct &out) {
 int run_group(secpe_server *s, std::vector<QState *> &g) {
     secpe_ctx *ctx = s->ctx;
     const int phase = g[0]->phase, r = g[0]->r;
-    Eval E{ctx, s->keys, {}, g[0]->ridx};
+    Eval E{ctx, g[0]->keys, {}, g[0]->ridx};
     for (QState *st : g) E.qseeds.push_back(st->q.qseed);
     const int B = (int)g.size(), n = ctx->n, L = ctx->L;
     if (phase == -1) {
@@ -207,8 +215,8 @@ extern "C" int secpe_server_create(secpe_ctx *ctx, const secpe_keys *keys, uint6
     s->keys = keys;
     s->budget = hbm_budget_bytes;
     s->max_batch = max_batch;
-    const size_t keyb = sizeof(u64) * (size_t)ctx->n * ctx->nprimes * 2 * ((ctx->L + ctx->alpha) / ctx->alpha);
-    s->keys_bytes = keyb * (1 + keys->gks.size()) + sizeof(u64) * (size_t)ctx->n * ctx->nprimes;
+    s->keys_bytes = key_set_bytes(ctx, keys);
+    s->key_sets[keys] = s->keys_bytes;
     s->scratch_bytes = step_scratch_bytes(ctx, max_batch);
     if (s->keys_bytes + s->scratch_bytes + query_state_bytes(ctx) > s->budget) {
         delete s;
@@ -239,12 +247,21 @@ extern "C" int secpe_server_submit(secpe_server *s, const secpe_query *q, int64_
         if (!c.data || c.level != ctx->L || c.cap < ctx->L + 1) return SECPE_EINVAL;
         if (std::fabs(c.scale - ctx->scale) > ctx->scale * std::ldexp(1.0, -40)) return SECPE_ESCALE;
     }
-    if (!s->keys->rlk || !galois_key(s->keys, galois_elt(ctx, -cp))) return SECPE_EKEY;
+    const secpe_keys *keys = q->keys ? q->keys : s->keys;
+    if (!keys->rlk || !galois_key(keys, galois_elt(ctx, -cp))) return SECPE_EKEY;
     for (int i = 0; i < r; i++)
-        if (!galois_key(s->keys, galois_elt(ctx, 1 << i))) return SECPE_EKEY;
+        if (!galois_key(keys, galois_elt(ctx, 1 << i))) return SECPE_EKEY;
+    if (!s->key_sets.count(keys)) {
+        // a new tenant: its keys are resident from now on
+        const size_t kb = key_set_bytes(ctx, keys);
+        if (s->keys_bytes + kb + s->scratch_bytes + query_state_bytes(ctx) > s->budget) return SECPE_EADMIT;
+        s->key_sets[keys] = kb;
+        s->keys_bytes += kb;
+    }
     QState st;
     st.ticket = s->next_ticket++;
     st.q = *q;
+    st.keys = keys;
     st.r = r;
     st.cp = cp;
     st.t_submit = now_s();
@@ -285,14 +302,16 @@ extern "C" int secpe_server_step(secpe_server *s, void *stream, int *launched) {
         if (!oldest || st.t_admit < oldest->t_admit) oldest = &st;
     }
     if (!oldest) return SECPE_OK;
-    // queries at the same point of the circuit: same phase and kind (the
-    // duplication needs the same C' key; a QuickMax round k is common to all
-    // queries with r > k; the final phase k is shared by queries with r = k)
+    // queries at the same point of the circuit: same tenant, phase and kind
+    // (the duplication needs the same C' key; a QuickMax round k is common to
+    // all queries with r > k; the final phase k is shared by queries with r = k)
     auto kind = [](const QState &st) { return st.phase < 0 ? 2 * st.cp : (st.phase < st.r ? 0 : 1); };
     std::vector<QState *> g;
     for (auto &kv : s->q) {
         QState &st = kv.second;
-        if (st.cancelled || st.done || st.phase != oldest->phase || kind(st) != kind(*oldest)) continue;
+        if (st.cancelled || st.done || st.phase != oldest->phase || kind(st) != kind(*oldest) ||
+            st.keys != oldest->keys)
+            continue;
         g.push_back(&st);
     }
     std::sort(g.begin(), g.end(), [](const QState *a, const QState *b) { return a->t_admit < b->t_admit; });

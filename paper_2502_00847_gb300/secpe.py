@@ -46,7 +46,7 @@ class CtC(ctypes.Structure):
 class QueryC(ctypes.Structure):
     _fields_ = [("cts", ctypes.POINTER(CtC)), ("K", ctypes.c_int32), ("C", ctypes.c_int32),
                 ("d_min", ctypes.c_double), ("d_max", ctypes.c_double), ("qseed", ctypes.c_uint64),
-                ("z_out", ctypes.POINTER(CtC))]
+                ("z_out", ctypes.POINTER(CtC)), ("keys", ctypes.c_void_p)]
 
 
 class CtBatchC(ctypes.Structure):
@@ -564,7 +564,9 @@ def _query_array(queries):
         cts = (CtC * len(q["cts"]))(*[c.struct() for c in q["cts"]])
         z = q["z_out"].struct()
         keep.append((cts, z))
-        qarr[i] = QueryC(cts, len(q["cts"]), q["C"], q["d_min"], q["d_max"], q["qseed"], ctypes.pointer(z))
+        tk = q.get("keys")
+        qarr[i] = QueryC(cts, len(q["cts"]), q["C"], q["d_min"], q["d_max"], q["qseed"], ctypes.pointer(z),
+                         tk.h.value if tk is not None else None)
     return qarr, keep
 
 
@@ -674,13 +676,15 @@ class Server:
         self.h, self.ctx, self.keys = h, ctx, keys
         self._keep = {}
 
-    def submit(self, cts, C, d_min, d_max, qseed, z_out):
+    def submit(self, cts, C, d_min, d_max, qseed, z_out, keys=None):
+        """keys: the query's tenant key set (default: the server's)."""
         arr = (CtC * len(cts))(*[c.struct() for c in cts])
         z = z_out.struct()
-        qc = QueryC(arr, len(cts), C, d_min, d_max, qseed, ctypes.pointer(z))
+        qc = QueryC(arr, len(cts), C, d_min, d_max, qseed, ctypes.pointer(z),
+                    keys.h.value if keys is not None else None)
         t = ctypes.c_int64()
         _check(lib().secpe_server_submit(self.h, ctypes.byref(qc), ctypes.byref(t)), "secpe_server_submit")
-        self._keep[t.value] = (arr, z, qc, z_out, cts)
+        self._keep[t.value] = (arr, z, qc, z_out, cts, keys)
         return t.value
 
     def step(self):
@@ -692,7 +696,7 @@ class Server:
         d = ctypes.c_int32()
         _check(lib().secpe_server_poll(self.h, ticket, ctypes.byref(d)), "secpe_server_poll")
         if d.value == 1:
-            arr, z, qc, z_out, cts = self._keep[ticket]
+            z, z_out = self._keep[ticket][1], self._keep[ticket][3]
             z_out.update(z)
         return d.value
 

@@ -117,3 +117,52 @@ def test_missing_key_cancel_and_timeout(env):
     assert srv.wait(t1, 60.0) == 1
     assert np.array_equal(z1.residues(), ref[0])
     assert ctx.stream_status() == 0
+
+
+def test_two_tenants_in_one_server(env):
+    """Queries of two tenants (different secret keys) interleaved: each is
+    batched only with its own tenant, equals the one-query path with its own
+    keys bit for bit, and the second key set is counted as resident."""
+    ctx, keys, qs, inputs, ref, secpe = env
+    keys_b = secpe.Keys(ctx, 32, ROT)
+    inputs_b = [[secpe.encrypt_logits(ctx, keys_b, q.logits[i], q.d_min, q.enc_seeds[i]) for i in range(q.K)]
+                for q in qs]
+    ref_b = []
+    for q, cts in zip(qs, inputs_b):
+        y = secpe.ensemble_aggregate(ctx, cts, q.d_min, q.d_max)
+        ref_b.append(secpe.encrypted_argmax(ctx, keys_b, y, q.C, q.qseed).residues())
+    srv = secpe.Server(ctx, keys, hbm_budget_bytes=8 << 30, max_batch=8)
+    kb0 = srv.stats()["keys_bytes"]
+    subs = []
+    for i in range(len(qs)):
+        subs.append(("a", i, submit(srv, ctx, qs[i], inputs[i])))
+        z = ctx.new_ct()
+        subs.append(("b", i, (srv.submit(inputs_b[i], qs[i].C, qs[i].d_min, qs[i].d_max, qs[i].qseed, z,
+                                         keys=keys_b), z)))
+    assert srv.stats()["keys_bytes"] == 2 * kb0
+    for who, i, (t, z) in subs:
+        assert srv.wait(t, 60.0) == 1
+        assert np.array_equal(z.residues(), ref[i] if who == "a" else ref_b[i]), (who, i)
+        k = keys if who == "a" else keys_b
+        assert int(np.argmax(secpe.decrypt(ctx, k, z, qs[i].C))) == int(np.argmax(qs[i].logits.mean(0)))
+
+
+def test_two_tenants_in_one_batch(env):
+    """secpe_argmax_batch over queries of two tenants: one batch per key set,
+    bit-identical to the one-query path with each query's keys."""
+    ctx, keys, qs, inputs, ref, secpe = env
+    keys_b = secpe.Keys(ctx, 33, ROT)
+    inputs_b = [[secpe.encrypt_logits(ctx, keys_b, q.logits[i], q.d_min, q.enc_seeds[i]) for i in range(q.K)]
+                for q in qs]
+    batch = []
+    for i, q in enumerate(qs):
+        batch.append(dict(cts=inputs[i], C=q.C, d_min=q.d_min, d_max=q.d_max, qseed=q.qseed, z_out=ctx.new_ct()))
+        batch.append(dict(cts=inputs_b[i], C=q.C, d_min=q.d_min, d_max=q.d_max, qseed=q.qseed, z_out=ctx.new_ct(),
+                          keys=keys_b))
+    secpe.argmax_batch(ctx, keys, batch)
+    for i, q in enumerate(qs):
+        assert np.array_equal(batch[2 * i]["z_out"].residues(), ref[i])
+        y = secpe.ensemble_aggregate(ctx, inputs_b[i], q.d_min, q.d_max)
+        zb = secpe.encrypted_argmax(ctx, keys_b, y, q.C, q.qseed)
+        assert np.array_equal(batch[2 * i + 1]["z_out"].residues(), zb.residues())
+        assert int(np.argmax(secpe.decrypt(ctx, keys_b, zb, q.C))) == int(np.argmax(q.logits.mean(0)))
