@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--rates", default="50,200,500,1000,2000")
     ap.add_argument("--serve-queries", type=int, default=384, help="queries submitted per arrival rate")
     ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--tenants", type=int, default=1,
+                    help="serving: tenants with their own resident key sets (queries batch within a tenant)")
     ap.add_argument("--params", default="argmax8", choices=["argmax", "argmax8"],
                     help="Argmax parameter set: argmax8 (8 special 60-bit primes, dnum=3; the default) or "
                          "argmax (4 special, dnum=6)")
@@ -620,17 +622,19 @@ def run_serve(args, rank):
     pkg_build.build()
     ctx = secpe.Context.from_params(PRESETS[args.params])
     ctx.autotune()
-    keys = secpe.Keys(ctx, 1000 + rank, ROT_STEPS)
+    # one key set per tenant; pool query i belongs to tenant i % tenants
+    tenants = [secpe.Keys(ctx, 1000 + rank + 7919 * t, ROT_STEPS) for t in range(args.tenants)]
     n, cap = ctx.n, ctx.L + 1
     pool = workloads.argmax_queries(64, seed=5)
+    tkeys = [tenants[i % args.tenants] for i in range(len(pool))]
     n_cts = sum(q.K for q in pool)
     inputs = torch.empty((n_cts, 2, cap, n), dtype=torch.int64, device="cuda")
     views, off = [], 0
-    for q in pool:
+    for qi, q in enumerate(pool):
         cts = []
         for i in range(q.K):
             c = secpe.Ciphertext(inputs[off], 0, ctx.scale)
-            secpe.encrypt_logits(ctx, keys, q.logits[i], q.d_min, q.enc_seeds[i], out=c)
+            secpe.encrypt_logits(ctx, tkeys[qi], q.logits[i], q.d_min, q.enc_seeds[i], out=c)
             cts.append(c)
             off += 1
         views.append(cts)
@@ -641,7 +645,7 @@ def run_serve(args, rank):
         torch.cuda.synchronize()
         t = time.perf_counter()
         y = secpe.ensemble_aggregate(ctx, views[i], q.d_min, q.d_max)
-        secpe.encrypted_argmax(ctx, keys, y, q.C, q.qseed, out=zt)
+        secpe.encrypted_argmax(ctx, tkeys[i], y, q.C, q.qseed, out=zt)
         torch.cuda.synchronize()
         svc.append(time.perf_counter() - t)
     results = []
@@ -650,7 +654,7 @@ def run_serve(args, rank):
         nq = args.serve_queries
         arrivals = np.cumsum(rng.exponential(1.0 / lam, nq))
         pick = rng.integers(0, len(pool), nq)
-        srv = secpe.Server(ctx, keys, hbm_budget_bytes=int(args.budget_gb * 1e9), max_batch=64)
+        srv = secpe.Server(ctx, tenants[0], hbm_budget_bytes=int(args.budget_gb * 1e9), max_batch=64)
         zbufs = {}
         pending = {}
         lat = []
@@ -663,7 +667,8 @@ def run_serve(args, rank):
             while nxt < nq and arrivals[nxt] <= now:
                 i = int(pick[nxt])
                 z = ctx.new_ct()
-                tk = srv.submit(views[i], pool[i].C, pool[i].d_min, pool[i].d_max, pool[i].qseed + nxt, z)
+                tk = srv.submit(views[i], pool[i].C, pool[i].d_min, pool[i].d_max, pool[i].qseed + nxt, z,
+                                keys=tkeys[i])
                 pending[tk] = arrivals[nxt]
                 zbufs[tk] = z
                 nxt += 1
@@ -704,8 +709,9 @@ def run_serve(args, rank):
         print(json.dumps({"mode": "serve", "metric": METRIC,
                           "config": {"workload": "serving loop: Poisson arrivals, %d queries per rate from a pool of "
                                                  "64 (K~U{4,8,16}, C~U{2,3,4,6,14,64}, seed 5), N=2^16, HBM "
-                                                 "budget %.0f GB, max batch 64" % (args.serve_queries,
-                                                                                   args.budget_gb)},
+                                                 "budget %.0f GB, max batch 64, %d tenant key set(s) resident"
+                                                 % (args.serve_queries, args.budget_gb, args.tenants),
+                                     "tenants": args.tenants},
                           "plain_service_ms_mean": 1e3 * float(np.mean(svc)), "rates": results}))
 
 
