@@ -8,7 +8,8 @@
 // obtained on the host by running the exact column network on unit vectors,
 // so they are the same linear map as the CUDA-core kernels.  Residues are
 // split into 8-bit limbs, x = sum_b x_b 2^(8b), W = sum_a W_a 2^(8a); the
-// products W_a X_b are computed with mma.sync m16n8k32 u8 x u8 -> s32, and
+// products W_a X_b are computed with mma.sync m16n8k32 u8 x u8 -> s32 from
+// operand tiles staged in shared memory, and
 // the 15 diagonal sums S_d = sum_{a+b=d} W_a X_b (each < 8 * 256 * 255^2 <
 // 2^31, exact in INT32) are recombined as sum_d S_d 2^(8d) mod q with one
 // Montgomery reduction.  (sm_103a has no tcgen05 kind::i8; the u8 mma.sync
@@ -54,48 +55,80 @@ __device__ __forceinline__ void mma_u8(int (&c)[4], uint32_t a0, uint32_t a1, ui
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// One warp computes a 16 (rows of the output column transform) x 8 (columns)
-// tile of one limb; 4 warps per CTA cover 16 x 32.
-__global__ void __launch_bounds__(128) k_tc_colpass(const __grid_constant__ TcArgs a) {
+// CTA tile: 32 output rows x 64 columns of one limb.  All 8 byte planes of
+// the 32 matrix rows and of the 64 input columns are staged in shared memory
+// once (rows padded to 272 bytes, so that the fragment loads of a warp hit 32
+// distinct banks), and every limb pair (a, b) is computed from there: no
+// operand is read from global memory twice by a CTA.  8 warps as 2 x 4, each
+// 16 rows x 16 columns (two m16n8 tiles); the diagonal sums S_d accumulate
+// in the s32 fragments (at most 8 * 256 * 255^2 < 2^31).  The legacy integer
+// mma path of this part runs near 130 int8 TOPS here (about 16 us per limb),
+// so the pass stays a precision variant, not a fast path.
+constexpr int TC_BM = 32, TC_BN = 64, TC_PITCH = 272;
+constexpr int TC_SMEM = 8 * (TC_BM + TC_BN) * TC_PITCH;  // 208,896 bytes
+
+__global__ void __launch_bounds__(256, 1) k_tc_colpass(const __grid_constant__ TcArgs a) {
+    extern __shared__ __align__(16) unsigned char tsm[];
+    unsigned char *Ws = tsm;                         // [8][32][272]
+    unsigned char *Xs = tsm + 8 * TC_BM * TC_PITCH;  // [8][64][272]
     const long long lid = blockIdx.z;
     const LimbRef L = limb_of(a.ls, a.c.n, lid);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const int row0 = blockIdx.y * 16;                 // output rows (j1)
-    const int col0 = blockIdx.x * 32 + warp * 8;      // columns (k2)
+    const int row0 = blockIdx.y * TC_BM, col0 = blockIdx.x * TC_BN;
     const unsigned char *W = a.planes + ((size_t)L.prime * 2 + (a.inverse ? 1 : 0)) * 8 * 65536;
     const unsigned char *X = a.xt + lid * 8ll * 65536;
+    for (int i = threadIdx.x; i < 8 * TC_BM * 16; i += 256) {
+        const int pl = i / (TC_BM * 16), r = (i >> 4) % TC_BM, ch = i & 15;
+        *(uint4 *)(Ws + (pl * TC_BM + r) * TC_PITCH + ch * 16) =
+            __ldg((const uint4 *)(W + (size_t)pl * 65536 + (size_t)(row0 + r) * 256 + ch * 16));
+    }
+    for (int i = threadIdx.x; i < 8 * TC_BN * 16; i += 256) {
+        const int pl = i / (TC_BN * 16), r = (i >> 4) % TC_BN, ch = i & 15;
+        *(uint4 *)(Xs + (pl * TC_BN + r) * TC_PITCH + ch * 16) =
+            *(const uint4 *)(X + (size_t)pl * 65536 + (size_t)(col0 + r) * 256 + ch * 16);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int wr = (warp & 1) * 16, wc = (warp >> 1) * 16;
     const u64 q = a.c.q[L.prime], qinv = a.c.qinv_neg[L.prime];
-    acc128 acc[4];
+    acc128 acc[2][4];
 #pragma unroll
-    for (int e = 0; e < 4; e++) acc[e] = {0, 0};
+    for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+        for (int e = 0; e < 4; e++) acc[nt][e] = {0, 0};
     for (int d = 0; d < 15; d++) {
-        int s[4] = {0, 0, 0, 0};
+        int s[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
         const int alo = d > 7 ? d - 7 : 0, ahi = d < 7 ? d : 7;
         for (int pa = alo; pa <= ahi; pa++) {
-            const unsigned char *Wa = W + (size_t)pa * 65536;
-            const unsigned char *Xb = X + (size_t)(d - pa) * 65536;
-#pragma unroll 2
+            const unsigned char *Wa = Ws + (pa * TC_BM + wr) * TC_PITCH + 4 * t;
+            const unsigned char *Xb = Xs + ((d - pa) * TC_BN + wc) * TC_PITCH + 4 * t;
+#pragma unroll 4
             for (int kc = 0; kc < 256; kc += 32) {
-                const uint32_t a0 = __ldg((const uint32_t *)(Wa + (row0 + g) * 256 + kc + 4 * t));
-                const uint32_t a1 = __ldg((const uint32_t *)(Wa + (row0 + g + 8) * 256 + kc + 4 * t));
-                const uint32_t a2 = __ldg((const uint32_t *)(Wa + (row0 + g) * 256 + kc + 16 + 4 * t));
-                const uint32_t a3 = __ldg((const uint32_t *)(Wa + (row0 + g + 8) * 256 + kc + 16 + 4 * t));
-                const uint32_t b0 = __ldg((const uint32_t *)(Xb + (col0 + g) * 256 + kc + 4 * t));
-                const uint32_t b1 = __ldg((const uint32_t *)(Xb + (col0 + g) * 256 + kc + 16 + 4 * t));
-                mma_u8(s, a0, a1, a2, a3, b0, b1);
+                const uint32_t a0 = *(const uint32_t *)(Wa + g * TC_PITCH + kc);
+                const uint32_t a1 = *(const uint32_t *)(Wa + (g + 8) * TC_PITCH + kc);
+                const uint32_t a2 = *(const uint32_t *)(Wa + g * TC_PITCH + kc + 16);
+                const uint32_t a3 = *(const uint32_t *)(Wa + (g + 8) * TC_PITCH + kc + 16);
+#pragma unroll
+                for (int nt = 0; nt < 2; nt++) {
+                    const unsigned char *xb = Xb + (nt * 8 + g) * TC_PITCH + kc;
+                    mma_u8(s[nt], a0, a1, a2, a3, *(const uint32_t *)xb, *(const uint32_t *)(xb + 16));
+                }
             }
         }
         const u64 cd = a.cmont[(size_t)L.prime * 15 + d];
 #pragma unroll
-        for (int e = 0; e < 4; e++) mac(acc[e], (u64)(uint32_t)s[e], cd);
-    }
-    // c0, c1: row g, cols 2t, 2t+1; c2, c3: row g + 8
+        for (int nt = 0; nt < 2; nt++)
 #pragma unroll
-    for (int e = 0; e < 4; e++) {
-        const int r = row0 + g + (e >> 1) * 8, cl = col0 + 2 * t + (e & 1);
-        L.ptr[r * 256 + cl] = redc(acc[e].hi, acc[e].lo, q, qinv);
+            for (int e = 0; e < 4; e++) mac(acc[nt][e], (u64)(uint32_t)s[nt][e], cd);
     }
+    // fragment element e: row g (+8 for e >= 2), columns 2t, 2t+1
+#pragma unroll
+    for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int r = row0 + wr + g + (e >> 1) * 8, cl = col0 + wc + nt * 8 + 2 * t + (e & 1);
+            L.ptr[r * 256 + cl] = redc(acc[nt][e].hi, acc[nt][e].lo, q, qinv);
+        }
 }
 
 // ------------------------------------------------------------ host tables
@@ -221,7 +254,15 @@ static int tc_colpass(secpe_ctx *ctx, const LimbSet &ls, bool inverse, const TcT
     a.inverse = inverse ? 1 : 0;
     SECPE_LAUNCH(ctx, k_tc_split, dim3(8, 8, (unsigned)nl), dim3(32, 8), 0, a);
     KprofScope kp(ctx, "tc_colpass", 16.0 * ctx->n * nl);
-    SECPE_LAUNCH(ctx, k_tc_colpass, dim3(8, 16, (unsigned)nl), 128, 0, a);
+    static bool attr_set[64];
+    int dev = 0;
+    SECPE_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return SECPE_ECUDA;
+    if (!attr_set[dev]) {
+        SECPE_CUDA(cudaFuncSetAttribute(k_tc_colpass, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+        attr_set[dev] = true;
+    }
+    SECPE_LAUNCH(ctx, k_tc_colpass, dim3(256 / TC_BN, 256 / TC_BM, (unsigned)nl), 256, TC_SMEM, a);
     return SECPE_OK;
 }
 
