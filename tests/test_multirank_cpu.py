@@ -51,7 +51,7 @@ def test_reference_arm_prints_on_rank0_only(monkeypatch, capsys):
         queries, steps, warmup, gpus, params = 4, 1, 0, 2, "argmax8"
     called = []
     monkeypatch.setattr(bench, "oracle_sample",
-                        lambda params_name, seconds_budget=0: called.append(params_name) or (1.0, 1.0, 0.0))
+                        lambda params_name, seconds_budget=0: called.append(params_name) or (1.0, 1.0, 0.0, 4))
     bench.run_reference(A, 2, 1)
     assert capsys.readouterr().out == "" and not called
     bench.run_reference(A, 2, 0)
