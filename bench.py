@@ -51,6 +51,8 @@ def parse():
                     help="primitive micro-benchmark (N=2^16, 24+4 primes, dnum=3) instead of the Argmax step")
     ap.add_argument("--micro-ops", default="ntt,keyswitch,hmult,rescale,rotate")
     ap.add_argument("--micro-batch", default="1,8,64")
+    ap.add_argument("--tc-identity-count", type=int, default=10000,
+                    help="seeded random ciphertexts of the precision variant's bit-identity checks")
     ap.add_argument("--serve", action="store_true",
                     help="serving loop: Poisson arrivals, continuous batching, p50/p99 latency")
     ap.add_argument("--rates", default="50,200,500,1000,2000")
@@ -578,6 +580,10 @@ def run_micro(args, rank):
             ms = timed(lambda: secpe.ntt_cts_tc(ctx, x, B, 2 * cap * n, cap, L))
             res["ntt_tc_B%d" % B] = {"ms": ms, "us_per_limb": ms * 1e3 / (B * 2 * cap),
                                      "GBps_alg": B * 2 * cap * limb * 4 / (ms / 1e3) / 1e9}
+        if "ksk_tc" in ops:
+            ms = timed(lambda: secpe.keyswitch_batch_tc(ctx, keys, 0, a, o))
+            alg = B * (cap * limb + 2 * cap * limb) + ksk_bytes
+            res["keyswitch_tc_B%d" % B] = {"ms": ms, "GBps_alg": alg / (ms / 1e3) / 1e9, "alg_bytes": alg}
         if "keyswitch" in ops:
             ms = timed(lambda: secpe.keyswitch_batch(ctx, keys, 0, a, o))
             alg = B * (cap * limb + 2 * cap * limb) + ksk_bytes
@@ -597,7 +603,7 @@ def run_micro(args, rank):
         torch.cuda.empty_cache()
     if "ntt_tc_identity" in ops:
         # precision variant: bit identity with the CUDA-core NTT over 10^4 seeded random ciphertexts
-        total, chunk, mism = 10000, 50, 0
+        total, chunk, mism = args.tc_identity_count, 50, 0
         t_tc = t_cc = 0.0
         for s0 in range(0, total, chunk):
             g2 = torch.Generator(device="cpu").manual_seed(30000 + s0)
@@ -622,6 +628,33 @@ def run_micro(args, rank):
             mism += int((u != v).any(dim=(1, 2, 3)).sum().item())
         res["ntt_tc_identity"] = {"ciphertexts": total, "mismatching_ciphertexts": mism,
                                   "forward_ms_cuda_cores": t_cc, "forward_ms_tensor_pipe": t_tc}
+    if "ksk_tc_identity" in ops:
+        # precision variant: key switching with tensor-pipe transforms and inner product, bit identity with
+        # the CUDA-core key switch over seeded random ciphertexts (polynomial 0 of each, top level)
+        total, chunk, mism = args.tc_identity_count, 50, 0
+        t_tc = t_cc = 0.0
+        for s0 in range(0, total, chunk):
+            c = min(chunk, total - s0)
+            g2 = torch.Generator(device="cpu").manual_seed(40000 + s0)
+            t = torch.empty((c, 2, cap, n), dtype=torch.int64)
+            for i in range(cap):
+                t[:, :, i] = torch.randint(0, primes[i], (c, 2, n), generator=g2, dtype=torch.int64)
+            dd = secpe.CtBatch(t.cuda(), L, ctx.scale)
+            u = secpe.CtBatch(torch.zeros_like(dd.data), 0, ctx.scale)
+            v = secpe.CtBatch(torch.zeros_like(dd.data), 0, ctx.scale)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            secpe.keyswitch_batch(ctx, keys, 0, dd, u)
+            e[1].record()
+            secpe.keyswitch_batch_tc(ctx, keys, 0, dd, v)
+            e[2].record()
+            torch.cuda.synchronize()
+            t_cc += e[0].elapsed_time(e[1])
+            t_tc += e[1].elapsed_time(e[2])
+            mism += int((u.data != v.data).any(dim=(1, 2, 3)).sum().item())
+            del dd, u, v
+        res["ksk_tc_identity"] = {"ciphertexts": total, "mismatching_ciphertexts": mism, "level": L,
+                                  "ms_cuda_cores": t_cc, "ms_tensor_pipe": t_tc}
     if rank == 0:
         desc = ("24x50-bit + 4x60-bit special primes, dnum=3" if args.micro_params == "micro" else
                 "q0 60-bit + 23x50-bit + %dx60-bit special primes, dnum=%d" % (P.n_p, P.dnum))

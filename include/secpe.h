@@ -160,11 +160,15 @@ int secpe_ntt(secpe_ctx *ctx, uint64_t *limbs, const int32_t *prime_idx, int cou
 int secpe_ntt_cts(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, int cap, int level,
                   int inverse, void *stream);
 /* Precision variant (N = 2^16 only): the same transforms, bit-identical,
- * with the column pass (a fixed 256 x 256 matrix per prime applied to every
- * column) computed as an exact contraction on the tensor pipe: residues and
- * matrix entries split into 8-bit limbs, u8 x u8 -> s32 products, diagonal
- * sums recombined modulo q.  The row pass stays on CUDA cores.  The first
- * call on a context builds the matrices (28 MiB for 28 primes). */
+ * computed as exact dense contractions on the tensor pipe.  The transform of
+ * the ring R_Q (Sec. 2.2) factors into a fixed 256 x 256 matrix per prime on
+ * every column, an element-wise twist, and a fixed 256 x 256 matrix per
+ * prime on every row (the inverse in reverse order).  Each matrix product
+ * splits residues and matrix entries into 8-bit limbs, forms u8 x u8 -> s32
+ * products and recombines the diagonal sums modulo q.  The first call on a
+ * context builds the matrices and twists (3 MiB per prime).  Scratch (the
+ * byte planes, 512 KiB per limb, at most 1 GiB) comes from the stream-ordered
+ * allocator. */
 int secpe_ntt_tc(secpe_ctx *ctx, uint64_t *limbs, const int32_t *prime_idx, int count, int inverse,
                  void *stream);
 int secpe_ntt_cts_tc(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, int cap, int level,
@@ -224,6 +228,16 @@ typedef struct {
  * of out receives (ks0, ks1) in its polynomials 0 and 1 at d's level. */
 int secpe_keyswitch_batch(secpe_ctx *ctx, const secpe_keys *keys, int galois_step, const secpe_ctbatch *d,
                           secpe_ctbatch *out, void *stream);
+/* Precision variant of secpe_keyswitch_batch (N = 2^16, dnum <= 8): every
+ * NTT/INTT of the key switch runs as the exact tensor-pipe contraction of
+ * secpe_ntt_tc, and the key inner product sum_j x_j k_{j,s} over the digits
+ * as exact 8-bit-limb u8 x u8 -> s32 products on the tensor pipe (one
+ * product per coefficient: rows = (output polynomial, diagonal), columns =
+ * items); the base conversions of ModUp and ModDown stay on CUDA cores.
+ * The result is bit-identical to secpe_keyswitch_batch.  Same arguments,
+ * layout and errors; SECPE_EINVAL for other ring sizes or dnum > 8. */
+int secpe_keyswitch_batch_tc(secpe_ctx *ctx, const secpe_keys *keys, int galois_step, const secpe_ctbatch *d,
+                             secpe_ctbatch *out, void *stream);
 int secpe_mul_relin_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ctbatch *a,
                           const secpe_ctbatch *b, secpe_ctbatch *out, void *stream);
 int secpe_rotate_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ctbatch *in, int steps,

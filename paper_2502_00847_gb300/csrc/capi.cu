@@ -777,6 +777,28 @@ extern "C" int secpe_keyswitch_batch(secpe_ctx *ctx, const secpe_keys *keys, int
     return finish(ctx, SECPE_OK);
 }
 
+extern "C" int secpe_keyswitch_batch_tc(secpe_ctx *ctx, const secpe_keys *keys, int galois_step,
+                                        const secpe_ctbatch *d, secpe_ctbatch *out, void *stream) {
+    if (!ctx || !keys || !out) return SECPE_EINVAL;
+    if (ctx->log_n != 16 || ctx->dnum > 8) return SECPE_EINVAL;
+    SECPE_CHECK(check_batch(ctx, d));
+    if (!out->data || out->batch != d->batch || out->cap < d->level + 1 || out->stride < 2ull * out->cap * ctx->n)
+        return SECPE_EINVAL;
+    CallScope cs(ctx, stream);
+    const u64 *key = galois_step == 0 ? keys->rlk : galois_key(keys, galois_elt(ctx, galois_step));
+    if (!key) return SECPE_EKEY;
+    struct TcMode {
+        secpe_ctx *c;
+        explicit TcMode(secpe_ctx *x) : c(x) { c->tc_mode = 1; }
+        ~TcMode() { c->tc_mode = 0; }
+    } tm(ctx);
+    CtB o = {(u64 *)out->data, out->batch, (long long)out->stride, out->cap, d->level, d->scale, ctx->n};
+    SECPE_CHECK(keyswitch(ctx, (const u64 *)d->data, (long long)d->stride, d->batch, d->level, key, o, false, false));
+    out->level = d->level;
+    out->scale = d->scale;
+    return finish(ctx, SECPE_OK);
+}
+
 extern "C" int secpe_mul_relin_batch(secpe_ctx *ctx, const secpe_keys *keys_, const secpe_ctbatch *a,
                                      const secpe_ctbatch *b, secpe_ctbatch *out, void *stream) {
     if (!ctx || !keys_ || !out) return SECPE_EINVAL;

@@ -126,6 +126,10 @@ struct secpe_ctx {
     std::vector<u64> h_qinv_neg, h_r2, h_mu;
     std::vector<ulonglong2> h_mu_inv;  // host mirror of DevCtx::mu_inv
     std::vector<u64> h_mdr_pre_scaled; // [l*(k+1) + j] floor(M/2) * [(M/s_j)^-1] mod s_j
+    // set for the duration of a precision-variant call: every NTT/INTT and
+    // the key inner product run on the tensor pipe (ntt_tc.cu), and the
+    // unfused key-switching kernels are used
+    int tc_mode = 0;
 };
 
 struct secpe_keys {

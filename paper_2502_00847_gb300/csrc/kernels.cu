@@ -781,6 +781,8 @@ int launch_modup_bconv(secpe_ctx *ctx, const u64 *x, u64 *ext, long long ext_ite
 
 int launch_ksk_ip(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const u64 *ext,
                   long long ext_item_stride, const KsDigits &dg, const u64 *key, u64 *acc, int B, int lv) {
+    if (ctx->tc_mode)
+        return launch_ksk_ip_tc(ctx, d, d_item_stride, ext, ext_item_stride, dg, key, acc, B, lv);
     const int nt = lv + 1 + ctx->npsp;
     // inputs (one residue per digit and target), key once, outputs (2 polys)
     KprofScope kp(ctx, "ksk_ip", 8.0 * ctx->n * ((double)B * dg.ndig * nt + 2.0 * dg.ndig * nt + 2.0 * B * nt));

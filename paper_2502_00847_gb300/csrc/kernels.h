@@ -37,6 +37,10 @@ int launch_modup_bconv(secpe_ctx *ctx, const u64 *x, u64 *ext, long long ext_ite
                        int B, int lv, int j, int lo, int hi, int ntgt);
 int launch_ksk_ip(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const u64 *ext,
                   long long ext_item_stride, const KsDigits &dg, const u64 *key, u64 *acc, int B, int lv);
+// The same inner product as exact 8-bit-limb contractions on the tensor
+// pipe (precision variant, ntt_tc.cu; N = 2^16, at most 8 digits).
+int launch_ksk_ip_tc(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const u64 *ext,
+                     long long ext_item_stride, const KsDigits &dg, const u64 *key, u64 *acc, int B, int lv);
 int launch_moddown_bconv(secpe_ctx *ctx, const u64 *acc, u64 *conv, int B, int lv);
 int launch_moddown_fin(secpe_ctx *ctx, const u64 *acc, const u64 *conv, const CtB &o, int lv, bool acc0,
                        bool acc1);

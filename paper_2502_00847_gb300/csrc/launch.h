@@ -101,7 +101,7 @@ int ntt16_pass(secpe_ctx *ctx, int slot, const LimbSet &ls);
 int wait_selftest(secpe_ctx *ctx, int arrive, long polls);
 // One ModUp-shaped base-conversion pass over buf (ntt_fused.cu).
 int bconv_pass_probe(secpe_ctx *ctx, u64 *buf, int nitem, int ntgt);
-// Precision variant (ntt_tc.cu): NTT/INTT with the column pass on the tensor pipe.
+// Precision variant (ntt_tc.cu): NTT/INTT with both passes on the tensor pipe.
 int ntt_limbset_tc(secpe_ctx *ctx, const LimbSet &ls, bool inverse);
 void tc_forget_ctx(const secpe_ctx *ctx);
 

@@ -346,6 +346,15 @@ int ntt_limbset(secpe_ctx *ctx, const LimbSet &ls, bool inverse, const LimbSet *
     a.scale_off = scale_off;
     a.has_src = src ? 1 : 0;
     a.src = src ? *src : ls;
+    if (ctx->tc_mode && ctx->log_n == 16) {
+        // precision variant: both passes on the tensor pipe (no folded scalings)
+        if (scale_tab) return SECPE_EINVAL;
+        if (src) {
+            a.tiles = 1;
+            SECPE_LAUNCH(ctx, k_copy_limbs, grid1d(nl * ctx->n, 256), 256, 0, a, nl * ctx->n);
+        }
+        return ntt_limbset_tc(ctx, ls, inverse);
+    }
     if (src && ctx->log_n != 16 && ctx->log_n != 12) {
         a.tiles = 1;
         SECPE_LAUNCH(ctx, k_copy_limbs, grid1d(nl * ctx->n, 256), 256, 0, a, nl * ctx->n);

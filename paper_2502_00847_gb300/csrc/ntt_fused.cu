@@ -311,7 +311,7 @@ __global__ void k_wait_selftest(const __grid_constant__ DevCtx c, int arrive, lo
 }  // namespace
 
 // ---------------------------------------------------------------- host side
-bool fused_path(const secpe_ctx *ctx) { return ctx->log_n == 16; }
+bool fused_path(const secpe_ctx *ctx) { return ctx->log_n == 16 && !ctx->tc_mode; }
 
 int wait_selftest(secpe_ctx *ctx, int arrive, long polls) {
     if (polls < 1 || polls > SECPE_WAIT_LIMIT) return SECPE_EINVAL;

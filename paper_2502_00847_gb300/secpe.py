@@ -28,7 +28,7 @@ EXPORTS = [
     "secpe_keyswitch_batch", "secpe_mul_relin_batch", "secpe_rotate_batch", "secpe_rescale_batch",
     "secpe_rescale_noalloc", "secpe_server_create", "secpe_server_destroy", "secpe_server_submit",
     "secpe_server_cancel", "secpe_server_step", "secpe_server_poll", "secpe_server_wait", "secpe_server_forget",
-    "secpe_server_stats", "secpe_ntt_tc", "secpe_ntt_cts_tc", "secpe_expand_seeded",
+    "secpe_server_stats", "secpe_ntt_tc", "secpe_ntt_cts_tc", "secpe_expand_seeded", "secpe_keyswitch_batch_tc",
 ]
 
 
@@ -131,6 +131,7 @@ def lib():
         "secpe_tuning_set": (i32, [vp, i32, i32]),
         "secpe_device_wait_selftest": (i32, [vp, i32, ctypes.c_int64, vp]),
         "secpe_keyswitch_batch": (i32, [vp, vp, i32, P(CtBatchC), P(CtBatchC), vp]),
+        "secpe_keyswitch_batch_tc": (i32, [vp, vp, i32, P(CtBatchC), P(CtBatchC), vp]),
         "secpe_mul_relin_batch": (i32, [vp, vp, P(CtBatchC), P(CtBatchC), P(CtBatchC), vp]),
         "secpe_rotate_batch": (i32, [vp, vp, P(CtBatchC), i32, P(CtBatchC), vp]),
         "secpe_rescale_batch": (i32, [vp, P(CtBatchC), P(CtBatchC), vp]),
@@ -637,6 +638,16 @@ def keyswitch_batch(ctx, keys, galois_step, d, out):
     cd, co = d.struct(), out.struct()
     _check(lib().secpe_keyswitch_batch(ctx.h, keys.h, galois_step, ctypes.byref(cd), ctypes.byref(co), _stream()),
            "secpe_keyswitch_batch")
+    out.update(co)
+    return out
+
+
+def keyswitch_batch_tc(ctx, keys, galois_step, d, out):
+    """Precision variant of keyswitch_batch (tensor-pipe transforms and key
+    inner product); bit-identical to it."""
+    cd, co = d.struct(), out.struct()
+    _check(lib().secpe_keyswitch_batch_tc(ctx.h, keys.h, galois_step, ctypes.byref(cd), ctypes.byref(co),
+                                          _stream()), "secpe_keyswitch_batch_tc")
     out.update(co)
     return out
 

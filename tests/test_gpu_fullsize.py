@@ -97,6 +97,35 @@ def test_micro_keyswitch_dnum3_bit_exact():
     g0, g1 = secpe.keyswitch(ctx, keys, 0, dt, lv)
     assert np.array_equal(g0.cpu().numpy().view(np.uint64), k0)
     assert np.array_equal(g1.cpu().numpy().view(np.uint64), k1)
+    # precision variant (tensor-pipe transforms and 3-digit inner product) against the oracle
+    x = torch.zeros((1, 2, lv + 1, ctx.n), dtype=torch.int64, device="cuda")
+    x[0, 0] = dt
+    out = secpe.CtBatch(torch.zeros_like(x), 0, ctx.scale)
+    secpe.keyswitch_batch_tc(ctx, keys, 0, secpe.CtBatch(x, lv, ctx.scale), out)
+    assert np.array_equal(out.data[0, 0].cpu().numpy().view(np.uint64), k0)
+    assert np.array_equal(out.data[0, 1].cpu().numpy().view(np.uint64), k1)
+
+
+def test_tensor_pipe_keyswitch_bit_identical(env):
+    """Precision variant of key switching: every NTT/INTT and the key inner
+    product on the tensor pipe give the residues of the CUDA-core key switch
+    (relinearisation and Galois keys; 6 digits at the top level, fewer below;
+    ragged batches of 9 and 3 items)."""
+    import torch
+    o, ctx, keys, secpe = env
+    cap = ctx.L + 1
+    for lv, B, step in [(ctx.L, 9, 0), (ctx.L, 1, 1), (11, 3, -2), (0, 2, 0)]:
+        x = workloads.residues((B, 2, cap, ctx.n), o.primes[:cap], seed=40 + lv)
+        xt = torch.from_numpy(x.view(np.int64)).cuda()
+        d = secpe.CtBatch(xt, lv, ctx.scale)
+        ref = secpe.CtBatch(torch.zeros_like(xt), 0, ctx.scale)
+        out = secpe.CtBatch(torch.zeros_like(xt), 0, ctx.scale)
+        secpe.keyswitch_batch(ctx, keys, step, d, ref)
+        secpe.keyswitch_batch_tc(ctx, keys, step, d, out)
+        torch.cuda.synchronize()
+        assert out.level == ref.level == lv
+        assert torch.equal(ref.data[:, :, : lv + 1], out.data[:, :, : lv + 1]), (lv, B, step)
+        assert torch.equal(xt, torch.from_numpy(x.view(np.int64)).cuda())  # input untouched
 
 
 def test_batched_argmax_mix(env):
@@ -130,8 +159,9 @@ def test_batched_argmax_mix(env):
 
 
 def test_tensor_pipe_ntt_bit_identical(env):
-    """Precision variant: column pass as an exact 8-bit-limb contraction on the
-    tensor pipe; forward and inverse bit-identical to the CUDA-core NTT."""
+    """Precision variant: both passes (columns, twist, rows) as exact
+    8-bit-limb contractions on the tensor pipe; forward and inverse
+    bit-identical to the CUDA-core NTT and to the oracle's transform."""
     import torch
     o, ctx, keys, secpe = env
     rng = np.random.default_rng(33)
