@@ -25,6 +25,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "encrypted ensemble-Argmax/s at N=2^16, batched vs plain; keyswitch GB/s; p99"
+# DRAM bytes per algorithmic byte of the N = 2^16 transform-pass family
+# (plain NTT/INTT passes, base-conversion pass A, inner-product and
+# epilogue passes B), measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) over every family launch of one HMult + relinearise
+# + rescale of 8 ciphertexts at level 23 (q0 + 23 x 50-bit, 8 special primes,
+# dnum = 3): 2.818 GB of DRAM traffic against 3.045 GB algorithmic.  The
+# step's family launches are the same kernels on more items, so their
+# traffic is taken in the same proportion to their algorithmic bytes.
+NTT16_DRAM_PER_ALG_BYTE = 2.818 / 3.045
 ROT_STEPS = [-2, -4, -8, -16, -64, 1, 2, 4, 8, 16, 32]
 
 
@@ -51,6 +60,9 @@ def parse():
                     help="primitive micro-benchmark (N=2^16, 24+4 primes, dnum=3) instead of the Argmax step")
     ap.add_argument("--micro-ops", default="ntt,keyswitch,hmult,rescale,rotate")
     ap.add_argument("--micro-batch", default="1,8,64")
+    ap.add_argument("--micro-probe", default="", choices=["", "hmult", "keyswitch", "ntt"],
+                    help="after timing, one more call of this op inside the NVTX range 'micro_probe' with the "
+                         "--kprof class profiled (its algorithmic bytes, for DRAM-traffic captures)")
     ap.add_argument("--tc-identity-count", type=int, default=10000,
                     help="seeded random ciphertexts of the precision variant's bit-identity checks")
     ap.add_argument("--serve", action="store_true",
@@ -492,7 +504,12 @@ def run_ours(args, world, rank, local):
     achieved = kp["bytes"] / (kp["total_ms"] / 1e3) / 1e9 if kp["total_ms"] > 0 else None
     roofline = {"bound": "hbm", "kernel": args.kprof, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-                "traffic": None, "launches_per_step": kp["launches"] / kp_steps,
+                "traffic": (NTT16_DRAM_PER_ALG_BYTE * kp["bytes"] / max(1, kp["launches"])
+                            if args.kprof == "ntt16" else None),
+                "traffic_source": ("ncu DRAM bytes per algorithmic byte of the family in one HMult+relin+rescale "
+                                   "of 8 ciphertexts (0.925), times this step's algorithmic bytes per launch"
+                                   if args.kprof == "ntt16" else None),
+                "launches_per_step": kp["launches"] / kp_steps,
                 "kernel_ms_per_step": kp["total_ms"] / kp_steps,
                 "bytes_per_launch": kp["bytes"] / max(1, kp["launches"])}
     if rank == 0:
@@ -594,6 +611,18 @@ def run_micro(args, rank):
         if "rescale" in ops:
             ms = timed(lambda: secpe.rescale_batch(ctx, a, o))
             res["rescale_B%d" % B] = {"ms": ms, "us_per_ct": ms * 1e3 / B}
+        if args.micro_probe:
+            probe = {"hmult": lambda: secpe.mul_relin_batch(ctx, keys, a, b, o),
+                     "keyswitch": lambda: secpe.keyswitch_batch(ctx, keys, 0, a, o),
+                     "ntt": lambda: secpe.ntt_cts(ctx, x, B, 2 * cap * n, cap, L)}[args.micro_probe]
+            torch.cuda.synchronize()
+            ctx.kprof_begin(args.kprof)
+            torch.cuda.nvtx.range_push("micro_probe")
+            probe()
+            torch.cuda.nvtx.range_pop()
+            kp = ctx.kprof_end()
+            res["probe_%s_B%d" % (args.micro_probe, B)] = {"kprof": args.kprof, "launches": kp["launches"],
+                                                           "alg_bytes": kp["bytes"], "ms": kp["total_ms"]}
         if "rotate" in ops:
             per = []
             for j in range(16):

@@ -186,9 +186,10 @@ int secpe_mul_relin(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *a, c
 /* Rounded division by the last prime; out may alias in. */
 int secpe_rescale(secpe_ctx *ctx, const secpe_ct *in, secpe_ct *out, void *stream);
 /* Same result as secpe_rescale (bit for bit), for callers that may not
- * allocate device memory during a call (graph capture that forbids
- * allocation calls, fixed-footprint serving loops, hosts that own all
- * device memory).  The paper has no counterpart: this is a deployment
+ * allocate device memory during a call: serving loops that must keep a
+ * fixed device-memory footprint and keep the allocator off their critical
+ * path, and host frameworks that own all device memory and forbid hidden
+ * allocations.  The paper has no counterpart: this is a deployment
  * variant.  Its scratch is a fixed file-scope device array of
  * 2 * 65536 * 24 words (24 MiB) that every GPU loading the library keeps
  * until exit; a call needs 2 * N * (level + 1) words and returns

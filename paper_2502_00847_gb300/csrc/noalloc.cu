@@ -2,12 +2,10 @@
 //
 // secpe_rescale normally takes its scratch buffers (the inverse NTT of the
 // last limb and the converted limbs) from the CUDA stream-ordered allocator.
-// Some callers cannot allow any allocation during the call: code that runs
-// while a CUDA graph is being captured under a mode that forbids
-// cudaMalloc-family calls, serving loops that must keep a fixed device
-// memory footprint and never touch the allocator on the critical path, and
-// hosts that manage all device memory through their own pool and forbid
-// hidden allocations.  secpe_rescale_noalloc serves them: its scratch is
+// Some callers cannot allow any allocation during the call: serving loops
+// that must keep a fixed device memory footprint and never touch the
+// allocator on the critical path, and hosts that manage all device memory
+// through their own pool and forbid hidden allocations.  secpe_rescale_noalloc serves them: its scratch is
 // one file-scope __device__ array of fixed size, reserved when the library
 // is loaded, that every GPU holding this library keeps until the process
 // exits.
