@@ -17,6 +17,11 @@
  *   stack of cap RNS limbs of N residues in NTT (evaluation) form, limb i
  *   modulo q_i.  Only limbs 0..level are meaningful.  The library never
  *   frees caller buffers.  Batched calls take arrays of secpe_ct.
+ * - Every device buffer passed in (ciphertext data, limb arrays, key-switch
+ *   operands) must start on a 16-byte boundary and every item stride (in
+ *   words) must be even; cudaMalloc and PyTorch allocations satisfy this.
+ *   Other pointers or strides are rejected with SECPE_EINVAL before anything
+ *   is launched (the kernels use 16-byte vector accesses and bulk copies).
  * - The context and key objects own their device memory (allocated with the
  *   CUDA stream-ordered allocator) and release it in *_destroy.
  * - There is no CPU fallback: without a usable CUDA device every call that

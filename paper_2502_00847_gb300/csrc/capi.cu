@@ -35,13 +35,14 @@ Ct view(secpe_ctx *ctx, const secpe_ct *c) {
 }
 
 int check_ct(const secpe_ctx *ctx, const secpe_ct *c) {
-    if (!c || !c->data || c->level < 0 || c->level > ctx->L || c->cap < c->level + 1) return SECPE_EINVAL;
+    if (!c || !c->data || !aligned16(c->data) || c->level < 0 || c->level > ctx->L || c->cap < c->level + 1)
+        return SECPE_EINVAL;
     if (!(c->scale > 0.0)) return SECPE_EINVAL;
     return SECPE_OK;
 }
 
 int copy_out(secpe_ctx *ctx, const Ct &src, secpe_ct *dst) {
-    if (!dst || !dst->data || dst->cap < src.level() + 1) return SECPE_EINVAL;
+    if (!dst || !dst->data || !aligned16(dst->data) || dst->cap < src.level() + 1) return SECPE_EINVAL;
     const size_t n = ctx->n;
     if ((u64 *)dst->data != src.v.data)
         SECPE_CUDA(cudaMemcpy2DAsync(dst->data, sizeof(u64) * dst->cap * n, src.v.data, sizeof(u64) * src.v.cap * n,
@@ -228,7 +229,7 @@ extern "C" int secpe_keys_export(const secpe_ctx *cctx, const secpe_keys *keys, 
 // ---------------------------------------------------------------- client
 extern "C" int secpe_encrypt_coeffs(secpe_ctx *ctx, const secpe_keys *keys, const int64_t *m, int level,
                                     double scale, uint64_t seed, secpe_ct *out, void *stream) {
-    if (!ctx || !keys || !m || !out || !out->data || level < 0 || level > ctx->L || out->cap < level + 1 ||
+    if (!ctx || !keys || !m || !out || !out->data || !aligned16(out->data) || level < 0 || level > ctx->L || out->cap < level + 1 ||
         !(scale > 0))
         return SECPE_EINVAL;
     CallScope cs(ctx, stream);
@@ -317,7 +318,7 @@ extern "C" int secpe_decrypt(secpe_ctx *ctx, const secpe_keys *keys, const secpe
 // ---------------------------------------------------------------- primitives
 extern "C" int secpe_ntt(secpe_ctx *ctx, uint64_t *limbs, const int32_t *prime_idx, int count, int inverse,
                          void *stream) {
-    if (!ctx || !limbs || !prime_idx || count < 0) return SECPE_EINVAL;
+    if (!ctx || !limbs || !aligned16(limbs) || !prime_idx || count < 0) return SECPE_EINVAL;
     CallScope cs(ctx, stream);
     for (int s = 0; s < count; s += SECPE_MAX_LIMBSET) {
         const int c = std::min(SECPE_MAX_LIMBSET, count - s);
@@ -333,8 +334,8 @@ extern "C" int secpe_ntt(secpe_ctx *ctx, uint64_t *limbs, const int32_t *prime_i
 
 extern "C" int secpe_ntt_cts(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, int cap, int level,
                              int inverse, void *stream) {
-    if (!ctx || !base || batch < 0 || level < 0 || level >= cap || level > ctx->L ||
-        ct_stride < 2ull * cap * ctx->n)
+    if (!ctx || !base || !aligned16(base) || (ct_stride & 1) || batch < 0 || level < 0 || level >= cap ||
+        level > ctx->L || ct_stride < 2ull * cap * ctx->n)
         return SECPE_EINVAL;
     CallScope cs(ctx, stream);
     LimbSet ls = make_limbset((u64 *)base, batch, (long long)ct_stride, 2, (long long)cap * ctx->n, level + 1, 0);
@@ -421,7 +422,9 @@ extern "C" int secpe_rotate(secpe_ctx *ctx, const secpe_keys *keys_, const secpe
 
 extern "C" int secpe_keyswitch(secpe_ctx *ctx, const secpe_keys *keys, int galois_step, const uint64_t *d,
                                int level, int cap, uint64_t *ks0, uint64_t *ks1, void *stream) {
-    if (!ctx || !keys || !d || !ks0 || !ks1 || level < 0 || level > ctx->L || cap < level + 1) return SECPE_EINVAL;
+    if (!ctx || !keys || !d || !ks0 || !ks1 || !aligned16(d) || !aligned16(ks0) || !aligned16(ks1) || level < 0 ||
+        level > ctx->L || cap < level + 1)
+        return SECPE_EINVAL;
     CallScope cs(ctx, stream);
     const u64 *key = galois_step == 0 ? keys->rlk : galois_key(keys, galois_elt(ctx, galois_step));
     if (!key) return SECPE_EKEY;
@@ -732,8 +735,9 @@ extern "C" int secpe_kprof_report(const secpe_ctx *ctx, char *buf, size_t len, s
 // ---------------------------------------------------------------- batched primitives
 namespace {
 int check_batch(const secpe_ctx *ctx, const secpe_ctbatch *b) {
-    if (!b || !b->data || b->batch < 1 || b->batch > SECPE_MAX_BATCH_CONST || b->level < 0 || b->level > ctx->L ||
-        b->cap < b->level + 1 || b->stride < 2ull * b->cap * ctx->n || !(b->scale > 0))
+    if (!b || !b->data || !aligned16(b->data) || (b->stride & 1) || b->batch < 1 || b->batch > SECPE_MAX_BATCH_CONST ||
+        b->level < 0 || b->level > ctx->L || b->cap < b->level + 1 || b->stride < 2ull * b->cap * ctx->n ||
+        !(b->scale > 0))
         return SECPE_EINVAL;
     return SECPE_OK;
 }
@@ -748,6 +752,15 @@ Ct bview(secpe_ctx *ctx, const secpe_ctbatch *b) {
     r.v.n = ctx->n;
     return r;
 }
+// Output batch of a batched call: checked before anything is launched (the
+// capacity is checked against the result's level when it is copied).
+int check_batch_out(const secpe_ctx *ctx, const secpe_ctbatch *out, int batch) {
+    if (!out || !out->data || !aligned16(out->data) || (out->stride & 1) || out->batch != batch || out->cap < 1 ||
+        out->stride < 2ull * out->cap * ctx->n)
+        return SECPE_EINVAL;
+    return SECPE_OK;
+}
+
 int copy_batch_out(secpe_ctx *ctx, const Ct &src, secpe_ctbatch *dst) {
     if (dst->cap < src.level() + 1 || dst->batch != src.B()) return SECPE_EINVAL;
     const size_t n = ctx->n;
@@ -765,7 +778,8 @@ extern "C" int secpe_keyswitch_batch(secpe_ctx *ctx, const secpe_keys *keys, int
                                      const secpe_ctbatch *d, secpe_ctbatch *out, void *stream) {
     if (!ctx || !keys || !out) return SECPE_EINVAL;
     SECPE_CHECK(check_batch(ctx, d));
-    if (!out->data || out->batch != d->batch || out->cap < d->level + 1 || out->stride < 2ull * out->cap * ctx->n)
+    if (!out->data || !aligned16(out->data) || (out->stride & 1) || out->batch != d->batch ||
+        out->cap < d->level + 1 || out->stride < 2ull * out->cap * ctx->n)
         return SECPE_EINVAL;
     CallScope cs(ctx, stream);
     const u64 *key = galois_step == 0 ? keys->rlk : galois_key(keys, galois_elt(ctx, galois_step));
@@ -782,7 +796,8 @@ extern "C" int secpe_keyswitch_batch_tc(secpe_ctx *ctx, const secpe_keys *keys, 
     if (!ctx || !keys || !out) return SECPE_EINVAL;
     if (ctx->log_n != 16 || ctx->dnum > 8) return SECPE_EINVAL;
     SECPE_CHECK(check_batch(ctx, d));
-    if (!out->data || out->batch != d->batch || out->cap < d->level + 1 || out->stride < 2ull * out->cap * ctx->n)
+    if (!out->data || !aligned16(out->data) || (out->stride & 1) || out->batch != d->batch ||
+        out->cap < d->level + 1 || out->stride < 2ull * out->cap * ctx->n)
         return SECPE_EINVAL;
     CallScope cs(ctx, stream);
     const u64 *key = galois_step == 0 ? keys->rlk : galois_key(keys, galois_elt(ctx, galois_step));
@@ -804,6 +819,7 @@ extern "C" int secpe_mul_relin_batch(secpe_ctx *ctx, const secpe_keys *keys_, co
     if (!ctx || !keys_ || !out) return SECPE_EINVAL;
     SECPE_CHECK(check_batch(ctx, a));
     SECPE_CHECK(check_batch(ctx, b));
+    SECPE_CHECK(check_batch_out(ctx, out, a->batch));
     EVAL_PROLOGUE(ctx, stream);
     Ct r;
     SECPE_CHECK(E.mul(bview(ctx, a), bview(ctx, b), r));
@@ -814,6 +830,7 @@ extern "C" int secpe_rotate_batch(secpe_ctx *ctx, const secpe_keys *keys_, const
                                   secpe_ctbatch *out, void *stream) {
     if (!ctx || !keys_ || !out) return SECPE_EINVAL;
     SECPE_CHECK(check_batch(ctx, in));
+    SECPE_CHECK(check_batch_out(ctx, out, in->batch));
     EVAL_PROLOGUE(ctx, stream);
     Ct r;
     SECPE_CHECK(E.rotate(bview(ctx, in), steps, r));
@@ -823,6 +840,7 @@ extern "C" int secpe_rotate_batch(secpe_ctx *ctx, const secpe_keys *keys_, const
 extern "C" int secpe_rescale_batch(secpe_ctx *ctx, const secpe_ctbatch *in, secpe_ctbatch *out, void *stream) {
     if (!ctx || !out) return SECPE_EINVAL;
     SECPE_CHECK(check_batch(ctx, in));
+    SECPE_CHECK(check_batch_out(ctx, out, in->batch));
     const secpe_keys *keys_ = nullptr;
     EVAL_PROLOGUE(ctx, stream);
     Ct r;
@@ -833,7 +851,7 @@ extern "C" int secpe_rescale_batch(secpe_ctx *ctx, const secpe_ctbatch *in, secp
 // ---------------------------------------------------------------- precision variant
 extern "C" int secpe_ntt_tc(secpe_ctx *ctx, uint64_t *limbs, const int32_t *prime_idx, int count, int inverse,
                             void *stream) {
-    if (!ctx || !limbs || !prime_idx || count < 0 || ctx->log_n != 16) return SECPE_EINVAL;
+    if (!ctx || !limbs || !aligned16(limbs) || !prime_idx || count < 0 || ctx->log_n != 16) return SECPE_EINVAL;
     CallScope cs(ctx, stream);
     for (int s = 0; s < count; s += SECPE_MAX_LIMBSET) {
         const int c = std::min(SECPE_MAX_LIMBSET, count - s);
@@ -849,8 +867,8 @@ extern "C" int secpe_ntt_tc(secpe_ctx *ctx, uint64_t *limbs, const int32_t *prim
 
 extern "C" int secpe_ntt_cts_tc(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, int cap, int level,
                                 int inverse, void *stream) {
-    if (!ctx || !base || batch < 0 || level < 0 || level >= cap || level > ctx->L || ctx->log_n != 16 ||
-        ct_stride < 2ull * cap * ctx->n)
+    if (!ctx || !base || !aligned16(base) || (ct_stride & 1) || batch < 0 || level < 0 || level >= cap ||
+        level > ctx->L || ctx->log_n != 16 || ct_stride < 2ull * cap * ctx->n)
         return SECPE_EINVAL;
     CallScope cs(ctx, stream);
     LimbSet ls = make_limbset((u64 *)base, batch, (long long)ct_stride, 2, (long long)cap * ctx->n, level + 1, 0);
@@ -859,8 +877,8 @@ extern "C" int secpe_ntt_cts_tc(secpe_ctx *ctx, uint64_t *base, int batch, size_
 
 extern "C" int secpe_expand_seeded(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, int cap, int level,
                                    const uint64_t *seeds, void *stream) {
-    if (!ctx || !base || !seeds || batch < 0 || level < 0 || level > ctx->L || cap < level + 1 ||
-        ct_stride < 2ull * cap * ctx->n)
+    if (!ctx || !base || !aligned16(base) || (ct_stride & 1) || !seeds || batch < 0 || level < 0 || level > ctx->L ||
+        cap < level + 1 || ct_stride < 2ull * cap * ctx->n)
         return SECPE_EINVAL;
     CallScope cs(ctx, stream);
     PrimeList pl;

@@ -398,12 +398,13 @@ static int argmax_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const sec
     if (nq_ > SECPE_MAX_BATCH_CONST) return SECPE_EINVAL;
     std::vector<int> order(nq_), rr(nq_), cps(nq_);
     for (int b = 0; b < nq_; b++) {
-        if (q[b].C < 2 || q[b].K < 1 || !q[b].cts || !q[b].z_out) return SECPE_EINVAL;
+        if (q[b].C < 2 || q[b].K < 1 || !q[b].cts || !q[b].z_out || !q[b].z_out->data || !aligned16(q[b].z_out->data))
+            return SECPE_EINVAL;
         rr[b] = log2_ceil_pow(q[b].C, cps[b]);
         if (2 * cps[b] > n / 2) return SECPE_EINVAL;
         for (int i = 0; i < q[b].K; i++) {
             const secpe_ct &c = q[b].cts[i];
-            if (!c.data || c.level != L || c.cap < L + 1) return SECPE_EINVAL;
+            if (!c.data || !aligned16(c.data) || c.level != L || c.cap < L + 1) return SECPE_EINVAL;
             if (!scales_match(c.scale, ctx->scale)) return SECPE_ESCALE;
         }
     }

@@ -109,6 +109,11 @@ struct Tuning {
     bool tuned = false;
 };
 
+// Device buffers handed to the C ABI must start on a 16-byte boundary and
+// item strides must be even (in words): the kernels read and write residues
+// with 16-byte vector accesses and bulk copies.
+static inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
 struct secpe_ctx {
     secpe_params p;
     int n, log_n, nq, npsp, nprimes, L, dnum, alpha;

@@ -55,7 +55,8 @@ int scratch_address(u64 **out) {
 }  // namespace
 
 extern "C" int secpe_rescale_noalloc(secpe_ctx *ctx, const secpe_ct *in, secpe_ct *out, void *stream) {
-    if (!ctx || !in || !out || !in->data || !out->data) return SECPE_EINVAL;
+    if (!ctx || !in || !out || !in->data || !out->data || !aligned16(in->data) || !aligned16(out->data))
+        return SECPE_EINVAL;
     if (in->level < 1 || in->level > ctx->L || in->cap < in->level + 1 || !(in->scale > 0.0)) return SECPE_EINVAL;
     if (out->cap < in->level) return SECPE_EINVAL;
     const int n = ctx->n, lv = in->level;

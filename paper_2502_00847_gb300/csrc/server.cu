@@ -236,7 +236,8 @@ extern "C" void secpe_server_destroy(secpe_server *s) {
 }
 
 extern "C" int secpe_server_submit(secpe_server *s, const secpe_query *q, int64_t *ticket) {
-    if (!s || !q || !ticket || !q->cts || !q->z_out || q->K < 1 || q->C < 2 || !(q->d_max > q->d_min))
+    if (!s || !q || !ticket || !q->cts || !q->z_out || !q->z_out->data || !aligned16(q->z_out->data) || q->K < 1 ||
+        q->C < 2 || !(q->d_max > q->d_min))
         return SECPE_EINVAL;
     const secpe_ctx *ctx = s->ctx;
     int r;
@@ -244,7 +245,7 @@ extern "C" int secpe_server_submit(secpe_server *s, const secpe_query *q, int64_
     if (2 * cp > ctx->n / 2) return SECPE_EINVAL;
     for (int i = 0; i < q->K; i++) {
         const secpe_ct &c = q->cts[i];
-        if (!c.data || c.level != ctx->L || c.cap < ctx->L + 1) return SECPE_EINVAL;
+        if (!c.data || !aligned16(c.data) || c.level != ctx->L || c.cap < ctx->L + 1) return SECPE_EINVAL;
         if (std::fabs(c.scale - ctx->scale) > ctx->scale * std::ldexp(1.0, -40)) return SECPE_ESCALE;
     }
     const secpe_keys *keys = q->keys ? q->keys : s->keys;

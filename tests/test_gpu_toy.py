@@ -221,6 +221,18 @@ def test_error_paths(env):
     with pytest.raises(secpe.SecpeError) as e:
         secpe.add(ctx, ct, other)
     assert e.value.code == -4
+    # buffers off a 16-byte boundary are rejected on the host, nothing is launched
+    import torch
+    flat = torch.zeros(ct.data.numel() + 1, dtype=torch.int64, device="cuda")
+    mis = secpe.Ciphertext(flat[1:].view(ct.data.shape), ct.level, ct.scale)
+    assert mis.data.data_ptr() % 16 == 8
+    before = ctx.counters()["launches"]
+    for call in (lambda: secpe.add(ctx, ct, mis), lambda: secpe.rescale(ctx, mis),
+                 lambda: secpe.ntt(ctx, flat[1:1 + ctx.n].view(1, ctx.n), [0])):
+        with pytest.raises(secpe.SecpeError) as e:
+            call()
+        assert e.value.code == -1
+    assert ctx.counters()["launches"] == before
     assert ctx.stream_status() == 0
 
 
