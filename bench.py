@@ -231,13 +231,13 @@ def oracle_sample(params_name, seconds_budget=20.0, workers=None):
 
 def op_mix_per_query(queries, reserve_params=None):
     """Keyswitch-equivalent op counts of the workload (relins + rotations),
-    from the circuit's structure: per query with C' = 2^r, 5 relinearisations
-    per degree-9 polynomial, relins = 20 (r + 1) + r, rotations = r + 1
+    from the circuit's structure: per query with C' = 2^r, 4 relinearisations
+    per degree-9 polynomial, relins = 16 (r + 1) + r, rotations = r + 1
     (sign_dg = sign_df = 2)."""
     tot_relin, tot_rot = 0, 0
     for q in queries:
         r = (q.C - 1).bit_length()
-        tot_relin += 20 * (r + 1) + r
+        tot_relin += 16 * (r + 1) + r
         tot_rot += r + 1
     return tot_relin / len(queries), tot_rot / len(queries)
 

@@ -573,32 +573,29 @@ class Oracle:
         return ct
 
     def poly9(self, x, c, s_out):
-        """Odd degree-9 p(x) = c1 x + c3 x^3 + c5 x^5 + c7 x^7 + c9 x^9 by the
-        fixed depth-4 baby-step giant-step DAG:
-          x2 = x*x, x3 = x*x2, x4 = x2*x2, x8 = x4*x4,
-          B = c5 x + c7 x3, T = x4 * B, U = x8 * (c9 x), A = c1 x + c3 x3,
-          p = A + (T + U),
-        the constant multiplies landing at the scales that make the addends'
-        scales equal to s_out; T and U are added before their single
-        relinearisation (5 key switches per polynomial); A and B are each one
-        linear combination with a single rescale (3 constant-multiply
-        rescales per polynomial)."""
+        """Odd degree-9 p(x) = c1 x + c3 x^3 + c5 x^5 + c7 x^7 + c9 x^9 (SecPE
+        Eq. comp: degree-9 f and g, evaluated baby-step giant-step).  READING
+        of the schedule: baby steps in y = x^2, giant step x^4,
+            p = x (c1 + c3 y) + x^5 (c5 + c7 y + c9 y^2),
+        by the depth-4 DAG
+          x2 = x*x, x4 = x2*x2, x5 = x4*x,
+          P1 = c7 x2 + c9 x4 + c5, P0 = c3 x2 + c1   (one rescale each),
+          p = relin_rescale(x5 (x) P1 + x (x) P0),
+        the two 3-component products being added before their single
+        relinearisation: 4 key switches per polynomial.  P1 lands at the
+        scale that gives p the scale s_out, P0 at the scale that makes both
+        products' scales equal."""
         c1, c3, c5, c7, c9 = c
         lv = x.level
         q3 = float(self.primes[lv - 3])
         x2 = self.mul(x, x)
-        x3 = self.mul(x, x2)
         x4 = self.mul(x2, x2)
-        x8 = self.mul(x4, x4)
-        sB = s_out * q3 / x4.scale
-        B = self.lincomb([(x, c5), (x3, c7)], sB, lv - 3)
-        s9 = s_out * q3 / x8.scale
-        X9 = self.mul_const(x, c9, s9, lv - 3)
-        # T = x4 * B and U = x8 * (c9 x) share one relinearisation (READING:
-        # lazy relinearisation, the 3-component products are added first)
-        TU = self.relin_rescale(self.add3(self.tensor(x4, B), self.tensor(x8, X9)))
-        A = self.lincomb([(x, c1), (x3, c3)], s_out, lv - 4)
-        return self.add(A, TU)
+        x5 = self.mul(x4, x)
+        s1 = s_out * q3 / x5.scale
+        P1 = self.add_const(self.lincomb([(x2, c7), (x4, c9)], s1, lv - 3), c5)
+        s0 = x5.scale * s1 / x.scale
+        P0 = self.add_const(self.lincomb([(x2, c3)], s0, lv - 3), c1)
+        return self.relin_rescale(self.add3(self.tensor(x5, P1), self.tensor(x, P0)))
 
     def sign(self, x, out_levels, last_factor=1.0):
         """Sign(x) = f^df(g^dg(x)) (SecPE Eq. comp); before each polynomial,

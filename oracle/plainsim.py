@@ -15,14 +15,11 @@ from .signpoly import sign_coeffs_float
 def poly9(x, c):
     c1, c3, c5, c7, c9 = c
     x2 = x * x
-    x3 = x * x2
     x4 = x2 * x2
-    x8 = x4 * x4
-    B = c5 * x + c7 * x3
-    T = x4 * B
-    U = x8 * (c9 * x)
-    A = c1 * x + c3 * x3
-    return A + (T + U)
+    x5 = x4 * x
+    P1 = c7 * x2 + c9 * x4 + c5
+    P0 = c3 * x2 + c1
+    return x5 * P1 + x * P0
 
 
 def sign(x, dg=2, df=2):

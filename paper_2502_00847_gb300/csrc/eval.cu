@@ -266,37 +266,42 @@ int Eval::ensure(const Ct &x, int k, Ct &out) {
     return SECPE_OK;
 }
 
+// Odd degree-9 p(x) = c1 x + c3 x^3 + c5 x^5 + c7 x^7 + c9 x^9 (Eq. comp),
+// baby steps in y = x^2 and giant step x^4 (BSGS):
+//   p = x (c1 + c3 y) + x^5 (c5 + c7 y + c9 y^2),
+// at depth 4: x2 = x*x, x4 = x2*x2, x5 = x4*x; P1 = c7 x2 + c9 x4 + c5 and
+// P0 = c3 x2 + c1 (one rescale each); the 3-component products x5 (x) P1
+// and x (x) P0 are added and relinearised once (4 key switches per
+// polynomial).  P1 lands at the scale that gives p the scale s_out, P0 at
+// the scale that makes the two products' scales equal.
 int Eval::poly9(const Ct &x, const double *c, double s_out, Ct &out) {
     const int lv = x.level();
     if (lv < 4 + ctx->p.reserve) return SECPE_ELEVEL;
     const double q3 = (double)ctx->primes[lv - 3];
     // temporaries are released as soon as they are dead (Ct() frees them)
-    Ct x2, x3, x4, x8, Bv, X9, T3, U3, TU3, TU, A;
+    Ct x2, x4, x5, L1, P1, L0, P0, T3, U3, TU3;
     SECPE_CHECK(mul(x, x, x2));
-    SECPE_CHECK(mul(x, x2, x3));
     SECPE_CHECK(mul(x2, x2, x4));
-    x2 = Ct();
-    SECPE_CHECK(mul(x4, x4, x8));
-    const double sB = s_out * q3 / x4.scale();
-    SECPE_CHECK(lincomb({&x, &x3}, {{c[2]}, {c[3]}}, sB, lv - 3, Bv));
-    const double s9 = s_out * q3 / x8.scale();
-    SECPE_CHECK(mul_const(x, {c[4]}, s9, lv - 3, X9));
-    // T = x4 * B and U = x8 * (c9 x) are added as 3-component ciphertexts and
-    // relinearised once
-    SECPE_CHECK(tensor(x4, Bv, T3));
+    SECPE_CHECK(mul(x4, x, x5));
+    const double s1 = s_out * q3 / x5.scale();
+    SECPE_CHECK(lincomb({&x2, &x4}, {{c[3]}, {c[4]}}, s1, lv - 3, L1));
     x4 = Ct();
-    Bv = Ct();
-    SECPE_CHECK(tensor(x8, X9, U3));
-    x8 = Ct();
-    X9 = Ct();
+    SECPE_CHECK(add_const(L1, c[2], P1));
+    L1 = Ct();
+    const double s0 = x5.scale() * s1 / x.scale();
+    SECPE_CHECK(lincomb({&x2}, {{c[1]}}, s0, lv - 3, L0));
+    x2 = Ct();
+    SECPE_CHECK(add_const(L0, c[0], P0));
+    L0 = Ct();
+    SECPE_CHECK(tensor(x5, P1, T3));
+    x5 = Ct();
+    P1 = Ct();
+    SECPE_CHECK(tensor(x, P0, U3));
+    P0 = Ct();
     SECPE_CHECK(add3(T3, U3, TU3));
     T3 = Ct();
     U3 = Ct();
-    SECPE_CHECK(relin_rescale(TU3, TU));
-    TU3 = Ct();
-    SECPE_CHECK(lincomb({&x, &x3}, {{c[0]}, {c[1]}}, s_out, lv - 4, A));
-    x3 = Ct();
-    return add(A, TU, out);
+    return relin_rescale(TU3, out);
 }
 
 // The last polynomial's coefficients are multiplied by last_factor, so the
