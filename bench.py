@@ -280,7 +280,7 @@ def run_ours(args, world, rank, local):
     import numpy as np
     import torch
 
-    from oracle.params import PRESETS
+    from paper_2502_00847_gb300.presets import PRESETS
     from paper_2502_00847_gb300 import build as pkg_build
     from paper_2502_00847_gb300 import secpe, workloads
 
@@ -542,7 +542,7 @@ def run_micro(args, rank):
     import numpy as np
     import torch
 
-    from oracle.params import PRESETS
+    from paper_2502_00847_gb300.presets import PRESETS
     from paper_2502_00847_gb300 import build as pkg_build
     from paper_2502_00847_gb300 import secpe
 
@@ -700,7 +700,7 @@ def run_serve(args, rank):
     import numpy as np
     import torch
 
-    from oracle.params import PRESETS
+    from paper_2502_00847_gb300.presets import PRESETS
     from paper_2502_00847_gb300 import build as pkg_build
     from paper_2502_00847_gb300 import secpe, workloads
 

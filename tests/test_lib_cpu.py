@@ -72,3 +72,16 @@ def test_context_without_gpu_fails_loudly(lib):
     with pytest.raises(secpe.SecpeError) as e:
         secpe.Context.from_params(TOY)
     assert e.value.code == -6
+
+
+def test_package_presets_match_the_oracles():
+    """The library's named parameter sets (numbers only) are the ones the
+    oracle defines, field by field."""
+    import dataclasses
+
+    from oracle import params as oparams
+    from paper_2502_00847_gb300 import presets
+    assert set(presets.PRESETS) == set(oparams.PRESETS)
+    for name, p in presets.PRESETS.items():
+        for f in dataclasses.fields(p):
+            assert getattr(p, f.name) == getattr(oparams.PRESETS[name], f.name), (name, f.name)
