@@ -597,11 +597,16 @@ class Oracle:
         P0 = self.add_const(self.lincomb([(x2, c3)], s0, lv - 3), c1)
         return self.relin_rescale(self.add3(self.tensor(x5, P1), self.tensor(x, P0)))
 
-    def sign(self, x, out_levels, last_factor=1.0):
+    def sign(self, x, out_levels, last_factor=1.0, lowest=False):
         """Sign(x) = f^df(g^dg(x)) (SecPE Eq. comp); before each polynomial,
         refresh if fewer than 4 (+ out_levels for the last) levels remain.
         The last polynomial's coefficients are multiplied by last_factor
-        (last_factor * Sign(x) at no extra level)."""
+        (last_factor * Sign(x) at no extra level).  READING (level-aware
+        evaluation; the paper does not discuss levels): with `lowest`, used
+        for the final Sign of Alg. 1, which nothing follows, each
+        polynomial's input is dropped to the levels the rest of the Sign
+        needs, 4 (polynomials left) + out_levels + reserve; refreshes are
+        the same as without it."""
         self.counters["signs"] += 1
         g, f = sign_coeffs_float()
         polys = [g] * self.p.sign_dg + [f] * self.p.sign_df
@@ -609,6 +614,9 @@ class Oracle:
             last = i == len(polys) - 1
             need = 4 + (out_levels if last else 0)
             x = self.ensure(x, need)
+            keep = 4 * (len(polys) - i) + out_levels + self.p.reserve
+            if lowest and x.level > keep:
+                x = self.drop(x, keep)
             x = self.poly9(x, [last_factor * ci for ci in c] if last else c, self.p.scale)
         return x
 
@@ -646,7 +654,7 @@ class Oracle:
             y = self.max(a, y)
         al = self.mul_const(y_dup, 1.0, y.scale, y.level)
         d = self.sub(al, y)
-        s = self.sign(d, 0)
+        s = self.sign(d, 0, lowest=True)
         return self.add_const(s, 1.0)
 
     def aggregate(self, cts, d_min, d_max):

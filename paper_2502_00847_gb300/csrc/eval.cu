@@ -305,8 +305,12 @@ int Eval::poly9(const Ct &x, const double *c, double s_out, Ct &out) {
 }
 
 // The last polynomial's coefficients are multiplied by last_factor, so the
-// result is last_factor * Sign(x) at no extra level.
-int Eval::sign(const Ct &x, int out_levels, Ct &out, double last_factor) {
+// result is last_factor * Sign(x) at no extra level.  With `lowest` (the
+// final Sign of Alg. 1, which nothing follows), the input of every
+// polynomial is dropped to the levels the rest of the Sign needs,
+// 4 (polynomials left) + out_levels + reserve, so that a polynomial after a
+// refresh runs on as few limbs as possible; the refresh count is unchanged.
+int Eval::sign(const Ct &x, int out_levels, Ct &out, double last_factor, bool lowest) {
     double g[5], f[5];
     sign_coeffs(g, f);
     ctx->counters.signs += x.B();
@@ -319,6 +323,8 @@ int Eval::sign(const Ct &x, int out_levels, Ct &out, double last_factor) {
         for (int k = 0; k < 5; k++) c[k] = (i < ctx->p.sign_dg ? g[k] : f[k]) * (last ? last_factor : 1.0);
         Ct e, p;
         SECPE_CHECK(ensure(cur, need, e));
+        const int keep = 4 * (np - i) + out_levels + ctx->p.reserve;
+        if (lowest && e.level() > keep) e = ct_drop(e, keep);
         SECPE_CHECK(poly9(e, c, ctx->scale, p));
         cur = p;
     }
@@ -368,7 +374,7 @@ int Eval::argmax(const Ct &y, int C, Ct &out) {
     Ct al, d, s;
     SECPE_CHECK(mul_const(ydup, {1.0}, y1.scale(), y1.level(), al));
     SECPE_CHECK(sub(al, y1, d));
-    SECPE_CHECK(sign(d, 0, s));
+    SECPE_CHECK(sign(d, 0, s, 1.0, true));
     return add_const(s, 1.0, out);
 }
 
@@ -477,7 +483,7 @@ static int argmax_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const sec
             Ct al, d, sgn, z;
             SECPE_CHECK(Ef.mul_const(df, {1.0}, yf.scale(), yf.level(), al));
             SECPE_CHECK(Ef.sub(al, yf, d));
-            SECPE_CHECK(Ef.sign(d, 0, sgn));
+            SECPE_CHECK(Ef.sign(d, 0, sgn, 1.0, true));
             SECPE_CHECK(Ef.add_const(sgn, 1.0, z));
             for (int s = cnt_gt; s < cnt_ge; s++) {
                 secpe_ct *zo = q[order[s]].z_out;

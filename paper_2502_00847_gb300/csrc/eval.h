@@ -73,7 +73,7 @@ struct Eval {
     int refresh(const Ct &x, Ct &out);
     int ensure(const Ct &x, int k, Ct &out);
     int poly9(const Ct &x, const double *c, double s_out, Ct &out);
-    int sign(const Ct &x, int out_levels, Ct &out, double last_factor = 1.0);
+    int sign(const Ct &x, int out_levels, Ct &out, double last_factor = 1.0, bool lowest = false);
     int max(const Ct &a, const Ct &y, Ct &out);
     int argmax(const Ct &y, int C, Ct &out);
 };

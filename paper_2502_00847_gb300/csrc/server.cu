@@ -188,7 +188,7 @@ int run_group(secpe_server *s, std::vector<QState *> &g) {
     SECPE_CHECK(gather(ctx, g, true, yd));
     SECPE_CHECK(E.mul_const(yd, {1.0}, y.scale(), y.level(), al));
     SECPE_CHECK(E.sub(al, y, d));
-    SECPE_CHECK(E.sign(d, 0, sg));
+    SECPE_CHECK(E.sign(d, 0, sg, 1.0, true));
     SECPE_CHECK(E.add_const(sg, 1.0, z));
     for (int b = 0; b < B; b++) {
         secpe_ct *zo = g[b]->q.z_out;
