@@ -312,3 +312,33 @@ def test_lazy_relinearisation_counts(toy_oracle):
     from oracle import plainsim
     ref = plainsim.sign(np.linspace(-0.4, 0.4, 8))
     assert np.max(np.abs(o.decrypt(s, 8) - ref)) < 2.0 ** -12
+
+
+@pytest.mark.parametrize("C,seed", [(2, 4), (4, 5)])
+def test_level_aware_final_sign_keeps_refreshes(C, seed, monkeypatch):
+    """Alg. 1's final Sign evaluated at the lowest sufficient levels (each
+    polynomial's input dropped to 4 (polynomials left) + reserve): the same
+    refresh count as with the greedy levels, z at the reserve level, and the
+    same decoded result within the Sign tolerance."""
+    from oracle import TOY
+    o = Oracle(TOY)
+    cp = 1 << (C - 1).bit_length()
+    r = cp.bit_length() - 1
+    o.keygen(700 + seed, rot_steps=[-cp] + [1 << i for i in range(r)])
+    rng = np.random.default_rng(seed)
+    logits = rng.uniform(-1, 1, (3, C))
+    cts = [o.encrypt_logits(logits[i], C, -1.0, seed=2000 + i) for i in range(3)]
+    y = o.aggregate(cts, -1.0, 1.0)
+    o.reset_counters()
+    z = o.argmax(y, C, qseed=9)
+    low_refreshes = o.counters["refreshes"]
+    assert z.level == o.p.reserve
+    zd = o.decrypt(z, C)
+    greedy = Oracle.sign
+    monkeypatch.setattr(Oracle, "sign", lambda self, x, out_levels, last_factor=1.0, lowest=False:
+                        greedy(self, x, out_levels, last_factor, False))
+    o.reset_counters()
+    zg = o.argmax(y, C, qseed=9)
+    assert o.counters["refreshes"] == low_refreshes
+    assert zg.level > z.level
+    assert np.max(np.abs(o.decrypt(zg, C) - zd)) < 2.0**-12
