@@ -28,10 +28,11 @@
 // holds byte d - a of k_{j,s} at column (j, a) (a Toeplitz band built in
 // registers from the key residue), column b of the right operand holds the
 // bytes of x_j[b], so S[(s, d)][b] = sum_j sum_{a+a'=d} x_{j,a} k_{j,s,a'}
-// is the d-th diagonal sum of the limb products (< 8 * 8 * 255^2 per
-// 4 digits).  The keys are stored in Montgomery form (k 2^64 mod p), so the
-// recombination constants are the plain powers 2^(8d) mod p and the one
-// Montgomery reduction also removes the key's factor 2^64.
+// is the d-th diagonal sum of the limb products (at most 8 limb pairs per
+// digit and 8 digits: < 64 * 255^2 < 2^31).  The keys are stored in
+// Montgomery form (k 2^64 mod p), so the recombination constants are the
+// plain powers 2^(8d) mod p and the one Montgomery reduction also removes
+// the key's factor 2^64.
 //
 // sm_103a has no tcgen05 kind::i8; the u8 mma.sync form is the integer
 // tensor path the compiler accepts for this target.
