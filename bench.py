@@ -21,19 +21,25 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "encrypted ensemble-Argmax/s at N=2^16, batched vs plain; keyswitch GB/s; p99"
-# DRAM bytes per algorithmic byte of the N = 2^16 transform-pass family
-# (plain NTT/INTT passes, base-conversion pass A, inner-product and
-# epilogue passes B), measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) over every family launch of one HMult + relinearise
-# + rescale of 8 ciphertexts at level 23 (q0 + 23 x 50-bit, 8 special primes,
-# dnum = 3): 2.818 GB of DRAM traffic against 3.045 GB algorithmic.  The
-# step's family launches are the same kernels on more items, so their
-# traffic is taken in the same proportion to their algorithmic bytes.
-NTT16_DRAM_PER_ALG_BYTE = 2.818 / 3.045
+# DRAM bytes per byte that the launches themselves read and write (every
+# transform pass a read and a write of each residue) of the N = 2^16
+# transform-pass family (plain NTT/INTT passes, base-conversion pass A,
+# inner-product and epilogue passes B), measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) over every family launch of
+# one HMult + relinearise + rescale of 8 ciphertexts at level 23 (q0 + 23 x
+# 50-bit, 8 special primes, dnum = 3): 2.818 GB of DRAM traffic against
+# 3.045 GB read and written.  The step's family launches are the same
+# kernels on more items, so their traffic is taken in the same proportion.
+NTT16_DRAM_PER_MODEL_BYTE = 2.818 / 3.045
+# integer multiply pipe: 152 SMs, 64 32-bit multiplies (IMAD-class) per clock per SM
+SM_COUNT = 152
+MUL32_PER_CLK_PER_SM = 64
 ROT_STEPS = [-2, -4, -8, -16, -64, 1, 2, 4, 8, 16, 32]
 
 
@@ -46,8 +52,8 @@ def parse():
     ap.add_argument("--queries", type=int, default=256)
     ap.add_argument("--classes", default="2,3,4,6,14,64",
                     help="class counts C drawn uniformly per query (the default is the mix)")
-    ap.add_argument("--plain-queries", type=int, default=16,
-                    help="queries timed on the one-query-per-launch path")
+    ap.add_argument("--plain-queries", type=int, default=-1,
+                    help="queries timed on the one-query-per-launch path (-1: all of the mix, 0: none)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--kprof", default="ntt16",
@@ -68,7 +74,16 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving loop: Poisson arrivals, continuous batching, p50/p99 latency")
     ap.add_argument("--rates", default="50,200,500,1000,2000")
-    ap.add_argument("--serve-queries", type=int, default=384, help="queries submitted per arrival rate")
+    ap.add_argument("--serve-rate", type=float, default=64.0,
+                    help="default run: one short serving run at this rate (queries/s; 0: none)")
+    ap.add_argument("--serve-window", type=float, default=8.0, help="default run: its arrival window (s)")
+    ap.add_argument("--packed-sets", type=int, default=256,
+                    help="default run: packed query sets of the slot-packing line (0: none)")
+    ap.add_argument("--no-keyswitch-gbps", dest="keyswitch_gbps", action="store_false",
+                    help="default run: skip the primitive-set key-switch GB/s")
+    ap.add_argument("--serve-seconds", type=float, default=30.0, help="arrival window per rate")
+    ap.add_argument("--serve-queries", type=int, default=3000, help="at most this many queries per rate")
+    ap.add_argument("--no-plain-serve", action="store_true", help="serving: skip the plain path's real run")
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--tenants", type=int, default=1,
                     help="serving: tenants with their own resident key sets (queries batch within a tenant)")
@@ -184,56 +199,27 @@ def hbm_peak():
 
 
 # ---------------------------------------------------------------- oracle
-def _oracle_copy(job):
-    """One copy of the oracle sample: full-size HMult+relin+rescale at levels
-    23/15/7 and one rotation at level 12 (single thread)."""
-    params_name, seed, seconds_budget = job
-    import numpy as np
-    from oracle import PRESETS, Oracle
-    o = Oracle(PRESETS[params_name])
-    t0 = time.perf_counter()
-    o.keygen(11 + seed, rot_steps=[1])
-    rng = np.random.default_rng(seed)
-    a = o.encrypt(rng.uniform(-1, 1, 8), seed=1 + seed)
-    samples = []
-    for lv in (23, 15, 7):
-        x = o.drop(a, lv)
-        t = time.perf_counter()
-        o.mul(x, x)
-        samples.append(time.perf_counter() - t)
-        if time.perf_counter() - t0 > seconds_budget:
-            break
-    t = time.perf_counter()
-    o.rotate(o.drop(a, 12), 1)
-    t_rot = time.perf_counter() - t
-    return sum(samples) / len(samples), t_rot
+# The CPU oracle (test infrastructure) is run only by the cpu_baseline leg of
+# the GPU arm and by the reference arm, in worker processes started with
+# spawn.
+ORACLE_KEY_SEED = 4711
+ORACLE_ROT = (-2, 1)
 
 
-def oracle_sample(params_name, seconds_budget=20.0, workers=None):
-    """Times the CPU oracle on full-size primitives of the workload: one copy
-    per host core (at most 16) runs concurrently in a process pool started
-    with spawn, so the per-copy times include the contention of a fully
-    loaded host.  Returns (HMult seconds, rotation seconds, wall seconds,
-    cores used)."""
+def oracle_cores():
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+def oracle_pool(cores):
     import multiprocessing
-    n = workers or max(1, min(16, os.cpu_count() or 1))
-    t0 = time.perf_counter()
-    jobs = [(params_name, i, seconds_budget) for i in range(n)]
-    if n == 1:
-        res = [_oracle_copy(jobs[0])]
-    else:
-        with multiprocessing.get_context("spawn").Pool(n) as pool:
-            res = pool.map(_oracle_copy, jobs)
-    t_mul = sum(r[0] for r in res) / n
-    t_rot = sum(r[1] for r in res) / n
-    return t_mul, t_rot, time.perf_counter() - t0, n
+    return multiprocessing.get_context("spawn").Pool(cores)
 
 
-def op_mix_per_query(queries, reserve_params=None):
-    """Keyswitch-equivalent op counts of the workload (relins + rotations),
-    from the circuit's structure: per query with C' = 2^r, 4 relinearisations
-    per degree-9 polynomial, relins = 16 (r + 1) + r, rotations = r + 1
-    (sign_dg = sign_df = 2)."""
+def op_mix_per_query(queries):
+    """Key switches per query of the workload, from the circuit's structure:
+    with C' = 2^r, 4 relinearisations per degree-9 polynomial, 16 per Sign,
+    r + 1 Signs and r products of Max: relins = 16 (r + 1) + r; rotations =
+    r + 1 (sign_dg = sign_df = 2).  The GPU counters of a step equal these."""
     tot_relin, tot_rot = 0, 0
     for q in queries:
         r = (q.C - 1).bit_length()
@@ -242,34 +228,98 @@ def op_mix_per_query(queries, reserve_params=None):
     return tot_relin / len(queries), tot_rot / len(queries)
 
 
-def run_reference(args, world, rank):
-    from oracle import PRESETS
+def oracle_whole_queries(pool, cores, params_name):
+    """Every host core runs one whole query (C = 2, K = 4: ensemble
+    aggregation + Alg. 1 at N = 2^16, the cheapest query of the mix)
+    concurrently; returns its mean time, key switches and refreshes."""
+    from oracle import jobs as ojobs
     from paper_2502_00847_gb300 import workloads
+    qs = [workloads.argmax_queries(1, seed=500 + i, K_choices=(4,), C_choices=(2,))[0] for i in range(cores)]
+    jobs = [(params_name, ORACLE_KEY_SEED, ORACLE_ROT, q.logits, q.d_min, q.d_max, q.qseed, q.enc_seeds)
+            for q in qs]
+    t0 = time.perf_counter()
+    res = pool.map(ojobs.ensemble_query, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    for q, r in zip(qs, res):
+        assert int(np.argmax(r["decoded"])) == int(np.argmax(q.logits.mean(0))), "oracle argmax wrong"
+    c = res[0]["counters"]
+    return {"t_query": statistics.mean(r["seconds"] for r in res),
+            "ks_query": c["relins"] + c["rotations"], "refreshes": c["refreshes"], "wall": wall}
+
+
+def cpu_rate(whole, ks_mix):
+    """queries/s of the host cores on the mix: the measured whole query's time
+    per key switch times the mix's key switches per query."""
+    return whole["cores"] * whole["ks_query"] / (ks_mix * whole["t_query"])
+
+
+def cpu_baseline_line(whole, ks_mix, relin_pq, rot_pq, value=None):
+    v = cpu_rate(whole, ks_mix) if value is None else value
+    return {"value": v, "unit": "queries/s", "cores": whole["cores"], "kind": "oracle",
+            "sample": "each of %d host cores ran one whole query of the workload (C=2, K=4: aggregation + "
+                      "Alg. 1 at N=2^16, %d key switches, %d refresh) concurrently: %.1f s per query; scaled to "
+                      "the mix by key switches per query (%.1f relins + %.1f rotations); %.0f s wall"
+                      % (whole["cores"], whole["ks_query"], whole["refreshes"], whole["t_query"], relin_pq,
+                         rot_pq, whole["wall"])}
+
+
+def workloads_argmax_queries(n):
+    from paper_2502_00847_gb300 import workloads
+    return workloads.argmax_queries(n, seed=4)
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands on the host cores.  Before the steps, every core
+    runs one whole query (the calibration above, untimed); each step then is
+    a bounded sample of the workload: every core runs one HMult +
+    relinearisation + rescale at one of 16 levels spread over 2..L (the
+    circuit's dominant operation over the levels it visits), concurrently.
+    A step's rate is the whole-query rate scaled by how fast that sample ran
+    against the same sample in the first warm-up step."""
+    from oracle import PRESETS
+    from oracle import jobs as ojobs
     if rank != 0:
         return
     P = PRESETS[args.params]
-    qs = workloads.argmax_queries(args.queries, seed=4)
+    qs = workloads_argmax_queries(args.queries)
     relin_pq, rot_pq = op_mix_per_query(qs)
-    times = []
-    for i in range(args.warmup + args.steps):
-        t_mul, t_rot, _, cores = oracle_sample(args.params, seconds_budget=5.0)
-        per_query = relin_pq * t_mul + rot_pq * t_rot
-        if i >= args.warmup:
-            times.append(per_query)
-    per_query = sum(times) / len(times)
-    value = cores / per_query
+    ks_mix = relin_pq + rot_pq
+    cores = oracle_cores()
+    L = P.n_q - 1
+    levels = [2 + round(i * (L - 2) / (cores - 1)) if cores > 1 else L for i in range(cores)]
+    pool = oracle_pool(cores)
+    try:
+        whole = oracle_whole_queries(pool, cores, args.params)
+        whole["cores"] = cores
+        base_rate = cpu_rate(whole, ks_mix)
+        ref_t, rates, walls = None, [], []
+        for i in range(args.warmup + args.steps):
+            jobs = [(args.params, ORACLE_KEY_SEED, ORACLE_ROT, lv, 1000 * i + c) for c, lv in enumerate(levels)]
+            t0 = time.perf_counter()
+            ts = pool.map(ojobs.hmult_sample, jobs, chunksize=1)
+            wall = time.perf_counter() - t0
+            t_mean = statistics.mean(ts)
+            if ref_t is None:
+                ref_t = t_mean
+            if i >= args.warmup:
+                rates.append(base_rate * ref_t / t_mean)
+                walls.append(wall)
+    finally:
+        pool.close()
+        pool.join()
+    value = statistics.mean(rates)
+    cb = cpu_baseline_line(whole, ks_mix, relin_pq, rot_pq, value=value)
+    cb["sample"] += ("; per step: one HMult+relin+rescale per core at levels %s, concurrently (%.2f s wall per "
+                     "step); a step's rate = the whole-query rate x (first warm-up sample time / step sample time)"
+                     % (levels, statistics.mean(walls)))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_query * 1e3 * args.queries,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(walls),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": "batched encrypted ensemble Argmax, N=2^16, %d queries, K~U{4,8,16}, "
-                               "C~U{2,3,4,6,14,64}" % args.queries, "queries": args.queries,
+                               "C~U{2,3,4,6,14,64}, seed 4" % args.queries, "queries": args.queries,
                    "params": "q0 60-bit + 23x50-bit, %d special 60-bit, dnum=%d, Delta=2^50" % (P.n_p, P.dnum)},
-        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                         "sample": "per step: oracle HMult+relin+rescale at levels 23/15/7 and one rotation "
-                                   "at level 12, N=2^16, one copy per host core (%d, concurrent); queries/s = "
-                                   "cores / per-query time extrapolated with the mix's %.1f relins + %.1f "
-                                   "rotations per query" % (cores, relin_pq, rot_pq)},
+        "cpu_baseline": cb,
         "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -393,27 +443,27 @@ def run_ours(args, world, rank, local):
                "note": "refresh = test-only stand-in for bootstrapping (decrypt, CRT lift, re-encrypt); "
                        "measured on one direct step after the timed region"}
 
-    # plain path: the same kernels, one query per call, sequentially
+    # plain path: the same kernels, one query per call, sequentially, over
+    # every query of the mix (the same workload as the batched step)
     plain = None
-    if args.plain_queries > 0 and rank == 0:
-        npq = min(args.plain_queries, len(qs))
-        # a sample of the mix with the same class-count distribution as the full mix
-        idx = list(range(npq))
+    if args.plain_queries != 0 and rank == 0:
+        npq = len(qs) if args.plain_queries < 0 else min(args.plain_queries, len(qs))
         zt = ctx.new_ct()
-        for i in idx[:2]:
+        for i in range(min(2, npq)):
             y = secpe.ensemble_aggregate(ctx, batch[i]["cts"], qs[i].d_min, qs[i].d_max)
             secpe.encrypted_argmax(ctx, keys, y, qs[i].C, qs[i].qseed, out=zt)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for i in idx:
+        for i in range(npq):
             y = secpe.ensemble_aggregate(ctx, batch[i]["cts"], qs[i].d_min, qs[i].d_max)
             secpe.encrypted_argmax(ctx, keys, y, qs[i].C, qs[i].qseed, out=zt)
         e1.record()
         torch.cuda.synchronize()
         pms = e0.elapsed_time(e1)
         plain = {"value": npq / (pms / 1e3), "unit": "queries/s", "queries": npq,
-                 "note": "one ciphertext batch of 1 per launch, sequential; first %d queries of the mix" % npq}
+                 "note": "one query per call (aggregate + encrypted_argmax, batch of 1 per launch), sequential, "
+                         "%s" % ("every query of the mix" if npq == len(qs) else "first %d queries" % npq)}
 
     # end to end through host buffers (pinned): every step copies its inputs in
     # as seeded ciphertexts (c0 + the 8-byte encryption seed; c1 is regenerated
@@ -489,29 +539,79 @@ def run_ours(args, world, rank, local):
         except RuntimeError as e:
             e2e = {"value": None, "unit": "queries/s", "error": str(e)[:200]}
 
+    # a short serving run at one rate (continuous batching vs the plain path,
+    # both run for real on the same arrivals), on the resident mix
+    serve = None
+    if args.serve_rate > 0 and rank == 0:
+        serve = serve_rate(ctx, keys, [keys] * len(qs), [b["cts"] for b in batch], qs, args.serve_rate,
+                           args.serve_window, 5, int(args.budget_gb * 1e9), 64, 10 ** 6)
+
+    # key switching of the primitive set (config 2: 24 x 50-bit + 4 special,
+    # dnum = 3) at B = 1 and B = 8, algorithmic bytes = input + key + output
+    ksw = keyswitch_gbps(secpe, torch, dev, args.steps) if args.keyswitch_gbps and rank == 0 else None
+
+    # measured throughput of the integer multiply pipe (the ALU roofline)
+    probe = ctx.mul32_probe() if rank == 0 else None
+
+    # rooflines of the N = 2^16 transform-pass family (the kernel class timed
+    # live over the timed step): HBM (algorithmic bytes) and integer ALU
+    # (algorithmic 32-bit multiplies); the binding one is the higher fraction
+    hbm, hbm_kind = hbm_peak()
+    fam_s = kp["total_ms"] / 1e3
+    per_launch = lambda x: x / max(1, kp["launches"])
+    gbs = kp["bytes"] / fam_s / 1e9 if fam_s > 0 else None
+    r_hbm = {"bound": "hbm", "kernel": args.kprof, "achieved": gbs, "peak": hbm, "unit": "GB/s",
+             "frac": gbs / hbm if gbs else None, "peak_kind": hbm_kind,
+             "traffic": (NTT16_DRAM_PER_MODEL_BYTE * per_launch(kp["model_bytes"]) if args.kprof == "ntt16" else None),
+             "traffic_source": ("ncu dram bytes read+write per byte the family's launches read and write "
+                                "(0.925, one HMult+relin+rescale of 8 ciphertexts), times this step's such bytes "
+                                "per launch" if args.kprof == "ntt16" else None),
+             "bytes_per_launch": per_launch(kp["bytes"]),
+             "traffic_model": per_launch(kp["model_bytes"]),
+             "traffic_model_note": "bytes each launch itself reads and writes (every transform pass a read and a "
+                                   "write of each residue, intermediates included)"}
+    smax = clk.get("sm_max_mhz") or 2070.0
+    alu_peak = MUL32_PER_CLK_PER_SM * SM_COUNT * smax * 1e6 / 1e12
+    tmul = kp["mul32"] / fam_s / 1e12 if fam_s > 0 else None
+    r_alu = {"bound": "alu", "kernel": args.kprof, "achieved": tmul, "peak": alu_peak, "unit": "Tmul32/s",
+             "frac": tmul / alu_peak if tmul else None,
+             "peak_kind": "derived: %d SMs x %d 32-bit multiplies per clock per SM x %.0f MHz"
+                          % (SM_COUNT, MUL32_PER_CLK_PER_SM, smax),
+             "probe": probe / 1e12 if probe else None,
+             "frac_of_probe": (tmul / (probe / 1e12)) if (tmul and probe) else None,
+             "probe_note": "secpe_mul32_probe: 128-bit multiply-accumulate chains (8 32-bit multiplies each) "
+                           "on register data, all SMs",
+             "mul32_per_launch": per_launch(kp["mul32"]),
+             "traffic": None}
+    common = {"launches_per_step": kp["launches"] / kp_steps, "kernel_ms_per_step": kp["total_ms"] / kp_steps,
+              "family_share_of_step": (kp["total_ms"] / kp_steps) / ms_per_step}
+    r_hbm.update(common)
+    r_alu.update(common)
+    roofline, other = (r_alu, r_hbm) if (r_alu["frac"] or 0) >= (r_hbm["frac"] or 0) else (r_hbm, r_alu)
+
+    # free the device state of the one-query-per-ciphertext mix
+    del inputs, zbuf, batch
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+    # slot-packed multi-query Argmax: the mix's tasks, every ciphertext set
+    # filled to capacity (N/(4C') inputs per ciphertext)
+    packed = (run_packed(secpe, torch, workloads, ctx, keys, dev, min(args.steps, 5), args.packed_sets)
+              if args.packed_sets and rank == 0 else None)
+
     cpu = None
     if not args.no_cpu and rank == 0:
-        t_mul, t_rot, wall, cores = oracle_sample(args.params)
         relin_pq, rot_pq = op_mix_per_query(qs)
-        per_query = relin_pq * t_mul + rot_pq * t_rot
-        cpu = {"value": cores / per_query, "unit": "queries/s", "cores": cores, "kind": "oracle",
-               "sample": "oracle HMult+relin+rescale at levels 23/15/7 and one rotation at level 12, N=2^16, "
-                         "one copy per host core (%d, concurrent, %.1f s wall); one query per core, per-query "
-                         "time extrapolated with the mix's %.1f relins + %.1f rotations"
-                         % (cores, wall, relin_pq, rot_pq)}
+        cores = oracle_cores()
+        pool = oracle_pool(cores)
+        try:
+            whole = oracle_whole_queries(pool, cores, args.params)
+        finally:
+            pool.close()
+            pool.join()
+        whole["cores"] = cores
+        cpu = cpu_baseline_line(whole, relin_pq + rot_pq, relin_pq, rot_pq)
 
-    peak, peak_kind = hbm_peak()
-    achieved = kp["bytes"] / (kp["total_ms"] / 1e3) / 1e9 if kp["total_ms"] > 0 else None
-    roofline = {"bound": "hbm", "kernel": args.kprof, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-                "traffic": (NTT16_DRAM_PER_ALG_BYTE * kp["bytes"] / max(1, kp["launches"])
-                            if args.kprof == "ntt16" else None),
-                "traffic_source": ("ncu DRAM bytes per algorithmic byte of the family in one HMult+relin+rescale "
-                                   "of 8 ciphertexts (0.925), times this step's algorithmic bytes per launch"
-                                   if args.kprof == "ntt16" else None),
-                "launches_per_step": kp["launches"] / kp_steps,
-                "kernel_ms_per_step": kp["total_ms"] / kp_steps,
-                "bytes_per_launch": kp["bytes"] / max(1, kp["launches"])}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
@@ -525,14 +625,111 @@ def run_ours(args, world, rank, local):
                        "parallelism": "dp%d (independent queries per GPU)" % world,
                        "launch": ("one CUDA graph per step (%d nodes)" % graph_nodes) if graph_nodes
                                  else "direct call per step",
+                       "refresh": "test-only interactive stand-in for bootstrapping (decrypt, CRT lift, "
+                                  "re-encrypt), included in every step",
                        "autotune": {k: v["ctas_per_sm"] for k, v in tuning.items()}},
-            "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+            "plain": plain, "e2e": e2e, "roofline": roofline, "roofline_other": other, "cpu_baseline": cpu,
+            "keyswitch_GBps": ksw, "serve": serve, "packed": packed,
+            "p99_ms": serve["served"]["p99_ms"] if serve else None,
             "clocks": clk, "gpu_launches": cnt["launches"], "refresh": refresh,
             **({"breakdown": breakdown} if breakdown else {}),
             "per_step_ops": {k: cnt[k] / args.steps for k in ("rotations", "signs", "relins", "refreshes",
                                                                "keyswitches")},
         }
         print(json.dumps(line))
+
+
+def run_packed(secpe, torch, workloads, ctx, keys, dev, steps, n_sets=256):
+    """Slot packing (SecPE Sec. 3.2 after Alg. 1): n_sets packed query sets
+    drawn like the mix's queries (K ~ U{4,8,16}, C ~ U{2,...,64}, seed 6),
+    each filled to N/(4C') inputs, encrypted by the library's packed encoder;
+    one step = secpe_argmax_batch over all sets (the same circuit as the
+    one-query-per-ciphertext step, on full slot vectors)."""
+    sets = workloads.packed_queries(n_sets, ctx.n // 2, seed=6)
+    n_cts = sum(s.K for s in sets)
+    cap = ctx.L + 1
+    t0 = time.perf_counter()
+    data = torch.empty((n_cts, 2, cap, ctx.n), dtype=torch.int64, device=dev)
+    batch, off = [], 0
+    for s in sets:
+        cts = []
+        for i in range(s.K):
+            c = secpe.Ciphertext(data[off], 0, ctx.scale)
+            secpe.encrypt_logits_packed(ctx, keys, s.prompt(i), s.d_min, s.enc_seeds[i], out=c)
+            cts.append(c)
+            off += 1
+        batch.append(dict(cts=cts, C=s.C, d_min=s.d_min, d_max=s.d_max, qseed=s.qseed, z_out=ctx.new_ct()))
+    torch.cuda.synchronize()
+    t_enc = time.perf_counter() - t0
+    secpe.argmax_batch(ctx, keys, batch)
+    torch.cuda.synchronize()
+    # every input of the first sets against its exact argmax
+    checked = 0
+    for s, b in list(zip(sets, batch))[:8]:
+        zd = secpe.decrypt_packed(ctx, keys, b["z_out"], s.P, s.C)
+        assert np.array_equal(zd.argmax(1), s.logits.mean(1).argmax(1)), "wrong packed argmax"
+        checked += s.P
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        secpe.argmax_batch(ctx, keys, batch)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    inputs = sum(s.P for s in sets)
+    del batch, data
+    torch.cuda.empty_cache()
+    return {"value": inputs / (ms / 1e3), "unit": "queries/s", "inputs_per_step": inputs, "sets": len(sets),
+            "input_ciphertexts": n_cts, "ms_per_step": ms, "steps": steps, "inputs_checked": checked,
+            "encrypt_s": t_enc,
+            "workload": "slot-packed: %d query sets with the mix's K and C (seed 6), each filled to N/(4C') "
+                        "inputs per ciphertext; one step = secpe_argmax_batch over all sets (direct call)"
+                        % len(sets)}
+
+
+def keyswitch_gbps(secpe, torch, dev, steps):
+    """Key switching with the relinearisation key of the primitive set (N =
+    2^16, 24 x 50-bit + 4 x 60-bit special primes, dnum = 3) on uniform
+    residues (seed 2) at B = 1 and B = 8 items per launch; GB/s of
+    algorithmic bytes (input B (L+1) limbs + key 2 dnum (L+1+k) limbs + output
+    2 B (L+1) limbs, 8 N bytes each) over the mean launch time."""
+    from paper_2502_00847_gb300.presets import MICRO
+    ctx = secpe.Context.from_params(MICRO)
+    ctx.autotune()
+    keys = secpe.Keys(ctx, 2, [])
+    n, cap, L = ctx.n, ctx.L + 1, ctx.L
+    primes = ctx.primes()
+    limb = n * 8
+    dnum = -(-ctx.n_q // -(-ctx.n_q // MICRO.dnum))
+    ksk = dnum * 2 * (cap + ctx.n_p) * limb
+    gen = torch.Generator(device=dev).manual_seed(2)
+    out = {}
+    for B in (1, 8):
+        x = torch.empty((B, 2, cap, n), dtype=torch.int64, device=dev)
+        for i in range(cap):
+            x[:, :, i] = torch.randint(0, primes[i], (B, 2, n), generator=gen, dtype=torch.int64, device=dev)
+        a = secpe.CtBatch(x, L, ctx.scale)
+        o = secpe.CtBatch(torch.zeros_like(x), 0, ctx.scale)
+        for _ in range(3):
+            secpe.keyswitch_batch(ctx, keys, 0, a, o)
+        reps = max(10, steps)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            secpe.keyswitch_batch(ctx, keys, 0, a, o)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        alg = B * 3 * cap * limb + ksk
+        out["B%d" % B] = {"GBps": alg / (ms / 1e3) / 1e9, "ms": ms, "alg_bytes": alg}
+        del x, a, o
+    out["note"] = ("primitive set N=2^16, 24x50-bit + 4x60-bit special, dnum=3, relinearisation key, top level; "
+                   "algorithmic bytes = input + key + output; the key (84 MiB) is L2-sized, so back-to-back "
+                   "launches can reuse it from L2")
+    keys.close()
+    ctx.close()
+    return out
 
 
 def run_micro(args, rank):
@@ -692,12 +889,89 @@ def run_micro(args, rank):
                           "steps": args.steps, "warmup": args.warmup, "results": res}))
 
 
+def serve_rate(ctx, keys, tkeys, views, queries, lam, seconds, seed, budget_bytes, max_batch, max_queries,
+               plain=True):
+    """One arrival rate of the serving loop.  Poisson arrivals at `lam`/s for
+    `seconds` (at most max_queries), each a query drawn from `queries` (its
+    input ciphertexts `views` resident on the device, its key set tkeys[i]).
+
+    served: secpe_server_* with continuous batching and admission by the HBM
+    budget; latency = arrival -> z ready on the device (host clock).
+    plain:  the same arrivals served for real by the plain path, one query
+    per call (aggregate + encrypted_argmax) in arrival order on the same GPU;
+    latency = arrival -> that call's completion."""
+    import torch
+    from paper_2502_00847_gb300 import secpe
+    rng = np.random.default_rng(seed)
+    nq = max(1, min(max_queries, int(round(lam * seconds))))
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, nq))
+    pick = rng.integers(0, len(queries), nq)
+    srv = secpe.Server(ctx, keys, hbm_budget_bytes=budget_bytes, max_batch=max_batch)
+    zbufs, pending, lat, batch_sizes, inflight = {}, {}, [], [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nxt = 0
+    while nxt < nq or pending:
+        now = time.perf_counter() - t0
+        while nxt < nq and arrivals[nxt] <= now:
+            i = int(pick[nxt])
+            z = ctx.new_ct()
+            tk = srv.submit(views[i], queries[i].C, queries[i].d_min, queries[i].d_max, queries[i].qseed + nxt, z,
+                            keys=tkeys[i])
+            pending[tk] = arrivals[nxt]
+            zbufs[tk] = z
+            nxt += 1
+        launched = srv.step()
+        if launched:
+            batch_sizes.append(launched)
+            ev = torch.cuda.Event()
+            ev.record()
+            inflight.append(ev)
+            if len(inflight) > 4:   # bounds how far the host runs ahead of the GPU
+                inflight.pop(0).synchronize()
+        done = [tk for tk in pending if srv.poll(tk) == 1]
+        now = time.perf_counter() - t0
+        for tk in done:
+            lat.append(now - pending.pop(tk))
+            srv.forget(tk)
+            zbufs.pop(tk)
+        if not launched and not done and nxt < nq:
+            time.sleep(max(0.0, min(0.002, arrivals[nxt] - now)))
+        elif not launched and not done:
+            torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array(lat)
+    out = {"rate_qps": lam, "queries": nq, "arrival_window_s": float(arrivals[-1]),
+           "served": {"throughput_qps": nq / wall, "p50_ms": 1e3 * float(np.median(lat)),
+                      "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                      "mean_batch": float(np.mean(batch_sizes)) if batch_sizes else 0.0}}
+    if plain:
+        zt = ctx.new_ct()
+        plat = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a, i in zip(arrivals, pick):
+            i = int(i)
+            now = time.perf_counter() - t0
+            if now < a:
+                time.sleep(a - now)
+            y = secpe.ensemble_aggregate(ctx, views[i], queries[i].d_min, queries[i].d_max)
+            secpe.encrypted_argmax(ctx, tkeys[i], y, queries[i].C, queries[i].qseed, out=zt)
+            torch.cuda.synchronize()
+            plat.append(time.perf_counter() - t0 - a)
+        pwall = time.perf_counter() - t0
+        plat = np.array(plat)
+        out["plain"] = {"throughput_qps": nq / pwall, "p50_ms": 1e3 * float(np.median(plat)),
+                        "p99_ms": 1e3 * float(np.percentile(plat, 99)),
+                        "note": "run for real: one query per call in arrival order"}
+    return out
+
+
 def run_serve(args, rank):
-    """Serving loop (Poisson arrivals at each rate, continuous batching by
-    secpe_server_*, admission by an HBM budget) against the plain path: the
-    same queries served one at a time in arrival order (FIFO queue with the
-    measured one-query service times)."""
-    import numpy as np
+    """Serving loop (config 5): Poisson arrivals at each rate, continuous
+    batching by secpe_server_*, admission by an HBM budget, against the plain
+    path run for real on the same arrivals."""
     import torch
 
     from paper_2502_00847_gb300.presets import PRESETS
@@ -723,81 +997,21 @@ def run_serve(args, rank):
             cts.append(c)
             off += 1
         views.append(cts)
-    # plain service time per pool query (one query per call)
-    zt = ctx.new_ct()
-    svc = []
-    for i, q in enumerate(pool):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        y = secpe.ensemble_aggregate(ctx, views[i], q.d_min, q.d_max)
-        secpe.encrypted_argmax(ctx, tkeys[i], y, q.C, q.qseed, out=zt)
-        torch.cuda.synchronize()
-        svc.append(time.perf_counter() - t)
     results = []
-    rng = np.random.default_rng(5)
-    for lam in [float(x) for x in args.rates.split(",")]:
-        nq = args.serve_queries
-        arrivals = np.cumsum(rng.exponential(1.0 / lam, nq))
-        pick = rng.integers(0, len(pool), nq)
-        srv = secpe.Server(ctx, tenants[0], hbm_budget_bytes=int(args.budget_gb * 1e9), max_batch=64)
-        zbufs = {}
-        pending = {}
-        lat = []
-        t0 = time.perf_counter()
-        nxt = 0
-        batch_sizes = []
-        inflight = []  # one event per enqueued phase: bounds how far the host runs ahead of the GPU
-        while nxt < nq or pending:
-            now = time.perf_counter() - t0
-            while nxt < nq and arrivals[nxt] <= now:
-                i = int(pick[nxt])
-                z = ctx.new_ct()
-                tk = srv.submit(views[i], pool[i].C, pool[i].d_min, pool[i].d_max, pool[i].qseed + nxt, z,
-                                keys=tkeys[i])
-                pending[tk] = arrivals[nxt]
-                zbufs[tk] = z
-                nxt += 1
-            launched = srv.step()
-            if launched:
-                batch_sizes.append(launched)
-                ev = torch.cuda.Event()
-                ev.record()
-                inflight.append(ev)
-                if len(inflight) > 4:
-                    inflight.pop(0).synchronize()
-            done = [tk for tk in pending if srv.poll(tk) == 1]
-            now = time.perf_counter() - t0
-            for tk in done:
-                lat.append(now - pending.pop(tk))
-                srv.forget(tk)
-                zbufs.pop(tk)
-            if not launched and not done and nxt < nq:
-                time.sleep(max(0.0, min(0.002, arrivals[nxt] - now)))
-            elif not launched and not done:
-                torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        srv.close()
-        # plain path: FIFO single server with the measured service times
-        finish, plat = 0.0, []
-        for a, i in zip(arrivals, pick):
-            finish = max(finish, a) + svc[int(i)]
-            plat.append(finish - a)
-        lat = np.array(lat)
-        plat = np.array(plat)
-        results.append({"rate_qps": lam, "queries": nq,
-                        "served": {"throughput_qps": nq / (wall - arrivals[0]), "p50_ms": 1e3 * np.median(lat),
-                                   "p99_ms": 1e3 * np.percentile(lat, 99),
-                                   "mean_batch": float(np.mean(batch_sizes)) if batch_sizes else 0},
-                        "plain": {"throughput_qps": nq / (finish - arrivals[0]), "p50_ms": 1e3 * np.median(plat),
-                                  "p99_ms": 1e3 * np.percentile(plat, 99)}})
+    for k, lam in enumerate(float(x) for x in args.rates.split(",")):
+        results.append(serve_rate(ctx, tenants[0], tkeys, views, pool, lam, args.serve_seconds, 5 + int(lam),
+                                  int(args.budget_gb * 1e9), 64, args.serve_queries,
+                                  plain=not args.no_plain_serve))
     if rank == 0:
         print(json.dumps({"mode": "serve", "metric": METRIC,
-                          "config": {"workload": "serving loop: Poisson arrivals, %d queries per rate from a pool of "
-                                                 "64 (K~U{4,8,16}, C~U{2,3,4,6,14,64}, seed 5), N=2^16, HBM "
-                                                 "budget %.0f GB, max batch 64, %d tenant key set(s) resident"
-                                                 % (args.serve_queries, args.budget_gb, args.tenants),
+                          "config": {"workload": "serving loop: Poisson arrivals, %.0f s per rate (at most %d "
+                                                 "queries), queries from a pool of 64 (K~U{4,8,16}, "
+                                                 "C~U{2,3,4,6,14,64}, seed 5), N=2^16, HBM budget %.0f GB, max "
+                                                 "batch 64, %d tenant key set(s) resident"
+                                                 % (args.serve_seconds, args.serve_queries, args.budget_gb,
+                                                    args.tenants),
                                      "tenants": args.tenants},
-                          "plain_service_ms_mean": 1e3 * float(np.mean(svc)), "rates": results}))
+                          "rates": results}))
 
 
 def main():

@@ -26,6 +26,15 @@
  *   CUDA stream-ordered allocator) and release it in *_destroy.
  * - There is no CPU fallback: without a usable CUDA device every call that
  *   needs one returns SECPE_ECUDA.
+ * - A context serves one host thread at a time: every call that takes a
+ *   stream records it in the context (its temporaries are allocated and
+ *   freed on it, its launches and profiler events go to it) for the duration
+ *   of the call, and the counters, profiler and device status word are
+ *   per context.  Calls from several host threads on one context must be
+ *   serialised by the caller; use one context per thread (or per stream) to
+ *   run them concurrently.  Successive calls on different streams are fine
+ *   when the caller orders the streams (events) wherever one call's outputs
+ *   are another's inputs.
  */
 #ifndef SECPE_H
 #define SECPE_H
@@ -110,10 +119,15 @@ int secpe_device_wait_selftest(secpe_ctx *ctx, int arrive, int64_t polls, void *
 const char *secpe_strerror(int code);
 
 /* ---- keys ------------------------------------------------------------- */
-/* Secret key s (ternary), relinearisation key (s^2 -> s) and one Galois key
+/* Key generation of the RNS-CKKS scheme (SecPE Sec. 2.2; the user holds the
+ * secret key, Sec. 3.1 step 1, the server the evaluation keys, step 3).
+ * Secret key s (ternary), relinearisation key (s^2 -> s) and one Galois key
  * per rotation step in rot_steps (r > 0: RotL by r; r < 0: RotR by -r), all
  * drawn from the counter-based SplitMix64 streams of `seed` (same streams
- * as the CPU oracle).  Synchronous. */
+ * as the CPU oracle).  The keys object owns its device memory (about
+ * dnum * 2 * (n_q + n_p) * N words per key); steps are taken modulo N/2.
+ * Synchronous; SECPE_EINVAL for null pointers or n_rot < 0, SECPE_ENOMEM or
+ * SECPE_ECUDA when the keys cannot be allocated. */
 int secpe_keygen(secpe_ctx *ctx, uint64_t seed, const int32_t *rot_steps, int n_rot,
                  secpe_keys **out);
 void secpe_keys_destroy(secpe_keys *keys);
@@ -138,6 +152,38 @@ int secpe_encrypt(secpe_ctx *ctx, const secpe_keys *keys, const double *v, int n
  * beyond. */
 int secpe_encrypt_logits(secpe_ctx *ctx, const secpe_keys *keys, const double *v, int C,
                          double d_min, uint64_t seed, secpe_ct *out, void *stream);
+/* Slot packing (SecPE Sec. 3.2, the paragraph after Alg. 1: one ciphertext
+ * of N/2 slots carries the inputs of several queries that share the task,
+ * i.e. the class count C and the prompt ensemble, and Alg. 1 runs on all of
+ * them at once).  Query b of P occupies the block of 2C' slots starting at
+ * slot 2C'b (C' = next power of two >= C): its C logits, then d_min up to
+ * C', then C' zeros, the room the duplication y + RotR(y, C') fills.
+ * Rotations by C' and by 2^i < C' keep every window Alg. 1 reads inside the
+ * block, so after secpe_argmax_batch / secpe_encrypted_argmax (with C, one
+ * query per packed ciphertext set) block b's first C slots hold query b's
+ * z.  The K prompts of a packed query are K packed ciphertexts (prompt i of
+ * every packed input in ciphertext i); K, d_min, d_max are shared.
+ *
+ * secpe_packed_capacity: inputs per ciphertext, N / (4 C') (0 when one block
+ * does not fit); host only.  SECPE_EINVAL for log_n outside 4..17 or C < 1. */
+int secpe_packed_capacity(int log_n, int C);
+/* Host only: the integer coefficients m[N] of the packed slot vector of
+ * v[P][C] (row-major) at scale `scale`: the canonical embedding of
+ * secpe_encrypt computed in O(N log N) by a length-N complex DFT over the
+ * odd powers of zeta (equal to the direct sums up to floating-point
+ * rounding), rounded half away from zero.  SECPE_EINVAL for P outside
+ * 1..capacity or a coefficient beyond 2^62. */
+int secpe_encode_packed(int log_n, double scale, const double *v, int P, int C, double d_min, int64_t *m_out);
+/* Host only: the first C slots of each of the P blocks, out[P][C], from
+ * centred coefficients (secpe_decrypt_coeffs) divided by `scale`. */
+int secpe_decode_packed(int log_n, double scale, const double *coeffs, int P, int C, double *out);
+/* secpe_encode_packed + secpe_encrypt_coeffs at the top level, scale Delta. */
+int secpe_encrypt_logits_packed(secpe_ctx *ctx, const secpe_keys *keys, const double *v, int P, int C,
+                                double d_min, uint64_t seed, secpe_ct *out, void *stream);
+/* Decrypts a packed result: out[P][C] (host) = the first C slots of every
+ * block.  Synchronous. */
+int secpe_decrypt_packed(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *ct, int P, int C, double *out,
+                         void *stream);
 /* Seeded ciphertexts: c1 of a fresh encryption is the uniform polynomial
  * drawn from the stream of its encryption seed, so a client can send c0 and
  * the 8-byte seed only.  This regenerates c1 (limbs 0..level) on the device
@@ -146,7 +192,11 @@ int secpe_encrypt_logits(secpe_ctx *ctx, const secpe_keys *keys, const double *v
  * to the ciphertext secpe_encrypt* produced. */
 int secpe_expand_seeded(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, int cap, int level,
                         const uint64_t *seeds, void *stream);
-/* Decrypts and decodes slots 0..n-1 to host doubles.  Synchronous. */
+/* Decryption and decoding by the user (SecPE Sec. 3.1 step 4; Sec. 2.2 Dec
+ * and the canonical-embedding decoding): m = c0 + c1 s over the ciphertext's
+ * limbs, exact CRT to centred integers, slots 0..n-1 (slot j at
+ * zeta^(5^j)) divided by the ciphertext's scale, to host doubles (v_out[n]).
+ * Synchronous; SECPE_EINVAL for n outside 0..N/2. */
 int secpe_decrypt(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *ct, double *v_out,
                   int n, void *stream);
 /* Centred coefficients of c0 + c1*s as doubles (host, N values). */
@@ -188,7 +238,10 @@ int secpe_add_const(secpe_ctx *ctx, const secpe_ct *a, double c, secpe_ct *out, 
 /* Tensor, relinearise, rescale: out at level min(level_a, level_b) - 1. */
 int secpe_mul_relin(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *a, const secpe_ct *b,
                     secpe_ct *out, void *stream);
-/* Rounded division by the last prime; out may alias in. */
+/* Rescale (SecPE Sec. 2.2: after a product the scale is divided by the last
+ * prime q_l): rounded division (c + floor(q_l/2) - [c + floor(q_l/2)]_{q_l})
+ * / q_l of every coefficient, out at level l - 1 with scale s / q_l; out
+ * may alias in.  SECPE_ELEVEL at level 0. */
 int secpe_rescale(secpe_ctx *ctx, const secpe_ct *in, secpe_ct *out, void *stream);
 /* Same result as secpe_rescale (bit for bit), for callers that may not
  * allocate device memory during a call: serving loops that must keep a
@@ -198,13 +251,22 @@ int secpe_rescale(secpe_ctx *ctx, const secpe_ct *in, secpe_ct *out, void *strea
  * variant.  Its scratch is a fixed file-scope device array of
  * 2 * 65536 * 24 words (24 MiB) that every GPU loading the library keeps
  * until exit; a call needs 2 * N * (level + 1) words and returns
- * SECPE_EINVAL beyond that (N = 2^16: level <= 23).  The first call on a
- * device looks up the array's device address (make it before any stream
- * capture).  All calls share the array: calls that may overlap on the GPU
- * race and must not be issued.  No cudaMalloc/cudaFree or other allocating
- * call is made.  out may alias in. */
+ * SECPE_EINVAL beyond that (N = 2^16: level <= 23).  Under CUDA's default
+ * lazy module loading the array is reserved on a device by the first call
+ * there (its set-up looks up the array's device address and loads the
+ * module), so that call can fail with SECPE_ECUDA on a full device: make one
+ * warm-up call per device at start-up, before admitting requests and before
+ * any stream capture.  After it, no cudaMalloc/cudaFree or other allocating
+ * call is made.  All calls share the array: calls that may overlap on the
+ * GPU race and must not be issued.  Errors as secpe_rescale (SECPE_ELEVEL
+ * at level 0).  out may be in itself (same data and cap); any other overlap
+ * of the two buffers returns SECPE_EINVAL. */
 int secpe_rescale_noalloc(secpe_ctx *ctx, const secpe_ct *in, secpe_ct *out, void *stream);
-/* RotL(in, steps) for steps > 0, RotR(in, -steps) for steps < 0. */
+/* Rotation of the slot vector (SecPE Sec. 2.2 RotL / RotR, used by Alg. 1):
+ * RotL(in, steps) for steps > 0, RotR(in, -steps) for steps < 0, as the
+ * automorphism X -> X^(5^steps) followed by hybrid key switching with the
+ * Galois key of that step; out at in's level and scale (out may alias in).
+ * SECPE_EKEY when the key was not generated. */
 int secpe_rotate(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *in, int steps,
                  secpe_ct *out, void *stream);
 /* Hybrid key switching of one polynomial d ([cap][N], limbs 0..level, NTT
@@ -212,16 +274,22 @@ int secpe_rotate(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *in, int
  * a rotation step: writes ks0, ks1 ([cap][N] each). */
 int secpe_keyswitch(secpe_ctx *ctx, const secpe_keys *keys, int galois_step, const uint64_t *d,
                     int level, int cap, uint64_t *ks0, uint64_t *ks1, void *stream);
-/* Test-only, INSECURE stand-in for bootstrapping: decrypt, exact CRT lift,
- * re-encrypt at the top level with the same scale; randomness from the
- * stream (qseed, refresh_index). */
+/* Test-only, INSECURE stand-in for bootstrapping (SecPE Sec. 2.2 and Sec. 4.1
+ * rely on bootstrapping to restore levels without describing it): decrypt
+ * with the secret key held by the keys object, exact CRT lift, re-encrypt at
+ * the top level with the same scale; randomness from the stream (qseed,
+ * refresh_index).  It makes the evaluation interactive and must not be used
+ * where the server may not see plaintexts. */
 int secpe_refresh_testonly(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *in,
                            uint64_t qseed, uint64_t refresh_index, secpe_ct *out, void *stream);
 
 /* ---- batched primitives -------------------------------------------------- */
-/* `batch` ciphertexts at data + i*stride (words), each [2][cap][N], all at
- * the same level and scale.  Outputs are written to caller memory with the
- * same conventions; the output level/scale fields are set by the call. */
+/* The primitives of SecPE Sec. 2.2 (key switching, product + relinearisation
+ * + rescale, rotation, rescale) on `batch` ciphertexts at once, each launch
+ * serving all of them: batch ciphertexts at data + i*stride (words), each
+ * [2][cap][N], all at the same level and scale.  Outputs are written to
+ * caller memory with the same conventions; the output level/scale fields
+ * are set by the call. */
 typedef struct {
     uint64_t *data;
     int32_t batch;
@@ -309,11 +377,14 @@ void secpe_graph_destroy(secpe_graph *g);
 
 /* ---- continuous-batching server ---------------------------------------- */
 /* A server keeps the state of admitted queries on the device and advances
- * them phase by phase (aggregation + duplication, QuickMax rounds, final
- * Sign); each secpe_server_step runs one phase, batched over every query at
- * the same point of the circuit as the oldest admitted query (up to
- * max_batch), so queries submitted while others run join at the next phase
- * boundary.  Queries of different tenants (secpe_query.keys; null = the
+ * them phase by phase through SecPE's circuit (Sec. 3.1 step 3 and Alg. 1:
+ * aggregation + duplication, QuickMax rounds, final Sign).  Each
+ * secpe_server_step admits what fits, then enqueues one phase of every query
+ * in flight: queries at the same point of the circuit (same tenant, phase
+ * and class-count power) form a group evaluated as one batch of at most
+ * max_batch queries, groups in the order of their oldest member.  A query
+ * submitted while others are mid-circuit therefore starts in the next step,
+ * its launches interleaved on the stream with theirs.  Queries of different tenants (secpe_query.keys; null = the
  * server's keys) are batched only with queries of the same tenant.  Every
  * key set seen is counted as resident; a query is admitted when those keys +
  * in-flight states + one step's scratch + its state fit hbm_budget_bytes;
@@ -335,8 +406,8 @@ void secpe_server_destroy(secpe_server *srv);
 int secpe_server_submit(secpe_server *srv, const secpe_query *q, int64_t *ticket);
 /* Drops a query that has not completed (its state is released). */
 int secpe_server_cancel(secpe_server *srv, int64_t ticket);
-/* Admits what fits, then enqueues one batched phase on `stream`; *launched
- * = number of queries in that phase (0 when idle). */
+/* Admits what fits, then enqueues one phase of every query in flight on
+ * `stream`; *launched = number of queries advanced (0 when idle). */
 int secpe_server_step(secpe_server *srv, void *stream, int *launched);
 /* *done = 1 when the query's result is ready on the device, 0 if not yet,
  * -1 if cancelled. */
@@ -377,16 +448,35 @@ int secpe_autotune(secpe_ctx *ctx, secpe_tuning *out, void *stream);
 int secpe_tuning_set(secpe_ctx *ctx, int kernel, int ctas_per_sm);
 
 /* ---- instrumentation --------------------------------------------------- */
+/* Device memory of the stream-ordered allocator on the current device (the
+ * default memory pool, from which the library takes its temporaries and
+ * which keeps freed blocks cached): *used = bytes in live allocations,
+ * *reserved = bytes the pool holds from the driver.  With trim != 0 the
+ * device is synchronised and the pool's unused blocks are returned to the
+ * driver first.  Either output may be null.  SECPE_ECUDA without a device. */
+int secpe_pool_usage(int trim, uint64_t *used, uint64_t *reserved);
 /* Times, with CUDA events recorded on the launching stream around each
  * launch, every launch of the library kernels whose name contains
  * name_filter ("ntt", "ksk_ip", "modup", "moddown", ...), up to
  * max_launches launches, until secpe_kprof_end.  `bytes` accumulates each
- * recorded launch's algorithmic bytes (the minimal DRAM traffic of the
- * operation: operands read once, results written once). */
+ * recorded launch's share of its operation's algorithmic bytes (the minimal
+ * DRAM traffic of the operation: its operands read once, its results
+ * written once, its intermediates not at all; a standalone NTT/INTT is 16 N
+ * bytes per limb, a key switch of B items at level l is B (l + 1) limbs in +
+ * the key's 2 dnum(l) (l + 1 + n_p) limbs + B 2 (l + 1) limbs out, 8 N bytes
+ * each).  `model_bytes` accumulates what the recorded launches themselves
+ * read and write (each transform pass a read and a write of every residue,
+ * intermediates included).  `mul32` accumulates their algorithmic 32-bit
+ * multiplies: the 32 x 32-bit partial-product halves (mul.lo / mul.hi) of
+ * the 64-bit modular products the kernels form (15 per Shoup product, 19
+ * per Montgomery product, 8 per 128-bit multiply-accumulate, 11 per
+ * Montgomery reduction; 60 per residue per 8-stage transform pass). */
 typedef struct {
     int64_t launches;
     double total_ms;
     double bytes;
+    double model_bytes;
+    double mul32;
 } secpe_kprof;
 int secpe_kprof_begin(secpe_ctx *ctx, const char *name_filter, int max_launches);
 /* Synchronises the device, sums the recorded durations, stops recording. */
@@ -398,6 +488,16 @@ int secpe_kprof_end(secpe_ctx *ctx, secpe_kprof *out);
  * null) and the full text's size + 1 into *needed.  SECPE_EINVAL while the
  * profiler is still recording. */
 int secpe_kprof_report(const secpe_ctx *ctx, char *buf, size_t len, size_t *needed);
+/* Throughput probe of the integer multiply pipe (the roofline of the
+ * transform and base-conversion kernels): one launch of
+ * (SMs x ctas_per_sm) CTAs of 256 threads, each thread running 4
+ * independent 128-bit multiply-accumulate chains (8 32-bit multiplies each,
+ * the form the kernels use) for `iters` iterations on register data,
+ * timed with CUDA events on `stream` after one untimed launch.  Writes the
+ * achieved 32-bit multiplies per second to *mul32_per_s (host).  Scratch:
+ * one 8-byte word per thread from the stream-ordered allocator.  iters in
+ * 1 .. 2^20, ctas_per_sm in 1 .. 32. */
+int secpe_mul32_probe(secpe_ctx *ctx, int ctas_per_sm, int iters, double *mul32_per_s, void *stream);
 
 #ifdef __cplusplus
 }

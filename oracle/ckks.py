@@ -298,6 +298,38 @@ class Oracle:
         full = np.concatenate([v, np.full(cp - n_classes, float(d_min))])
         return self.encrypt(full, seed)
 
+    # ------------------------------------------------------- slot packing
+    def packed_capacity(self, n_classes):
+        """Inputs per ciphertext under slot packing (SecPE Sec. 3.2, after
+        Alg. 1): each input needs a block of 2C' slots, C' values and the C'
+        slots its duplication fills, so N/2 slots hold N/(4C') inputs."""
+        cp = 1 << (n_classes - 1).bit_length()
+        return (self.n // 2) // (2 * cp)
+
+    def pack_slots(self, V, d_min):
+        """Slot vector of the inputs V[P][C] (READING of the slot-batching
+        paragraph: input b in the block of 2C' slots starting at 2C'b, its C
+        logits, then d_min up to C' as for one query, then C' zeros)."""
+        V = np.asarray(V, dtype=np.float64)
+        P, C = V.shape
+        cp = 1 << (C - 1).bit_length()
+        assert P <= self.packed_capacity(C)
+        out = np.zeros(P * 2 * cp, dtype=np.float64)
+        for b in range(P):
+            out[b * 2 * cp: b * 2 * cp + C] = V[b]
+            out[b * 2 * cp + C: b * 2 * cp + cp] = d_min
+        return out
+
+    def encrypt_logits_packed(self, V, d_min, seed):
+        """One prompt's logit vectors of P inputs in one ciphertext."""
+        return self.encrypt(self.pack_slots(V, d_min), seed)
+
+    def decrypt_packed(self, ct, P, n_classes):
+        """The first C slots of each of the P blocks, [P][C]."""
+        cp = 1 << (n_classes - 1).bit_length()
+        s = self.decrypt(ct, P * 2 * cp)
+        return np.stack([s[b * 2 * cp: b * 2 * cp + n_classes] for b in range(P)])
+
     def decrypt_coeffs(self, ct):
         """Centred integer coefficients of c0 + c1*s by exact CRT."""
         lv = ct.level

@@ -69,3 +69,21 @@ def ensemble_argmax(logits, d_min, d_max, slots, dg=2, df=2):
         y[: len(p)] += p
     y = y * (1.0 / (K * (d_max - d_min)))
     return argmax_slots(y, C, dg, df)[:C]
+
+
+def ensemble_argmax_packed(logits, d_min, d_max, slots, dg=2, df=2):
+    """logits[P][K][C] of P inputs packed in one slot vector (input b in the
+    block of 2C' slots at 2C'b) -> z[P][C] (plaintext Alg. 1 pipeline on the
+    packed vector, every block read back)."""
+    logits = np.asarray(logits, dtype=np.float64)
+    P, K, C = logits.shape
+    cp = 1 << (C - 1).bit_length()
+    y = np.zeros(slots)
+    for b in range(P):
+        for i in range(K):
+            p = pad_logits(logits[b, i], C, d_min)
+            y[b * 2 * cp: b * 2 * cp + cp] += p
+    y = y * (1.0 / (K * (d_max - d_min)))
+    z = argmax_slots(y, C, dg, df)
+    return np.stack([z[b * 2 * cp: b * 2 * cp + C] for b in range(P)])
+

@@ -10,6 +10,8 @@
 namespace enc {
 bool encode_real(int n, const double *v, int nv, double scale, std::vector<long long> &m);
 void decode_real(int n, const double *coeffs, double scale, int nslots, double *out);
+bool encode_real_fft(int n, const double *v, int nv, double scale, std::vector<long long> &m);
+void decode_real_fft(int n, const double *coeffs, double scale, int nslots, double *out);
 }  // namespace enc
 
 int argmax_batch_impl(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_);
@@ -276,6 +278,54 @@ extern "C" int secpe_encrypt_logits(secpe_ctx *ctx, const secpe_keys *keys, cons
     return secpe_encrypt(ctx, keys, full.data(), cp, seed, out, stream);
 }
 
+// ---- slot packing: P inputs of C classes per ciphertext, block b at slots
+// [2 C' b, 2 C' (b + 1)): v_b in the first C slots, d_min up to C', zeros in
+// the upper half (room for Alg. 1's duplication within the block).
+static int pow2_at_least(int C) {
+    int cp = 1;
+    while (cp < C) cp <<= 1;
+    return cp;
+}
+
+extern "C" int secpe_packed_capacity(int log_n, int C) {
+    if (log_n < 4 || log_n > 17 || C < 1) return SECPE_EINVAL;
+    const long long slots = 1ll << (log_n - 1), cp = pow2_at_least(C);
+    return 2 * cp > slots ? 0 : (int)(slots / (2 * cp));
+}
+
+extern "C" int secpe_encode_packed(int log_n, double scale, const double *v, int P, int C, double d_min,
+                                   int64_t *m_out) {
+    const int cap = secpe_packed_capacity(log_n, C);
+    if (cap < 0 || !v || !m_out || P < 1 || P > cap || !(scale > 0.0)) return SECPE_EINVAL;
+    const int n = 1 << log_n, cp = pow2_at_least(C);
+    std::vector<double> slots((size_t)P * 2 * cp, 0.0);
+    for (int b = 0; b < P; b++)
+        for (int j = 0; j < cp; j++) slots[(size_t)b * 2 * cp + j] = j < C ? v[(size_t)b * C + j] : d_min;
+    std::vector<long long> m;
+    if (!enc::encode_real_fft(n, slots.data(), (int)slots.size(), scale, m)) return SECPE_EINVAL;
+    std::memcpy(m_out, m.data(), sizeof(int64_t) * n);
+    return SECPE_OK;
+}
+
+extern "C" int secpe_decode_packed(int log_n, double scale, const double *coeffs, int P, int C, double *out) {
+    const int cap = secpe_packed_capacity(log_n, C);
+    if (cap < 0 || !coeffs || !out || P < 1 || P > cap || !(scale > 0.0)) return SECPE_EINVAL;
+    const int n = 1 << log_n, cp = pow2_at_least(C);
+    std::vector<double> slots((size_t)P * 2 * cp);
+    enc::decode_real_fft(n, coeffs, scale, (int)slots.size(), slots.data());
+    for (int b = 0; b < P; b++)
+        for (int j = 0; j < C; j++) out[(size_t)b * C + j] = slots[(size_t)b * 2 * cp + j];
+    return SECPE_OK;
+}
+
+extern "C" int secpe_encrypt_logits_packed(secpe_ctx *ctx, const secpe_keys *keys, const double *v, int P, int C,
+                                           double d_min, uint64_t seed, secpe_ct *out, void *stream) {
+    if (!ctx) return SECPE_EINVAL;
+    std::vector<int64_t> m(ctx->n);
+    SECPE_CHECK(secpe_encode_packed(ctx->log_n, ctx->scale, v, P, C, d_min, m.data()));
+    return secpe_encrypt_coeffs(ctx, keys, m.data(), ctx->L, ctx->scale, seed, out, stream);
+}
+
 static int decrypt_to_host_coeffs(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *ct,
                                   std::vector<double> &coeffs) {
     const int n = ctx->n, lv = ct->level;
@@ -302,6 +352,18 @@ extern "C" int secpe_decrypt_coeffs(secpe_ctx *ctx, const secpe_keys *keys, cons
     SECPE_CHECK(decrypt_to_host_coeffs(ctx, keys, ct, c));
     std::memcpy(coeffs_out, c.data(), sizeof(double) * ctx->n);
     return SECPE_OK;
+}
+
+extern "C" int secpe_decrypt_packed(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *ct, int P, int C,
+                                    double *out, void *stream) {
+    if (!ctx || !keys || !out) return SECPE_EINVAL;
+    const int cap = secpe_packed_capacity(ctx->log_n, C);
+    if (cap < 0 || P < 1 || P > cap) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, ct));
+    CallScope cs(ctx, stream);
+    std::vector<double> c;
+    SECPE_CHECK(decrypt_to_host_coeffs(ctx, keys, ct, c));
+    return secpe_decode_packed(ctx->log_n, ct->scale, c.data(), P, C, out);
 }
 
 extern "C" int secpe_decrypt(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *ct, double *v_out, int n,
@@ -667,6 +729,25 @@ extern "C" void secpe_graph_destroy(secpe_graph *g) {
     if (cudaDeviceSynchronize() == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGraphMemTrim(dev);
 }
 
+extern "C" int secpe_pool_usage(int trim, uint64_t *used, uint64_t *reserved) {
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return SECPE_ECUDA;
+    }
+    if (trim) {
+        SECPE_CUDA(cudaDeviceSynchronize());
+        SECPE_CUDA(cudaMemPoolTrimTo(pool, 0));
+    }
+    unsigned long long u = 0, r = 0;  // the attributes are 64-bit values
+    SECPE_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u));
+    SECPE_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r));
+    if (used) *used = (uint64_t)u;
+    if (reserved) *reserved = (uint64_t)r;
+    return SECPE_OK;
+}
+
 extern "C" int secpe_kprof_begin(secpe_ctx *ctx, const char *name_filter, int max_launches) {
     if (!ctx || !name_filter || max_launches < 1 || max_launches > (1 << 20)) return SECPE_EINVAL;
     KProf &k = ctx->kprof;
@@ -680,6 +761,8 @@ extern "C" int secpe_kprof_begin(secpe_ctx *ctx, const char *name_filter, int ma
     k.used = 0;
     k.launches = 0;
     k.bytes = 0.0;
+    k.model_bytes = 0.0;
+    k.mul32 = 0.0;
     k.active = true;
     return SECPE_OK;
 }
@@ -700,7 +783,36 @@ extern "C" int secpe_kprof_end(secpe_ctx *ctx, secpe_kprof *out) {
     out->launches = k.used;
     out->total_ms = ms;
     out->bytes = k.bytes;
+    out->model_bytes = k.model_bytes;
+    out->mul32 = k.mul32;
     return SECPE_OK;
+}
+
+extern "C" int secpe_mul32_probe(secpe_ctx *ctx, int ctas_per_sm, int iters, double *mul32_per_s, void *stream) {
+    if (!ctx || !mul32_per_s || iters < 1 || iters > (1 << 20) || ctas_per_sm < 1 || ctas_per_sm > 32)
+        return SECPE_EINVAL;
+    CallScope cs(ctx, stream);
+    int dev = 0, sms = 0;
+    SECPE_CUDA(cudaGetDevice(&dev));
+    SECPE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long blocks = (long long)sms * ctas_per_sm, threads = blocks * 256;
+    DevBuf sink;
+    SECPE_CHECK(sink.alloc(ctx, sizeof(u64) * (size_t)threads));
+    cudaEvent_t e0, e1;
+    SECPE_CUDA(cudaEventCreate(&e0));
+    SECPE_CUDA(cudaEventCreate(&e1));
+    int st = launch_mul32_probe(ctx, (unsigned)blocks, iters, sink.u());
+    if (st == SECPE_OK && cudaEventRecord(e0, ctx->stream) != cudaSuccess) st = SECPE_ECUDA;
+    if (st == SECPE_OK) st = launch_mul32_probe(ctx, (unsigned)blocks, iters, sink.u());
+    if (st == SECPE_OK && cudaEventRecord(e1, ctx->stream) != cudaSuccess) st = SECPE_ECUDA;
+    float ms = 0.f;
+    if (st == SECPE_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        st = SECPE_ECUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SECPE_OK) return st;
+    *mul32_per_s = ms > 0.f ? (double)threads * iters * 4.0 * MUL32_MAC / (ms * 1e-3) : 0.0;
+    return finish(ctx, SECPE_OK);
 }
 
 extern "C" int secpe_kprof_report(const secpe_ctx *ctx, char *buf, size_t len, size_t *needed) {

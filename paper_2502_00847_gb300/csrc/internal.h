@@ -98,7 +98,9 @@ struct KProf {
     std::vector<float> ms;        // duration of pair i, filled by secpe_kprof_end
     int used = 0;                 // pairs recorded
     int64_t launches = 0;
-    double bytes = 0.0;
+    double bytes = 0.0;        // algorithmic bytes (operands read once, results written once)
+    double model_bytes = 0.0;  // bytes each launch itself reads and writes (intermediates included)
+    double mul32 = 0.0;        // algorithmic 32-bit multiplies
 };
 
 // Launch configurations chosen by secpe_autotune: CTAs per SM (3 or 4, i.e.

@@ -901,3 +901,32 @@ int launch_mdr_fin(secpe_ctx *ctx, const u64 *acc, const u64 *conv, const u64 *d
                  dis, dps, o.data, o.stride, o.cap, lv);
     return SECPE_OK;
 }
+
+// ---------------------------------------------------------------- probe
+namespace {
+// Four independent multiply-accumulate chains per thread; each round feeds
+// the high words back into the multiplicands so no round can be folded.
+__global__ void __launch_bounds__(256) k_mul32_probe(int iters, u64 *sink) {
+    const u64 t = (u64)blockIdx.x * 256u + threadIdx.x;
+    u64 x0 = t * 0x9E3779B97F4A7C15ull + 1, x1 = x0 ^ 0xBF58476D1CE4E5B9ull, x2 = x0 ^ 0x94D049BB133111EBull,
+        x3 = x0 ^ 0xD1B54A32D192ED03ull;
+    const u64 y = 0xFFFFFFFFFFFFFFC5ull ^ t;
+    acc128 a0 = {0, 0}, a1 = {1, 0}, a2 = {2, 0}, a3 = {3, 0};
+    for (int i = 0; i < iters; i++) {
+        mac(a0, x0, y);
+        mac(a1, x1, y);
+        mac(a2, x2, y);
+        mac(a3, x3, y);
+        x0 ^= a0.hi;
+        x1 ^= a1.hi;
+        x2 ^= a2.hi;
+        x3 ^= a3.hi;
+    }
+    sink[t] = a0.lo ^ a0.hi ^ a1.lo ^ a1.hi ^ a2.lo ^ a2.hi ^ a3.lo ^ a3.hi;
+}
+}  // namespace
+
+int launch_mul32_probe(secpe_ctx *ctx, unsigned blocks, int iters, u64 *sink) {
+    SECPE_LAUNCH(ctx, k_mul32_probe, blocks, 256, 0, iters, sink);
+    return SECPE_OK;
+}

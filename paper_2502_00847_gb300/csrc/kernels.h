@@ -60,6 +60,9 @@ int launch_ksk_gen(secpe_ctx *ctx, const u64 *a, const u64 *e_ntt, const u64 *s,
 int launch_from_mont(secpe_ctx *ctx, const u64 *in, u64 *out, int nlimb_total);
 int launch_limb_mul(secpe_ctx *ctx, const u64 *a, const u64 *b, u64 *o);
 int launch_limb_automorph(secpe_ctx *ctx, const u64 *in, u64 *o, unsigned g);
+// Integer multiply throughput probe: `blocks` CTAs of 256 threads, 4
+// independent 128-bit multiply-accumulate chains per thread, `iters` rounds.
+int launch_mul32_probe(secpe_ctx *ctx, unsigned blocks, int iters, u64 *sink);
 int launch_mdr_prep(secpe_ctx *ctx, const u64 *d, long long dis, long long dps, u64 *acc, int B, int lv);
 int launch_mdr_bconv(secpe_ctx *ctx, const u64 *acc, u64 *conv, int B, int lv);
 int launch_mdr_fin(secpe_ctx *ctx, const u64 *acc, const u64 *conv, const u64 *d, long long dis, long long dps,

@@ -47,7 +47,8 @@ int keyswitch_acc(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, 
     LimbSet dst = make_limbset(dcoef.u(), B, (long long)(lv + 1) * n, 1, 0, lv + 1, 0);
     LimbSet src = make_limbset((u64 *)d, B, d_item_stride, 1, 0, lv + 1, 0);
     const bool fused = fused_path(ctx);
-    SECPE_CHECK(ntt_limbset(ctx, dst, true, &src, fused ? ctx->dev.ninv_modup : nullptr, lv * ctx->nq));
+    // (the profiler charges this INTT the key switch's input d, read once)
+    SECPE_CHECK(ntt_limbset(ctx, dst, true, &src, fused ? ctx->dev.ninv_modup : nullptr, lv * ctx->nq, 8.0 * n));
 
     DevBuf ext;
     SECPE_CHECK(ext.alloc(ctx, sizeof(u64) * (size_t)B * tot * n));
@@ -81,7 +82,7 @@ int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int 
     LimbSet pls = make_limbset(acc.u() + (size_t)(lv + 1) * n, B, 2ll * nt * n, 2, (long long)nt * n, k, ctx->nq);
     SECPE_CHECK(tmp.alloc(ctx, sizeof(u64) * (size_t)B * 2 * (lv + 1) * n));
     if (fused_path(ctx)) {
-        SECPE_CHECK(ntt_limbset(ctx, pls, true, nullptr, ctx->dev.ninv_moddown, 0));
+        SECPE_CHECK(ntt_limbset(ctx, pls, true, nullptr, ctx->dev.ninv_moddown, 0, 0.0));  // intermediate
         return moddown_fused(ctx, acc.u(), B, lv, out, acc0, acc1, tmp.u());
     }
     SECPE_CHECK(ntt_limbset(ctx, pls, true));
@@ -118,7 +119,8 @@ int rescale_batch(secpe_ctx *ctx, const CtB &in, const CtB &out) {
     SECPE_CHECK(z.alloc(ctx, sizeof(u64) * (size_t)B * 2 * lv * n));
     LimbSet ysrc = make_limbset(in.data + (size_t)lv * n, B, in.stride, 2, in.pstride(), 1, lv);
     LimbSet ydst = make_limbset(y.u(), B, 2ll * n, 2, n, 1, lv);
-    SECPE_CHECK(ntt_limbset(ctx, ydst, true, &ysrc));
+    // (charged the input's last limbs, read once)
+    SECPE_CHECK(ntt_limbset(ctx, ydst, true, &ysrc, nullptr, 0, 8.0 * n));
     if (fused_path(ctx)) return rescale_fused(ctx, in, y.u(), out, z.u());
     SECPE_CHECK(launch_rescale_prep(ctx, y.u(), z.u(), B, lv));
     LimbSet zls = make_limbset(z.u(), B, 2ll * lv * n, 2, (long long)lv * n, lv, 0);

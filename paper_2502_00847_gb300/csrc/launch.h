@@ -59,22 +59,42 @@ struct KprofLaunch {
 // the context's kernel profiler is active and `name` matches its filter.
 // Under stream capture the records become event record nodes of the graph
 // (each replay re-records them).
+// `bytes` are the launch's share of its operation's algorithmic bytes,
+// `model` (default: the same) what the launch itself reads and writes,
+// `mul32` its algorithmic 32-bit multiplies (MUL32_* below).
 struct KprofScope {
     secpe_ctx *ctx;
     int idx = -1;
-    KprofScope(secpe_ctx *c, const char *name, double bytes) : ctx(c) {
+    KprofScope(secpe_ctx *c, const char *name, double bytes, double model = -1.0, double mul32 = 0.0) : ctx(c) {
         KProf &k = c->kprof;
         if (!k.active || k.all || std::string(name).find(k.filter) == std::string::npos) return;
         if (2 * (k.used + 1) > (int)k.ev.size()) return;
         idx = k.used++;
         k.launches++;
         k.bytes += bytes;
+        k.model_bytes += model < 0.0 ? bytes : model;
+        k.mul32 += mul32;
         kprof_record(k.ev[2 * idx], c->stream);
     }
     ~KprofScope() {
         if (idx >= 0) kprof_record(ctx->kprof.ev[2 * idx + 1], ctx->stream);
     }
 };
+
+// Algorithmic 32-bit multiplies (one mul.lo or mul.hi on 32-bit words each)
+// of the 64-bit operations as the kernels form them from 32 x 32 partial
+// products: the high half of a 64 x 64 product takes 7 (three of the four
+// partial products in both halves and the high half of the lowest), the low
+// half 4 (the lowest in both halves, the two cross products' low halves),
+// the full 128-bit product or multiply-accumulate 8.
+//   Shoup product x*w - hi(x*w')*q:              7 + 4 + 4 = 15
+//   Montgomery reduction (lo*q') then hi(m*q):   4 + 7     = 11
+//   Montgomery product: full product + reduction          = 19
+// One radix-2 pass of 8 stages over a residue costs 8 half-butterflies of
+// one Shoup product each: 60 per residue; the inverse transform's last stage
+// adds one more Shoup product per butterfly (the folded N^-1): 7.5.
+constexpr double MUL32_SHOUP = 15.0, MUL32_REDC = 11.0, MUL32_MAC = 8.0, MUL32_MONT = 19.0;
+constexpr double MUL32_PASS = 60.0, MUL32_INV_LAST = 7.5;
 
 static inline unsigned grid1d(long long work, int block) {
     return (unsigned)((work + block - 1) / block);
@@ -88,8 +108,13 @@ static inline unsigned grid1d(long long work, int block) {
 // For the N = 2^16 inverse, `scale_tab` (device, pairs) replaces the final
 // N^-1 of limb j by scale_tab[2 (scale_off + j)] (and the folded twiddle by
 // the next entry): the INTT then also applies a per-limb constant.
+// `alg_per_limb` is the algorithmic bytes the transform is charged per limb
+// in the profiler: by default 16 N (a transform reads and writes every
+// residue once); transforms inside an operation charge what the operation
+// reads or writes through them (8 N for an input read once, 0 for an
+// intermediate).
 int ntt_limbset(secpe_ctx *ctx, const LimbSet &ls, bool inverse, const LimbSet *src = nullptr,
-                const ulonglong2 *scale_tab = nullptr, int scale_off = 0);
+                const ulonglong2 *scale_tab = nullptr, int scale_off = 0, double alg_per_limb = -1.0);
 
 // N = 2^16 only: the row pass (last 8 stages of the forward NTT, first 8 of
 // the inverse) alone, in place.

@@ -6,17 +6,25 @@
 // that must keep a fixed device memory footprint and never touch the
 // allocator on the critical path, and hosts that manage all device memory
 // through their own pool and forbid hidden allocations.  secpe_rescale_noalloc serves them: its scratch is
-// one file-scope __device__ array of fixed size, reserved when the library
-// is loaded, that every GPU holding this library keeps until the process
-// exits.
+// one file-scope __device__ array of fixed size that every GPU holding this
+// library keeps until the process exits.  Under CUDA's default lazy module
+// loading the array is reserved on a device when this file's module is
+// first loaded there, which is the first call's set-up (cudaGetSymbolAddress):
+// that first call can still fail with SECPE_ECUDA if the device is full, so
+// make one warm-up call per device at start-up, before admitting requests
+// and before any stream capture.
 //
 // Limits and contract:
 //  * the scratch holds SECPE_NOALLOC_SCRATCH_WORDS 64-bit words; a call
 //    needs 2 * N * (level + 1) words and is rejected with SECPE_EINVAL when
 //    that is larger (N = 2^16 allows levels up to 23);
 //  * the device address of the array is looked up once per device, with
-//    that device current, by the first call on it; make that first call
+//    that device current, by the first call on it (which also loads the
+//    module and so reserves the array); make that first call at start-up,
 //    before any stream capture;
+//  * out may be in itself (same data and cap: every output residue depends
+//    only on the input residue at the same position and on the scratch);
+//    any other overlap of the two buffers is rejected with SECPE_EINVAL;
 //  * all calls share the one array and it keeps the last call's contents:
 //    calls whose kernels may overlap on the GPU (different streams without
 //    ordering) race on it and must not be issued.
@@ -55,10 +63,19 @@ int scratch_address(u64 **out) {
 }  // namespace
 
 extern "C" int secpe_rescale_noalloc(secpe_ctx *ctx, const secpe_ct *in, secpe_ct *out, void *stream) {
+    // the validation of secpe_rescale, with its error codes
     if (!ctx || !in || !out || !in->data || !out->data || !aligned16(in->data) || !aligned16(out->data))
         return SECPE_EINVAL;
-    if (in->level < 1 || in->level > ctx->L || in->cap < in->level + 1 || !(in->scale > 0.0)) return SECPE_EINVAL;
+    if (in->level < 0 || in->level > ctx->L || in->cap < in->level + 1 || !(in->scale > 0.0)) return SECPE_EINVAL;
+    if (in->level < 1) return SECPE_ELEVEL;
     if (out->cap < in->level) return SECPE_EINVAL;
+    {
+        // out is written while in is still read: only the exact in-place layout is safe
+        const u64 *ib = (const u64 *)in->data, *ie = ib + 2ull * in->cap * ctx->n;
+        const u64 *ob = (const u64 *)out->data, *oe = ob + 2ull * out->cap * ctx->n;
+        const bool overlap = ob < ie && ib < oe;
+        if (overlap && !(ob == ib && out->cap == in->cap)) return SECPE_EINVAL;
+    }
     const int n = ctx->n, lv = in->level;
     const unsigned long long need = 2ull * n * (lv + 1);
     if (need > SECPE_NOALLOC_SCRATCH_WORDS) return SECPE_EINVAL;

@@ -334,7 +334,7 @@ LimbSet make_limbset(u64 *base, int nitem, long long item_stride, int npoly, lon
 }
 
 int ntt_limbset(secpe_ctx *ctx, const LimbSet &ls, bool inverse, const LimbSet *src, const ulonglong2 *scale_tab,
-                int scale_off) {
+                int scale_off, double alg_per_limb) {
     const long long nl = (long long)ls.nitem * ls.npoly * ls.nlimb;
     if (nl == 0) return SECPE_OK;
     if (ls.npoly * ls.nlimb > SECPE_MAX_LIMBSET) return SECPE_EINVAL;
@@ -363,20 +363,24 @@ int ntt_limbset(secpe_ctx *ctx, const LimbSet &ls, bool inverse, const LimbSet *
     if (ctx->log_n == 16) {
         a.tiles = 16;
         if (nl * 16 >= (1ll << 31)) return SECPE_EINVAL;
-        const double pass_bytes = 16.0 * ctx->n * nl;  // one read + one write per residue
+        // each pass reads and writes every residue (model); the transform as
+        // a whole is charged alg_per_limb, half to each pass
+        const double model = 16.0 * ctx->n * nl;
+        const double alg = 0.5 * (alg_per_limb < 0.0 ? 16.0 * ctx->n : alg_per_limb) * nl;
+        const double mul = MUL32_PASS * ctx->n * nl;
         if (!inverse) {
             {
-                KprofScope kp(ctx, "ntt16_colpass", pass_bytes);
+                KprofScope kp(ctx, "ntt16_colpass", alg, model, mul);
                 SECPE_CHECK(launch_pass16(ctx, TUNE_COLPASS, a, nl));
             }
-            KprofScope kp(ctx, "ntt16_rowpass", pass_bytes);
+            KprofScope kp(ctx, "ntt16_rowpass", alg, model, mul);
             SECPE_CHECK(launch_pass16(ctx, TUNE_ROWPASS, a, nl));
         } else {
             {
-                KprofScope kp(ctx, "intt16_rowpass", pass_bytes);
+                KprofScope kp(ctx, "intt16_rowpass", alg, model, mul);
                 SECPE_CHECK(launch_pass16(ctx, TUNE_IROWPASS, a, nl));
             }
-            KprofScope kp(ctx, "intt16_colpass", pass_bytes);
+            KprofScope kp(ctx, "intt16_colpass", alg, model, mul + MUL32_INV_LAST * ctx->n * nl);
             SECPE_CHECK(launch_pass16(ctx, TUNE_ICOLPASS, a, nl));
         }
         return SECPE_OK;

@@ -288,7 +288,13 @@ int launch_colpass_bconv(secpe_ctx *ctx, const BConvArgs &a) {
     for (int i = 1; i < a.ngroups; i++)
         if (a.g[i].nsrc != ns) ns = 0;
     const unsigned grid = (unsigned)(nl * 16);
-    KprofScope kp(ctx, "ntt16_colpass_bconv", 16.0 * ctx->n * nl);
+    // reads and writes intermediates of its operation only (algorithmic 0);
+    // per residue: one multiply-accumulate per source, a reduction, a pass
+    double mul = 0.0;
+    for (int li = 0; li < a.ls.npoly * a.ls.nlimb; li++)
+        mul += MUL32_MAC * a.g[a.ls.aux[li]].nsrc + MUL32_REDC + MUL32_PASS;
+    mul *= (double)ctx->n * a.ls.nitem;
+    KprofScope kp(ctx, "ntt16_colpass_bconv", 0.0, 16.0 * ctx->n * nl, mul);
     if (ctx->tune.ctas[TUNE_BCONV] == 4) return launch_bconv_ns<4>(ctx, a, ns, grid);
     return launch_bconv_ns<3>(ctx, a, ns, grid);
 }
@@ -415,15 +421,26 @@ int modup_ip_fused(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const 
     ip.acc = acc;
     ip.lv = lv;
     ip.nitem = B;
-    KprofScope kp(ctx, "ntt16_rowpass_ip", 8.0 * n * ((double)B * (tot + lv + 1) + 2.0 * dg.ndig * nt + 2.0 * B * nt));
+    // algorithmic: the key-switching key, read once for the batch (d and
+    // the accumulators are the operation's input, charged to its INTT, and
+    // intermediates); per target residue: a pass B per digit not holding
+    // the target prime, two Montgomery products per digit
+    const int k = ctx->npsp;
+    const double ip_mul = (double)n * B *
+                          (MUL32_PASS * ((double)(lv + 1) * (dg.ndig - 1) + (double)k * dg.ndig) +
+                           2.0 * MUL32_MONT * dg.ndig * nt);
+    KprofScope kp(ctx, "ntt16_rowpass_ip", 8.0 * n * 2.0 * dg.ndig * nt,
+                  8.0 * n * ((double)B * (tot + lv + 1) + 2.0 * dg.ndig * nt + 2.0 * B * nt), ip_mul);
     SECPE_LAUNCH(ctx, k_rowpass_ip, (unsigned)((long long)nt * 16 * B), 256, 0, ip);
     return SECPE_OK;
 }
 
 // out (+)= (X - NTT(FastBConv(src))) * w [+ Y * w2] over limbs 0..nl-1 of B items x 2 polys.
+// x_input: X is an input of the operation (rescale), not an intermediate
+// (the profiler charges it as algorithmic bytes only then).
 int bconv_ntt_epi(secpe_ctx *ctx, const BConvSrc &S, int B, int nl, u64 *tmp, const u64 *X, long long xis,
-                  long long xps, const CtB &out, const ulonglong2 *w, bool acc0, bool acc1, const u64 *Y = nullptr,
-                  long long yis = 0, long long yps = 0, const ulonglong2 *w2 = nullptr) {
+                  long long xps, const CtB &out, const ulonglong2 *w, bool acc0, bool acc1, bool x_input,
+                  const u64 *Y = nullptr, long long yis = 0, long long yps = 0, const ulonglong2 *w2 = nullptr) {
     const int n = ctx->n;
     BConvArgs a;
     a.c = ctx->dev;
@@ -448,7 +465,14 @@ int bconv_ntt_epi(secpe_ctx *ctx, const BConvSrc &S, int B, int nl, u64 *tmp, co
     ep.yps = yps;
     ep.w2 = w2;
     const long long nlimbs = (long long)B * 2 * nl;
-    KprofScope kp(ctx, "ntt16_rowpass_epi", 8.0 * n * nlimbs * (acc0 || acc1 ? 4.0 : 3.0));
+    // algorithmic per item: the output (2 nl limbs), X when it is an input,
+    // the accumulated output polynomials' old values, and Y with the two
+    // top limbs of its polynomials that the preceding steps consumed
+    const double alg = 8.0 * n * B *
+                       (2.0 * nl + (x_input ? 2.0 * nl : 0.0) + (acc0 ? nl : 0) + (acc1 ? nl : 0) +
+                        (Y ? 2.0 * (nl + 1) : 0.0));
+    const double epi_mul = (double)n * nlimbs * (MUL32_PASS + MUL32_SHOUP * (Y ? 2.0 : 1.0));
+    KprofScope kp(ctx, "ntt16_rowpass_epi", alg, 8.0 * n * nlimbs * (acc0 || acc1 ? 4.0 : 3.0), epi_mul);
     // the bulk copy of the X tile needs 16-byte aligned tiles
     if (((uintptr_t)X & 15) || (xis & 1) || (xps & 1)) return SECPE_EINVAL;
     static bool attr_set[64];
@@ -487,7 +511,7 @@ int moddown_fused(secpe_ctx *ctx, const u64 *acc, int B, int lv, const CtB &out,
     S.hat_stride = ctx->nq;
     S.post = ctx->dev.md_hP;
     return bconv_ntt_epi(ctx, S, B, lv + 1, tmp, acc, 2ll * nt * n, (long long)nt * n, out, ctx->dev.md_pinv, acc0,
-                         acc1);
+                         acc1, false);
 }
 
 // Rescale of `in` by q_l into out, y = INTT of the last limb [B][2][N].
@@ -504,7 +528,7 @@ int rescale_fused(secpe_ctx *ctx, const CtB &in, const u64 *y, const CtB &out, u
     S.hat_stride = 0;
     S.post = ctx->dev.rs_hmod + (size_t)lv * ctx->nq;
     return bconv_ntt_epi(ctx, S, in.B, lv, tmp, in.data, in.stride, in.pstride(), out,
-                         ctx->dev.rs_qinv + (size_t)lv * ctx->nq, false, false);
+                         ctx->dev.rs_qinv + (size_t)lv * ctx->nq, false, false, true);
 }
 
 // Relinearisation's ModDown fused with the rescale: acc [B][2][nt][N] from
@@ -518,7 +542,7 @@ int moddown_rescale_fused(secpe_ctx *ctx, u64 *acc, const u64 *d, int B, int lv,
     LimbSet src = make_limbset(acc + (size_t)lv * n, B, 2ll * nt * n, 2, (long long)nt * n, ks, 0);
     for (int p = 0; p < 2; p++)
         for (int j = 0; j < ks; j++) src.prime_of[p * ks + j] = (int8_t)(j == 0 ? lv : ctx->nq + j - 1);
-    SECPE_CHECK(ntt_limbset(ctx, src, true, nullptr, ctx->dev.mdr_ninv, lv * ks));
+    SECPE_CHECK(ntt_limbset(ctx, src, true, nullptr, ctx->dev.mdr_ninv, lv * ks, 0.0));  // intermediate
     BConvSrc S;
     S.base = acc + (size_t)lv * n;
     S.is = 2ll * nt * n;
@@ -532,6 +556,6 @@ int moddown_rescale_fused(secpe_ctx *ctx, u64 *acc, const u64 *d, int B, int lv,
     S.hat_stride = ctx->nq;
     S.post = ctx->dev.mdr_post + (size_t)lv * ctx->nq;
     return bconv_ntt_epi(ctx, S, B, lv, tmp, acc, 2ll * nt * n, (long long)nt * n, out,
-                         ctx->dev.mdr_w + (size_t)lv * ctx->nq, false, false, d, dis, dps,
+                         ctx->dev.mdr_w + (size_t)lv * ctx->nq, false, false, false, d, dis, dps,
                          ctx->dev.rs_qinv + (size_t)lv * ctx->nq);
 }

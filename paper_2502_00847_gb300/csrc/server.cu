@@ -5,10 +5,13 @@
 // k = 0..r-1 = QuickMax round k, phase r = final Sign(y_dup - y_max) + 1.
 // All queries of one tenant (key set) at the same phase of the same
 // class-count power C' share level, scale and refresh history, so the server
-// runs one phase for a whole group as one batched evaluation.  Each call to secpe_server_step
-// picks the group that holds the oldest admitted query, adds every other
-// query at the same point (up to max_batch), and enqueues that phase on the
-// stream; queries submitted meanwhile join at the next phase boundary.
+// runs one phase for a whole group as one batched evaluation.  Each call to
+// secpe_server_step admits what fits, then enqueues one phase of every group
+// of admitted queries (groups of at most max_batch queries, in the order of
+// their oldest member): every query in flight advances by one phase per
+// step, and a query submitted while others are mid-circuit starts its
+// aggregation in the next step, its launches interleaved on the stream with
+// theirs.
 // Per-query state (y_dup, y) stays resident on the device between phases.
 // Admission: a query is admitted when the state it will hold fits the HBM
 // budget next to the keys, the states in flight and the largest scratch of
@@ -18,6 +21,7 @@
 #include <chrono>
 #include <deque>
 #include <map>
+#include <tuple>
 
 #include "eval.h"
 
@@ -295,32 +299,35 @@ extern "C" int secpe_server_step(secpe_server *s, void *stream, int *launched) {
     ctx->stream = (cudaStream_t)stream;
     if (launched) *launched = 0;
     try_admit(s);
-    // the oldest admitted query not done decides the group
-    QState *oldest = nullptr;
+    // queries at the same point of the circuit form a group: same tenant,
+    // phase and kind (the duplication needs the same C' key; a QuickMax round
+    // k is common to all queries with r > k; the final phase k is shared by
+    // queries with r = k)
+    auto kind = [](const QState &st) { return st.phase < 0 ? 2 * st.cp : (st.phase < st.r ? 0 : 1); };
+    std::map<std::tuple<const secpe_keys *, int, int>, std::vector<QState *>> groups;
     for (auto &kv : s->q) {
         QState &st = kv.second;
         if (st.cancelled || st.done || st.phase < -1) continue;
-        if (!oldest || st.t_admit < oldest->t_admit) oldest = &st;
+        groups[std::make_tuple(st.keys, st.phase, kind(st))].push_back(&st);
     }
-    if (!oldest) return SECPE_OK;
-    // queries at the same point of the circuit: same tenant, phase and kind
-    // (the duplication needs the same C' key; a QuickMax round k is common to
-    // all queries with r > k; the final phase k is shared by queries with r = k)
-    auto kind = [](const QState &st) { return st.phase < 0 ? 2 * st.cp : (st.phase < st.r ? 0 : 1); };
-    std::vector<QState *> g;
-    for (auto &kv : s->q) {
-        QState &st = kv.second;
-        if (st.cancelled || st.done || st.phase != oldest->phase || kind(st) != kind(*oldest) ||
-            st.keys != oldest->keys)
-            continue;
-        g.push_back(&st);
+    std::vector<std::vector<QState *>> runs;
+    auto older = [](const QState *a, const QState *b) { return a->t_admit < b->t_admit; };
+    for (auto &kv : groups) {
+        std::vector<QState *> &g = kv.second;
+        std::sort(g.begin(), g.end(), older);
+        for (size_t i = 0; i < g.size(); i += (size_t)s->max_batch)
+            runs.emplace_back(g.begin() + i, g.begin() + std::min(g.size(), i + (size_t)s->max_batch));
     }
-    std::sort(g.begin(), g.end(), [](const QState *a, const QState *b) { return a->t_admit < b->t_admit; });
-    if ((int)g.size() > s->max_batch) g.resize(s->max_batch);
-    SECPE_CHECK(run_group(s, g));
-    if (launched) *launched = (int)g.size();
-    for (QState *st : g)
-        if (st->done) release(s, *st);
+    std::sort(runs.begin(), runs.end(),
+              [&](const std::vector<QState *> &a, const std::vector<QState *> &b) { return older(a[0], b[0]); });
+    int total = 0;
+    for (std::vector<QState *> &g : runs) {
+        SECPE_CHECK(run_group(s, g));
+        total += (int)g.size();
+        for (QState *st : g)
+            if (st->done) release(s, *st);
+    }
+    if (launched) *launched = total;
     return cudaGetLastError() == cudaSuccess ? SECPE_OK : SECPE_ECUDA;
 }
 

@@ -29,6 +29,8 @@ EXPORTS = [
     "secpe_rescale_noalloc", "secpe_server_create", "secpe_server_destroy", "secpe_server_submit",
     "secpe_server_cancel", "secpe_server_step", "secpe_server_poll", "secpe_server_wait", "secpe_server_forget",
     "secpe_server_stats", "secpe_ntt_tc", "secpe_ntt_cts_tc", "secpe_expand_seeded", "secpe_keyswitch_batch_tc",
+    "secpe_pool_usage", "secpe_mul32_probe", "secpe_packed_capacity", "secpe_encode_packed",
+    "secpe_decode_packed", "secpe_encrypt_logits_packed", "secpe_decrypt_packed",
 ]
 
 
@@ -71,7 +73,8 @@ class TuningC(ctypes.Structure):
 
 
 class KprofC(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+    _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("model_bytes", ctypes.c_double), ("mul32", ctypes.c_double)]
 
 
 _lib = None
@@ -148,6 +151,13 @@ def lib():
         "secpe_ntt_tc": (i32, [vp, vp, P(i32), i32, i32, vp]),
         "secpe_ntt_cts_tc": (i32, [vp, vp, i32, ctypes.c_size_t, i32, i32, i32, vp]),
         "secpe_expand_seeded": (i32, [vp, vp, i32, ctypes.c_size_t, i32, i32, P(u64), vp]),
+        "secpe_pool_usage": (i32, [i32, P(u64), P(u64)]),
+        "secpe_mul32_probe": (i32, [vp, i32, i32, P(dbl), vp]),
+        "secpe_packed_capacity": (i32, [i32, i32]),
+        "secpe_encode_packed": (i32, [i32, dbl, P(dbl), i32, i32, dbl, P(ctypes.c_int64)]),
+        "secpe_decode_packed": (i32, [i32, dbl, P(dbl), i32, i32, P(dbl)]),
+        "secpe_encrypt_logits_packed": (i32, [vp, vp, P(dbl), i32, i32, dbl, u64, P(CtC), vp]),
+        "secpe_decrypt_packed": (i32, [vp, vp, P(CtC), i32, i32, P(dbl), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -238,7 +248,15 @@ class Context:
     def kprof_end(self):
         k = KprofC()
         _check(lib().secpe_kprof_end(self.h, ctypes.byref(k)), "secpe_kprof_end")
-        return dict(launches=int(k.launches), total_ms=float(k.total_ms), bytes=float(k.bytes))
+        return dict(launches=int(k.launches), total_ms=float(k.total_ms), bytes=float(k.bytes),
+                    model_bytes=float(k.model_bytes), mul32=float(k.mul32))
+
+    def mul32_probe(self, ctas_per_sm=8, iters=4096):
+        """secpe_mul32_probe: achieved 32-bit multiplies per second of the
+        128-bit multiply-accumulate form on this GPU."""
+        r = ctypes.c_double(0.0)
+        _check(lib().secpe_mul32_probe(self.h, ctas_per_sm, iters, ctypes.byref(r), _stream()), "secpe_mul32_probe")
+        return float(r.value)
 
     def autotune(self):
         """Times the candidate launch configurations of the N = 2^16 kernels and
@@ -377,6 +395,57 @@ def encrypt_logits(ctx, keys, v, d_min, seed, out=None):
     return out
 
 
+def _dblp(arr):
+    return arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def packed_capacity(log_n, C):
+    """secpe_packed_capacity: inputs of C classes per ciphertext."""
+    r = lib().secpe_packed_capacity(log_n, C)
+    if r < 0:
+        raise SecpeError(r, "secpe_packed_capacity")
+    return r
+
+
+def encode_packed(log_n, scale, v, d_min):
+    """secpe_encode_packed (host only): coefficients of the packed slot vector of v[P][C]."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    P, C = v.shape
+    m = np.zeros(1 << log_n, dtype=np.int64)
+    _check(lib().secpe_encode_packed(log_n, scale, _dblp(v), P, C, d_min,
+                                     m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "secpe_encode_packed")
+    return m
+
+
+def decode_packed(log_n, scale, coeffs, P, C):
+    """secpe_decode_packed (host only): out[P][C] from centred coefficients."""
+    coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
+    out = np.zeros((P, C), dtype=np.float64)
+    _check(lib().secpe_decode_packed(log_n, scale, _dblp(coeffs), P, C, _dblp(out)), "secpe_decode_packed")
+    return out
+
+
+def encrypt_logits_packed(ctx, keys, v, d_min, seed, out=None):
+    """secpe_encrypt_logits_packed: one prompt's logits of P inputs, v[P][C]."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    P, C = v.shape
+    out = ctx.new_ct() if out is None else out
+    c = out.struct()
+    _check(lib().secpe_encrypt_logits_packed(ctx.h, keys.h, _dblp(v), P, C, d_min, ctypes.c_uint64(seed),
+                                             ctypes.byref(c), _stream()), "secpe_encrypt_logits_packed")
+    out.update(c)
+    return out
+
+
+def decrypt_packed(ctx, keys, ct, P, C):
+    """secpe_decrypt_packed: out[P][C], the first C slots of every block."""
+    out = np.zeros((P, C), dtype=np.float64)
+    c = ct.struct()
+    _check(lib().secpe_decrypt_packed(ctx.h, keys.h, ctypes.byref(c), P, C, _dblp(out), _stream()),
+           "secpe_decrypt_packed")
+    return out
+
+
 def expand_seeded(ctx, cts_tensor, level, seeds):
     """Regenerate c1 of `cts_tensor` ([batch][2][cap][N]) from the encryption seeds."""
     seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
@@ -487,6 +556,14 @@ def rescale_noalloc(ctx, a, out):
            "secpe_rescale_noalloc")
     out.update(co)
     return out
+
+
+def pool_usage(trim=False):
+    """secpe_pool_usage: (used, reserved) bytes of the current device's
+    stream-ordered pool, after returning its unused blocks when trim."""
+    used, reserved = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(lib().secpe_pool_usage(1 if trim else 0, ctypes.byref(used), ctypes.byref(reserved)), "secpe_pool_usage")
+    return int(used.value), int(reserved.value)
 
 
 def rotate(ctx, keys, a, steps, out=None):

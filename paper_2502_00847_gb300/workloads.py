@@ -12,6 +12,9 @@ available, so the logits are drawn from fixed distributions:
            logits N(0, 1) (float32) clipped to [-4, 4]; if the mean vector's
            top-1 gap is < 0.02, the gap is added to the top class of every
            prompt; public bounds [-4.25, 4.25].
+* packed:  sets of inputs sharing a task (K, C drawn as above), as many per
+           set as slot packing fits (or a fraction), each input drawn as an
+           argmax query.
 """
 from dataclasses import dataclass
 
@@ -66,6 +69,58 @@ def argmax_queries(n_queries, seed=4, K_choices=ARGMAX_K, C_choices=ARGMAX_C, ma
             logits[:, top] += margin - gap
         out.append(Query(logits, ARGMAX_BOUNDS[0], ARGMAX_BOUNDS[1], qseed=(seed << 32) + qi,
                          enc_seeds=[(seed << 40) + (qi << 8) + i for i in range(K)]))
+    return out
+
+
+@dataclass
+class PackedQuery:
+    """P inputs of one task (same C and prompt ensemble K) that share one
+    ciphertext per prompt under slot packing."""
+    logits: np.ndarray  # [P][K][C] float64
+    d_min: float
+    d_max: float
+    qseed: int
+    enc_seeds: list     # one encryption seed per prompt (ciphertext)
+
+    @property
+    def P(self):
+        return self.logits.shape[0]
+
+    @property
+    def K(self):
+        return self.logits.shape[1]
+
+    @property
+    def C(self):
+        return self.logits.shape[2]
+
+    def prompt(self, i):
+        """[P][C]: prompt i's logits of every input (ciphertext i's content)."""
+        return np.ascontiguousarray(self.logits[:, i, :])
+
+
+def packed_queries(n_sets, slots, seed=6, K_choices=ARGMAX_K, C_choices=ARGMAX_C, margin=0.02, fill=1.0):
+    """Packed query sets with the Argmax mix's task distribution: each set
+    draws K and C like one query of the mix and holds round(fill * slots /
+    (2 C')) inputs, each input drawn like a query of the mix (N(0,1) float32
+    logits clipped to [-4, 4], top-1 mean gap planted to >= margin)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for si in range(n_sets):
+        K = int(rng.choice(K_choices))
+        C = int(rng.choice(C_choices))
+        cp = 1 << (C - 1).bit_length()
+        P = max(1, int(round(fill * (slots // (2 * cp)))))
+        logits = np.clip(rng.standard_normal((P, K, C)).astype(np.float32), -4.0, 4.0).astype(np.float64)
+        for b in range(P):
+            mean = logits[b].mean(0)
+            top = int(np.argmax(mean))
+            srt = np.sort(mean)
+            gap = srt[-1] - srt[-2]
+            if gap < margin:
+                logits[b, :, top] += margin - gap
+        out.append(PackedQuery(logits, ARGMAX_BOUNDS[0], ARGMAX_BOUNDS[1], qseed=(seed << 32) + si,
+                               enc_seeds=[(seed << 40) + (si << 8) + i for i in range(K)]))
     return out
 
 

@@ -1,8 +1,8 @@
-"""Continuous-batching server (secpe_server_*): queries submitted while others
-are in flight join at phase boundaries; each result is bit-identical alone
-and in the mix, and equal to the one-query path; admission by HBM budget,
-missing keys, cancellation and bounded waits are host-side failure paths
-(no GPU fault)."""
+"""Continuous-batching server (secpe_server_*): every query in flight advances
+one phase per step, so queries submitted while others are mid-circuit start
+at once and can finish first; each result is bit-identical alone and in the
+mix, and equal to the one-query path; admission by HBM budget, missing keys,
+cancellation and bounded waits are host-side failure paths (no GPU fault)."""
 import numpy as np
 import pytest
 
@@ -46,7 +46,7 @@ def test_interleaved_submissions_match_single_query_path(env):
     # two queries, a few phases, then the rest arrive while those are in flight
     for i in (0, 1):
         tickets.append(submit(srv, ctx, qs[i], inputs[i]))
-    assert srv.step() == 1          # oldest first: query 0's aggregation
+    assert srv.step() == 2          # both start at once (two groups: different C')
     assert srv.step() >= 1
     for i in (2, 3, 4):
         tickets.append(submit(srv, ctx, qs[i], inputs[i]))
@@ -166,3 +166,41 @@ def test_two_tenants_in_one_batch(env):
         zb = secpe.encrypted_argmax(ctx, keys_b, y, q.C, q.qseed)
         assert np.array_equal(batch[2 * i + 1]["z_out"].residues(), zb.residues())
         assert int(np.argmax(secpe.decrypt(ctx, keys_b, zb, q.C))) == int(np.argmax(q.logits.mean(0)))
+
+
+def test_arrival_mid_flight_finishes_before_the_cohort(env):
+    """Two queries with C = 16 (six phases) are two phases in when a C = 2
+    query (three phases) arrives: it starts in the next step, overlapping the
+    cohort's QuickMax rounds, and completes while the cohort is still in
+    flight; all three results equal their one-query evaluations bit for bit."""
+    ctx, keys, qs, inputs, ref, secpe = env
+    rot = [1, 2, 4, 8, -2, -16]
+    k2 = secpe.Keys(ctx, 34, rot)
+    big = [workloads.toy_query(seed=s, K=2, C=16) for s in (61, 62)]
+    small = workloads.toy_query(seed=63, K=3, C=2)
+    cts = {id(q): [secpe.encrypt_logits(ctx, k2, q.logits[i], q.d_min, q.enc_seeds[i]) for i in range(q.K)]
+           for q in big + [small]}
+    solo = {}
+    for q in big + [small]:
+        y = secpe.ensemble_aggregate(ctx, cts[id(q)], q.d_min, q.d_max)
+        solo[id(q)] = secpe.encrypted_argmax(ctx, k2, y, q.C, q.qseed).residues()
+    import torch
+    srv = secpe.Server(ctx, k2, hbm_budget_bytes=8 << 30, max_batch=8)
+    tb = [submit(srv, ctx, q, cts[id(q)]) for q in big]
+    assert srv.step() == 2
+    assert srv.step() == 2
+    ts = submit(srv, ctx, small, cts[id(small)])
+    finished_first = False
+    for _ in range(20):
+        n = srv.step()
+        torch.cuda.synchronize()
+        if srv.poll(ts[0]) == 1:
+            finished_first = all(srv.poll(t) == 0 for t, _ in tb)
+            break
+        assert n == 3, "the new query did not run beside the cohort"
+    assert finished_first, "the mid-flight arrival waited for the cohort"
+    for q, (t, z) in zip(big + [small], tb + [ts]):
+        assert srv.wait(t, 60.0) == 1
+        assert np.array_equal(z.residues(), solo[id(q)])
+        assert int(np.argmax(secpe.decrypt(ctx, k2, z, q.C))) == int(np.argmax(q.logits.mean(0)))
+

@@ -44,16 +44,37 @@ def test_two_ranks_shard_queries_and_take_max_time():
 
 
 def test_reference_arm_prints_on_rank0_only(monkeypatch, capsys):
+    """Rank 0 alone runs the oracle reference arm (a fake pool stands in for
+    the host-core workers); its line has real step times and the same
+    cpu_baseline fields as the GPU arm's."""
     sys.path.insert(0, ROOT)
+    import json
     import bench
 
     class A:
-        queries, steps, warmup, gpus, params = 4, 1, 0, 2, "argmax8"
+        queries, steps, warmup, gpus, params = 4, 2, 1, 2, "argmax8"
     called = []
-    monkeypatch.setattr(bench, "oracle_sample",
-                        lambda params_name, seconds_budget=0: called.append(params_name) or (1.0, 1.0, 0.0, 4))
+
+    class FakePool:
+        def map(self, fn, jobs, chunksize=1):
+            called.append(len(jobs))
+            return [0.5] * len(jobs)
+
+        def close(self):
+            pass
+
+        def join(self):
+            pass
+
+    monkeypatch.setattr(bench, "oracle_pool", lambda cores: FakePool())
+    monkeypatch.setattr(bench, "oracle_whole_queries",
+                        lambda pool, cores, params: {"t_query": 40.0, "ks_query": 35, "refreshes": 1, "wall": 45.0})
     bench.run_reference(A, 2, 1)
     assert capsys.readouterr().out == "" and not called
     bench.run_reference(A, 2, 0)
-    line = capsys.readouterr().out.strip()
-    assert '"impl": "reference"' in line and called
+    line = json.loads(capsys.readouterr().out.strip())
+    assert line["impl"] == "reference" and len(called) == A.warmup + A.steps
+    cores = line["cpu_baseline"]["cores"]
+    relin, rot = bench.op_mix_per_query(bench.workloads_argmax_queries(A.queries))
+    assert abs(line["value"] - cores * 35 / ((relin + rot) * 40.0)) < 1e-12
+    assert line["cpu_baseline"]["value"] == line["value"] and line["e2e"]["value"] == line["value"]
