@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=64.0,
                     help="default run: one short serving run at this rate (queries/s; 0: none)")
     ap.add_argument("--serve-window", type=float, default=8.0, help="default run: its arrival window (s)")
+    ap.add_argument("--no-phoenix", dest="phoenix", action="store_false",
+                    help="default run: skip the Phoenix baseline legs")
     ap.add_argument("--packed-sets", type=int, default=256,
                     help="default run: packed query sets of the slot-packing line (0: none)")
     ap.add_argument("--no-keyswitch-gbps", dest="keyswitch_gbps", action="store_false",
@@ -546,6 +548,11 @@ def run_ours(args, world, rank, local):
         serve = serve_rate(ctx, keys, [keys] * len(qs), [b["cts"] for b in batch], qs, args.serve_rate,
                            args.serve_window, 5, int(args.budget_gb * 1e9), 64, 10 ** 6)
 
+    # the Phoenix baseline (Sec. 3.2) on the same queries and GPU, and the
+    # paper's comparison point n = 256
+    phoenix = (run_phoenix(secpe, torch, workloads, ctx, batch, qs, 1000 + rank, ms_per_step)
+               if args.phoenix and rank == 0 else None)
+
     # key switching of the primitive set (config 2: 24 x 50-bit + 4 special,
     # dnum = 3) at B = 1 and B = 8, algorithmic bytes = input + key + output
     ksw = keyswitch_gbps(secpe, torch, dev, args.steps) if args.keyswitch_gbps and rank == 0 else None
@@ -629,7 +636,7 @@ def run_ours(args, world, rank, local):
                                   "re-encrypt), included in every step",
                        "autotune": {k: v["ctas_per_sm"] for k, v in tuning.items()}},
             "plain": plain, "e2e": e2e, "roofline": roofline, "roofline_other": other, "cpu_baseline": cpu,
-            "keyswitch_GBps": ksw, "serve": serve, "packed": packed,
+            "keyswitch_GBps": ksw, "serve": serve, "packed": packed, "phoenix": phoenix,
             "p99_ms": serve["served"]["p99_ms"] if serve else None,
             "clocks": clk, "gpu_launches": cnt["launches"], "refresh": refresh,
             **({"breakdown": breakdown} if breakdown else {}),
@@ -637,6 +644,58 @@ def run_ours(args, world, rank, local):
                                                                "keyswitches")},
         }
         print(json.dumps(line))
+
+
+def run_phoenix(secpe, torch, workloads, ctx, batch, qs, key_seed, secpe_ms):
+    """The Phoenix Argmax (m = C' - 1 comparisons + 1 Sign) over the whole mix
+    as one secpe_phoenix_argmax_batch call (one warm-up, one timed step),
+    against the SecPE step; and one query with n = C = 256 (K = 4), SecPE's
+    one-query call against Phoenix's, the paper's comparison point."""
+    keys = secpe.Keys(ctx, key_seed, list(range(1, 64)) + [-2, -4, -8, -16, -64])
+    pb = [dict(b, z_out=ctx.new_ct()) for b in batch]
+    secpe.phoenix_argmax_batch(ctx, keys, pb)
+    torch.cuda.synchronize()
+    for q, b in zip(qs, pb):
+        zd = secpe.decrypt(ctx, keys, b["z_out"], q.C)
+        assert int(np.argmax(zd)) == int(np.argmax(q.logits.mean(0))), "wrong Phoenix argmax"
+    ctx.reset_counters()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    secpe.phoenix_argmax_batch(ctx, keys, pb)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    cnt = ctx.counters()
+    del pb
+    keys.close()
+    out = {"value": len(qs) / (ms / 1e3), "unit": "queries/s", "ms_per_step": ms,
+           "secpe_over_phoenix": ms / secpe_ms,
+           "per_step_ops": {k: cnt[k] for k in ("signs", "rotations", "relins", "refreshes")},
+           "workload": "the same 256-query mix, one secpe_phoenix_argmax_batch call per step (direct)"}
+    # the paper's comparison point: one query of n = 256 classes
+    k256 = secpe.Keys(ctx, key_seed + 1, list(range(1, 256)) + [-256])
+    q = workloads.argmax_queries(1, seed=256, K_choices=(4,), C_choices=(256,))[0]
+    cts = [secpe.encrypt_logits(ctx, k256, q.logits[i], q.d_min, q.enc_seeds[i]) for i in range(q.K)]
+    y = secpe.ensemble_aggregate(ctx, cts, q.d_min, q.d_max)
+    times = {}
+    for name, fn in (("secpe", secpe.encrypted_argmax), ("phoenix", secpe.phoenix_argmax)):
+        z = fn(ctx, k256, y, q.C, q.qseed)
+        torch.cuda.synchronize()
+        assert int(np.argmax(secpe.decrypt(ctx, k256, z, q.C))) == int(np.argmax(q.logits.mean(0))), name
+        ctx.reset_counters()
+        e0.record()
+        fn(ctx, k256, y, q.C, q.qseed, out=z)
+        e1.record()
+        torch.cuda.synchronize()
+        c = ctx.counters()
+        times[name] = {"ms": e0.elapsed_time(e1), "signs": c["signs"], "rotations": c["rotations"],
+                       "relins": c["relins"]}
+    k256.close()
+    out["n256"] = dict(times, speedup=times["phoenix"]["ms"] / times["secpe"]["ms"],
+                       paper_speedup=20.8,
+                       note="one query, n = C = 256, K = 4, each Argmax one call; the paper's 20.8x is SEAL+HEXL "
+                            "on a CPU (Sec. 4.5), context only")
+    return out
 
 
 def run_packed(secpe, torch, workloads, ctx, keys, dev, steps, n_sets=256):

@@ -356,6 +356,25 @@ typedef struct {
 int secpe_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q,
                        int n_queries, void *stream);
 
+/* The baseline SecPE compares its Argmax with (Sec. 3.2, Phoenix): after the
+ * same duplication y + RotR(y, C'), every slot is compared with its
+ * m = C' - 1 cyclic neighbours, s = sum_{i=1..m} Sign(y - RotL(y, i)); the
+ * max slot has s = m and every other s <= m - 2, so
+ * z = (Sign((s - (m - 1)) / (2m)) + 1) / 2: m + 1 Signs and m + 1 rotations
+ * against SecPE's log2 C' + 1 of each.  The m comparisons start from the
+ * same ciphertext and run as one batch.  Comparison i draws its refresh
+ * randomness from the seed stream(qseed, 7, i), the final Sign from
+ * stream(qseed, 7, 0).  Needs Galois keys for RotR(C') and RotL(i),
+ * i = 1..C'-1 (SECPE_EKEY otherwise).  Same conventions as
+ * secpe_encrypted_argmax; z ends at the reserve level. */
+int secpe_phoenix_argmax(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *y, int C, uint64_t qseed,
+                         secpe_ct *z_out, void *stream);
+/* Aggregation + the Phoenix Argmax of n_queries queries, batched like
+ * secpe_argmax_batch (one batch per key set and C'); results equal
+ * secpe_ensemble_aggregate + secpe_phoenix_argmax per query bit for bit. */
+int secpe_phoenix_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int n_queries,
+                               void *stream);
+
 /* Graph-captured batched Argmax.  secpe_argmax_batch_capture records the
  * whole evaluation of secpe_argmax_batch for these queries (every launch,
  * stream-ordered allocation and copy) into one CUDA graph, on a stream of its

@@ -39,6 +39,7 @@ U64 = np.uint64
 
 # stream domains of the counter-based sampler (shared convention)
 DOM_SECRET, DOM_KSK_A, DOM_KSK_E, DOM_ENC_A, DOM_ENC_E, DOM_REFRESH = 1, 2, 3, 4, 5, 6
+DOM_PHOENIX = 7  # refresh seeds of the comparison Signs of the Phoenix baseline
 
 
 def round_half_away(v):
@@ -688,6 +689,35 @@ class Oracle:
         d = self.sub(al, y)
         s = self.sign(d, 0, lowest=True)
         return self.add_const(s, 1.0)
+
+    def phoenix_argmax(self, y, n_classes, qseed):
+        """The Phoenix Argmax the paper compares against (SecPE Sec. 3.2):
+        every slot compared with its m = C' - 1 cyclic neighbours,
+        s = sum_i Sign(y - RotL(y, i)), i = 1..m, then z from s by a linear
+        map and one more Sign: m + 1 Signs and m + 1 rotations.  READINGS
+        (the paper defers the details to Phoenix): the comparisons wrap
+        around the C' slots of y, padded as for Alg. 1, through the same
+        duplication y + RotR(y, C'); the max slot has s = m and every other
+        slot s <= m - 2, so z = (Sign((s - (m - 1)) / (2m)) + 1) / 2, the 1/2
+        folded into the last polynomial of that Sign; comparison i draws its
+        refresh randomness from the seed stream(qseed, 7, i) and the final
+        Sign from stream(qseed, 7, 0), each counting refreshes from 0."""
+        if n_classes < 2:
+            raise ValueError("argmax needs at least 2 classes")
+        cp = 1 << (n_classes - 1).bit_length()
+        if 2 * cp > self.n // 2:
+            raise ValueError("2*C' exceeds the slot count")
+        m = cp - 1
+        y = self.add(y, self.rotate(y, -cp))
+        s = None
+        for i in range(1, m + 1):
+            self.qseed, self.ridx = self.stream(qseed, DOM_PHOENIX, i), 0
+            si = self.sign(self.sub(y, self.rotate(y, i)), 1)
+            s = si if s is None else self.add(s, si)
+        t = self.mul_const(self.add_const(s, -(m - 1.0)), 1.0 / (2 * m), self.p.scale, s.level - 1)
+        self.qseed, self.ridx = self.stream(qseed, DOM_PHOENIX, 0), 0
+        z = self.sign(t, 0, last_factor=0.5, lowest=True)
+        return self.add_const(z, 0.5)
 
     def aggregate(self, cts, d_min, d_max):
         """Ensemble aggregation (SecPE Sec. 3.1 step 3) with the normalisation

@@ -87,3 +87,28 @@ def ensemble_argmax_packed(logits, d_min, d_max, slots, dg=2, df=2):
     z = argmax_slots(y, C, dg, df)
     return np.stack([z[b * 2 * cp: b * 2 * cp + C] for b in range(P)])
 
+
+def phoenix_argmax_slots(y, n_classes, dg=2, df=2):
+    """The Phoenix Argmax on a slot vector: s = sum_{i=1..m} Sign(y -
+    RotL(y, i)) after the duplication, z = (Sign((s - (m-1)) / (2m)) + 1)/2."""
+    cp = 1 << (n_classes - 1).bit_length()
+    m = cp - 1
+    y = y + rotl(y, -cp)
+    s = np.zeros_like(y)
+    for i in range(1, m + 1):
+        s = s + sign(y - rotl(y, i), dg, df)
+    t = (s - (m - 1.0)) * (1.0 / (2 * m))
+    return 0.5 * sign(t, dg, df) + 0.5
+
+
+def ensemble_phoenix_argmax(logits, d_min, d_max, slots, dg=2, df=2):
+    """logits[K][C] -> z over the first C slots (plaintext Phoenix pipeline)."""
+    logits = np.asarray(logits, dtype=np.float64)
+    K, C = logits.shape
+    y = np.zeros(slots)
+    for i in range(K):
+        p = pad_logits(logits[i], C, d_min)
+        y[: len(p)] += p
+    y = y * (1.0 / (K * (d_max - d_min)))
+    return phoenix_argmax_slots(y, C, dg, df)[:C]
+

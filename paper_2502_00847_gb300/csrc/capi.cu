@@ -15,6 +15,7 @@ void decode_real_fft(int n, const double *coeffs, double scale, int nslots, doub
 }  // namespace enc
 
 int argmax_batch_impl(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_);
+int phoenix_batch_impl(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_);
 
 namespace {
 
@@ -575,6 +576,25 @@ extern "C" int secpe_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const 
     if (n_queries == 0) return SECPE_OK;
     CallScope cs(ctx, stream);
     return finish(ctx, argmax_batch_impl(ctx, keys, q, n_queries));
+}
+
+extern "C" int secpe_phoenix_argmax(secpe_ctx *ctx, const secpe_keys *keys_, const secpe_ct *y, int C,
+                                    uint64_t qseed, secpe_ct *z_out, void *stream) {
+    if (!ctx || !keys_) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, y));
+    EVAL_PROLOGUE(ctx, stream);
+    E.qseeds.assign(1, qseed);
+    Ct r;
+    SECPE_CHECK(E.phoenix(view(ctx, y), C, r));
+    return finish(ctx, copy_out(ctx, r, z_out));
+}
+
+extern "C" int secpe_phoenix_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q,
+                                          int n_queries, void *stream) {
+    if (!ctx || !q || n_queries < 0) return SECPE_EINVAL;
+    if (n_queries == 0) return SECPE_OK;
+    CallScope cs(ctx, stream);
+    return finish(ctx, phoenix_batch_impl(ctx, keys, q, n_queries));
 }
 
 // ---------------------------------------------------------------- autotuning

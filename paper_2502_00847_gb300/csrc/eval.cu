@@ -378,6 +378,67 @@ int Eval::argmax(const Ct &y, int C, Ct &out) {
     return add_const(s, 1.0, out);
 }
 
+// The Phoenix Argmax that SecPE Sec. 3.2 compares against: after the same
+// duplication, every slot is compared with its m = C' - 1 cyclic
+// neighbours, s = sum_{i=1..m} Sign(y - RotL(y, i)); the max slot has
+// s = m, every other s <= m - 2, so z = (Sign((s - (m - 1)) / (2m)) + 1) / 2
+// (the 1/2 folded into the last polynomial): m + 1 Signs and m + 1
+// rotations.  The m comparisons start from the same ciphertext, so they run
+// as one batch of m * B items (in chunks that bound memory).  Comparison i
+// of query b takes its refresh randomness from the seed
+// stream(qseed_b, DOM_PHOENIX, i), the final Sign from stream(qseed_b,
+// DOM_PHOENIX, 0), each counting refreshes from 0.
+int Eval::phoenix(const Ct &y, int C, Ct &out) {
+    if (C < 2) return SECPE_EINVAL;
+    int cp;
+    log2_ceil_pow(C, cp);
+    if (2 * cp > ctx->n / 2) return SECPE_EINVAL;
+    const int m = cp - 1, B = y.B();
+    if ((int)qseeds.size() != B) return SECPE_EINVAL;
+    Ct rot, ydup;
+    SECPE_CHECK(rotate(y, -cp, rot));
+    SECPE_CHECK(add(y, rot, ydup));
+    rot = Ct();
+    const int lv = ydup.level();
+    const int chunk = std::max(1, std::min(SECPE_MAX_BATCH_CONST, 128) / B);
+    Ct s;
+    for (int i0 = 1; i0 <= m; i0 += chunk) {
+        const int nm = std::min(m + 1, i0 + chunk) - i0;
+        Ct D, S;
+        SECPE_CHECK(ct_alloc(ctx, nm * B, lv, ydup.scale(), D));
+        Eval Ec{ctx, keys, {}, 0};
+        for (int i = i0; i < i0 + nm; i++) {
+            Ct r;
+            SECPE_CHECK(rotate(ydup, i, r));
+            Ct dst = ct_slice(D, (i - i0) * B, (i - i0 + 1) * B);
+            SECPE_CHECK(launch_addsub(ctx, ydup.v, r.v, dst.v, lv + 1, true));
+            for (int b = 0; b < B; b++) Ec.qseeds.push_back(hm::sm_stream(qseeds[b], DOM_PHOENIX, (u64)i));
+        }
+        SECPE_CHECK(Ec.sign(D, 1, S));
+        D = Ct();
+        for (int i = 0; i < nm; i++) {
+            Ct Si = ct_slice(S, i * B, (i + 1) * B);
+            if (!s.buf) {
+                s = Si;
+            } else {
+                Ct sum;
+                SECPE_CHECK(add(s, Si, sum));
+                s = sum;
+            }
+        }
+    }
+    Ct t0, t;
+    SECPE_CHECK(add_const(s, -(m - 1.0), t0));
+    s = Ct();
+    SECPE_CHECK(mul_const(t0, {1.0 / (2.0 * m)}, ctx->scale, t0.level() - 1, t));
+    t0 = Ct();
+    Eval Ef{ctx, keys, {}, 0};
+    for (int b = 0; b < B; b++) Ef.qseeds.push_back(hm::sm_stream(qseeds[b], DOM_PHOENIX, 0));
+    Ct zs;
+    SECPE_CHECK(Ef.sign(t, 0, zs, 0.5, true));
+    return add_const(zs, 0.5, out);
+}
+
 // ---------------------------------------------------------------- batch
 // Queries are ordered by r = log2 C' (descending) so that at phase k the
 // queries still in QuickMax form a prefix of the batch and the queries that
@@ -385,29 +446,43 @@ int Eval::argmax(const Ct &y, int C, Ct &out) {
 // range share level, scale and refresh history, so each range is a single
 // batched evaluation.
 static int argmax_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_);
+static int phoenix_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_);
+typedef int (*tenant_fn)(secpe_ctx *, const secpe_keys *, const secpe_query *, int);
 
 // Queries of different tenants are evaluated as one batch per key set.
-int argmax_batch_impl(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_) {
+static int per_tenant(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_, tenant_fn fn) {
     std::vector<const secpe_keys *> sets;
     for (int b = 0; b < nq_; b++) {
         const secpe_keys *k = q[b].keys ? q[b].keys : keys;
         if (!k) return SECPE_EINVAL;
         if (std::find(sets.begin(), sets.end(), k) == sets.end()) sets.push_back(k);
     }
-    if (sets.size() == 1) return argmax_batch_tenant(ctx, sets[0], q, nq_);
+    if (sets.size() == 1) return fn(ctx, sets[0], q, nq_);
     for (const secpe_keys *k : sets) {
         std::vector<secpe_query> part;
         for (int b = 0; b < nq_; b++)
             if ((q[b].keys ? q[b].keys : keys) == k) part.push_back(q[b]);
-        SECPE_CHECK(argmax_batch_tenant(ctx, k, part.data(), (int)part.size()));
+        SECPE_CHECK(fn(ctx, k, part.data(), (int)part.size()));
     }
     return SECPE_OK;
 }
 
-static int argmax_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_) {
+int argmax_batch_impl(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_) {
+    return per_tenant(ctx, keys, q, nq_, argmax_batch_tenant);
+}
+
+int phoenix_batch_impl(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_) {
+    return per_tenant(ctx, keys, q, nq_, phoenix_batch_tenant);
+}
+
+// Checks the queries and orders them by r = log2 C' (descending, stable).
+static int sort_queries(const secpe_ctx *ctx, const secpe_query *q, int nq_, std::vector<int> &order,
+                        std::vector<int> &rr, std::vector<int> &cps) {
     const int n = ctx->n, L = ctx->L;
     if (nq_ > SECPE_MAX_BATCH_CONST) return SECPE_EINVAL;
-    std::vector<int> order(nq_), rr(nq_), cps(nq_);
+    order.resize(nq_);
+    rr.resize(nq_);
+    cps.resize(nq_);
     for (int b = 0; b < nq_; b++) {
         if (q[b].C < 2 || q[b].K < 1 || !q[b].cts || !q[b].z_out || !q[b].z_out->data || !aligned16(q[b].z_out->data))
             return SECPE_EINVAL;
@@ -421,33 +496,77 @@ static int argmax_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const sec
     }
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return rr[x] > rr[y]; });
-    Eval E{ctx, keys, {}, 0};
+    return SECPE_OK;
+}
 
-    // 1. aggregation into Y (sorted order), level L: one launch sums every
-    // query's K inputs
+// Ensemble aggregation of every query (SecPE Sec. 3.1 step 3, Eq. norm
+// scale) into Yn in sorted order, level L - 1: one launch sums every
+// query's K inputs, one scalar product per query applies 1/(K (D_max - D_min)).
+static int aggregate_sorted(secpe_ctx *ctx, Eval &E, const secpe_query *q, const std::vector<int> &order, Ct &Yn) {
+    const int nq_ = (int)order.size(), L = ctx->L;
     Ct Y;
     SECPE_CHECK(ct_alloc(ctx, nq_, L, ctx->scale, Y));
-    {
-        std::vector<const u64 *> src;
-        std::vector<int> cap, qoff(1, 0);
-        for (int s = 0; s < nq_; s++) {
-            const secpe_query &Q = q[order[s]];
-            for (int i = 0; i < Q.K; i++) {
-                src.push_back((const u64 *)Q.cts[i].data);
-                cap.push_back(Q.cts[i].cap);
-            }
-            qoff.push_back((int)src.size());
-        }
-        SECPE_CHECK(launch_sum_cts(ctx, src, cap, qoff, Y.v, L + 1));
-    }
+    std::vector<const u64 *> src;
+    std::vector<int> cap, qoff(1, 0);
     std::vector<double> w(nq_);
     for (int s = 0; s < nq_; s++) {
         const secpe_query &Q = q[order[s]];
+        for (int i = 0; i < Q.K; i++) {
+            src.push_back((const u64 *)Q.cts[i].data);
+            cap.push_back(Q.cts[i].cap);
+        }
+        qoff.push_back((int)src.size());
         w[s] = 1.0 / (Q.K * (Q.d_max - Q.d_min));
     }
+    SECPE_CHECK(launch_sum_cts(ctx, src, cap, qoff, Y.v, L + 1));
+    return E.mul_const(Y, w, ctx->scale, L - 1, Yn);
+}
+
+// z of the sorted items [s, e) of z into the queries' z_out buffers.
+static int copy_z(secpe_ctx *ctx, const secpe_query *q, const std::vector<int> &order, int s0, const Ct &z) {
+    const int n = ctx->n;
+    for (int s = s0; s < s0 + z.B(); s++) {
+        secpe_ct *zo = q[order[s]].z_out;
+        if (zo->cap < z.level() + 1) return SECPE_EINVAL;
+        const u64 *src = z.v.data + (long long)(s - s0) * z.v.stride;
+        SECPE_CUDA(cudaMemcpy2DAsync(zo->data, sizeof(u64) * zo->cap * n, src, sizeof(u64) * z.v.cap * n,
+                                     sizeof(u64) * (z.level() + 1) * n, 2, cudaMemcpyDeviceToDevice, ctx->stream));
+        zo->level = z.level();
+        zo->scale = z.scale();
+    }
+    return SECPE_OK;
+}
+
+// The Phoenix baseline over a batch: aggregation as for SecPE, then one
+// batched Eval::phoenix per group of equal C'.
+static int phoenix_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_) {
+    std::vector<int> order, rr, cps;
+    SECPE_CHECK(sort_queries(ctx, q, nq_, order, rr, cps));
+    Eval E{ctx, keys, {}, 0};
     Ct Yn;
-    SECPE_CHECK(E.mul_const(Y, w, ctx->scale, L - 1, Yn));
-    Y = Ct();
+    SECPE_CHECK(aggregate_sorted(ctx, E, q, order, Yn));
+    for (int s = 0; s < nq_;) {
+        int e = s;
+        while (e < nq_ && rr[order[e]] == rr[order[s]]) e++;
+        Eval Eg{ctx, keys, {}, 0};
+        for (int k = s; k < e; k++) Eg.qseeds.push_back(q[order[k]].qseed);
+        Ct z;
+        SECPE_CHECK(Eg.phoenix(ct_slice(Yn, s, e), q[order[s]].C, z));
+        SECPE_CHECK(copy_z(ctx, q, order, s, z));
+        s = e;
+    }
+    return SECPE_OK;
+}
+
+static int argmax_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_) {
+    const int L = ctx->L;
+    std::vector<int> order, rr, cps;
+    SECPE_CHECK(sort_queries(ctx, q, nq_, order, rr, cps));
+    Eval E{ctx, keys, {}, 0};
+
+    // 1. aggregation into Yn (sorted order), level L - 1
+    Ct Yn;
+    SECPE_CHECK(aggregate_sorted(ctx, E, q, order, Yn));
 
     // 2. duplication y + RotR(y, C') per group of equal r
     std::vector<Ct> ydup_parts;
@@ -485,16 +604,7 @@ static int argmax_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const sec
             SECPE_CHECK(Ef.sub(al, yf, d));
             SECPE_CHECK(Ef.sign(d, 0, sgn, 1.0, true));
             SECPE_CHECK(Ef.add_const(sgn, 1.0, z));
-            for (int s = cnt_gt; s < cnt_ge; s++) {
-                secpe_ct *zo = q[order[s]].z_out;
-                if (zo->cap < z.level() + 1) return SECPE_EINVAL;
-                const u64 *src = z.v.data + (long long)(s - cnt_gt) * z.v.stride;
-                SECPE_CUDA(cudaMemcpy2DAsync(zo->data, sizeof(u64) * zo->cap * n, src, sizeof(u64) * z.v.cap * n,
-                                             sizeof(u64) * (z.level() + 1) * n, 2, cudaMemcpyDeviceToDevice,
-                                             ctx->stream));
-                zo->level = z.level();
-                zo->scale = z.scale();
-            }
+            SECPE_CHECK(copy_z(ctx, q, order, cnt_gt, z));
         }
         if (cnt_gt == 0) break;
         Eval Er{ctx, keys, {}, ridx};

@@ -76,6 +76,8 @@ struct Eval {
     int sign(const Ct &x, int out_levels, Ct &out, double last_factor = 1.0, bool lowest = false);
     int max(const Ct &a, const Ct &y, Ct &out);
     int argmax(const Ct &y, int C, Ct &out);
+    // the Phoenix Argmax baseline (m + 1 Signs, m + 1 rotations, m = C' - 1)
+    int phoenix(const Ct &y, int C, Ct &out);
 };
 
 // Hybrid key switching (keyswitch.cu): d = limbs 0..lv of one polynomial per

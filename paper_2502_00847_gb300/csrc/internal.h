@@ -170,4 +170,4 @@ long long round_half_away(double v);
 
 // stream domains of the counter-based sampler
 enum { DOM_SECRET = 1, DOM_KSK_A = 2, DOM_KSK_E = 3, DOM_ENC_A = 4, DOM_ENC_E = 5,
-       DOM_REFRESH = 6 };
+       DOM_REFRESH = 6, DOM_PHOENIX = 7 };

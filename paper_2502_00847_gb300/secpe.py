@@ -30,7 +30,8 @@ EXPORTS = [
     "secpe_server_cancel", "secpe_server_step", "secpe_server_poll", "secpe_server_wait", "secpe_server_forget",
     "secpe_server_stats", "secpe_ntt_tc", "secpe_ntt_cts_tc", "secpe_expand_seeded", "secpe_keyswitch_batch_tc",
     "secpe_pool_usage", "secpe_mul32_probe", "secpe_packed_capacity", "secpe_encode_packed",
-    "secpe_decode_packed", "secpe_encrypt_logits_packed", "secpe_decrypt_packed",
+    "secpe_decode_packed", "secpe_encrypt_logits_packed", "secpe_decrypt_packed", "secpe_phoenix_argmax",
+    "secpe_phoenix_argmax_batch",
 ]
 
 
@@ -154,6 +155,8 @@ def lib():
         "secpe_pool_usage": (i32, [i32, P(u64), P(u64)]),
         "secpe_mul32_probe": (i32, [vp, i32, i32, P(dbl), vp]),
         "secpe_packed_capacity": (i32, [i32, i32]),
+        "secpe_phoenix_argmax": (i32, [vp, vp, P(CtC), i32, u64, P(CtC), vp]),
+        "secpe_phoenix_argmax_batch": (i32, [vp, vp, P(QueryC), i32, vp]),
         "secpe_encode_packed": (i32, [i32, dbl, P(dbl), i32, i32, dbl, P(ctypes.c_int64)]),
         "secpe_decode_packed": (i32, [i32, dbl, P(dbl), i32, i32, P(dbl)]),
         "secpe_encrypt_logits_packed": (i32, [vp, vp, P(dbl), i32, i32, dbl, u64, P(CtC), vp]),
@@ -653,6 +656,26 @@ def argmax_batch(ctx, keys, queries):
     qseed, z_out (Ciphertext).  Updates each z_out's level/scale."""
     qarr, keep = _query_array(queries)
     _check(lib().secpe_argmax_batch(ctx.h, keys.h, qarr, len(queries), _stream()), "secpe_argmax_batch")
+    for q, (_, z) in zip(queries, keep):
+        q["z_out"].update(z)
+
+
+def phoenix_argmax(ctx, keys, y, C, qseed, out=None):
+    """secpe_phoenix_argmax: the Phoenix baseline Argmax on a normalised y."""
+    out = ctx.new_ct() if out is None else out
+    cy, co = y.struct(), out.struct()
+    _check(lib().secpe_phoenix_argmax(ctx.h, keys.h, ctypes.byref(cy), C, ctypes.c_uint64(qseed),
+                                      ctypes.byref(co), _stream()), "secpe_phoenix_argmax")
+    out.update(co)
+    return out
+
+
+def phoenix_argmax_batch(ctx, keys, queries):
+    """secpe_phoenix_argmax_batch: aggregation + Phoenix Argmax, batched
+    (queries as for argmax_batch)."""
+    qarr, keep = _query_array(queries)
+    _check(lib().secpe_phoenix_argmax_batch(ctx.h, keys.h, qarr, len(queries), _stream()),
+           "secpe_phoenix_argmax_batch")
     for q, (_, z) in zip(queries, keep):
         q["z_out"].update(z)
 
