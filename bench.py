@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=64.0,
                     help="default run: one short serving run at this rate (queries/s; 0: none)")
     ap.add_argument("--serve-window", type=float, default=8.0, help="default run: its arrival window (s)")
+    ap.add_argument("--no-clip", dest="clip", action="store_false",
+                    help="default run: skip the CLIP-style linear-step pipeline")
     ap.add_argument("--no-phoenix", dest="phoenix", action="store_false",
                     help="default run: skip the Phoenix baseline legs")
     ap.add_argument("--packed-sets", type=int, default=256,
@@ -553,6 +555,10 @@ def run_ours(args, world, rank, local):
     phoenix = (run_phoenix(secpe, torch, workloads, ctx, batch, qs, 1000 + rank, ms_per_step)
                if args.phoenix and rank == 0 else None)
 
+    # the CLIP-style pipeline: encrypted linear step (K = 80 templates) +
+    # aggregation + Argmax for a batch of encrypted images
+    clip = run_clip(secpe, torch, workloads, ctx, 1000 + rank) if args.clip and rank == 0 else None
+
     # key switching of the primitive set (config 2: 24 x 50-bit + 4 special,
     # dnum = 3) at B = 1 and B = 8, algorithmic bytes = input + key + output
     ksw = keyswitch_gbps(secpe, torch, dev, args.steps) if args.keyswitch_gbps and rank == 0 else None
@@ -636,7 +642,7 @@ def run_ours(args, world, rank, local):
                                   "re-encrypt), included in every step",
                        "autotune": {k: v["ctas_per_sm"] for k, v in tuning.items()}},
             "plain": plain, "e2e": e2e, "roofline": roofline, "roofline_other": other, "cpu_baseline": cpu,
-            "keyswitch_GBps": ksw, "serve": serve, "packed": packed, "phoenix": phoenix,
+            "keyswitch_GBps": ksw, "serve": serve, "packed": packed, "phoenix": phoenix, "clip": clip,
             "p99_ms": serve["served"]["p99_ms"] if serve else None,
             "clocks": clk, "gpu_launches": cnt["launches"], "refresh": refresh,
             **({"breakdown": breakdown} if breakdown else {}),
@@ -696,6 +702,50 @@ def run_phoenix(secpe, torch, workloads, ctx, batch, qs, key_seed, secpe_ms):
                        note="one query, n = C = 256, K = 4, each Argmax one call; the paper's 20.8x is SEAL+HEXL "
                             "on a CPU (Sec. 4.5), context only")
     return out
+
+
+def run_clip(secpe, torch, workloads, ctx, key_seed, d=512, C=10, K=80, B=16):
+    """CLIP-style prompt ensembling (Sec. 2.3) end to end on the device: one
+    task's plaintext text embeddings T[K][C][d] (K = 80 templates), B
+    encrypted image embeddings; per image secpe_linear_apply (K logit
+    ciphertexts, batched over the prompts), then one secpe_argmax_batch over
+    the B images.  One warm-up, one timed pass."""
+    cp = 1 << (C - 1).bit_length()
+    rot = [cp << t for t in range(d.bit_length() - 1)] + [-cp] + [1 << i for i in range(cp.bit_length() - 1)]
+    keys = secpe.Keys(ctx, key_seed, rot)
+    T, xs, qseeds, seeds = workloads.clip_images(d, C, K, B)
+    lin = secpe.Linear(ctx, T=T, d_min=workloads.ARGMAX_BOUNDS[0])
+    xcts = [secpe.encrypt_replicated(ctx, keys, x, C, s) for x, s in zip(xs, seeds)]
+    outs = [[ctx.new_ct() for _ in range(K)] for _ in range(B)]
+    batch = [dict(cts=outs[b], C=C, d_min=workloads.ARGMAX_BOUNDS[0], d_max=workloads.ARGMAX_BOUNDS[1],
+                  qseed=qseeds[b], z_out=ctx.new_ct()) for b in range(B)]
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+
+    def run():
+        e0.record()
+        for b in range(B):
+            lin.apply(keys, xcts[b], outs[b])
+        e1.record()
+        secpe.argmax_batch(ctx, keys, batch)
+        e2.record()
+        torch.cuda.synchronize()
+
+    run()
+    for b in range(B):
+        zd = secpe.decrypt(ctx, keys, batch[b]["z_out"], C)
+        assert int(np.argmax(zd)) == int(np.argmax(np.einsum("kcd,d->kc", T, xs[b]).mean(0))), "wrong CLIP argmax"
+    ctx.reset_counters()
+    run()
+    cnt = ctx.counters()
+    ms_lin, ms_arg = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    lin.close()
+    keys.close()
+    del outs, batch, xcts
+    return {"value": B / ((ms_lin + ms_arg) / 1e3), "unit": "images/s", "images": B, "ms_linear": ms_lin,
+            "ms_argmax": ms_arg, "rotations": cnt["rotations"],
+            "workload": "CLIP-style zero-shot: d=%d, C=%d, K=%d templates, %d encrypted images; per image the "
+                        "linear step (K plaintext products, log2(d) rotate-adds batched over the prompts, mask, "
+                        "pad), then aggregation + Alg. 1 for all images in one batch" % (d, C, K, B)}
 
 
 def run_packed(secpe, torch, workloads, ctx, keys, dev, steps, n_sets=256):

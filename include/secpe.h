@@ -337,6 +337,42 @@ int secpe_ensemble_aggregate(secpe_ctx *ctx, const secpe_ct *cts, int K, double 
 int secpe_encrypted_argmax(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *y, int C,
                            uint64_t qseed, secpe_ct *z_out, void *stream);
 
+/* ---- upstream encrypted linear step (CLIP-style prompt ensembling) ------- */
+/* SecPE Sec. 2.3 scores an image embedding x = I(x_in) (d values) against
+ * the text embedding T_i[c] of prompt template i and class c, y_i[c] =
+ * <T_i[c], x>, and aggregates the K logit vectors before the Argmax
+ * (Sec. 3.1 step 3); here x is encrypted and the T_i are the server's
+ * plaintext weights.  Layout (d a power of two, C' = next power of two >= C,
+ * d C' <= N/2): the user encrypts x with x[j] repeated in the C' slots
+ * [j C', (j+1) C') (secpe_encrypt_replicated); for each prompt the server
+ * multiplies by the plaintext with T_i[c][j] at slot j C' + c (encoded at
+ * scale q_L), adds log2(d) rotations by C' 2^t, multiplies by a plaintext
+ * mask (1 on slots [0, C), scale q_(L-1)) and adds a plaintext with d_min on
+ * [C, C') (scale Delta).  Each output is the layout secpe_encrypt_logits
+ * produces, at level L - 2 with x's scale, ready for secpe_argmax_batch.
+ * Needs Galois keys for C' 2^t, t < log2 d. */
+typedef struct secpe_linear secpe_linear;
+/* Encodes T[K][C][d] (host, row-major) with the packed encoder and uploads
+ * the K weight plaintexts, the mask and the pad (device memory owned by the
+ * object, about (K (L+1) + 2L) N words).  SECPE_EINVAL for d not a power of
+ * two or d C' > N/2. */
+int secpe_linear_create(secpe_ctx *ctx, const double *T, int K, int C, int d, double d_min, secpe_linear **out);
+/* The same from integer coefficients chosen by the caller: W_m[K][N] at
+ * scale q_L, mask_m[N] at scale q_(L-1), pad_m[N] at scale Delta. */
+int secpe_linear_create_coeffs(secpe_ctx *ctx, const int64_t *W_m, const int64_t *mask_m, const int64_t *pad_m,
+                               int K, int C, int d, secpe_linear **out);
+void secpe_linear_destroy(secpe_linear *lin);
+/* outs[K] (caller device buffers, cap >= L - 1) = the K prompts' logit
+ * ciphertexts of x (level L, scale Delta); the K prompts run as one batch.
+ * SECPE_ELEVEL / SECPE_ESCALE for other inputs, SECPE_EKEY for a missing
+ * rotation key. */
+int secpe_linear_apply(secpe_ctx *ctx, const secpe_keys *keys, const secpe_linear *lin, const secpe_ct *x,
+                       secpe_ct *outs, void *stream);
+/* Client: encrypts x[d] with x[j] in the C' slots [j C', (j+1) C'), top
+ * level, scale Delta (packed encoder). */
+int secpe_encrypt_replicated(secpe_ctx *ctx, const secpe_keys *keys, const double *x, int d, int C, uint64_t seed,
+                             secpe_ct *out, void *stream);
+
 /* One ensemble query for the batched driver. */
 typedef struct {
     const secpe_ct *cts;  /* K input ciphertexts (top level, scale Delta) */

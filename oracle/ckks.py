@@ -719,6 +719,74 @@ class Oracle:
         z = self.sign(t, 0, last_factor=0.5, lowest=True)
         return self.add_const(z, 0.5)
 
+    # ---------------------------------------- upstream encrypted linear step
+    def mul_plain(self, ct, m, pt_scale):
+        """Slot-wise product with the plaintext of integer coefficients m
+        encoded at scale pt_scale, then the rescale: scale s * pt_scale / q_l."""
+        lv = ct.level
+        P = self.ntt_of_signed(np.array([int(v) for v in m], dtype=np.int64), list(range(lv + 1)))
+        c = np.empty_like(ct.c)
+        for k in range(2):
+            for pi in range(lv + 1):
+                c[k, pi] = self.vmul(ct.c[k, pi], P[pi], pi)
+        return self.rescale(Ct(c, lv, ct.scale * pt_scale))
+
+    def add_plain(self, ct, m):
+        """ct + (plaintext of integer coefficients m, 0): m must be encoded at
+        ct's scale."""
+        P = self.ntt_of_signed(np.array([int(v) for v in m], dtype=np.int64), list(range(ct.level + 1)))
+        out = ct.copy()
+        for pi in range(ct.level + 1):
+            out.c[0, pi] = self.vadd(ct.c[0, pi], P[pi], pi)
+        return out
+
+    def replicated_slots(self, x, n_classes):
+        """x[d] with x[j] repeated in the C' slots [j C', (j+1) C') (READING of
+        the layout of the CLIP-style linear step, Sec. 2.3)."""
+        cp = 1 << (n_classes - 1).bit_length()
+        return np.repeat(np.asarray(x, dtype=np.float64), cp)
+
+    def encrypt_replicated(self, x, n_classes, seed):
+        return self.encrypt(self.replicated_slots(x, n_classes), seed)
+
+    def linear_plaintexts(self, T, d_min, level=None):
+        """Integer coefficients of the linear step's plaintexts for weights
+        T[K][C][d]: W_i (T_i[c][j] at slot j C' + c) at scale q_level, the
+        mask (1 on slots [0, C)) at scale q_(level-1), the pad (d_min on
+        [C, C')) at scale Delta."""
+        level = self.ctx.L if level is None else level
+        T = np.asarray(T, dtype=np.float64)
+        K, C, d = T.shape
+        cp = 1 << (C - 1).bit_length()
+        Wm = []
+        for i in range(K):
+            v = np.zeros(d * cp)
+            for j in range(d):
+                v[j * cp: j * cp + C] = T[i, :, j]
+            Wm.append(self.encode_coeffs(v, float(self.primes[level])))
+        mask = np.zeros(cp)
+        mask[:C] = 1.0
+        pad = np.zeros(cp)
+        pad[C:] = d_min
+        return Wm, self.encode_coeffs(mask, float(self.primes[level - 1])), self.encode_coeffs(pad, self.p.scale)
+
+    def linear_logits(self, x, plaintexts, n_classes, d):
+        """The K prompts' logit ciphertexts y_i = mask (.) sum_t RotL(W_i (.)
+        x, C' 2^t) (accumulated) + pad, each product rescaled: for prompt i,
+        slot c < C holds <T_i[c], x> (SecPE Sec. 2.3, CLIP ensembling)."""
+        Wm, mask_m, pad_m = plaintexts
+        cp = 1 << (n_classes - 1).bit_length()
+        outs = []
+        for m in Wm:
+            p = self.mul_plain(x, m, float(self.primes[x.level]))
+            s = cp
+            while s < cp * d:
+                p = self.add(p, self.rotate(p, s))
+                s <<= 1
+            p = self.mul_plain(p, mask_m, float(self.primes[p.level]))
+            outs.append(self.add_plain(p, pad_m))
+        return outs
+
     def aggregate(self, cts, d_min, d_max):
         """Ensemble aggregation (SecPE Sec. 3.1 step 3) with the normalisation
         of Eq. norm folded into one constant: y = (sum_i ct_i) * w,

@@ -476,9 +476,12 @@ int phoenix_batch_impl(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query
 }
 
 // Checks the queries and orders them by r = log2 C' (descending, stable).
+// Every input ciphertext of the call must be at one level, *lin (the top
+// level for fresh encryptions, lower after an upstream linear step).
 static int sort_queries(const secpe_ctx *ctx, const secpe_query *q, int nq_, std::vector<int> &order,
-                        std::vector<int> &rr, std::vector<int> &cps) {
-    const int n = ctx->n, L = ctx->L;
+                        std::vector<int> &rr, std::vector<int> &cps, int *lin) {
+    const int n = ctx->n;
+    *lin = -1;
     if (nq_ > SECPE_MAX_BATCH_CONST) return SECPE_EINVAL;
     order.resize(nq_);
     rr.resize(nq_);
@@ -490,20 +493,25 @@ static int sort_queries(const secpe_ctx *ctx, const secpe_query *q, int nq_, std
         if (2 * cps[b] > n / 2) return SECPE_EINVAL;
         for (int i = 0; i < q[b].K; i++) {
             const secpe_ct &c = q[b].cts[i];
-            if (!c.data || !aligned16(c.data) || c.level != L || c.cap < L + 1) return SECPE_EINVAL;
+            if (*lin < 0) *lin = c.level;
+            if (!c.data || !aligned16(c.data) || c.level != *lin || c.level > ctx->L || c.cap < c.level + 1)
+                return SECPE_EINVAL;
             if (!scales_match(c.scale, ctx->scale)) return SECPE_ESCALE;
         }
     }
+    if (*lin < ctx->p.reserve + 1) return SECPE_ELEVEL;
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return rr[x] > rr[y]; });
     return SECPE_OK;
 }
 
 // Ensemble aggregation of every query (SecPE Sec. 3.1 step 3, Eq. norm
-// scale) into Yn in sorted order, level L - 1: one launch sums every
-// query's K inputs, one scalar product per query applies 1/(K (D_max - D_min)).
-static int aggregate_sorted(secpe_ctx *ctx, Eval &E, const secpe_query *q, const std::vector<int> &order, Ct &Yn) {
-    const int nq_ = (int)order.size(), L = ctx->L;
+// scale) into Yn in sorted order, at the inputs' level L - 1: one launch
+// sums every query's K inputs, one scalar product per query applies
+// 1/(K (D_max - D_min)).
+static int aggregate_sorted(secpe_ctx *ctx, Eval &E, const secpe_query *q, const std::vector<int> &order, int L,
+                            Ct &Yn) {
+    const int nq_ = (int)order.size();
     Ct Y;
     SECPE_CHECK(ct_alloc(ctx, nq_, L, ctx->scale, Y));
     std::vector<const u64 *> src;
@@ -541,10 +549,11 @@ static int copy_z(secpe_ctx *ctx, const secpe_query *q, const std::vector<int> &
 // batched Eval::phoenix per group of equal C'.
 static int phoenix_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_) {
     std::vector<int> order, rr, cps;
-    SECPE_CHECK(sort_queries(ctx, q, nq_, order, rr, cps));
+    int lin;
+    SECPE_CHECK(sort_queries(ctx, q, nq_, order, rr, cps, &lin));
     Eval E{ctx, keys, {}, 0};
     Ct Yn;
-    SECPE_CHECK(aggregate_sorted(ctx, E, q, order, Yn));
+    SECPE_CHECK(aggregate_sorted(ctx, E, q, order, lin, Yn));
     for (int s = 0; s < nq_;) {
         int e = s;
         while (e < nq_ && rr[order[e]] == rr[order[s]]) e++;
@@ -559,14 +568,14 @@ static int phoenix_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const se
 }
 
 static int argmax_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int nq_) {
-    const int L = ctx->L;
     std::vector<int> order, rr, cps;
-    SECPE_CHECK(sort_queries(ctx, q, nq_, order, rr, cps));
+    int L;  // the inputs' level
+    SECPE_CHECK(sort_queries(ctx, q, nq_, order, rr, cps, &L));
     Eval E{ctx, keys, {}, 0};
 
     // 1. aggregation into Yn (sorted order), level L - 1
     Ct Yn;
-    SECPE_CHECK(aggregate_sorted(ctx, E, q, order, Yn));
+    SECPE_CHECK(aggregate_sorted(ctx, E, q, order, L, Yn));
 
     // 2. duplication y + RotR(y, C') per group of equal r
     std::vector<Ct> ydup_parts;

@@ -31,7 +31,8 @@ EXPORTS = [
     "secpe_server_stats", "secpe_ntt_tc", "secpe_ntt_cts_tc", "secpe_expand_seeded", "secpe_keyswitch_batch_tc",
     "secpe_pool_usage", "secpe_mul32_probe", "secpe_packed_capacity", "secpe_encode_packed",
     "secpe_decode_packed", "secpe_encrypt_logits_packed", "secpe_decrypt_packed", "secpe_phoenix_argmax",
-    "secpe_phoenix_argmax_batch",
+    "secpe_phoenix_argmax_batch", "secpe_linear_create", "secpe_linear_create_coeffs", "secpe_linear_destroy",
+    "secpe_linear_apply", "secpe_encrypt_replicated",
 ]
 
 
@@ -157,6 +158,12 @@ def lib():
         "secpe_packed_capacity": (i32, [i32, i32]),
         "secpe_phoenix_argmax": (i32, [vp, vp, P(CtC), i32, u64, P(CtC), vp]),
         "secpe_phoenix_argmax_batch": (i32, [vp, vp, P(QueryC), i32, vp]),
+        "secpe_linear_create": (i32, [vp, P(dbl), i32, i32, i32, dbl, P(vp)]),
+        "secpe_linear_create_coeffs": (i32, [vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64), i32, i32,
+                                             i32, P(vp)]),
+        "secpe_linear_destroy": (None, [vp]),
+        "secpe_linear_apply": (i32, [vp, vp, vp, P(CtC), P(CtC), vp]),
+        "secpe_encrypt_replicated": (i32, [vp, vp, P(dbl), i32, i32, u64, P(CtC), vp]),
         "secpe_encode_packed": (i32, [i32, dbl, P(dbl), i32, i32, dbl, P(ctypes.c_int64)]),
         "secpe_decode_packed": (i32, [i32, dbl, P(dbl), i32, i32, P(dbl)]),
         "secpe_encrypt_logits_packed": (i32, [vp, vp, P(dbl), i32, i32, dbl, u64, P(CtC), vp]),
@@ -678,6 +685,58 @@ def phoenix_argmax_batch(ctx, keys, queries):
            "secpe_phoenix_argmax_batch")
     for q, (_, z) in zip(queries, keep):
         q["z_out"].update(z)
+
+
+def encrypt_replicated(ctx, keys, x, C, seed, out=None):
+    """secpe_encrypt_replicated: x[d] with x[j] in the C' slots [j C', (j+1) C')."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = ctx.new_ct() if out is None else out
+    c = out.struct()
+    _check(lib().secpe_encrypt_replicated(ctx.h, keys.h, _dblp(x), len(x), C, ctypes.c_uint64(seed),
+                                          ctypes.byref(c), _stream()), "secpe_encrypt_replicated")
+    out.update(c)
+    return out
+
+
+class Linear:
+    """secpe_linear: the encoded plaintext weights of the CLIP-style linear
+    step (from T[K][C][d] doubles, or from integer coefficients)."""
+
+    def __init__(self, ctx, T=None, d_min=None, coeffs=None, K=None, C=None, d=None):
+        h = ctypes.c_void_p()
+        if coeffs is None:
+            T = np.ascontiguousarray(T, dtype=np.float64)
+            K, C, d = T.shape
+            _check(lib().secpe_linear_create(ctx.h, _dblp(T), K, C, d, d_min, ctypes.byref(h)), "secpe_linear_create")
+        else:
+            Wm, mask, pad = (np.ascontiguousarray(np.asarray(a, dtype=np.int64)) for a in coeffs)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            _check(lib().secpe_linear_create_coeffs(ctx.h, Wm.ctypes.data_as(i64p), mask.ctypes.data_as(i64p),
+                                                    pad.ctypes.data_as(i64p), K, C, d, ctypes.byref(h)),
+                   "secpe_linear_create_coeffs")
+        self.h, self.ctx, self.K = h, ctx, K
+
+    def apply(self, keys, x, outs=None):
+        """The K logit ciphertexts of x (secpe_linear_apply)."""
+        outs = [self.ctx.new_ct() for _ in range(self.K)] if outs is None else outs
+        arr = (CtC * self.K)(*[o.struct() for o in outs])
+        cx = x.struct()
+        _check(lib().secpe_linear_apply(self.ctx.h, keys.h, self.h, ctypes.byref(cx), arr, _stream()),
+               "secpe_linear_apply")
+        for o, c in zip(outs, arr):
+            o.update(c)
+        return outs
+
+    def close(self):
+        if self.h:
+            lib().secpe_linear_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Graph:

@@ -124,6 +124,72 @@ def packed_queries(n_sets, slots, seed=6, K_choices=ARGMAX_K, C_choices=ARGMAX_C
     return out
 
 
+@dataclass
+class ClipTask:
+    """CLIP-style zero-shot classification inputs (Sec. 2.3): an image
+    embedding x[d] and plaintext text embeddings T[K][C][d] of K prompt
+    templates and C classes, drawn so that the ensembled logits
+    mean_i T_i x have a top-1 gap >= margin."""
+    T: np.ndarray
+    x: np.ndarray
+    d_min: float
+    d_max: float
+    qseed: int
+    enc_seed: int
+
+    @property
+    def K(self):
+        return self.T.shape[0]
+
+    @property
+    def C(self):
+        return self.T.shape[1]
+
+    @property
+    def d(self):
+        return self.T.shape[2]
+
+    def logits(self):
+        return np.einsum("kcd,d->kc", self.T, self.x)
+
+
+def clip_task(d=64, C=10, K=3, seed=7, margin=0.05):
+    """Unit-norm embeddings (as CLIP normalises them) scaled so the logits
+    stay well inside [-4.25, 4.25]; redrawn until the margin holds."""
+    rng = np.random.default_rng(seed)
+    while True:
+        x = rng.standard_normal(d)
+        x /= np.linalg.norm(x)
+        base = rng.standard_normal((C, d))
+        T = base[None] + 0.3 * rng.standard_normal((K, C, d))
+        T /= np.linalg.norm(T, axis=2, keepdims=True)
+        T *= 3.0
+        mean = np.einsum("kcd,d->kc", T, x).mean(0)
+        srt = np.sort(mean)
+        if srt[-1] - srt[-2] >= margin:
+            return ClipTask(T, x, ARGMAX_BOUNDS[0], ARGMAX_BOUNDS[1], qseed=seed * 7919 + 3, enc_seed=seed * 1000 + 1)
+
+
+def clip_images(d=512, C=10, K=80, B=16, seed=8, margin=0.05):
+    """One zero-shot task (text embeddings T[K][C][d] of K templates, as in
+    CLIP's 80) and B image embeddings, each redrawn until its ensembled
+    logits have a top-1 gap >= margin: returns (T, [x_b], qseeds, enc_seeds)."""
+    rng = np.random.default_rng(seed)
+    base = rng.standard_normal((C, d))
+    T = base[None] + 0.3 * rng.standard_normal((K, C, d))
+    T /= np.linalg.norm(T, axis=2, keepdims=True)
+    T *= 3.0
+    xs = []
+    while len(xs) < B:
+        x = rng.standard_normal(d)
+        x /= np.linalg.norm(x)
+        mean = np.einsum("kcd,d->kc", T, x).mean(0)
+        srt = np.sort(mean)
+        if srt[-1] - srt[-2] >= margin:
+            xs.append(x)
+    return T, xs, [(seed << 32) + b for b in range(B)], [(seed << 40) + b for b in range(B)]
+
+
 def residues(shape, primes, seed):
     """Uniform residues [..., len(primes), N] for primitive micro-benchmarks."""
     rng = np.random.default_rng(seed)
