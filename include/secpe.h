@@ -56,13 +56,20 @@ extern "C" {
 #define SECPE_ETIMEOUT -7 /* a bounded device-side wait gave up */
 #define SECPE_EADMIT -8   /* request does not fit the admission budget */
 
+/* Rotation "step" naming the complex conjugation of the slots (Galois
+ * element 2N - 1) in secpe_keygen and secpe_rotate. */
+#define SECPE_STEP_CONJ 0x40000000
+
 /*
  * Parameter set.  Ring R_Q = Z_Q[X]/(X^N + 1), Q = q_0 ... q_L (SecPE
  * Sec. 2.2).  Primes (all = 1 mod 2N, all below 2^60):
  *   special primes: the n_p largest below 2^p_bits;
  *   q_0: the largest below 2^q0_bits not already taken when q0_bits differs
  *        from q_bits, otherwise the first prime of the sequence below;
- *   q_1..: alternately the nearest below and above 2^q_bits, below first.
+ *   q_1..: alternately the nearest below and above 2^q_bits, below first;
+ *   with boot_primes = b > 0, the top b primes q_(L-b+1)..q_L are instead
+ *        the b largest below 2^boot_bits (taken after the special primes,
+ *        before q_0), in decreasing order.
  * Key switching is hybrid with dnum digits of alpha = ceil(n_q/dnum) primes.
  * Sign = f^sign_df(g^sign_dg(x)) (SecPE Eq. comp); `reserve` levels are
  * kept below each depth-4 polynomial block before a refresh is forced.
@@ -79,6 +86,14 @@ typedef struct {
     int32_t sign_dg;    /* repetitions of g (paper: 2) */
     int32_t sign_df;    /* repetitions of f (paper: 2) */
     int32_t reserve;    /* levels kept in reserve (>= 1) */
+    int32_t secret_hw;  /* 0: uniform ternary secret; h > 0: sparse ternary
+                           secret with exactly h nonzero coefficients (the
+                           bound on the ModRaise overflow that
+                           bootstrapping's modular reduction needs) */
+    int32_t boot_primes; /* 0, or the number of top ciphertext primes
+                            (q_(L-boot_primes+1)..q_L) of boot_bits bits that
+                            bootstrapping's levels use */
+    int32_t boot_bits;
 } secpe_params;
 
 typedef struct secpe_ctx secpe_ctx;   /* primes, NTT tables, base-conversion tables */
@@ -121,10 +136,14 @@ const char *secpe_strerror(int code);
 /* ---- keys ------------------------------------------------------------- */
 /* Key generation of the RNS-CKKS scheme (SecPE Sec. 2.2; the user holds the
  * secret key, Sec. 3.1 step 1, the server the evaluation keys, step 3).
- * Secret key s (ternary), relinearisation key (s^2 -> s) and one Galois key
- * per rotation step in rot_steps (r > 0: RotL by r; r < 0: RotR by -r), all
- * drawn from the counter-based SplitMix64 streams of `seed` (same streams
- * as the CPU oracle).  The keys object owns its device memory (about
+ * Secret key s (ternary; with secret_hw = h > 0, sparse: word c = 0, 1, ..
+ * of the secret's stream puts sign (w & 1 ? -1 : +1) at position
+ * (w >> 1) mod N unless that position is taken, until h are placed),
+ * relinearisation key (s^2 -> s) and one Galois key per rotation step in
+ * rot_steps (r > 0: RotL by r; r < 0: RotR by -r; SECPE_STEP_CONJ: the
+ * complex conjugation of the slots, X -> X^(2N-1)), all drawn from the
+ * counter-based SplitMix64 streams of `seed` (same streams as the CPU
+ * oracle).  The keys object owns its device memory (about
  * dnum * 2 * (n_q + n_p) * N words per key); steps are taken modulo N/2.
  * Synchronous; SECPE_EINVAL for null pointers or n_rot < 0, SECPE_ENOMEM or
  * SECPE_ECUDA when the keys cannot be allocated. */

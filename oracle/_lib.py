@@ -59,6 +59,7 @@ def lib():
             "or_sm_stream": (u64, [u64, u64, u64]),
             "or_sample_ternary": (None, [u64, p, u64]),
             "or_sample_cbd21": (None, [u64, p, u64]),
+            "or_sample_sparse": (None, [u64, p, u64, u64]),
             "or_sample_uniform": (None, [u64, u64, u64, p, u64]),
         }
         for name, (res, args) in sigs.items():

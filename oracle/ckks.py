@@ -7,7 +7,9 @@ numpy / Python integers in the order the paper (or the stated reading) gives.
 
 Parity status per function:
   ring ops, NTT, basis conversion, rescale, key switching, encode/decode,
-  Sign/Max/QuickMax/Argmax: pinned (see tests/test_oracle_*.py).
+  Sign/Max/QuickMax/Argmax, the Phoenix baseline, slot packing, the
+  CLIP-style linear step and bootstrapping (boot.py): pinned (see
+  tests/test_oracle_*.py).
   Residue-level intermediate values of the encrypted circuit: the paper prints
   none (its worked example is a missing figure), so residues are defined by
   this oracle; the decoded values and the returned index are pinned by
@@ -40,6 +42,7 @@ U64 = np.uint64
 # stream domains of the counter-based sampler (shared convention)
 DOM_SECRET, DOM_KSK_A, DOM_KSK_E, DOM_ENC_A, DOM_ENC_E, DOM_REFRESH = 1, 2, 3, 4, 5, 6
 DOM_PHOENIX = 7  # refresh seeds of the comparison Signs of the Phoenix baseline
+STEP_CONJ = 0x40000000  # the rotation "step" naming the conjugation X -> X^(2N-1)
 
 
 def round_half_away(v):
@@ -157,6 +160,12 @@ class Oracle:
         self.lib.or_sample_ternary(key, _lib.ptr(out), self.n)
         return out
 
+    def sample_sparse(self, key, h):
+        """Sparse ternary vector with exactly h nonzero coefficients."""
+        out = np.empty(self.n, dtype=np.int64)
+        self.lib.or_sample_sparse(key, _lib.ptr(out), self.n, h)
+        return out
+
     def sample_cbd(self, key):
         out = np.empty(self.n, dtype=np.int64)
         self.lib.or_sample_cbd21(key, _lib.ptr(out), self.n)
@@ -204,6 +213,37 @@ class Oracle:
         vals = acc * (2.0 / self.n) * scale
         return np.array([round_half_away(float(x)) for x in vals], dtype=object)
 
+    def encode_complex(self, z, scale):
+        """Canonical-embedding encoding of a complex slot vector z (slots
+        0..len(z)-1, zeros beyond): the real coefficients
+        m_k = round(scale * (2/N) * Re(sum_j z_j zeta^(-5^j k)))
+            = round(scale * (2/N) * sum_j (Re z_j cos(pi e/N) + Im z_j sin(pi e/N))),
+        e = 5^j k mod 2N (the conjugate slots hold conj(z_j))."""
+        z = np.asarray(z, dtype=np.complex128)
+        n_s = len(z)
+        assert n_s <= self.n // 2
+        two_n = 2 * self.n
+        p5 = self._pow5(n_s)
+        ks = np.arange(self.n, dtype=np.int64)
+        acc = np.zeros(self.n, dtype=np.float64)
+        for j in range(n_s):
+            th = np.pi * ((p5[j] * ks) % two_n).astype(np.float64) / self.n
+            acc += z[j].real * np.cos(th) + z[j].imag * np.sin(th)
+        vals = acc * (2.0 / self.n) * scale
+        return np.array([round_half_away(float(x)) for x in vals], dtype=object)
+
+    def decode_complex(self, m, scale, n_slots):
+        """Slots 0..n_slots-1 of m(zeta^(5^j)) / scale, complex."""
+        mf = np.array([float(x) for x in m], dtype=np.float64)
+        two_n = 2 * self.n
+        p5 = self._pow5(n_slots)
+        ks = np.arange(self.n, dtype=np.int64)
+        out = np.empty(n_slots, dtype=np.complex128)
+        for j in range(n_slots):
+            th = np.pi * ((p5[j] * ks) % two_n).astype(np.float64) / self.n
+            out[j] = complex(np.dot(mf, np.cos(th)), np.dot(mf, np.sin(th)))
+        return out / scale
+
     def decode_coeffs(self, m, scale, n_slots):
         """Slots 0..n_slots-1 of the real part of m(zeta^(5^j)) / scale."""
         mf = np.array([float(x) for x in m], dtype=np.float64)
@@ -221,7 +261,8 @@ class Oracle:
         """Secret key, relinearisation key and Galois keys for RotL(r), r in
         rot_steps (negative r means RotR(-r))."""
         all_idx = list(range(len(self.primes)))
-        s = self.sample_ternary(self.stream(seed, DOM_SECRET, 0))
+        key = self.stream(seed, DOM_SECRET, 0)
+        s = self.sample_sparse(key, self.p.secret_hw) if self.p.secret_hw else self.sample_ternary(key)
         self.s_coeffs = s
         self.s_ntt = self.ntt_of_signed(s, all_idx)
         self.seed = seed
@@ -259,8 +300,11 @@ class Oracle:
         return out
 
     def galois(self, r):
-        """Galois element of RotL(r) (RotR(r') = RotL(N/2 - r'))."""
+        """Galois element of RotL(r) (RotR(r') = RotL(N/2 - r')); 2N - 1 for
+        the conjugation (r = STEP_CONJ)."""
         two_n = 2 * self.n
+        if r == STEP_CONJ:
+            return two_n - 1
         if r < 0:
             r = self.n // 2 + r
         return pow(5, r % (self.n // 2), two_n)

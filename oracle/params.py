@@ -106,6 +106,9 @@ class Params:
     sign_dg: int = 2
     sign_df: int = 2
     reserve: int = 1
+    secret_hw: int = 0   # 0: uniform ternary secret; h > 0: exactly h nonzero coefficients
+    boot_primes: int = 0  # top ciphertext primes of boot_bits bits for bootstrapping's levels
+    boot_bits: int = 0
 
     @property
     def n(self):
@@ -129,16 +132,21 @@ class Params:
 
 
 def select_primes(p):
-    """Ciphertext primes (q_0 first) and special primes for a Params."""
+    """Ciphertext primes (q_0 first) and special primes for a Params.  With
+    boot_primes = b > 0 the top b ciphertext primes are the b largest below
+    2^boot_bits (taken after the special primes, before q_0), in decreasing
+    order, above the q_bits-sized ones."""
     m = 2 * p.n
     special = primes_below(1 << p.p_bits, m, p.n_p)
     taken = set(special)
+    boot = primes_below(1 << p.boot_bits, m, p.boot_primes, taken) if p.boot_primes else []
+    taken.update(boot)
     qs = []
     if p.q0_bits != p.q_bits:
         q0 = primes_below(1 << p.q0_bits, m, 1, taken)[0]
         qs.append(q0)
         taken.add(q0)
-    need = p.n_q - len(qs)
+    need = p.n_q - p.boot_primes - len(qs)
     # alternate below / above 2^q_bits; enough candidates of each kind
     below = primes_below(1 << p.q_bits, m, need, taken)
     above = primes_above(1 << p.q_bits, m, need, taken)
@@ -147,6 +155,7 @@ def select_primes(p):
         seq.append(b)
         seq.append(a)
     qs.extend(seq[:need])
+    qs.extend(boot)
     return qs, special
 
 
@@ -166,7 +175,17 @@ ARGMAX = Params(log_n=16, q0_bits=60, q_bits=50, n_q=24, p_bits=60, n_p=4,
 # 128-bit budget at N = 2^16): half the extended limbs of ARGMAX's ModUp.
 ARGMAX8 = Params(log_n=16, q0_bits=60, q_bits=50, n_q=24, p_bits=60, n_p=8,
                  dnum=3, log_scale=50)
-PRESETS = {"toy": TOY, "micro": MICRO, "argmax": ARGMAX, "argmax8": ARGMAX8}
+# BOOT_TOY / BOOT16: bootstrapping sets.  q0 50-bit, computation primes of
+# 40 bits (Delta = 2^40), the top 16 primes 60-bit for bootstrapping's 16
+# levels (CoeffToSlot 1, EvalMod 14, SlotToCoeff 1), so its working labels
+# (near 2^60) stay at the primes' size; a sparse secret of weight 32 bounds
+# the ModRaise overflow by 16.5; special primes 60-bit with alpha <= n_p.
+BOOT_TOY = Params(log_n=12, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=3, dnum=12,
+                  log_scale=40, secret_hw=32, boot_primes=16, boot_bits=60)
+BOOT16 = Params(log_n=16, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=4, dnum=6,
+                log_scale=40, secret_hw=32, boot_primes=16, boot_bits=60)
+PRESETS = {"toy": TOY, "micro": MICRO, "argmax": ARGMAX, "argmax8": ARGMAX8, "boot_toy": BOOT_TOY,
+           "boot16": BOOT16}
 
 
 class Context:

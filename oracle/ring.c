@@ -238,6 +238,21 @@ void or_sample_ternary(u64 key, int64_t *out, u64 n) {
         out[i] = (int64_t)(u64)(((u128)w * 3) >> 64) - 1;
     }
 }
+/* Sparse ternary vector with exactly h nonzero entries: word c = 0, 1, ..   */
+/* places sign (w & 1 ? -1 : +1) at position (w >> 1) mod n unless that     */
+/* position already holds one.  n is a power of two, h <= n.                */
+void or_sample_sparse(u64 key, int64_t *out, u64 n, u64 h) {
+    u64 placed = 0;
+    for (u64 i = 0; i < n; i++) out[i] = 0;
+    for (u64 c = 0; placed < h; c++) {
+        u64 w = or_sm_word(key, c);
+        u64 pos = (w >> 1) % n;
+        if (out[pos] != 0) continue;
+        out[pos] = (w & 1) ? -1 : 1;
+        placed++;
+    }
+}
+
 /* Centred binomial with eta = 21: popcount of 21 bits minus popcount of the */
 /* next 21 bits of one word.                                                 */
 void or_sample_cbd21(u64 key, int64_t *out, u64 n) {

@@ -164,7 +164,16 @@ extern "C" int secpe_keygen(secpe_ctx *ctx, uint64_t seed, const int32_t *rot_st
         DevBuf s, s2;
         if ((st = s.alloc(ctx, sizeof(long long) * n)) != SECPE_OK) break;
         std::vector<u64> ks(1, hm::sm_stream(seed, DOM_SECRET, 0));
-        if ((st = launch_sample_small(ctx, ks, (long long *)s.p, 0)) != SECPE_OK) break;
+        if (ctx->p.secret_hw > 0) {
+            std::vector<long long> sh;
+            hm::sample_sparse_secret(ks[0], n, ctx->p.secret_hw, sh);
+            if (cudaMemcpy(s.p, sh.data(), sizeof(long long) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+                st = SECPE_ECUDA;
+                break;
+            }
+        } else if ((st = launch_sample_small(ctx, ks, (long long *)s.p, 0)) != SECPE_OK) {
+            break;
+        }
         PrimeList pl;
         pl.n = np;
         for (int t = 0; t < np; t++) pl.p[t] = t;

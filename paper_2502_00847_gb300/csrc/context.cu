@@ -33,7 +33,8 @@ extern "C" int secpe_ctx_create(const secpe_params *p, secpe_ctx **out) {
     if (!p || !out) return SECPE_EINVAL;
     *out = nullptr;
     if (p->dnum < 1 || p->dnum > p->n_q || p->log_scale < 10 || p->log_scale > 58 ||
-        p->reserve < 1 || p->sign_dg < 0 || p->sign_df < 0 || p->sign_dg + p->sign_df < 1)
+        p->reserve < 1 || p->sign_dg < 0 || p->sign_df < 0 || p->sign_dg + p->sign_df < 1 || p->secret_hw < 0 ||
+        (p->log_n >= 4 && p->log_n <= 17 && p->secret_hw > (1 << p->log_n)))
         return SECPE_EINVAL;
     std::vector<u64> qs, sp;
     if (!hm::select_primes(*p, qs, sp)) return SECPE_EINVAL;

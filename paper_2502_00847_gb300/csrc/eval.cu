@@ -37,6 +37,7 @@ Ct ct_drop(const Ct &x, int level) {
 }
 
 unsigned galois_elt(const secpe_ctx *ctx, int steps) {
+    if (steps == SECPE_STEP_CONJ) return 2u * ctx->n - 1u;
     const int half = ctx->n / 2;
     long long r = steps;
     if (r < 0) r = half + r;

@@ -90,6 +90,14 @@ bool select_primes(const secpe_params &p, std::vector<u64> &q, std::vector<u64> 
     below(1ull << p.p_bits, m, p.n_p, taken, special);
     if ((int)special.size() != p.n_p) return false;
     for (u64 x : special) taken.insert(x);
+    if (p.boot_primes < 0 || p.boot_primes > p.n_q - 2 || (p.boot_primes && (p.boot_bits < 20 || p.boot_bits > 60)))
+        return false;
+    std::vector<u64> boot;
+    if (p.boot_primes > 0) {
+        below(1ull << p.boot_bits, m, p.boot_primes, taken, boot);
+        if ((int)boot.size() != p.boot_primes) return false;
+        for (u64 x : boot) taken.insert(x);
+    }
     if (p.q0_bits != p.q_bits) {
         std::vector<u64> q0;
         below(1ull << p.q0_bits, m, 1, taken, q0);
@@ -97,15 +105,17 @@ bool select_primes(const secpe_params &p, std::vector<u64> &q, std::vector<u64> 
         q.push_back(q0[0]);
         taken.insert(q0[0]);
     }
-    int need = p.n_q - (int)q.size();
+    const int n_comp = p.n_q - p.boot_primes;
+    int need = n_comp - (int)q.size();
     std::vector<u64> lo, hi;
     below(1ull << p.q_bits, m, need, taken, lo);
     above(1ull << p.q_bits, m, need, taken, hi);
     if ((int)lo.size() < need) return false;
-    for (int i = 0; (int)q.size() < p.n_q; i++) {
+    for (int i = 0; (int)q.size() < n_comp; i++) {
         q.push_back(lo[i]);
-        if ((int)q.size() < p.n_q) q.push_back(hi[i]);
+        if ((int)q.size() < n_comp) q.push_back(hi[i]);
     }
+    for (u64 x : boot) q.push_back(x);
     for (u64 x : q)
         if (x >= (1ull << 60)) return false;
     return true;
@@ -141,5 +151,17 @@ u64 sm_stream(u64 seed, u64 domain, u64 index) {
 }
 
 long long round_half_away(double v) { return std::llround(v); }
+
+void sample_sparse_secret(u64 key, int n, int h, std::vector<long long> &s) {
+    s.assign(n, 0);
+    int placed = 0;
+    for (u64 c = 0; placed < h; c++) {
+        const u64 w = sm_mix(key + (c + 1) * kGamma);
+        const u64 pos = (w >> 1) & (u64)(n - 1);
+        if (s[pos] != 0) continue;
+        s[pos] = (w & 1) ? -1 : 1;
+        placed++;
+    }
+}
 
 }  // namespace hm

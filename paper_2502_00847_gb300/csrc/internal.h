@@ -164,6 +164,9 @@ u64 find_psi(u64 q, u64 n);
 uint32_t bitrev(uint32_t x, int bits);
 // Counter-based SplitMix64 stream (Steele, Lea, Flood 2014).
 u64 sm_mix(u64 z);
+// sparse ternary secret: h signs placed by the words of stream `key`
+// (word w: position (w >> 1) mod n unless taken, sign w & 1 ? -1 : +1)
+void sample_sparse_secret(u64 key, int n, int h, std::vector<long long> &s);
 u64 sm_stream(u64 seed, u64 domain, u64 index);
 long long round_half_away(double v);
 }  // namespace hm

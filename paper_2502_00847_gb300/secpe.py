@@ -39,7 +39,7 @@ EXPORTS = [
 class ParamsC(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int32) for name in (
         "log_n", "q0_bits", "q_bits", "n_q", "p_bits", "n_p", "dnum", "log_scale", "sign_dg", "sign_df",
-        "reserve")]
+        "reserve", "secret_hw", "boot_primes", "boot_bits")]
 
 
 class CtC(ctypes.Structure):
@@ -193,6 +193,9 @@ class SecpeError(RuntimeError):
         self.code = code
 
 
+STEP_CONJ = 0x40000000  # SECPE_STEP_CONJ: the conjugation "rotation"
+
+
 def _check(code, where):
     if code != 0:
         raise SecpeError(code, where)
@@ -211,9 +214,10 @@ class Context:
     """secpe_ctx: primes, NTT and base-conversion tables on the device."""
 
     def __init__(self, log_n, q0_bits, q_bits, n_q, p_bits, n_p, dnum, log_scale, sign_dg=2, sign_df=2,
-                 reserve=1):
+                 reserve=1, secret_hw=0, boot_primes=0, boot_bits=0):
         self.params = dict(log_n=log_n, q0_bits=q0_bits, q_bits=q_bits, n_q=n_q, p_bits=p_bits, n_p=n_p,
-                           dnum=dnum, log_scale=log_scale, sign_dg=sign_dg, sign_df=sign_df, reserve=reserve)
+                           dnum=dnum, log_scale=log_scale, sign_dg=sign_dg, sign_df=sign_df, reserve=reserve,
+                           secret_hw=secret_hw, boot_primes=boot_primes, boot_bits=boot_bits)
         p = ParamsC(**self.params)
         h = ctypes.c_void_p()
         _check(lib().secpe_ctx_create(ctypes.byref(p), ctypes.byref(h)), "secpe_ctx_create")
