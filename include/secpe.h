@@ -337,6 +337,48 @@ int secpe_rotate_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ctbat
                        secpe_ctbatch *out, void *stream);
 int secpe_rescale_batch(secpe_ctx *ctx, const secpe_ctbatch *in, secpe_ctbatch *out, void *stream);
 
+/* ---- bootstrapping --------------------------------------------------------- */
+/* SecPE Sec. 2.2 and Sec. 4.1 rely on bootstrapping to restore a
+ * ciphertext's levels (depth 14 at N = 2^16) without describing it; this is
+ * the sparse-slot CKKS bootstrapping of Cheon, Han, Kim, Kim and Song (2018)
+ * with the sub-sum of Chen, Chillotti and Song (2019), for a block of n
+ * slots (n a power of two, 2n <= N/2):
+ *   ModRaise of limb 0 to the top level; SubSum (rotations by n .. N/4);
+ *   CoeffToSlot (baby-step giant-step plaintext diagonals of the slots and
+ *   their conjugate: u = coefficient / q0 in slots [0, 2n) of every block);
+ *   EvalMod (sin(2 pi u) from the degree-12 Taylor polynomial of
+ *   cos(2 pi (u - 1/4) / 256) and 8 double angles); SlotToCoeff.
+ * It needs a context with secret_hw in 1..32 (the ModRaise overflow bound)
+ * and boot_primes >= 16 (its levels: 1 + 14 + 1, at the top), and the
+ * Galois keys of secpe_boot_rotation_steps (conjugation included).  The
+ * result is at level L - 16 with the input's label and decrypts to the
+ * n-periodic block sum of the input's slots: data in slots [0, n) and zeros
+ * beyond come back replicated in every block of n.  Non-interactive: no
+ * secret key is used.
+ *
+ * secpe_boot_rotation_steps: the rotation steps the keys need (host only);
+ * with steps null only *count is written. */
+typedef struct secpe_boot secpe_boot;
+int secpe_boot_rotation_steps(const secpe_ctx *ctx, int n, int32_t *steps, int capacity, int *count);
+/* Builds the plaintext diagonals with the library's encoder (2n for
+ * CoeffToSlot at scale q_L, 2n for SlotToCoeff) and uploads them (device
+ * memory owned by the plan: 2n (L + 1) + 2n (L - 14) limbs of N words). */
+int secpe_boot_create(secpe_ctx *ctx, int n, secpe_boot **out);
+/* The same from integer coefficients chosen by the caller: c2s_m[2][n][N]
+ * (the diagonals of the slots then of their conjugate, diagonal g bs + b
+ * rotated right by g bs, at scale q_L) and s2c_m[2n][N] (at scale
+ * q_(L-15) / label of the EvalMod output). */
+int secpe_boot_create_coeffs(secpe_ctx *ctx, int n, const int64_t *c2s_m, const int64_t *s2c_m,
+                             secpe_boot **out);
+void secpe_boot_destroy(secpe_boot *bt);
+/* Bootstraps `batch` ciphertexts (any level; limb 0 is used) as one batch:
+ * every evaluator launch serves the whole batch.  out->level/scale/batch
+ * are set.  SECPE_EKEY for a missing rotation key. */
+int secpe_bootstrap_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_boot *bt, const secpe_ctbatch *in,
+                          secpe_ctbatch *out, void *stream);
+int secpe_bootstrap(secpe_ctx *ctx, const secpe_keys *keys, const secpe_boot *bt, const secpe_ct *in,
+                    secpe_ct *out, void *stream);
+
 /* ---- SecPE circuit ----------------------------------------------------- */
 /* Sign(x) = f^df(g^dg(x)) (SecPE Eq. comp), each degree-9 polynomial by a
  * depth-4 baby-step giant-step DAG; refreshes (counter from *refresh_index,

@@ -67,6 +67,8 @@ void decode_real(int n, const double *coeffs, double scale, int nslots, double *
 // floating-point rounding.
 using cplx = std::complex<double>;
 
+bool encode_complex_fft(int n, const double *re, const double *im, int nv, double scale, std::vector<long long> &m);
+
 // In-place iterative radix-2 DFT of length n = 2^k: a_k <- sum_t a_t
 // e^(sign 2 pi i t k / n) (unscaled).
 static void fft(std::vector<cplx> &a, int sign) {
@@ -92,13 +94,20 @@ static void fft(std::vector<cplx> &a, int sign) {
 }
 
 bool encode_real_fft(int n, const double *v, int nv, double scale, std::vector<long long> &m) {
+    return encode_complex_fft(n, v, nullptr, nv, scale, m);
+}
+
+// Complex slots z_j = re_j + i im_j (im may be null): u_t = z_j at
+// 2t+1 = 5^j and conj(z_j) at 2t+1 = -5^j, which keeps m real.
+bool encode_complex_fft(int n, const double *re, const double *im, int nv, double scale, std::vector<long long> &m) {
     if (nv < 0 || nv > n / 2 || (n & (n - 1))) return false;
     const uint64_t two_n = 2ull * n;
     std::vector<cplx> u(n, cplx(0.0, 0.0));
     uint64_t e = 1;
     for (int j = 0; j < nv; j++) {
-        u[(e - 1) / 2] = v[j];
-        u[(two_n - e - 1) / 2] = v[j];
+        const double b = im ? im[j] : 0.0;
+        u[(e - 1) / 2] = cplx(re[j], b);
+        u[(two_n - e - 1) / 2] = cplx(re[j], -b);
         e = e * 5 % two_n;
     }
     fft(u, -1);

@@ -80,6 +80,16 @@ struct Eval {
     int phoenix(const Ct &y, int C, Ct &out);
 };
 
+// Per-slot plaintext products (linear.cu): o (+)= x (.) p with p in
+// Montgomery NTT form (item stride ps, 0 = one plaintext for all items; x
+// item stride xs, 0 = one input for all items); o = x + (p, 0).
+int launch_mul_plain(secpe_ctx *ctx, const CtB &x, long long xs, const u64 *p, long long ps, const CtB &o, int nl,
+                     bool acc = false);
+int launch_add_plain(secpe_ctx *ctx, const CtB &x, const u64 *p, const CtB &o, int nl);
+// B plaintexts from host int64 coefficients m[B][N]: NTT-form residues of
+// limbs 0..nl-1 (Montgomery form if mont) at dst [B][nl][N]; synchronous.
+int upload_plain(secpe_ctx *ctx, const int64_t *m, int B, int nl, bool mont, u64 *dst);
+
 // Hybrid key switching (keyswitch.cu): d = limbs 0..lv of one polynomial per
 // item (NTT form) at d + item*d_item_stride; writes (or adds, per poly) the
 // result into polys 0 and 1 of `out` (B items, level lv).

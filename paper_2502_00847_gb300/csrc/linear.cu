@@ -39,7 +39,7 @@ namespace {
 // every item), plaintext limb i of item b at p + b*ps + i*N in Montgomery
 // form (ps may be 0: one plaintext for every item).
 __global__ void k_mul_plain(DevCtx c, const u64 *x, long long xs, int cap_x, const u64 *p, long long ps, u64 *o,
-                            long long os, int cap_o, int nl) {
+                            long long os, int cap_o, int nl, int acc) {
     const int li = blockIdx.y;
     const int i = li % nl, kk = (li / nl) & 1, item = li / (2 * nl);
     const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -50,7 +50,13 @@ __global__ void k_mul_plain(DevCtx c, const u64 *x, long long xs, int cap_x, con
     ulonglong2 r;
     r.x = mont_mul(v.x, w.x, q, qi);
     r.y = mont_mul(v.y, w.y, q, qi);
-    *reinterpret_cast<ulonglong2 *>(o + item * os + ((long long)kk * cap_o + i) * c.n + e) = r;
+    ulonglong2 *op = reinterpret_cast<ulonglong2 *>(o + item * os + ((long long)kk * cap_o + i) * c.n + e);
+    if (acc) {
+        const ulonglong2 prev = *op;
+        r.x = add_mod(r.x, prev.x, q);
+        r.y = add_mod(r.y, prev.y, q);
+    }
+    *op = r;
 }
 
 // o = x + (p, 0): plaintext limbs (NTT form) added to c0 of every item.
@@ -84,6 +90,8 @@ dim3 grid_of(int n, int per_thread, long long rows) {
     return dim3((unsigned)((n / per_thread + 255) / 256), (unsigned)rows);
 }
 
+}  // namespace
+
 // B plaintexts from int64 coefficients m[B][N] (host): residues of limbs
 // 0..nl-1 in NTT form, optionally in Montgomery form, at dst [B][nl][N].
 int upload_plain(secpe_ctx *ctx, const int64_t *m, int B, int nl, bool mont, u64 *dst) {
@@ -105,6 +113,8 @@ int upload_plain(secpe_ctx *ctx, const int64_t *m, int B, int nl, bool mont, u64
     return SECPE_OK;
 }
 
+namespace {
+
 int pow2_ceil(int C) {
     int cp = 1;
     while (cp < C) cp <<= 1;
@@ -115,10 +125,11 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 }  // namespace
 
-int launch_mul_plain(secpe_ctx *ctx, const CtB &x, long long xs, const u64 *p, long long ps, const CtB &o, int nl) {
-    KprofScope kp(ctx, "ew_mul_plain", 8.0 * ctx->n * o.B * (4.0 * nl + (ps ? (double)nl : 0.0)));
+int launch_mul_plain(secpe_ctx *ctx, const CtB &x, long long xs, const u64 *p, long long ps, const CtB &o, int nl,
+                     bool acc) {
+    KprofScope kp(ctx, "ew_mul_plain", 8.0 * ctx->n * o.B * ((acc ? 6.0 : 4.0) * nl + (ps ? (double)nl : 0.0)));
     SECPE_LAUNCH(ctx, k_mul_plain, grid_of(ctx->n, 2, (long long)o.B * 2 * nl), 256, 0, ctx->dev, x.data, xs, x.cap,
-                 p, ps, o.data, o.stride, o.cap, nl);
+                 p, ps, o.data, o.stride, o.cap, nl, acc ? 1 : 0);
     return SECPE_OK;
 }
 

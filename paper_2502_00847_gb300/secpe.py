@@ -32,7 +32,8 @@ EXPORTS = [
     "secpe_pool_usage", "secpe_mul32_probe", "secpe_packed_capacity", "secpe_encode_packed",
     "secpe_decode_packed", "secpe_encrypt_logits_packed", "secpe_decrypt_packed", "secpe_phoenix_argmax",
     "secpe_phoenix_argmax_batch", "secpe_linear_create", "secpe_linear_create_coeffs", "secpe_linear_destroy",
-    "secpe_linear_apply", "secpe_encrypt_replicated",
+    "secpe_linear_apply", "secpe_encrypt_replicated", "secpe_boot_rotation_steps", "secpe_boot_create",
+    "secpe_boot_create_coeffs", "secpe_boot_destroy", "secpe_bootstrap_batch", "secpe_bootstrap",
 ]
 
 
@@ -164,6 +165,12 @@ def lib():
         "secpe_linear_destroy": (None, [vp]),
         "secpe_linear_apply": (i32, [vp, vp, vp, P(CtC), P(CtC), vp]),
         "secpe_encrypt_replicated": (i32, [vp, vp, P(dbl), i32, i32, u64, P(CtC), vp]),
+        "secpe_boot_rotation_steps": (i32, [vp, i32, P(i32), i32, P(i32)]),
+        "secpe_boot_create": (i32, [vp, i32, P(vp)]),
+        "secpe_boot_create_coeffs": (i32, [vp, i32, P(ctypes.c_int64), P(ctypes.c_int64), P(vp)]),
+        "secpe_boot_destroy": (None, [vp]),
+        "secpe_bootstrap_batch": (i32, [vp, vp, vp, P(CtBatchC), P(CtBatchC), vp]),
+        "secpe_bootstrap": (i32, [vp, vp, vp, P(CtC), P(CtC), vp]),
         "secpe_encode_packed": (i32, [i32, dbl, P(dbl), i32, i32, dbl, P(ctypes.c_int64)]),
         "secpe_decode_packed": (i32, [i32, dbl, P(dbl), i32, i32, P(dbl)]),
         "secpe_encrypt_logits_packed": (i32, [vp, vp, P(dbl), i32, i32, dbl, u64, P(CtC), vp]),
@@ -734,6 +741,58 @@ class Linear:
     def close(self):
         if self.h:
             lib().secpe_linear_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def boot_rotation_steps(ctx, n):
+    """secpe_boot_rotation_steps: the Galois key steps bootstrapping needs."""
+    cnt = ctypes.c_int32(0)
+    _check(lib().secpe_boot_rotation_steps(ctx.h, n, None, 0, ctypes.byref(cnt)), "secpe_boot_rotation_steps")
+    arr = (ctypes.c_int32 * cnt.value)()
+    _check(lib().secpe_boot_rotation_steps(ctx.h, n, arr, cnt.value, ctypes.byref(cnt)), "secpe_boot_rotation_steps")
+    return list(arr)
+
+
+class Boot:
+    """secpe_boot: a bootstrapping plan for blocks of n slots (plaintext
+    diagonals from the library's encoder, or from integer coefficients)."""
+
+    def __init__(self, ctx, n, coeffs=None):
+        h = ctypes.c_void_p()
+        if coeffs is None:
+            _check(lib().secpe_boot_create(ctx.h, n, ctypes.byref(h)), "secpe_boot_create")
+        else:
+            c2s, s2c = (np.ascontiguousarray(np.asarray(a, dtype=np.int64)) for a in coeffs)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            _check(lib().secpe_boot_create_coeffs(ctx.h, n, c2s.ctypes.data_as(i64p), s2c.ctypes.data_as(i64p),
+                                                  ctypes.byref(h)), "secpe_boot_create_coeffs")
+        self.h, self.ctx, self.n = h, ctx, n
+
+    def bootstrap(self, keys, ct, out=None):
+        out = self.ctx.new_ct() if out is None else out
+        ci, co = ct.struct(), out.struct()
+        _check(lib().secpe_bootstrap(self.ctx.h, keys.h, self.h, ctypes.byref(ci), ctypes.byref(co), _stream()),
+               "secpe_bootstrap")
+        out.update(co)
+        return out
+
+    def bootstrap_batch(self, keys, a, out):
+        """a, out: CtBatch (out's level/scale are set)."""
+        ca, co = a.struct(), out.struct()
+        _check(lib().secpe_bootstrap_batch(self.ctx.h, keys.h, self.h, ctypes.byref(ca), ctypes.byref(co),
+                                           _stream()), "secpe_bootstrap_batch")
+        out.update(co)
+        return out
+
+    def close(self):
+        if self.h:
+            lib().secpe_boot_destroy(self.h)
             self.h = None
 
     def __del__(self):
