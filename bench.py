@@ -758,7 +758,7 @@ def run_clip(secpe, torch, workloads, ctx, key_seed, d=512, C=10, K=80, B=16):
 def run_boot(secpe, torch, dev, refresh, n=128, batches=(1, 16)):
     """Sparse-slot CKKS bootstrapping (secpe_bootstrap_batch) at N = 2^16 on
     the boot16 set (q0 50-bit, 7 x 40-bit computation primes, 16 x 60-bit
-    bootstrapping primes, 4 special, dnum 6, sparse secret h = 32), blocks of
+    bootstrapping primes, 6 special, dnum 6, sparse secret h = 32), blocks of
     n = 128 slots (2C' for C' <= 64): one warm-up, then 3 timed batches at
     each batch size; checked against the input slots."""
     from paper_2502_00847_gb300.presets import BOOT16
@@ -770,7 +770,7 @@ def run_boot(secpe, torch, dev, refresh, n=128, batches=(1, 16)):
     t_plan = time.perf_counter() - t0
     rng = np.random.default_rng(16)
     out = {"params": "boot16: N=2^16, q0 50-bit, 7x40-bit computation + 16x60-bit bootstrapping primes, "
-                     "4 special 60-bit, dnum=6, sparse secret h=32", "block_slots": n,
+                     "6 special 60-bit, dnum=6, sparse secret h=32", "block_slots": n,
            "levels_consumed": 16, "output_level": ctx.L - 16, "plan_s": t_plan}
     for B in batches:
         vs = rng.uniform(-1, 1, (B, n))
@@ -987,7 +987,9 @@ def run_micro(args, rank):
             torch.cuda.nvtx.range_pop()
             kp = ctx.kprof_end()
             res["probe_%s_B%d" % (args.micro_probe, B)] = {"kprof": args.kprof, "launches": kp["launches"],
-                                                           "alg_bytes": kp["bytes"], "ms": kp["total_ms"]}
+                                                           "alg_bytes": kp["bytes"],
+                                                           "model_bytes": kp["model_bytes"],
+                                                           "mul32": kp["mul32"], "ms": kp["total_ms"]}
         if "rotate" in ops:
             per = []
             for j in range(16):

@@ -179,10 +179,12 @@ ARGMAX8 = Params(log_n=16, q0_bits=60, q_bits=50, n_q=24, p_bits=60, n_p=8,
 # 40 bits (Delta = 2^40), the top 16 primes 60-bit for bootstrapping's 16
 # levels (CoeffToSlot 1, EvalMod 14, SlotToCoeff 1), so its working labels
 # (near 2^60) stay at the primes' size; a sparse secret of weight 32 bounds
-# the ModRaise overflow by 16.5; special primes 60-bit with alpha <= n_p.
-BOOT_TOY = Params(log_n=12, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=3, dnum=12,
+# the ModRaise overflow by 16.5; 60-bit special primes, n_p > alpha, so that P
+# exceeds every digit by a whole prime or more and key switching adds only
+# rounding noise to the 2^60-sized labels (log2 QP = 1630 at N = 2^16).
+BOOT_TOY = Params(log_n=12, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=4, dnum=8,
                   log_scale=40, secret_hw=32, boot_primes=16, boot_bits=60)
-BOOT16 = Params(log_n=16, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=4, dnum=6,
+BOOT16 = Params(log_n=16, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=6, dnum=6,
                 log_scale=40, secret_hw=32, boot_primes=16, boot_bits=60)
 PRESETS = {"toy": TOY, "micro": MICRO, "argmax": ARGMAX, "argmax8": ARGMAX8, "boot_toy": BOOT_TOY,
            "boot16": BOOT16}

@@ -42,9 +42,9 @@ ARGMAX8 = ParamSet(log_n=16, q0_bits=60, q_bits=50, n_q=24, p_bits=60, n_p=8, dn
 # Bootstrapping sets: q0 50-bit, 40-bit computation primes (Delta = 2^40),
 # the top 16 primes 60-bit for the bootstrapping levels, sparse secret of
 # weight 32 (boot_toy N = 2^12, boot16 N = 2^16).
-BOOT_TOY = ParamSet(log_n=12, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=3, dnum=12, log_scale=40,
+BOOT_TOY = ParamSet(log_n=12, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=4, dnum=8, log_scale=40,
                     secret_hw=32, boot_primes=16, boot_bits=60)
-BOOT16 = ParamSet(log_n=16, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=4, dnum=6, log_scale=40,
+BOOT16 = ParamSet(log_n=16, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=6, dnum=6, log_scale=40,
                   secret_hw=32, boot_primes=16, boot_bits=60)
 PRESETS = {"toy": TOY, "micro": MICRO, "argmax": ARGMAX, "argmax8": ARGMAX8, "boot_toy": BOOT_TOY,
            "boot16": BOOT16}

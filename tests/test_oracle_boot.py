@@ -46,7 +46,7 @@ def test_sparse_secret_and_primes(boot):
     assert np.count_nonzero(s) == BOOT_TOY.secret_hw and set(np.unique(s)) <= {-1, 0, 1}
     bits = [p.bit_length() for p in o.primes]
     assert bits[0] == 50 and all(b in (40, 41) for b in bits[1:8])
-    assert all(b == 60 for b in bits[8:24]) and all(b == 60 for b in bits[24:])
+    assert all(b == 60 for b in bits[8:24]) and len(bits) == 28 and all(b == 60 for b in bits[24:])
 
 
 def test_complex_encoding_and_conjugation(boot):
