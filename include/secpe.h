@@ -352,9 +352,10 @@ int secpe_rescale_batch(secpe_ctx *ctx, const secpe_ctbatch *in, secpe_ctbatch *
  * and boot_primes >= 16 (its levels: 1 + 14 + 1, at the top), and the
  * Galois keys of secpe_boot_rotation_steps (conjugation included).  The
  * result is at level L - 16 with the input's label and decrypts to the
- * n-periodic block sum of the input's slots: data in slots [0, n) and zeros
- * beyond come back replicated in every block of n.  Non-interactive: no
- * secret key is used.
+ * n-periodic block average of the input's slots: an n-periodic input (a
+ * block of n slots repeated over the N/2 slots, e.g. a query packed into
+ * every block by secpe_encrypt_logits_packed) comes back unchanged.
+ * Non-interactive: no secret key is used.
  *
  * secpe_boot_rotation_steps: the rotation steps the keys need (host only);
  * with steps null only *count is written. */
@@ -452,6 +453,17 @@ typedef struct {
  * Results equal the one-query calls with the query's keys bit for bit. */
 int secpe_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q,
                        int n_queries, void *stream);
+/* SecPE Alg. 1 without the interactive stand-in: secpe_argmax_batch where
+ * every refresh is a bootstrap of the refreshed batch with plan `bt` (its
+ * block n must be a multiple of 2C' of every query).  Each query's inputs
+ * must be 2C'-periodic (its logits packed into every block of 2C' slots,
+ * secpe_encrypt_logits_packed with N/(4C') copies), so every intermediate
+ * is periodic and each bootstrap returns it unchanged.  For a context with
+ * bootstrapping primes the inputs sit at the top computation level L - 16 or
+ * below (the bootstrap returns there); errors as secpe_argmax_batch and
+ * secpe_bootstrap_batch. */
+int secpe_argmax_batch_boot(secpe_ctx *ctx, const secpe_keys *keys, const secpe_boot *bt, const secpe_query *q,
+                            int n_queries, void *stream);
 
 /* The baseline SecPE compares its Argmax with (Sec. 3.2, Phoenix): after the
  * same duplication y + RotR(y, C'), every slot is compared with its
@@ -538,6 +550,7 @@ int secpe_server_stats(const secpe_server *srv, secpe_server_stats_t *out);
  * calls, relinearisations, refreshes, key switches, kernel launches). */
 typedef struct {
     int64_t rotations, signs, relins, refreshes, keyswitches, launches;
+    int64_t bootstraps;  /* refreshes done by bootstrapping (secpe_argmax_batch_boot) */
 } secpe_counters;
 int secpe_get_counters(const secpe_ctx *ctx, secpe_counters *out);
 int secpe_reset_counters(secpe_ctx *ctx);

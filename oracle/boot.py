@@ -26,12 +26,15 @@ weight h and a block of n slots (2n <= N/2):
 4. EvalMod: u = m'/q0 + I', and sin(2 pi u) / (2 pi) = m'/q0 up to O(u^3):
    cos(2 pi (u - 1/4) / 2^r) by its Taylor polynomial (degree 12), then r
    double angles cos 2x = 2 cos^2 x - 1.
-5. SlotToCoeff: the inverse transform, z = (q0 / 2 pi) (N/2n) V (f_lo + i
-   f_hi) / label, back to the slot layout of the input.
+5. SlotToCoeff: the inverse transform, z = (q0 / 2 pi) V (f_lo + i f_hi) /
+   label, back to the slot layout of the input.
 
-The result decrypts to the n-periodic block sum of the input's slots:
-for data in slots [0, n) and zeros beyond, the data replicated in every
-block of n.  Every linear transform is a baby-step giant-step sum of
+The result decrypts to the n-periodic block average of the input's slots
+(READING: the convention under which bootstrapping is the identity on the
+inputs it is meant for): an n-periodic input (a block of n slots repeated,
+which the client produces by packing its query into every block) comes
+back unchanged; data in slots [0, n) with zeros beyond come back divided by
+N/(2n) and replicated.  Every linear transform is a baby-step giant-step sum of
 plaintext diagonals; every plaintext is encoded by the direct
 canonical-embedding sums of ckks.Oracle.encode_complex.
 """
@@ -85,7 +88,7 @@ class BootPlan:
         self.c2s_A = [A[j % (2 * n), (j + k) % n] for k in range(n)]
         self.c2s_B = [B[j % (2 * n), (j + k) % n] for k in range(n)]
         # SlotToCoeff: input period 2n (real), output period n: 2n diagonals
-        H = (self.q0 / (2 * math.pi)) * (S / n) * V              # n x n, before the output label
+        H = (self.q0 / (2 * math.pi)) * V                         # n x n, before the output label
         M = np.zeros((n, 2 * n), dtype=np.complex128)
         M[:, :n], M[:, n:] = H, 1j * H
         self.s2c_bs, self.s2c_gs = bsgs_split(2 * n)
@@ -201,16 +204,16 @@ class BootPlan:
         return cs
 
     def slot_to_coeff(self, f, out_scale):
-        """The block sum of the original slots, label out_scale: slots
-        (S/n) (q0 / 2 pi) V (f_lo + i f_hi) / out_scale, as plaintexts at
-        scale q_level out_scale / label(f) carrying (S/n)(q0/2pi) V."""
+        """The block average of the original slots, label out_scale: slots
+        (q0 / 2 pi) V (f_lo + i f_hi) / out_scale, as plaintexts at scale
+        q_level out_scale / label(f) carrying (q0 / 2 pi) V."""
         pt_scale = float(self.o.primes[f.level]) / f.scale
         return self._bsgs([(f, self.s2c_M)], None, self.s2c_bs, self.s2c_gs, "s2c", pt_scale,
                           out_scale=out_scale)
 
     def bootstrap(self, ct):
         """Level-0 (or any-level, dropped to 0) ciphertext -> the n-periodic
-        block sum of its slots at level L - 16, with ct's label."""
+        block average of its slots at level L - 16, with ct's label."""
         o = self.o
         lab = ct.scale
         x = self.mod_raise(o.drop(ct, 0))

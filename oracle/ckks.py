@@ -79,11 +79,12 @@ class Oracle:
         self.counters = {}
         self.ridx = 0
         self.qseed = 0
+        self.boot_plan = None   # a boot.BootPlan: refreshes become bootstraps (non-interactive)
         self.reset_counters()
 
     def reset_counters(self):
         self.counters = dict(rotations=0, signs=0, relins=0, refreshes=0,
-                             keyswitches=0)
+                             keyswitches=0, bootstraps=0)
 
     # ------------------------------------------------------------ ring layer
     def ntt(self, a, pi):
@@ -635,6 +636,12 @@ class Oracle:
         Sec. 2.2/4.1, which rely on bootstrapping without describing it):
         decrypt, lift exactly by CRT to centred integers, re-encrypt at the top
         level with the same scale, randomness from stream (qseed, refresh#)."""
+        if self.boot_plan is not None:
+            # non-interactive: a bootstrap (boot.py) instead of the stand-in
+            self.ridx += 1
+            self.counters["refreshes"] += 1
+            self.counters["bootstraps"] += 1
+            return self.boot_plan.bootstrap(ct)
         m = self.decrypt_coeffs(ct)
         idx = self.ridx
         self.ridx += 1

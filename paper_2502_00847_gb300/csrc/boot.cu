@@ -16,8 +16,9 @@
 //     omega = exp(i pi / 2n)).
 //  4. EvalMod: sin(2 pi u) as cos(2 pi (u - 1/4) / 2^8) by its degree-12
 //     Taylor polynomial in y = x^2 (P0(y) + y^3 P1(y)) and 8 double angles.
-//  5. SlotToCoeff: slots (N/2n)(q0 / 2 pi) V (f_lo + i f_hi) / label, the
-//     block sum of the input's slots, with the input's label.
+//  5. SlotToCoeff: slots (q0 / 2 pi) V (f_lo + i f_hi) / label, the block
+//     average of the input's slots, with the input's label: an n-periodic
+//     input comes back unchanged.
 //
 // Levels: the top 16 primes (CoeffToSlot 1, EvalMod 14, SlotToCoeff 1);
 // the output is at level L - 16.  Every operation is the batched evaluator's
@@ -126,8 +127,8 @@ void boot_diagonals(const secpe_ctx *ctx, int n, std::vector<std::vector<cplx>> 
                 c2s[(size_t)t * n + k][j] = Mx[(size_t)(src % (2 * n)) * n + (src + k) % n];
             }
         }
-    // SlotToCoeff: M (n x 2n) = [H, i H], H = (q0 / 2 pi)(S/n) V
-    const double h = (double)ctx->primes[0] / (2.0 * pi) * ((double)S / (double)n);
+    // SlotToCoeff: M (n x 2n) = [H, i H], H = (q0 / 2 pi) V
+    const double h = (double)ctx->primes[0] / (2.0 * pi);
     bsgs_split(2 * n, bs, gs);
     s2c.assign(2 * (size_t)n, std::vector<cplx>(S));
     for (int k = 0; k < 2 * n; k++) {
@@ -224,6 +225,8 @@ int check_boot(const secpe_ctx *ctx) {
 }
 
 }  // namespace
+
+int boot_block(const secpe_boot *bt) { return bt->n; }
 
 // Bootstrapping of a batch (labels kept, output at level L - 16).
 int boot_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_boot *bt, const Ct &in, Ct &out) {

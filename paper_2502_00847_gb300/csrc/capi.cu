@@ -606,6 +606,22 @@ extern "C" int secpe_phoenix_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys
     return finish(ctx, phoenix_batch_impl(ctx, keys, q, n_queries));
 }
 
+extern "C" int secpe_argmax_batch_boot(secpe_ctx *ctx, const secpe_keys *keys, const secpe_boot *bt,
+                                       const secpe_query *q, int n_queries, void *stream) {
+    if (!ctx || !bt || !q || n_queries < 0) return SECPE_EINVAL;
+    for (int i = 0; i < n_queries; i++) {
+        int cp = 1;
+        while (cp < q[i].C) cp <<= 1;
+        if (2 * cp > boot_block(bt)) return SECPE_EINVAL;
+    }
+    if (n_queries == 0) return SECPE_OK;
+    CallScope cs(ctx, stream);
+    ctx->boot = bt;
+    const int st = argmax_batch_impl(ctx, keys, q, n_queries);
+    ctx->boot = nullptr;
+    return finish(ctx, st);
+}
+
 // ---------------------------------------------------------------- autotuning
 static const char *const kTuneNames[TUNE_NSLOTS] = {"ntt16_colpass", "ntt16_rowpass", "intt16_colpass",
                                                      "intt16_rowpass", "colpass_bconv"};

@@ -224,6 +224,16 @@ int Eval::rotate(const Ct &x, int steps, Ct &out) {
 }
 
 int Eval::refresh(const Ct &x, Ct &out) {
+    if (ctx->boot) {
+        // non-interactive: a bootstrap of the batch replaces the stand-in
+        Ct o;
+        SECPE_CHECK(boot_batch(ctx, keys, ctx->boot, x, o));
+        ctx->counters.refreshes += x.B();
+        ctx->counters.bootstraps += x.B();
+        ridx++;
+        out = o;
+        return SECPE_OK;
+    }
     if (!keys || !keys->s_ntt) return SECPE_EKEY;
     const int B = x.B(), lv = x.level(), n = ctx->n, L = ctx->L;
     if ((int)qseeds.size() != B || B > SECPE_MAX_BATCH_CONST) return SECPE_EINVAL;

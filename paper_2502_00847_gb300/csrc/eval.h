@@ -93,6 +93,10 @@ int upload_plain(secpe_ctx *ctx, const int64_t *m, int B, int nl, bool mont, u64
 // Hybrid key switching (keyswitch.cu): d = limbs 0..lv of one polynomial per
 // item (NTT form) at d + item*d_item_stride; writes (or adds, per poly) the
 // result into polys 0 and 1 of `out` (B items, level lv).
+// Bootstrapping of a batch (boot.cu): labels kept, output at level L - 16.
+int boot_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_boot *bt, const Ct &in, Ct &out);
+int boot_block(const secpe_boot *bt);
+
 int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int lv, const u64 *key,
               const CtB &out, bool acc0, bool acc1);
 // ModUp + key inner product only: acc [B][2][lv+1+k][N] (allocated here).

@@ -126,6 +126,9 @@ struct secpe_ctx {
     std::vector<void *> allocations;
     int *d_status;
     secpe_counters counters;
+    // bootstrapping plan that replaces the refresh stand-in for the duration
+    // of a call (secpe_argmax_batch_boot); null otherwise
+    const secpe_boot *boot = nullptr;
     cudaStream_t stream;  // stream of the call in progress
     KProf kprof;
     Tuning tune;

@@ -216,21 +216,11 @@ __global__ void __launch_bounds__(256, 3) k_rowpass_ip(const __grid_constant__ I
     const long long tile_off = (long long)r0 * 256;
     u64 *__restrict__ o0 = a.acc + (long long)item * 2 * nt * a.c.n + (long long)t * a.c.n + tile_off;
     u64 *__restrict__ o1 = o0 + (long long)nt * a.c.n;
-    // the tile this CTA reads for digit jd: its extended limb, or d itself
-    // for the digit holding the target prime
-    auto digit_tile = [&](int jd) -> const u64 * {
-        const int lo = a.dg.lo[jd], hi = a.dg.hi[jd];
-        if (t >= lo && t < hi) return a.d + item * a.dis + (long long)t * a.c.n + tile_off;
-        const int ti = t < lo ? t : t - (hi - lo);
-        return a.ext + item * a.eis + (long long)(a.dg.off[jd] + ti) * a.c.n + tile_off;
-    };
     for (int jd = 0; jd < a.dg.ndig; jd++) {
         const int lo = a.dg.lo[jd], hi = a.dg.hi[jd];
         const u64 *kb = a.key + (long long)jd * 2 * kpoly + (long long)pt * a.c.n + tile_off;
         prefetch_tile_l2(kb);
         prefetch_tile_l2(kb + kpoly);
-        // the next digit's input tile is fetched to L2 while this one is transformed
-        if (jd + 1 < a.dg.ndig) prefetch_tile_l2(digit_tile(jd + 1));
         const bool own = t >= lo && t < hi;
         if (!own) {
             const int ti = t < lo ? t : t - (hi - lo);

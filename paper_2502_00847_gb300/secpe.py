@@ -34,6 +34,7 @@ EXPORTS = [
     "secpe_phoenix_argmax_batch", "secpe_linear_create", "secpe_linear_create_coeffs", "secpe_linear_destroy",
     "secpe_linear_apply", "secpe_encrypt_replicated", "secpe_boot_rotation_steps", "secpe_boot_create",
     "secpe_boot_create_coeffs", "secpe_boot_destroy", "secpe_bootstrap_batch", "secpe_bootstrap",
+    "secpe_argmax_batch_boot",
 ]
 
 
@@ -67,7 +68,7 @@ class ServerStatsC(ctypes.Structure):
 
 class CountersC(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
-        "rotations", "signs", "relins", "refreshes", "keyswitches", "launches")]
+        "rotations", "signs", "relins", "refreshes", "keyswitches", "launches", "bootstraps")]
 
 
 class TuningC(ctypes.Structure):
@@ -171,6 +172,7 @@ def lib():
         "secpe_boot_destroy": (None, [vp]),
         "secpe_bootstrap_batch": (i32, [vp, vp, vp, P(CtBatchC), P(CtBatchC), vp]),
         "secpe_bootstrap": (i32, [vp, vp, vp, P(CtC), P(CtC), vp]),
+        "secpe_argmax_batch_boot": (i32, [vp, vp, vp, P(QueryC), i32, vp]),
         "secpe_encode_packed": (i32, [i32, dbl, P(dbl), i32, i32, dbl, P(ctypes.c_int64)]),
         "secpe_decode_packed": (i32, [i32, dbl, P(dbl), i32, i32, P(dbl)]),
         "secpe_encrypt_logits_packed": (i32, [vp, vp, P(dbl), i32, i32, dbl, u64, P(CtC), vp]),
@@ -800,6 +802,15 @@ class Boot:
             self.close()
         except Exception:
             pass
+
+
+def argmax_batch_boot(ctx, keys, boot, queries):
+    """secpe_argmax_batch_boot: argmax_batch with every refresh a bootstrap."""
+    qarr, keep = _query_array(queries)
+    _check(lib().secpe_argmax_batch_boot(ctx.h, keys.h, boot.h, qarr, len(queries), _stream()),
+           "secpe_argmax_batch_boot")
+    for q, (_, z) in zip(queries, keep):
+        q["z_out"].update(z)
 
 
 class Graph:
