@@ -395,7 +395,8 @@ int secpe_ensemble_aggregate(secpe_ctx *ctx, const secpe_ct *cts, int K, double 
                              double d_max, secpe_ct *out, void *stream);
 /* SecPE Alg. 1 on a normalised ciphertext y with C >= 2 classes: returns z
  * with z ~ 1 at the argmax slot and ~ 0 at the other slots 0..C-1.
- * Needs Galois keys for RotR(C') and RotL(2^i), i < log2 C'. */
+ * Needs Galois keys for RotR(C') and RotL(2^i), i < log2 C'.  Levels follow
+ * secpe_level_plan (refresh level L). */
 int secpe_encrypted_argmax(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *y, int C,
                            uint64_t qseed, secpe_ct *z_out, void *stream);
 
@@ -434,6 +435,27 @@ int secpe_linear_apply(secpe_ctx *ctx, const secpe_keys *keys, const secpe_linea
  * level, scale Delta (packed encoder). */
 int secpe_encrypt_replicated(secpe_ctx *ctx, const secpe_keys *keys, const double *x, int d, int C, uint64_t seed,
                              secpe_ct *out, void *stream);
+
+/* Level plan of Alg. 1 (host only; level-aware QuickMax, a reading: SecPE
+ * does not discuss levels).  Alg. 1 for C >= 2 classes on y at entry_level
+ * (the aggregation's output level), evaluated greedily with refreshes that
+ * return refresh_level (a refresh comes before a step that lacks its levels:
+ * a QuickMax round needs 1 + reserve, each Sign polynomial 4 + reserve, the
+ * last of Max's Sign 5 + reserve), falls into ranges: the first starts at
+ * y, each refresh starts the next.  Range by range, in order, each range's
+ * first ciphertext is dropped to the lowest level at which every refresh
+ * still comes at the same step and the refreshed step keeps its levels (a
+ * lower start never raises a later level, so one level at a time finds
+ * it): the refresh count is unchanged and every step runs on at most as
+ * many limbs.
+ * targets[capacity] receives the levels of y entering round 0 (j = 0) and
+ * of the ciphertext right after refresh j; *count = refreshes + 1 (with
+ * targets null only *count is written).  secpe_encrypted_argmax,
+ * secpe_argmax_batch and the server follow it with refresh_level = L, and
+ * secpe_argmax_batch_boot with L - 16.  SECPE_EINVAL for bad arguments or
+ * capacity < *count, SECPE_ELEVEL if a refresh leaves too few levels. */
+int secpe_level_plan(const secpe_params *p, int C, int entry_level, int refresh_level, int32_t *targets,
+                     int capacity, int *count);
 
 /* One ensemble query for the batched driver. */
 typedef struct {

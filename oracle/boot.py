@@ -76,6 +76,7 @@ class BootPlan:
         self.q0 = o.primes[0]
         L = o.ctx.L
         self.level_c2s = L
+        self.out_level = L - 16    # the circuit's 16 levels (checked in bootstrap)
         V = subring_vandermonde(n)
         G = V.conj().T / n                                      # n x n
         A = np.zeros((2 * n, n), dtype=np.complex128)
@@ -220,4 +221,6 @@ class BootPlan:
         x = self.sub_sum(x)
         u = self.coeff_to_slot(x)
         f = self.eval_mod(u)
-        return self.slot_to_coeff(f, lab)
+        z = self.slot_to_coeff(f, lab)
+        assert z.level == self.out_level
+        return z

@@ -80,6 +80,7 @@ class Oracle:
         self.ridx = 0
         self.qseed = 0
         self.boot_plan = None   # a boot.BootPlan: refreshes become bootstraps (non-interactive)
+        self.plan = None        # level plan of the Argmax being evaluated (level_plan)
         self.reset_counters()
 
     def reset_counters(self):
@@ -651,10 +652,71 @@ class Oracle:
 
     # ------------------------------------------------------ SecPE circuit
     def ensure(self, ct, k):
-        """Refresh ct if fewer than k + reserve levels remain."""
+        """Refresh ct if fewer than k + reserve levels remain.  Inside an
+        Argmax with a level plan, the refreshed ciphertext is then dropped
+        to the plan's level for the range the refresh starts."""
         if ct.level < k + self.p.reserve:
-            return self.refresh(ct, self.qseed)
+            ct = self.refresh(ct, self.qseed)
+            if self.plan is not None and self.ridx < len(self.plan) and ct.level > self.plan[self.ridx]:
+                ct = self.drop(ct, self.plan[self.ridx])
         return ct
+
+    def refresh_level(self):
+        """Level of a refreshed ciphertext: the top level for the stand-in,
+        L - 16 for a bootstrap."""
+        return self.ctx.L if self.boot_plan is None else self.boot_plan.out_level
+
+    def level_plan(self, r, entry):
+        """READING (level-aware QuickMax; the paper does not discuss levels).
+        Alg. 1 with r QuickMax rounds on y at level `entry`, refreshing before
+        a step that lacks its levels (as ensure does), falls into ranges: the
+        first starts at y, each refresh starts the next.  Range by range, in
+        order, the plan lowers the range's first ciphertext by as many levels
+        as keep every refresh at the same step and leave the refreshed step
+        its levels.  A lower start never raises a later level, so the levels
+        that keep the refreshes in place form an interval, found by lowering
+        one level at a time.  (A range's ciphertexts can reach later ranges:
+        Max multiplies d, computed before a refresh inside Sign(d), by the
+        refreshed Sign, so the whole circuit is walked for every trial.)
+        Returns the level of each range's first ciphertext: [y after the
+        duplication, after refresh 1, 2, ...]."""
+        res, top = self.p.reserve, self.refresh_level()
+        n_poly = self.p.sign_dg + self.p.sign_df
+
+        def walk(plan):
+            """Indices of the level tests that refresh under `plan` (None if a
+            refreshed step lacks its levels)."""
+            points, count, ok = [], [0], [True]
+
+            def test(lv, k):
+                count[0] += 1
+                if lv >= k + res:
+                    return lv
+                points.append(count[0])
+                j = len(points)
+                out = min(top, plan[j]) if j < len(plan) else top
+                ok[0] = ok[0] and out >= k + res
+                return out
+
+            lv = min(entry, plan[0])
+            for _ in range(r):                  # QuickMax rounds: y <- Max(RotL(y, 2^i), y)
+                lv = test(lv, 1)
+                ld = lv                         # d = a - y stays at this level
+                for i in range(n_poly):         # Sign(d), one more level for the last
+                    lv = test(lv, 5 if i == n_poly - 1 else 4) - 4
+                lv = min(ld, lv) - 1            # t = d * Sign(d)/2; Max = t + u at t's level
+            for i in range(n_poly):             # final Sign, evaluated lowest
+                lv = min(test(lv, 4), 4 * (n_poly - i) + res) - 4
+            return points if ok[0] else None
+
+        points = walk([entry])
+        if points is None:
+            raise ValueError("not enough levels after a refresh")
+        plan = [entry] + [top] * len(points)
+        for j in range(len(plan)):
+            while plan[j] > 0 and walk(plan[:j] + [plan[j] - 1] + plan[j + 1:]) == points:
+                plan[j] -= 1
+        return plan
 
     def poly9(self, x, c, s_out):
         """Odd degree-9 p(x) = c1 x + c3 x^3 + c5 x^5 + c7 x^7 + c9 x^9 (SecPE
@@ -721,7 +783,7 @@ class Oracle:
         """SecPE Alg. 1 on a normalised ciphertext y with n_classes valid
         slots (padded to C' = 2^ceil(log2 C)): y <- y + RotR(y, C');
         QuickMax: for i < log2 C': y <- Max(RotL(y, 2^i), y); then
-        z = Sign(y_dup - y_max) + 1."""
+        z = Sign(y_dup - y_max) + 1; levels as level_plan sets them."""
         if n_classes < 2:
             raise ValueError("argmax needs at least 2 classes")
         self.qseed = qseed
@@ -732,13 +794,19 @@ class Oracle:
             raise ValueError("2*C' exceeds the slot count")
         y = self.add(y, self.rotate(y, -cp))
         y_dup = y
-        for i in range(r):
-            y = self.ensure(y, 1)
-            a = self.rotate(y, 1 << i)
-            y = self.max(a, y)
-        al = self.mul_const(y_dup, 1.0, y.scale, y.level)
-        d = self.sub(al, y)
-        s = self.sign(d, 0, lowest=True)
+        self.plan = self.level_plan(r, y.level)
+        try:
+            if y.level > self.plan[0]:
+                y = self.drop(y, self.plan[0])
+            for i in range(r):
+                y = self.ensure(y, 1)
+                a = self.rotate(y, 1 << i)
+                y = self.max(a, y)
+            al = self.mul_const(y_dup, 1.0, y.scale, y.level)
+            d = self.sub(al, y)
+            s = self.sign(d, 0, lowest=True)
+        finally:
+            self.plan = None
         return self.add_const(s, 1.0)
 
     def phoenix_argmax(self, y, n_classes, qseed):

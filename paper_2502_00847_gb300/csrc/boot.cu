@@ -228,6 +228,8 @@ int check_boot(const secpe_ctx *ctx) {
 
 int boot_block(const secpe_boot *bt) { return bt->n; }
 
+int boot_out_level(const secpe_ctx *ctx) { return ctx->L - kBootLevels; }
+
 // Bootstrapping of a batch (labels kept, output at level L - 16).
 int boot_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_boot *bt, const Ct &in, Ct &out) {
     const int L = ctx->L, n = ctx->n, B = in.B();

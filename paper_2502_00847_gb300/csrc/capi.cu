@@ -579,6 +579,22 @@ extern "C" int secpe_encrypted_argmax(secpe_ctx *ctx, const secpe_keys *keys_, c
     return finish(ctx, copy_out(ctx, r, z_out));
 }
 
+extern "C" int secpe_level_plan(const secpe_params *p, int C, int entry_level, int refresh_level, int32_t *targets,
+                                int capacity, int *count) {
+    if (!p || !count || C < 2 || p->reserve < 1 || p->sign_dg < 0 || p->sign_df < 0 || p->sign_dg + p->sign_df < 1 ||
+        entry_level < 0 || entry_level >= p->n_q || refresh_level < 1 || refresh_level >= p->n_q)
+        return SECPE_EINVAL;
+    int r = 0;
+    while ((1 << r) < C) r++;
+    LevelPlan lp;
+    SECPE_CHECK(make_level_plan(p->reserve, p->sign_dg + p->sign_df, refresh_level, r, entry_level, lp));
+    *count = (int)lp.target.size();
+    if (!targets) return SECPE_OK;
+    if (capacity < *count) return SECPE_EINVAL;
+    for (int j = 0; j < *count; j++) targets[j] = lp.target[j];
+    return SECPE_OK;
+}
+
 extern "C" int secpe_argmax_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_query *q, int n_queries,
                                   void *stream) {
     if (!ctx || !q || n_queries < 0) return SECPE_EINVAL;

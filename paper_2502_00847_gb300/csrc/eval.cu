@@ -6,6 +6,7 @@
 // polynomial block would run out of levels.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <numeric>
 
 #include "eval.h"
@@ -272,9 +273,100 @@ int Eval::refresh(const Ct &x, Ct &out) {
 }
 
 int Eval::ensure(const Ct &x, int k, Ct &out) {
-    if (x.level() < k + ctx->p.reserve) return refresh(x, out);
-    out = x;
+    if (x.level() >= k + ctx->p.reserve) {
+        out = x;
+        return SECPE_OK;
+    }
+    SECPE_CHECK(refresh(x, out));
+    // inside an Argmax: down to the plan's level for the range this refresh starts
+    if (plan && ridx < plan->target.size() && out.level() > plan->target[ridx])
+        out = ct_drop(out, plan->target[ridx]);
     return SECPE_OK;
+}
+
+int refresh_out_level(const secpe_ctx *ctx) { return ctx->boot ? boot_out_level(ctx) : ctx->L; }
+
+namespace {
+
+// The level tests of Alg. 1 on y at `entry` (r QuickMax rounds, then the
+// final Sign at its lowest levels), step for step as Eval::argmax takes
+// them, with each range starting at most at plan[j] (a refresh returns
+// min(top, plan[j]) after refresh j).  Fills the indices of the tests that
+// refresh; false if a refreshed step lacks its levels.  With lv and nref it
+// also records y's level and the refresh count when each phase starts.
+struct LevelWalk {
+    int res, top, n_poly, r, entry;
+
+    bool run(const std::vector<int> &plan, std::vector<int> &points, std::vector<int> *lv = nullptr,
+             std::vector<int> *nref = nullptr) const {
+        points.clear();
+        int count = 0;
+        bool ok = true;
+        auto test = [&](int l, int k) {
+            count++;
+            if (l >= k + res) return l;
+            points.push_back(count);
+            const size_t j = points.size();
+            const int out = j < plan.size() ? std::min(top, plan[j]) : top;
+            ok = ok && out >= k + res;
+            return out;
+        };
+        auto mark = [&](int l) {
+            if (!lv) return;
+            lv->push_back(l);
+            nref->push_back((int)points.size());
+        };
+        int l = std::min(entry, plan[0]);
+        for (int k = 0; k < r; k++) {  // QuickMax rounds
+            mark(l);
+            l = test(l, 1);
+            const int ld = l;  // d = a - y stays at this level
+            for (int i = 0; i < n_poly; i++) l = test(l, i == n_poly - 1 ? 5 : 4) - 4;
+            l = std::min(ld, l) - 1;  // t = d * Sign(d)/2; Max at t's level
+        }
+        mark(l);
+        for (int i = 0; i < n_poly; i++) l = std::min(test(l, 4), 4 * (n_poly - i) + res) - 4;
+        if (nref) nref->push_back((int)points.size());
+        return ok;
+    }
+};
+
+}  // namespace
+
+int make_level_plan(const secpe_ctx *ctx, int r, int entry, LevelPlan &plan) {
+    return make_level_plan(ctx->p.reserve, ctx->p.sign_dg + ctx->p.sign_df, refresh_out_level(ctx), r, entry, plan);
+}
+
+// Range by range, in order, the lowest start that keeps every refresh at
+// the same test and every refreshed step its levels.  A lower start never
+// raises a later level, so those starts form an interval: lower one level
+// at a time.  The whole circuit is walked for every trial, because a
+// range's ciphertexts reach later ranges (Max multiplies d, computed before
+// a refresh inside Sign(d), by the refreshed Sign).
+int make_level_plan(int res, int np, int top, int r, int entry, LevelPlan &plan) {
+    const LevelWalk w{res, top, np, r, entry};
+    std::vector<int> points, trial_points;
+    if (!w.run({entry}, points)) return SECPE_ELEVEL;
+    plan.target.assign(points.size() + 1, top);
+    plan.target[0] = entry;
+    for (size_t j = 0; j < plan.target.size(); j++) {
+        while (plan.target[j] > 0) {
+            std::vector<int> trial = plan.target;
+            trial[j]--;
+            if (!w.run(trial, trial_points) || trial_points != points) break;
+            plan.target[j]--;
+        }
+    }
+    plan.lv.clear();
+    plan.nref.clear();
+    w.run(plan.target, trial_points, &plan.lv, &plan.nref);
+    return SECPE_OK;
+}
+
+std::vector<int> LevelPlan::signature(int k) const {
+    std::vector<int> s{lv[k], nref[k]};
+    for (int j = nref[k] + 1; j <= nref[k + 1]; j++) s.push_back(target[j]);
+    return s;
 }
 
 // Odd degree-9 p(x) = c1 x + c3 x^3 + c5 x^5 + c7 x^7 + c9 x^9 (Eq. comp),
@@ -375,6 +467,14 @@ int Eval::argmax(const Ct &y, int C, Ct &out) {
     SECPE_CHECK(rotate(y, -cp, rot));
     SECPE_CHECK(add(y, rot, y1));
     ydup = y1;
+    LevelPlan lp;
+    SECPE_CHECK(make_level_plan(ctx, r, y1.level(), lp));
+    struct Reset {
+        const LevelPlan *&p;
+        ~Reset() { p = nullptr; }
+    } reset{plan};
+    plan = &lp;
+    if (y1.level() > lp.target[0]) y1 = ct_drop(y1, lp.target[0]);
     for (int i = 0; i < r; i++) {
         Ct ye, a, m;
         SECPE_CHECK(ensure(y1, 1, ye));
@@ -604,37 +704,67 @@ static int argmax_batch_tenant(secpe_ctx *ctx, const secpe_keys *keys, const sec
     }
     Yn = Ct();
 
-    // 3. phases
+    // 3. phases, level-aware: every query follows its plan (one per r).  A
+    // run is a range of sorted queries whose levels have agreed so far; it
+    // splits where their plans part (where one of them enters its last
+    // range), so each batched step has one level.
+    std::map<int, LevelPlan> plans;
+    for (int s = 0; s < nq_; s++) {
+        const int r = rr[order[s]];
+        if (!plans.count(r)) SECPE_CHECK(make_level_plan(ctx, r, L - 1, plans[r]));
+    }
+    struct Run {
+        int s, e;
+        Ct y;
+        u64 ridx;
+    };
+    std::vector<Run> runs{{0, nq_, Ydup, 0}};
     const int rmax = rr[order[0]];
-    Ct ycur = Ydup;  // covers prefix [0, cnt_ge(k))
-    u64 ridx = 0;
     for (int k = 0; k <= rmax; k++) {
         int cnt_gt = 0, cnt_ge = 0;
         for (int s = 0; s < nq_; s++) {
             if (rr[order[s]] > k) cnt_gt++;
             if (rr[order[s]] >= k) cnt_ge++;
         }
-        // queries finishing now: [cnt_gt, cnt_ge)
-        if (cnt_ge > cnt_gt) {
-            Eval Ef{ctx, keys, {}, ridx};
-            for (int s = cnt_gt; s < cnt_ge; s++) Ef.qseeds.push_back(q[order[s]].qseed);
-            Ct yf = ct_slice(ycur, cnt_gt, cnt_ge), df = ct_slice(Ydup, cnt_gt, cnt_ge);
+        // queries finishing now (r = k, one plan): [cnt_gt, cnt_ge)
+        for (const Run &ru : runs) {
+            const int s = std::max(ru.s, cnt_gt), e = std::min(ru.e, cnt_ge);
+            if (s >= e) continue;
+            const LevelPlan &lp = plans[k];
+            Eval Ef{ctx, keys, {}, ru.ridx, &lp};
+            for (int b = s; b < e; b++) Ef.qseeds.push_back(q[order[b]].qseed);
+            Ct yf = ct_slice(ru.y, s - ru.s, e - ru.s), df = ct_slice(Ydup, s, e);
+            if (yf.level() != lp.lv[k]) return SECPE_ELEVEL;
             Ct al, d, sgn, z;
             SECPE_CHECK(Ef.mul_const(df, {1.0}, yf.scale(), yf.level(), al));
             SECPE_CHECK(Ef.sub(al, yf, d));
             SECPE_CHECK(Ef.sign(d, 0, sgn, 1.0, true));
             SECPE_CHECK(Ef.add_const(sgn, 1.0, z));
-            SECPE_CHECK(copy_z(ctx, q, order, cnt_gt, z));
+            SECPE_CHECK(copy_z(ctx, q, order, s, z));
         }
         if (cnt_gt == 0) break;
-        Eval Er{ctx, keys, {}, ridx};
-        for (int s = 0; s < cnt_gt; s++) Er.qseeds.push_back(q[order[s]].qseed);
-        Ct yr = ct_slice(ycur, 0, cnt_gt), ye, a, m;
-        SECPE_CHECK(Er.ensure(yr, 1, ye));
-        SECPE_CHECK(Er.rotate(ye, 1 << k, a));
-        SECPE_CHECK(Er.max(a, ye, m));
-        ridx = Er.ridx;
-        ycur = m;
+        // QuickMax round k of the queries with r > k: [0, cnt_gt)
+        std::vector<Run> next;
+        for (const Run &ru : runs) {
+            const int e_act = std::min(ru.e, cnt_gt);
+            for (int s = ru.s; s < e_act;) {
+                const LevelPlan &lp = plans[rr[order[s]]];
+                const std::vector<int> sig = lp.signature(k);
+                int e = s + 1;
+                while (e < e_act && plans[rr[order[e]]].signature(k) == sig) e++;
+                Eval Er{ctx, keys, {}, ru.ridx, &lp};
+                for (int b = s; b < e; b++) Er.qseeds.push_back(q[order[b]].qseed);
+                Ct yr = ct_slice(ru.y, s - ru.s, e - ru.s), ye, a, m;
+                if (yr.level() > lp.lv[k]) yr = ct_drop(yr, lp.lv[k]);
+                if (yr.level() != lp.lv[k]) return SECPE_ELEVEL;
+                SECPE_CHECK(Er.ensure(yr, 1, ye));
+                SECPE_CHECK(Er.rotate(ye, 1 << k, a));
+                SECPE_CHECK(Er.max(a, ye, m));
+                next.push_back({s, e, m, Er.ridx});
+                s = e;
+            }
+        }
+        runs = std::move(next);
     }
     return SECPE_OK;
 }

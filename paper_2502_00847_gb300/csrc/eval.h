@@ -51,11 +51,31 @@ Ct ct_slice(const Ct &x, int s, int e);
 // same data, lower level (modulus drop)
 Ct ct_drop(const Ct &x, int level);
 
+// Level plan of one Argmax (level-aware QuickMax; the paper does not
+// discuss levels).  Alg. 1 with r QuickMax rounds, evaluated greedily
+// (refresh before a step that lacks its levels), falls into ranges: the
+// first starts at y after the duplication, each refresh starts the next.
+// Range by range, the plan starts each range as low as it can while every
+// refresh stays at the same step (and the refreshed step keeps its levels),
+// so the refresh count is unchanged and the steps run on fewer limbs.
+struct LevelPlan {
+    std::vector<int> target;  // [0]: level of y entering round 0; [j]: level after refresh j
+    std::vector<int> lv;      // planned level of y when phase k = 0..r starts (k = r: the final Sign)
+    std::vector<int> nref;    // refreshes before phase k, k = 0..r+1
+    // what two queries must share to run phase k as one batch
+    std::vector<int> signature(int k) const;
+};
+int make_level_plan(const secpe_ctx *ctx, int r, int entry, LevelPlan &plan);
+// the same from the reserve, the polynomials per Sign and the refresh's output level
+int make_level_plan(int res, int n_poly, int top, int r, int entry, LevelPlan &plan);
+int refresh_out_level(const secpe_ctx *ctx);
+
 struct Eval {
     secpe_ctx *ctx;
     const secpe_keys *keys;
     std::vector<u64> qseeds;  // per item, refresh randomness
     u64 ridx = 0;             // refresh counter (shared by the batch)
+    const LevelPlan *plan = nullptr;  // set inside an Argmax: drops after each refresh
 
     int add(const Ct &a, const Ct &b, Ct &out);
     int sub(const Ct &a, const Ct &b, Ct &out);
@@ -96,6 +116,7 @@ int upload_plain(secpe_ctx *ctx, const int64_t *m, int B, int nl, bool mont, u64
 // Bootstrapping of a batch (boot.cu): labels kept, output at level L - 16.
 int boot_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_boot *bt, const Ct &in, Ct &out);
 int boot_block(const secpe_boot *bt);
+int boot_out_level(const secpe_ctx *ctx);
 
 int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int lv, const u64 *key,
               const CtB &out, bool acc0, bool acc1);

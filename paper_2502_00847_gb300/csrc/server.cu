@@ -41,6 +41,7 @@ struct QState {
     int phase = -2;  // -2 waiting for admission, -1 aggregate+dup, 0..r-1 rounds, r final
     Ct ydup, y;
     u64 ridx = 0;
+    LevelPlan plan;  // the query's levels (level-aware QuickMax)
     bool done = false, cancelled = false;
     cudaEvent_t done_ev = nullptr;
     double t_submit = 0, t_admit = 0;
@@ -141,7 +142,7 @@ int gather(secpe_ctx *ctx, const std::vector<QState *> &g, bool dup, Ct &out) {
 int run_group(secpe_server *s, std::vector<QState *> &g) {
     secpe_ctx *ctx = s->ctx;
     const int phase = g[0]->phase, r = g[0]->r;
-    Eval E{ctx, g[0]->keys, {}, g[0]->ridx};
+    Eval E{ctx, g[0]->keys, {}, g[0]->ridx, &g[0]->plan};
     for (QState *st : g) E.qseeds.push_back(st->q.qseed);
     const int B = (int)g.size(), n = ctx->n, L = ctx->L;
     if (phase == -1) {
@@ -175,6 +176,9 @@ int run_group(secpe_server *s, std::vector<QState *> &g) {
     }
     Ct y;
     SECPE_CHECK(gather(ctx, g, false, y));
+    const int planned = g[0]->plan.lv[phase];
+    if (y.level() > planned) y = ct_drop(y, planned);
+    if (y.level() != planned) return SECPE_ELEVEL;
     if (phase < r) {
         Ct ye, a, m;
         SECPE_CHECK(E.ensure(y, 1, ye));
@@ -264,6 +268,7 @@ extern "C" int secpe_server_submit(secpe_server *s, const secpe_query *q, int64_
         s->keys_bytes += kb;
     }
     QState st;
+    SECPE_CHECK(make_level_plan(ctx, r, ctx->L - 1, st.plan));
     st.ticket = s->next_ticket++;
     st.q = *q;
     st.keys = keys;
@@ -302,13 +307,15 @@ extern "C" int secpe_server_step(secpe_server *s, void *stream, int *launched) {
     // queries at the same point of the circuit form a group: same tenant,
     // phase and kind (the duplication needs the same C' key; a QuickMax round
     // k is common to all queries with r > k; the final phase k is shared by
-    // queries with r = k)
+    // queries with r = k) and the same levels through the phase (their level
+    // plans' signature for it)
     auto kind = [](const QState &st) { return st.phase < 0 ? 2 * st.cp : (st.phase < st.r ? 0 : 1); };
-    std::map<std::tuple<const secpe_keys *, int, int>, std::vector<QState *>> groups;
+    std::map<std::tuple<const secpe_keys *, int, int, std::vector<int>>, std::vector<QState *>> groups;
     for (auto &kv : s->q) {
         QState &st = kv.second;
         if (st.cancelled || st.done || st.phase < -1) continue;
-        groups[std::make_tuple(st.keys, st.phase, kind(st))].push_back(&st);
+        const std::vector<int> sig = st.phase >= 0 ? st.plan.signature(st.phase) : std::vector<int>();
+        groups[std::make_tuple(st.keys, st.phase, kind(st), sig)].push_back(&st);
     }
     std::vector<std::vector<QState *>> runs;
     auto older = [](const QState *a, const QState *b) { return a->t_admit < b->t_admit; };

@@ -34,7 +34,7 @@ EXPORTS = [
     "secpe_phoenix_argmax_batch", "secpe_linear_create", "secpe_linear_create_coeffs", "secpe_linear_destroy",
     "secpe_linear_apply", "secpe_encrypt_replicated", "secpe_boot_rotation_steps", "secpe_boot_create",
     "secpe_boot_create_coeffs", "secpe_boot_destroy", "secpe_bootstrap_batch", "secpe_bootstrap",
-    "secpe_argmax_batch_boot",
+    "secpe_argmax_batch_boot", "secpe_level_plan",
 ]
 
 
@@ -167,6 +167,7 @@ def lib():
         "secpe_linear_apply": (i32, [vp, vp, vp, P(CtC), P(CtC), vp]),
         "secpe_encrypt_replicated": (i32, [vp, vp, P(dbl), i32, i32, u64, P(CtC), vp]),
         "secpe_boot_rotation_steps": (i32, [vp, i32, P(i32), i32, P(i32)]),
+        "secpe_level_plan": (i32, [P(ParamsC), i32, i32, i32, P(i32), i32, P(i32)]),
         "secpe_boot_create": (i32, [vp, i32, P(vp)]),
         "secpe_boot_create_coeffs": (i32, [vp, i32, P(ctypes.c_int64), P(ctypes.c_int64), P(vp)]),
         "secpe_boot_destroy": (None, [vp]),
@@ -193,6 +194,19 @@ def select_primes(**params):
     _check(lib().secpe_select_primes(ctypes.byref(p), _u64p(out), len(out)), "secpe_select_primes")
     vals = [int(x) for x in out]
     return vals[: p.n_q], vals[p.n_q:]
+
+
+def level_plan(C, entry_level, refresh_level, **params):
+    """Host-only secpe_level_plan: the levels of y entering round 0 and right
+    after each refresh of Alg. 1 (level-aware QuickMax)."""
+    p = ParamsC(**{f[0]: params.get(f[0], 0) for f in ParamsC._fields_})
+    cnt = ctypes.c_int32(0)
+    _check(lib().secpe_level_plan(ctypes.byref(p), C, entry_level, refresh_level, None, 0, ctypes.byref(cnt)),
+           "secpe_level_plan")
+    arr = (ctypes.c_int32 * cnt.value)()
+    _check(lib().secpe_level_plan(ctypes.byref(p), C, entry_level, refresh_level, arr, cnt.value, ctypes.byref(cnt)),
+           "secpe_level_plan")
+    return list(arr)
 
 
 class SecpeError(RuntimeError):

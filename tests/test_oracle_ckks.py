@@ -317,9 +317,10 @@ def test_lazy_relinearisation_counts(toy_oracle):
 @pytest.mark.parametrize("C,seed", [(2, 4), (4, 5)])
 def test_level_aware_final_sign_keeps_refreshes(C, seed, monkeypatch):
     """Alg. 1's final Sign evaluated at the lowest sufficient levels (each
-    polynomial's input dropped to 4 (polynomials left) + reserve): the same
-    refresh count as with the greedy levels, z at the reserve level, and the
-    same decoded result within the Sign tolerance."""
+    polynomial's input dropped to 4 (polynomials left) + reserve), with the
+    level plan: the same refresh count as with the greedy levels throughout,
+    z at the reserve level, and the same decoded result within the Sign
+    tolerance."""
     from oracle import TOY
     o = Oracle(TOY)
     cp = 1 << (C - 1).bit_length()
@@ -337,6 +338,8 @@ def test_level_aware_final_sign_keeps_refreshes(C, seed, monkeypatch):
     greedy = Oracle.sign
     monkeypatch.setattr(Oracle, "sign", lambda self, x, out_levels, last_factor=1.0, lowest=False:
                         greedy(self, x, out_levels, last_factor, False))
+    # greedy levels throughout: no level plan either
+    monkeypatch.setattr(Oracle, "level_plan", lambda self, r, entry: [entry])
     o.reset_counters()
     zg = o.argmax(y, C, qseed=9)
     assert o.counters["refreshes"] == low_refreshes
