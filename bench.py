@@ -89,6 +89,8 @@ def parse():
                     help="default run: packed query sets of the slot-packing line (0: none)")
     ap.add_argument("--no-keyswitch-gbps", dest="keyswitch_gbps", action="store_false",
                     help="default run: skip the primitive-set key-switch GB/s")
+    ap.add_argument("--no-word32", dest="word32", action="store_false",
+                    help="skip the word-size probe (32-bit against 64-bit residues)")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="arrival window per rate")
     ap.add_argument("--serve-queries", type=int, default=3000, help="at most this many queries per rate")
     ap.add_argument("--no-plain-serve", action="store_true", help="serving: skip the plain path's real run")
@@ -568,6 +570,7 @@ def run_ours(args, world, rank, local):
     # key switching of the primitive set (config 2: 24 x 50-bit + 4 special,
     # dnum = 3) at B = 1 and B = 8, algorithmic bytes = input + key + output
     ksw = keyswitch_gbps(secpe, torch, dev, args.steps) if args.keyswitch_gbps and rank == 0 else None
+    word = word_size_probe(secpe, torch, dev, args.steps) if args.word32 and rank == 0 else None
 
     # measured throughput of the integer multiply pipe (the ALU roofline)
     probe = ctx.mul32_probe() if rank == 0 else None
@@ -654,7 +657,7 @@ def run_ours(args, world, rank, local):
                                   "re-encrypt), included in every step",
                        "autotune": {k: v["ctas_per_sm"] for k, v in tuning.items()}},
             "plain": plain, "e2e": e2e, "roofline": roofline, "roofline_other": other, "cpu_baseline": cpu,
-            "keyswitch_GBps": ksw, "serve": serve, "packed": packed, "phoenix": phoenix, "clip": clip,
+            "keyswitch_GBps": ksw, "word_size": word, "serve": serve, "packed": packed, "phoenix": phoenix, "clip": clip,
             "bootstrap": boot,
             "p99_ms": serve["served"]["p99_ms"] if serve else None,
             "clocks": clk, "gpu_launches": cnt["launches"], "refresh": refresh,
@@ -956,6 +959,84 @@ def keyswitch_gbps(secpe, torch, dev, steps):
                    "launches can reuse it from L2")
     keys.close()
     ctx.close()
+    return out
+
+
+def _time_ms(torch, fn, reps):
+    """Mean milliseconds of fn() over reps launches (CUDA events on the current stream)."""
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def word_size_probe(secpe, torch, dev, steps):
+    """The word-size lever: the negacyclic NTT (forward + inverse) on the
+    64-bit residues of argmax8 (q0 60-bit + 23 x 50-bit, 1210 bits) against
+    32-bit residues of the word32 chain (29-bit primes, 42 limbs = 1218 bits),
+    16 polynomials each (192 / 168 MiB, above L2), and the 32-bit fast base
+    conversion of a 14-limb digit (406 bits, like argmax8's 8 x 50-bit digit)
+    to 42 primes for 16 items.  Uniform residues (seed 3)."""
+    from paper_2502_00847_gb300.presets import ARGMAX8, WORD32
+    import dataclasses
+    n, polys = 1 << 16, 16
+    reps = max(5, steps)
+    gen = torch.Generator(device=dev).manual_seed(3)
+    out = {}
+    ctx = secpe.Context.from_params(ARGMAX8)
+    p64 = ctx.primes()[:ctx.n_q]
+    bits64 = sum(int(q).bit_length() for q in p64)
+    idx64 = list(range(ctx.n_q)) * polys
+    x64 = torch.empty((len(idx64), n), dtype=torch.int64, device=dev)
+    for r, i in enumerate(idx64):
+        x64[r] = torch.randint(0, p64[i], (n,), generator=gen, dtype=torch.int64, device=dev)
+
+    def fi64():
+        secpe.ntt(ctx, x64, idx64)
+        secpe.ntt(ctx, x64, idx64, inverse=True)
+    ms64 = _time_ms(torch, fi64, reps)
+    nq64 = ctx.n_q
+    del x64
+    ctx.close()
+    q32, sp32 = secpe.select_primes(**dataclasses.asdict(WORD32))
+    t = secpe.Ntt32(q32 + sp32)
+    l32 = 42
+    bits32 = sum(int(q).bit_length() for q in q32[:l32])
+    idx32 = list(range(l32)) * polys
+    x32 = torch.empty((len(idx32), n), dtype=torch.int32, device=dev)
+    for r, i in enumerate(idx32):
+        x32[r] = torch.randint(0, q32[i], (n,), generator=gen, dtype=torch.int64, device=dev).to(torch.int32)
+
+    def fi32():
+        t.ntt(x32, idx32)
+        t.ntt(x32, idx32, inverse=True)
+    ms32 = _time_ms(torch, fi32, reps)
+    del x32
+    for name, ms, limbs, bits, word in (("ntt64", ms64, nq64, bits64, 8), ("ntt32", ms32, l32, bits32, 4)):
+        nl = limbs * polys
+        out[name] = {"ms_fwd_inv": ms, "limbs": nl, "modulus_bits": bits, "us_per_limb": 1e3 * ms / nl,
+                     "ns_per_kbit_coeff": 1e6 * ms / (polys * bits * n / 1000),
+                     "GBps": 4 * nl * n * word / (ms / 1e3) / 1e9}
+    out["ntt_speedup_per_modulus_bit"] = out["ntt64"]["ns_per_kbit_coeff"] / out["ntt32"]["ns_per_kbit_coeff"]
+    B, src, dst = 16, list(range(14)), list(range(14, 48)) + list(range(48, 56))
+    xin = torch.empty((B, len(src), n), dtype=torch.int32, device=dev)
+    for i in src:
+        xin[:, i] = torch.randint(0, q32[i], (B, n), generator=gen, dtype=torch.int64, device=dev).to(torch.int32)
+    xo = torch.empty((B, len(dst), n), dtype=torch.int32, device=dev)
+    msb = _time_ms(torch, lambda: t.bconv(xin, src, xo, dst), reps)
+    alg = B * (len(src) + len(dst)) * n * 4
+    out["bconv32"] = {"ms": msb, "items": B, "n_in": len(src), "n_out": len(dst), "GBps": alg / (msb / 1e3) / 1e9,
+                      "ns_per_output_limb": 1e6 * msb / (B * len(dst))}
+    out["note"] = ("NTT: forward + inverse, algorithmic bytes 4 x limbs x N x word (read + write per transform); "
+                   "bconv32: input + output bytes; 64-bit reference is the library's secpe_ntt on argmax8 primes")
+    t.close()
+    del xin, xo
     return out
 
 

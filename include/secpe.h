@@ -380,6 +380,32 @@ int secpe_bootstrap_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_bo
 int secpe_bootstrap(secpe_ctx *ctx, const secpe_keys *keys, const secpe_boot *bt, const secpe_ct *in,
                     secpe_ct *out, void *stream);
 
+/* ---- word-size probe: 32-bit residues ----------------------------------- */
+/* The negacyclic NTT and the fast base conversion (the RNS primitives of
+ * SecPE Sec. 2.2's CKKS) on 32-bit words, for primes q < 2^30 with
+ * q = 1 mod 2N: a measurement of the word size against the 64-bit path,
+ * with up to 128 primes per table (the circuit itself runs on 64-bit
+ * residues).  N = 2^16 only (log_n = 16).  The table holds the twiddles
+ * (device memory owned by it, 1 MiB per prime).  SECPE_EINVAL for another
+ * N or a prime that is not NTT-friendly, SECPE_ECUDA if allocation fails. */
+typedef struct secpe_ntt32_table secpe_ntt32_table;
+int secpe_ntt32_create(int log_n, const uint32_t *primes, int n_primes, secpe_ntt32_table **out);
+void secpe_ntt32_destroy(secpe_ntt32_table *t);
+/* In place on `count` limbs of N words at limbs + i N (device, 16-byte
+ * aligned), limb i under prime prime_idx[i] (host array, indices into the
+ * table).  Forward: natural order in, bit-reversed order out (psi^brv
+ * twiddles, as secpe_ntt); inverse: the exact inverse.  Values in [0, q). */
+int secpe_ntt32(const secpe_ntt32_table *t, uint32_t *limbs, const int32_t *prime_idx, int count, int inverse,
+                void *stream);
+/* FastBConv of coefficient-form limbs: for each of `batch` items, in
+ * [batch][n_in][N] under the distinct primes in_idx[n_in] (Q their product)
+ * to out [batch][n_out][N] under out_idx[n_out]:
+ * out_j = sum_i [x_i Qhat_i^-1]_{q_i} [Qhat_i]_{p_j} mod p_j, Qhat_i = Q/q_i
+ * (no correction of the multiple of Q it may add).  n_in <= 16,
+ * n_out <= 64; device buffers, 16-byte aligned. */
+int secpe_bconv32(const secpe_ntt32_table *t, const uint32_t *in, const int32_t *in_idx, int n_in, uint32_t *out,
+                  const int32_t *out_idx, int n_out, int batch, void *stream);
+
 /* ---- SecPE circuit ----------------------------------------------------- */
 /* Sign(x) = f^df(g^dg(x)) (SecPE Eq. comp), each degree-9 polynomial by a
  * depth-4 baby-step giant-step DAG; refreshes (counter from *refresh_index,

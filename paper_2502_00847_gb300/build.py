@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libsecpe.so")
 
 SOURCES = ["hostmath.cpp", "context.cu", "ntt.cu", "ntt_fused.cu", "kernels.cu", "keyswitch.cu", "eval.cu",
-           "capi.cu", "encode.cpp", "noalloc.cu", "server.cu", "ntt_tc.cu", "linear.cu", "boot.cu"]
+           "capi.cu", "encode.cpp", "noalloc.cu", "server.cu", "ntt_tc.cu", "linear.cu", "boot.cu", "ntt32.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",

@@ -46,5 +46,8 @@ BOOT_TOY = ParamSet(log_n=12, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=4, d
                     secret_hw=32, boot_primes=16, boot_bits=60)
 BOOT16 = ParamSet(log_n=16, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=6, dnum=6, log_scale=40,
                   secret_hw=32, boot_primes=16, boot_bits=60)
+# The word-size probe's prime chain: 48 + 8 primes of about 29 bits (below
+# 2^30), for the 32-bit transform and base conversion only.
+WORD32 = ParamSet(log_n=16, q0_bits=29, q_bits=29, n_q=48, p_bits=29, n_p=8, dnum=4, log_scale=58)
 PRESETS = {"toy": TOY, "micro": MICRO, "argmax": ARGMAX, "argmax8": ARGMAX8, "boot_toy": BOOT_TOY,
-           "boot16": BOOT16}
+           "boot16": BOOT16, "word32": WORD32}

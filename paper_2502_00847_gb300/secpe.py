@@ -34,7 +34,8 @@ EXPORTS = [
     "secpe_phoenix_argmax_batch", "secpe_linear_create", "secpe_linear_create_coeffs", "secpe_linear_destroy",
     "secpe_linear_apply", "secpe_encrypt_replicated", "secpe_boot_rotation_steps", "secpe_boot_create",
     "secpe_boot_create_coeffs", "secpe_boot_destroy", "secpe_bootstrap_batch", "secpe_bootstrap",
-    "secpe_argmax_batch_boot", "secpe_level_plan",
+    "secpe_argmax_batch_boot", "secpe_level_plan", "secpe_ntt32_create", "secpe_ntt32_destroy", "secpe_ntt32",
+    "secpe_bconv32",
 ]
 
 
@@ -168,6 +169,10 @@ def lib():
         "secpe_encrypt_replicated": (i32, [vp, vp, P(dbl), i32, i32, u64, P(CtC), vp]),
         "secpe_boot_rotation_steps": (i32, [vp, i32, P(i32), i32, P(i32)]),
         "secpe_level_plan": (i32, [P(ParamsC), i32, i32, i32, P(i32), i32, P(i32)]),
+        "secpe_ntt32_create": (i32, [i32, P(ctypes.c_uint32), i32, P(vp)]),
+        "secpe_ntt32_destroy": (None, [vp]),
+        "secpe_ntt32": (i32, [vp, vp, P(i32), i32, i32, vp]),
+        "secpe_bconv32": (i32, [vp, vp, P(i32), i32, vp, P(i32), i32, i32, vp]),
         "secpe_boot_create": (i32, [vp, i32, P(vp)]),
         "secpe_boot_create_coeffs": (i32, [vp, i32, P(ctypes.c_int64), P(ctypes.c_int64), P(vp)]),
         "secpe_boot_destroy": (None, [vp]),
@@ -977,6 +982,43 @@ class Server:
     def close(self):
         if self.h:
             lib().secpe_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ntt32:
+    """secpe_ntt32: the word-size probe's twiddle table for 32-bit primes
+    (q < 2^30, q = 1 mod 2N, N = 2^16); limbs are uint32 torch tensors."""
+
+    def __init__(self, primes, log_n=16):
+        arr = (ctypes.c_uint32 * len(primes))(*primes)
+        h = ctypes.c_void_p()
+        _check(lib().secpe_ntt32_create(log_n, arr, len(primes), ctypes.byref(h)), "secpe_ntt32_create")
+        self.h, self.primes = h, list(primes)
+
+    @staticmethod
+    def _idx(idx):
+        return (ctypes.c_int32 * len(idx))(*idx)
+
+    def ntt(self, limbs, prime_idx, inverse=False):
+        """In place on limbs [count][N] (a contiguous uint32 device tensor)."""
+        _check(lib().secpe_ntt32(self.h, ctypes.c_void_p(limbs.data_ptr()), self._idx(prime_idx), len(prime_idx),
+                                 int(inverse), _stream()), "secpe_ntt32")
+
+    def bconv(self, x, in_idx, out, out_idx):
+        """x [batch][n_in][N] -> out [batch][n_out][N] (uint32 device tensors)."""
+        _check(lib().secpe_bconv32(self.h, ctypes.c_void_p(x.data_ptr()), self._idx(in_idx), len(in_idx),
+                                   ctypes.c_void_p(out.data_ptr()), self._idx(out_idx), len(out_idx), x.shape[0],
+                                   _stream()), "secpe_bconv32")
+
+    def close(self):
+        if self.h:
+            lib().secpe_ntt32_destroy(self.h)
             self.h = None
 
     def __del__(self):
