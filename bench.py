@@ -64,7 +64,8 @@ def parse():
                     help="after the timed steps, one more step with every launch timed by kernel name")
     ap.add_argument("--micro", action="store_true",
                     help="primitive micro-benchmark (N=2^16, 24+4 primes, dnum=3) instead of the Argmax step")
-    ap.add_argument("--micro-ops", default="ntt,keyswitch,hmult,rescale,rotate")
+    ap.add_argument("--micro-ops", default="ntt,keyswitch,hmult,rescale,rotate",
+                    help="also: ntt_tc, ksk_tc, ntt_tc_identity, word32 (the word-size probe)")
     ap.add_argument("--micro-batch", default="1,8,64")
     ap.add_argument("--micro-probe", default="", choices=["", "hmult", "keyswitch", "ntt"],
                     help="after timing, one more call of this op inside the NVTX range 'micro_probe' with the "
@@ -1137,6 +1138,9 @@ def run_micro(args, rank):
             res["rotate_B%d" % B] = {"ms_mean": sum(per) / len(per), "ms_by_log2_step": per}
         del x, y, out
         torch.cuda.empty_cache()
+    if "word32" in ops:
+        # the word-size probe (32-bit against 64-bit residues), as in the default run's `word_size`
+        res["word_size"] = word_size_probe(secpe, torch, "cuda", args.steps)
     if "ntt_tc_identity" in ops:
         # precision variant: bit identity with the CUDA-core NTT over 10^4 seeded random ciphertexts
         total, chunk, mism = args.tc_identity_count, 50, 0

@@ -123,6 +123,26 @@ int Eval::tensor(const Ct &a, const Ct &b, Ct &out3) {
     return SECPE_OK;
 }
 
+int Eval::tensor2(const Ct &a, const Ct &b, const Ct &c, const Ct &e, Ct &out3) {
+    if (a.B() != b.B() || a.B() != c.B() || a.B() != e.B()) return SECPE_EINVAL;
+    if (!scales_match(a.scale() * b.scale(), c.scale() * e.scale())) return SECPE_ESCALE;
+    const int lv = std::min(std::min(a.level(), b.level()), std::min(c.level(), e.level()));
+    const int B = a.B(), n = ctx->n;
+    Ct d;
+    d.buf = std::make_shared<DevBuf>();
+    SECPE_CHECK(d.buf->alloc(ctx, sizeof(u64) * (size_t)B * 3 * (lv + 1) * n));
+    SECPE_CHECK(launch_tensor2(ctx, a.v, b.v, c.v, e.v, d.buf->u(), lv + 1));
+    d.v.data = d.buf->u();
+    d.v.B = B;
+    d.v.cap = lv + 1;
+    d.v.stride = 3ll * (lv + 1) * n;
+    d.v.level = lv;
+    d.v.scale = a.scale() * b.scale();
+    d.v.n = n;
+    out3 = d;
+    return SECPE_OK;
+}
+
 int Eval::add3(const Ct &a3, const Ct &b3, Ct &out3) {
     if (a3.B() != b3.B() || a3.level() != b3.level()) return SECPE_EINVAL;
     if (!scales_match(a3.scale(), b3.scale())) return SECPE_ESCALE;
@@ -382,7 +402,7 @@ int Eval::poly9(const Ct &x, const double *c, double s_out, Ct &out) {
     if (lv < 4 + ctx->p.reserve) return SECPE_ELEVEL;
     const double q3 = (double)ctx->primes[lv - 3];
     // temporaries are released as soon as they are dead (Ct() frees them)
-    Ct x2, x4, x5, L1, P1, L0, P0, T3, U3, TU3;
+    Ct x2, x4, x5, L1, P1, L0, P0, TU3;
     SECPE_CHECK(mul(x, x, x2));
     SECPE_CHECK(mul(x2, x2, x4));
     SECPE_CHECK(mul(x4, x, x5));
@@ -396,14 +416,10 @@ int Eval::poly9(const Ct &x, const double *c, double s_out, Ct &out) {
     x2 = Ct();
     SECPE_CHECK(add_const(L0, c[0], P0));
     L0 = Ct();
-    SECPE_CHECK(tensor(x5, P1, T3));
+    SECPE_CHECK(tensor2(x5, P1, x, P0, TU3));
     x5 = Ct();
     P1 = Ct();
-    SECPE_CHECK(tensor(x, P0, U3));
     P0 = Ct();
-    SECPE_CHECK(add3(T3, U3, TU3));
-    T3 = Ct();
-    U3 = Ct();
     return relin_rescale(TU3, out);
 }
 

@@ -82,6 +82,8 @@ struct Eval {
     int mul(const Ct &a, const Ct &b, Ct &out);
     // 3-component ciphertexts (stride 3 (level+1) N, scale tracked)
     int tensor(const Ct &a, const Ct &b, Ct &out3);
+    // a (x) b + c (x) e as one 3-component ciphertext (equal to add3 of the two tensors)
+    int tensor2(const Ct &a, const Ct &b, const Ct &c, const Ct &e, Ct &out3);
     int add3(const Ct &a3, const Ct &b3, Ct &out3);
     int relin_rescale(const Ct &d3, Ct &out);
     int mul_const(const Ct &x, const std::vector<double> &c, double target, int out_level, Ct &out);

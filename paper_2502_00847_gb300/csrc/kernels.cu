@@ -117,6 +117,67 @@ __global__ void __launch_bounds__(256) k_tensor(DevCtx c, const u64 *a, long lon
     }
 }
 
+// d = a (x) b + c (x) e (two 3-component products and their sum, one pass):
+// each output residue is one Montgomery reduction of the summed 128-bit
+// products (at most 4 of them, below q 2^64), so it equals the sum of the
+// two separate products residue for residue.
+struct Tensor2Args {
+    const u64 *p[4];  // a, b, c, e: item stride s[k], poly 1 at cap[k] N
+    long long s[4];
+    int cap[4];
+    u64 *d;
+    int nl;
+};
+
+__global__ void __launch_bounds__(256) k_tensor2(DevCtx c, const __grid_constant__ Tensor2Args t) {
+    const int li = blockIdx.y;
+    const int i = li % t.nl, item = li / t.nl;
+    const u64 q = c.q[i], qi = c.qinv_neg[i], r2 = c.r2[i];
+    const u64 *P[4];
+    long long pp[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        P[k] = t.p[k] + item * t.s[k] + (long long)i * c.n;
+        pp[k] = (long long)t.cap[k] * c.n;
+    }
+    u64 *D = t.d + (long long)item * 3 * t.nl * c.n + (long long)i * c.n;
+    const long long ps = (long long)t.nl * c.n;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int e = 2 * (threadIdx.x + 256 * (blockIdx.x * 4 + j));
+        if (e >= c.n) break;
+        const ulonglong2 a0 = ld2(P[0] + e), a1 = ld2(P[0] + pp[0] + e);
+        const ulonglong2 b0 = ld2(P[1] + e), b1 = ld2(P[1] + pp[1] + e);
+        const ulonglong2 c0 = ld2(P[2] + e), c1 = ld2(P[2] + pp[2] + e);
+        const ulonglong2 e0 = ld2(P[3] + e), e1 = ld2(P[3] + pp[3] + e);
+        ulonglong2 r0, r1, r2v;
+#define SECPE_TENSOR2_LANE(f)                                  \
+    {                                                          \
+        const u64 b0m = mont_mul(b0.f, r2, q, qi);             \
+        const u64 b1m = mont_mul(b1.f, r2, q, qi);             \
+        const u64 e0m = mont_mul(e0.f, r2, q, qi);             \
+        const u64 e1m = mont_mul(e1.f, r2, q, qi);             \
+        acc128 s0 = mul_full(a0.f, b0m);                       \
+        mac(s0, c0.f, e0m);                                    \
+        r0.f = redc(s0.hi, s0.lo, q, qi);                      \
+        acc128 s2 = mul_full(a1.f, b1m);                       \
+        mac(s2, c1.f, e1m);                                    \
+        r2v.f = redc(s2.hi, s2.lo, q, qi);                     \
+        acc128 s1 = mul_full(a0.f, b1m);                       \
+        mac(s1, a1.f, b0m);                                    \
+        mac(s1, c0.f, e1m);                                    \
+        mac(s1, c1.f, e0m);                                    \
+        r1.f = redc(s1.hi, s1.lo, q, qi);                      \
+    }
+        SECPE_TENSOR2_LANE(x)
+        SECPE_TENSOR2_LANE(y)
+#undef SECPE_TENSOR2_LANE
+        st2(D + e, r0);
+        st2(D + ps + e, r1);
+        st2(D + 2 * ps + e, r2v);
+    }
+}
+
 // ------------------------------------------------------------ constants
 struct KArr {
     long long k[SECPE_MAX_BATCH_CONST];
@@ -681,6 +742,23 @@ int launch_tensor(secpe_ctx *ctx, const CtB &a, const CtB &b, u64 *d, int nl) {
     KprofScope kp(ctx, "ew_tensor", 56.0 * ctx->n * a.B * nl);
     const dim3 grid((unsigned)((ctx->n + 2047) / 2048), (unsigned)((long long)a.B * nl));
     SECPE_LAUNCH(ctx, k_tensor, grid, 256, 0, ctx->dev, a.data, a.stride, a.cap, b.data, b.stride, b.cap, d, nl);
+    return SECPE_OK;
+}
+
+int launch_tensor2(secpe_ctx *ctx, const CtB &a, const CtB &b, const CtB &c, const CtB &e, u64 *d, int nl) {
+    if (a.B != b.B || a.B != c.B || a.B != e.B) return SECPE_EINVAL;
+    KprofScope kp(ctx, "ew_tensor2", 88.0 * ctx->n * a.B * nl);
+    Tensor2Args t;
+    const CtB *src[4] = {&a, &b, &c, &e};
+    for (int k = 0; k < 4; k++) {
+        t.p[k] = src[k]->data;
+        t.s[k] = src[k]->stride;
+        t.cap[k] = src[k]->cap;
+    }
+    t.d = d;
+    t.nl = nl;
+    const dim3 grid((unsigned)((ctx->n + 2047) / 2048), (unsigned)((long long)a.B * nl));
+    SECPE_LAUNCH(ctx, k_tensor2, grid, 256, 0, ctx->dev, t);
     return SECPE_OK;
 }
 

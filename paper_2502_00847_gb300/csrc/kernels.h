@@ -21,6 +21,8 @@ struct PrimeList {
 
 int launch_addsub(secpe_ctx *ctx, const CtB &a, const CtB &b, const CtB &o, int nl, bool sub, int npoly = 2);
 int launch_tensor(secpe_ctx *ctx, const CtB &a, const CtB &b, u64 *d, int nl);
+// d = a (x) b + c (x) e in one pass (3-component output, limbs 0..nl-1)
+int launch_tensor2(secpe_ctx *ctx, const CtB &a, const CtB &b, const CtB &c, const CtB &e, u64 *d, int nl);
 // Item q of dst (limbs 0..nl-1 of both polynomials) = the sum of the
 // ciphertexts src[qoff[q] .. qoff[q+1]) (each [2][cap[p]][N]); queries are
 // launched in chunks that fit one pointer table.

@@ -226,26 +226,46 @@ struct BConv32Args {
     uint32_t m32[kMaxOut32];          // floor(2^32 / p_j)
 };
 
-// One thread per coefficient of one item (grid: N/256 x batch).
+// Four adjacent coefficients of one item per thread (grid: N/1024 x batch):
+// 16-byte loads and stores, and each constant [Qhat_i]_{p_j}, staged in
+// shared memory, serves four products.
 __global__ void __launch_bounds__(256) k_bconv32(const __grid_constant__ BConv32Args a) {
-    const int c = blockIdx.x * 256 + threadIdx.x;
+    __shared__ uint32_t Ms[kMaxIn32 * kMaxOut32];
+    for (int e = threadIdx.x; e < a.n_in * a.n_out; e += 256) Ms[e] = a.M[e / a.n_out][e % a.n_out];
+    __syncthreads();
+    const int c = (blockIdx.x * 256 + threadIdx.x) * 4;
     const size_t item = blockIdx.y;
     const uint32_t *__restrict__ in = a.in + item * a.n_in * 65536 + c;
     uint32_t *__restrict__ out = a.out + item * a.n_out * 65536 + c;
-    uint32_t y[kMaxIn32];
+    uint32_t y[kMaxIn32][4];
 #pragma unroll
-    for (int i = 0; i < kMaxIn32; i++)
-        if (i < a.n_in) y[i] = red2_32(shoup32(in[(size_t)i * 65536], a.qhinv[i].x, a.qhinv[i].y, a.qin[i]), a.qin[i]);
+    for (int i = 0; i < kMaxIn32; i++) {
+        if (i >= a.n_in) break;
+        const uint4 v = *reinterpret_cast<const uint4 *>(in + (size_t)i * 65536);
+        const uint32_t qi = a.qin[i], w = a.qhinv[i].x, wp = a.qhinv[i].y;
+        y[i][0] = red2_32(shoup32(v.x, w, wp, qi), qi);
+        y[i][1] = red2_32(shoup32(v.y, w, wp, qi), qi);
+        y[i][2] = red2_32(shoup32(v.z, w, wp, qi), qi);
+        y[i][3] = red2_32(shoup32(v.w, w, wp, qi), qi);
+    }
     for (int j = 0; j < a.n_out; j++) {
-        unsigned long long acc = 0;
+        unsigned long long acc[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int i = 0; i < kMaxIn32; i++)
-            if (i < a.n_in) acc += (unsigned long long)y[i] * a.M[i][j];
-        const uint32_t p = a.p[j];
-        // acc = hi 2^32 + lo: [hi 2^32]_p by Shoup (in [0, 2p)), lo - floor(lo m / 2^32) p in [0, 2p)
-        const uint32_t hi = (uint32_t)(acc >> 32), lo = (uint32_t)acc;
-        const uint32_t r = shoup32(hi, a.r32[j].x, a.r32[j].y, p) + (lo - __umulhi(lo, a.m32[j]) * p);
-        out[(size_t)j * 65536] = red4_32(r, p);
+        for (int i = 0; i < kMaxIn32; i++) {
+            if (i >= a.n_in) break;
+            const unsigned long long m = Ms[i * a.n_out + j];
+#pragma unroll
+            for (int b = 0; b < 4; b++) acc[b] += y[i][b] * m;
+        }
+        const uint32_t p = a.p[j], rw = a.r32[j].x, rwp = a.r32[j].y, m32 = a.m32[j];
+        uint32_t r[4];
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            // acc = hi 2^32 + lo: [hi 2^32]_p by Shoup (in [0, 2p)), lo - floor(lo m / 2^32) p in [0, 2p)
+            const uint32_t hi = (uint32_t)(acc[b] >> 32), lo = (uint32_t)acc[b];
+            r[b] = red4_32(shoup32(hi, rw, rwp, p) + (lo - __umulhi(lo, m32) * p), p);
+        }
+        *reinterpret_cast<uint4 *>(out + (size_t)j * 65536) = make_uint4(r[0], r[1], r[2], r[3]);
     }
 }
 
@@ -380,6 +400,6 @@ extern "C" int secpe_bconv32(const secpe_ntt32_table *t, const uint32_t *in, con
         a.r32[j] = make_uint2(r, shoup32_host(r, pj));
         a.m32[j] = (uint32_t)((1ull << 32) / pj);
     }
-    k_bconv32<<<dim3(t->n / 256, batch), 256, 0, (cudaStream_t)stream>>>(a);
+    k_bconv32<<<dim3(t->n / 1024, batch), 256, 0, (cudaStream_t)stream>>>(a);
     return cudaGetLastError() == cudaSuccess ? SECPE_OK : SECPE_ECUDA;
 }

@@ -240,19 +240,32 @@ __global__ void __launch_bounds__(256, 3) k_rowpass_ip(const __grid_constant__ I
             __syncthreads();
         }
         const u64 *src = a.d + item * a.dis + (long long)t * a.c.n + tile_off;
-#pragma unroll 4
-        for (int i = 0; i < 16; i++) {
-            const int e = threadIdx.x + 256 * i;
-            const u64 v = own ? src[e] : sm[(e >> 8) * 272 + PADR(e & 255)];
-            const u64 k0 = kb[e], k1 = kb[kpoly + e];
-            u64 p0 = mont_mul(v, k0, q, qinv);
-            u64 p1 = mont_mul(v, k1, q, qinv);
-            if (jd) {
-                p0 = add_mod(p0, o0[e], q);
-                p1 = add_mod(p1, o1[e], q);
+        // four elements at a time: every load of the group is issued before
+        // the first product, so up to 20 loads per thread are in flight
+#pragma unroll
+        for (int i0 = 0; i0 < 16; i0 += 4) {
+            u64 v[4], k0[4], k1[4], a0[4], a1[4];
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                const int e = threadIdx.x + 256 * (i0 + b);
+                v[b] = own ? src[e] : sm[(e >> 8) * 272 + PADR(e & 255)];
+                k0[b] = kb[e];
+                k1[b] = kb[kpoly + e];
+                a0[b] = jd ? o0[e] : 0;
+                a1[b] = jd ? o1[e] : 0;
             }
-            o0[e] = p0;
-            o1[e] = p1;
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                const int e = threadIdx.x + 256 * (i0 + b);
+                u64 p0 = mont_mul(v[b], k0[b], q, qinv);
+                u64 p1 = mont_mul(v[b], k1[b], q, qinv);
+                if (jd) {
+                    p0 = add_mod(p0, a0[b], q);
+                    p1 = add_mod(p1, a1[b], q);
+                }
+                o0[e] = p0;
+                o1[e] = p1;
+            }
         }
         if (!own) __syncthreads();
     }
