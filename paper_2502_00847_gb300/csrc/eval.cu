@@ -94,12 +94,12 @@ int Eval::sub(const Ct &a, const Ct &b, Ct &out) {
     return SECPE_OK;
 }
 
-int Eval::rescale(const Ct &in, Ct &out) {
+int Eval::rescale(const Ct &in, Ct &out, const long long *add_k) {
     const int lv = in.level();
     if (lv < 1) return SECPE_ELEVEL;
     Ct o;
     SECPE_CHECK(ct_alloc(ctx, in.B(), lv - 1, in.scale() / (double)ctx->primes[lv], o));
-    SECPE_CHECK(rescale_batch(ctx, in.v, o.v));
+    SECPE_CHECK(rescale_batch(ctx, in.v, o.v, add_k));
     out = o;
     return SECPE_OK;
 }
@@ -190,7 +190,7 @@ int Eval::mul_const(const Ct &x, const std::vector<double> &c, double target, in
 // to out_level + 1 and multiplied by k_t = round(c_t target / s_t q),
 // q = q_{out_level+1}; the products are added and the sum rescaled once.
 int Eval::lincomb(const std::vector<const Ct *> &xs, const std::vector<std::vector<double>> &cs, double target,
-                  int out_level, Ct &out) {
+                  int out_level, Ct &out, const double *add_c) {
     const int nt = (int)xs.size();
     if (nt < 1 || nt > 2 || (int)cs.size() != nt) return SECPE_EINVAL;
     if (out_level < ctx->p.reserve || out_level < 0 || out_level + 1 > ctx->L) return SECPE_ELEVEL;
@@ -214,7 +214,14 @@ int Eval::lincomb(const std::vector<const Ct *> &xs, const std::vector<std::vect
     Ct tsum;
     SECPE_CHECK(ct_alloc(ctx, B, out_level + 1, target * qf, tsum));
     SECPE_CHECK(launch_lincomb(ctx, v, k, nt, tsum.v, out_level + 2));
-    SECPE_CHECK(rescale(tsum, out));
+    long long ka = 0;
+    if (add_c) {
+        // add_const's constant at the result's scale (target)
+        const double va = *add_c * target;
+        if (!(std::fabs(va) < 4.0e18)) return SECPE_EINVAL;
+        ka = hm::round_half_away(va);
+    }
+    SECPE_CHECK(rescale(tsum, out, add_c ? &ka : nullptr));
     out.v.scale = target;
     return SECPE_OK;
 }
@@ -402,20 +409,18 @@ int Eval::poly9(const Ct &x, const double *c, double s_out, Ct &out) {
     if (lv < 4 + ctx->p.reserve) return SECPE_ELEVEL;
     const double q3 = (double)ctx->primes[lv - 3];
     // temporaries are released as soon as they are dead (Ct() frees them)
-    Ct x2, x4, x5, L1, P1, L0, P0, TU3;
+    Ct x2, x4, x5, P1, P0, TU3;
     SECPE_CHECK(mul(x, x, x2));
     SECPE_CHECK(mul(x2, x2, x4));
     SECPE_CHECK(mul(x4, x, x5));
     const double s1 = s_out * q3 / x5.scale();
-    SECPE_CHECK(lincomb({&x2, &x4}, {{c[3]}, {c[4]}}, s1, lv - 3, L1));
+    // P1 = c7 x2 + c9 x4 + c5 and P0 = c3 x2 + c1, each constant added in the
+    // rescale's last pass (the same residues as a separate add_const)
+    SECPE_CHECK(lincomb({&x2, &x4}, {{c[3]}, {c[4]}}, s1, lv - 3, P1, &c[2]));
     x4 = Ct();
-    SECPE_CHECK(add_const(L1, c[2], P1));
-    L1 = Ct();
     const double s0 = x5.scale() * s1 / x.scale();
-    SECPE_CHECK(lincomb({&x2}, {{c[1]}}, s0, lv - 3, L0));
+    SECPE_CHECK(lincomb({&x2}, {{c[1]}}, s0, lv - 3, P0, &c[0]));
     x2 = Ct();
-    SECPE_CHECK(add_const(L0, c[0], P0));
-    L0 = Ct();
     SECPE_CHECK(tensor2(x5, P1, x, P0, TU3));
     x5 = Ct();
     P1 = Ct();

@@ -87,10 +87,11 @@ struct Eval {
     int add3(const Ct &a3, const Ct &b3, Ct &out3);
     int relin_rescale(const Ct &d3, Ct &out);
     int mul_const(const Ct &x, const std::vector<double> &c, double target, int out_level, Ct &out);
+    // add_c: optional constant added to the result (as add_const, in the rescale's last pass)
     int lincomb(const std::vector<const Ct *> &xs, const std::vector<std::vector<double>> &cs, double target,
-                int out_level, Ct &out);
+                int out_level, Ct &out, const double *add_c = nullptr);
     int add_const(const Ct &x, double c, Ct &out);
-    int rescale(const Ct &in, Ct &out);
+    int rescale(const Ct &in, Ct &out, const long long *add_k = nullptr);
     int rotate(const Ct &x, int steps, Ct &out);
     int refresh(const Ct &x, Ct &out);
     int ensure(const Ct &x, int k, Ct &out);
@@ -126,7 +127,7 @@ int keyswitch(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int 
 int keyswitch_acc(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, int lv, const u64 *key, DevBuf &acc);
 // Relinearise the 3-component tensor d [B][3][lv+1][N] and rescale: out at lv-1.
 int relin_rescale_batch(secpe_ctx *ctx, const u64 *d, int B, int lv, const u64 *key, const CtB &out);
-int rescale_batch(secpe_ctx *ctx, const CtB &in, const CtB &out);
+int rescale_batch(secpe_ctx *ctx, const CtB &in, const CtB &out, const long long *add_k = nullptr);
 unsigned galois_elt(const secpe_ctx *ctx, int steps);
 const u64 *galois_key(const secpe_keys *keys, unsigned g);
 int sign_coeffs(double g[5], double f[5]);
@@ -137,4 +138,6 @@ int modup_ip_fused(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const 
                    const KsDigits &dg, int tot, const u64 *key, u64 *ext, u64 *acc);
 int moddown_fused(secpe_ctx *ctx, const u64 *acc, int B, int lv, const CtB &out, bool acc0, bool acc1, u64 *tmp);
 int moddown_rescale_fused(secpe_ctx *ctx, u64 *acc, const u64 *d, int B, int lv, const CtB &out, u64 *tmp);
-int rescale_fused(secpe_ctx *ctx, const CtB &in, const u64 *y, const CtB &out, u64 *tmp);
+// add_k: optional constant k added to polynomial 0 of the result (a constant polynomial, as add_const)
+int rescale_fused(secpe_ctx *ctx, const CtB &in, const u64 *y, const CtB &out, u64 *tmp,
+                  const long long *add_k = nullptr);

@@ -111,7 +111,7 @@ int relin_rescale_batch(secpe_ctx *ctx, const u64 *d, int B, int lv, const u64 *
     return launch_mdr_fin(ctx, acc.u(), tmp.u(), d, dis, dps, out, lv);
 }
 
-int rescale_batch(secpe_ctx *ctx, const CtB &in, const CtB &out) {
+int rescale_batch(secpe_ctx *ctx, const CtB &in, const CtB &out, const long long *add_k) {
     const int lv = in.level, n = ctx->n, B = in.B;
     if (lv < 1) return SECPE_ELEVEL;
     DevBuf y, z;
@@ -121,10 +121,11 @@ int rescale_batch(secpe_ctx *ctx, const CtB &in, const CtB &out) {
     LimbSet ydst = make_limbset(y.u(), B, 2ll * n, 2, n, 1, lv);
     // (charged the input's last limbs, read once)
     SECPE_CHECK(ntt_limbset(ctx, ydst, true, &ysrc, nullptr, 0, 8.0 * n));
-    if (fused_path(ctx)) return rescale_fused(ctx, in, y.u(), out, z.u());
+    if (fused_path(ctx)) return rescale_fused(ctx, in, y.u(), out, z.u(), add_k);
     SECPE_CHECK(launch_rescale_prep(ctx, y.u(), z.u(), B, lv));
     LimbSet zls = make_limbset(z.u(), B, 2ll * lv * n, 2, (long long)lv * n, lv, 0);
     SECPE_CHECK(ntt_limbset(ctx, zls, false));
     SECPE_CHECK(launch_rescale_fin(ctx, in, z.u(), out, lv));
+    if (add_k) SECPE_CHECK(launch_addconst(ctx, out, out, lv, std::vector<long long>(1, *add_k)));
     return SECPE_OK;
 }

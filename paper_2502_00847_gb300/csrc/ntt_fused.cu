@@ -99,6 +99,8 @@ struct EpiArgs {
     const u64 *Y;         // optional: + Y * w2 (Y limb i at Y + item*yis + poly*yps + i*N)
     long long yis, yps;
     const ulonglong2 *w2;
+    int has_cadd;         // optional: + cadd[target prime] on polynomial 0 (a constant polynomial)
+    u64 cadd[SECPE_MAX_PRIMES];
 };
 
 // Dynamic shared memory: the padded transform tile (16 x 272 words), the
@@ -159,6 +161,7 @@ __global__ void __launch_bounds__(256, 3) k_rowpass_epi(const __grid_constant__ 
     u64 *__restrict__ O = a.out + item * a.ois + poly * a.ops + (long long)j * a.c.n + (size_t)r0 * 256;
     const ulonglong2 w = a.w[tp];
     const bool acc = poly == 0 ? a.acc0 : a.acc1;
+    const u64 cadd = (a.has_cadd && poly == 0) ? a.cadd[tp] : 0;
     if (a.Y) {
         const u64 *__restrict__ Y = a.Y + item * a.yis + poly * a.yps + (long long)j * a.c.n + (size_t)r0 * 256;
         const ulonglong2 w2 = a.w2[tp];
@@ -167,7 +170,9 @@ __global__ void __launch_bounds__(256, 3) k_rowpass_epi(const __grid_constant__ 
             const int e = threadIdx.x + 256 * i;
             const int r = e >> 8, p = e & 255;
             const u64 v = sm[r * 272 + PADR(p)];
-            O[e] = add_mod(mul_shoup(sub_mod(xs[e], v, q), w.x, w.y, q), mul_shoup(Y[e], w2.x, w2.y, q), q);
+            u64 res = add_mod(mul_shoup(sub_mod(xs[e], v, q), w.x, w.y, q), mul_shoup(Y[e], w2.x, w2.y, q), q);
+            if (cadd) res = add_mod(res, cadd, q);
+            O[e] = res;
         }
         return;
     }
@@ -178,6 +183,7 @@ __global__ void __launch_bounds__(256, 3) k_rowpass_epi(const __grid_constant__ 
         const u64 v = sm[r * 272 + PADR(p)];
         u64 res = mul_shoup(sub_mod(xs[e], v, q), w.x, w.y, q);
         if (acc) res = add_mod(res, O[e], q);
+        if (cadd) res = add_mod(res, cadd, q);
         O[e] = res;
     }
 }
@@ -453,7 +459,8 @@ int modup_ip_fused(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const 
 // (the profiler charges it as algorithmic bytes only then).
 int bconv_ntt_epi(secpe_ctx *ctx, const BConvSrc &S, int B, int nl, u64 *tmp, const u64 *X, long long xis,
                   long long xps, const CtB &out, const ulonglong2 *w, bool acc0, bool acc1, bool x_input,
-                  const u64 *Y = nullptr, long long yis = 0, long long yps = 0, const ulonglong2 *w2 = nullptr) {
+                  const u64 *Y = nullptr, long long yis = 0, long long yps = 0, const ulonglong2 *w2 = nullptr,
+                  const long long *add_k = nullptr) {
     const int n = ctx->n;
     BConvArgs a;
     a.c = ctx->dev;
@@ -477,6 +484,16 @@ int bconv_ntt_epi(secpe_ctx *ctx, const BConvSrc &S, int B, int nl, u64 *tmp, co
     ep.yis = yis;
     ep.yps = yps;
     ep.w2 = w2;
+    ep.has_cadd = add_k ? 1 : 0;
+    if (add_k) {
+        // the constant k as a residue of every output prime (output limb j is prime j)
+        if (nl > SECPE_MAX_PRIMES) return SECPE_EINVAL;
+        for (int j = 0; j < nl; j++) {
+            const u64 q = ctx->primes[j];
+            const u64 m = (u64)(*add_k < 0 ? -(*add_k) : *add_k) % q;
+            ep.cadd[j] = (*add_k < 0 && m) ? q - m : m;
+        }
+    }
     const long long nlimbs = (long long)B * 2 * nl;
     // algorithmic per item: the output (2 nl limbs), X when it is an input,
     // the accumulated output polynomials' old values, and Y with the two
@@ -528,7 +545,7 @@ int moddown_fused(secpe_ctx *ctx, const u64 *acc, int B, int lv, const CtB &out,
 }
 
 // Rescale of `in` by q_l into out, y = INTT of the last limb [B][2][N].
-int rescale_fused(secpe_ctx *ctx, const CtB &in, const u64 *y, const CtB &out, u64 *tmp) {
+int rescale_fused(secpe_ctx *ctx, const CtB &in, const u64 *y, const CtB &out, u64 *tmp, const long long *add_k) {
     const int n = ctx->n, lv = in.level;
     BConvSrc S;
     S.base = y;
@@ -541,7 +558,7 @@ int rescale_fused(secpe_ctx *ctx, const CtB &in, const u64 *y, const CtB &out, u
     S.hat_stride = 0;
     S.post = ctx->dev.rs_hmod + (size_t)lv * ctx->nq;
     return bconv_ntt_epi(ctx, S, in.B, lv, tmp, in.data, in.stride, in.pstride(), out,
-                         ctx->dev.rs_qinv + (size_t)lv * ctx->nq, false, false, true);
+                         ctx->dev.rs_qinv + (size_t)lv * ctx->nq, false, false, true, nullptr, 0, 0, nullptr, add_k);
 }
 
 // Relinearisation's ModDown fused with the rescale: acc [B][2][nt][N] from
