@@ -779,8 +779,8 @@ def run_boot(secpe, torch, dev, refresh, n=128, batches=(1, 16)):
     bt = secpe.Boot(ctx, n)
     t_plan = time.perf_counter() - t0
     rng = np.random.default_rng(16)
-    out = {"params": "boot16: N=2^16, q0 50-bit, 7x40-bit computation + 16x60-bit bootstrapping primes, "
-                     "6 special 60-bit, dnum=6, sparse secret h=32", "block_slots": n,
+    out = {"params": "boot16: N=2^16, q0 50-bit, 10x40-bit computation + 16x60-bit bootstrapping primes, "
+                     "5 special 60-bit, dnum=7, sparse secret h=32", "block_slots": n,
            "levels_consumed": 16, "output_level": ctx.L - 16, "plan_s": t_plan}
     for B in batches:
         vs = rng.uniform(-1, 1, (B, n // 2))
@@ -866,7 +866,7 @@ def run_noninteractive(secpe, torch, workloads, dev, n_queries, n=128):
     return {"value": n_queries / (ms / 1e3), "unit": "queries/s", "queries": n_queries, "ms": ms,
             "bootstraps_per_query": cnt["bootstraps"] / n_queries, "relins_per_query": cnt["relins"] / n_queries,
             "correct_indices": ok,
-            "workload": "the first %d queries of the mix on boot16 (Delta = 2^40, 7 computation levels between "
+            "workload": "the first %d queries of the mix on boot16 (Delta = 2^40, 10 computation levels between "
                         "bootstraps), inputs packed 2C'-periodic, every refresh a batched bootstrap" % n_queries}
 
 

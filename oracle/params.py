@@ -181,10 +181,13 @@ ARGMAX8 = Params(log_n=16, q0_bits=60, q_bits=50, n_q=24, p_bits=60, n_p=8,
 # (near 2^60) stay at the primes' size; a sparse secret of weight 32 bounds
 # the ModRaise overflow by 16.5; 60-bit special primes, n_p > alpha, so that P
 # exceeds every digit by a whole prime or more and key switching adds only
-# rounding noise to the 2^60-sized labels (log2 QP = 1630 at N = 2^16).
+# rounding noise to the 2^60-sized labels.  BOOT16 leaves 10 computation
+# levels above q0 after a bootstrap (two Sign polynomials of 4 levels plus
+# the reserve) within log2 QP = 1715 <= 1763 at N = 2^16: 27 ciphertext
+# primes, 5 special, 7 digits of at most 4 primes.
 BOOT_TOY = Params(log_n=12, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=4, dnum=8,
                   log_scale=40, secret_hw=32, boot_primes=16, boot_bits=60)
-BOOT16 = Params(log_n=16, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=6, dnum=6,
+BOOT16 = Params(log_n=16, q0_bits=50, q_bits=40, n_q=27, p_bits=60, n_p=5, dnum=7,
                 log_scale=40, secret_hw=32, boot_primes=16, boot_bits=60)
 # WORD32: the word-size probe's primes: 48 + 8 primes of about 29 bits
 # (below 2^30, so Harvey's lazy butterflies fit 32-bit words), a modulus of

@@ -44,7 +44,7 @@ ARGMAX8 = ParamSet(log_n=16, q0_bits=60, q_bits=50, n_q=24, p_bits=60, n_p=8, dn
 # weight 32 (boot_toy N = 2^12, boot16 N = 2^16).
 BOOT_TOY = ParamSet(log_n=12, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=4, dnum=8, log_scale=40,
                     secret_hw=32, boot_primes=16, boot_bits=60)
-BOOT16 = ParamSet(log_n=16, q0_bits=50, q_bits=40, n_q=24, p_bits=60, n_p=6, dnum=6, log_scale=40,
+BOOT16 = ParamSet(log_n=16, q0_bits=50, q_bits=40, n_q=27, p_bits=60, n_p=5, dnum=7, log_scale=40,
                   secret_hw=32, boot_primes=16, boot_bits=60)
 # The word-size probe's prime chain: 48 + 8 primes of about 29 bits (below
 # 2^30), for the 32-bit transform and base conversion only.
