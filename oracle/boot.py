@@ -148,10 +148,12 @@ class BootPlan:
     def _bsgs(self, inputs, diags, bs, gs, key, pt_scale, out_scale=None):
         """sum_k diag_k (.) RotL(x, k) over the inputs (x, diagonals) as
         sum_g RotL(sum_b RotR(diag_{g bs + b}, g bs) (.) RotL(x, b), g bs),
-        every inner sum rescaled once; plaintexts at pt_scale."""
+        every inner sum rescaled once; plaintexts at pt_scale; the baby steps
+        RotL(x, b) of one input by rotate_hoisted."""
         o = self.o
         lv = inputs[0][0].level
-        baby = [[x if b == 0 else o.rotate(x, b) for b in range(bs)] for x, _ in inputs]
+        # the baby steps of one input share one ModUp (hoisting)
+        baby = [[x] + o.rotate_hoisted(x, list(range(1, bs))) for x, _ in inputs]
         total = None
         for g in range(gs):
             acc = np.zeros((2, lv + 1, o.n), dtype=np.uint64)

@@ -433,6 +433,65 @@ class Oracle:
                 acc1[t] = self.vadd(acc1[t], self.vmul(ext[t], ksk[j, 1, t], t), t)
         return acc0, acc1
 
+    def modup_ext(self, d, level):
+        """ModUp of d (NTT form, limbs 0..level) as keyswitch_acc computes
+        it: per digit j, ext[j][t] (NTT form) for every prime t of Q_l u P
+        outside the digit, by FastBConv of the digit's INTT (no correction)."""
+        q_idx = list(range(level + 1))
+        tgt = q_idx + self.ctx.special_idx()
+        coef = d.copy()
+        for pi in q_idx:
+            self.intt(coef[pi], pi)
+        exts = []
+        for dig in self.ctx.digits(level):
+            others = [t for t in tgt if t not in dig]
+            conv = self.fast_bconv(np.stack([coef[pi] for pi in dig]), dig, others)
+            ext = {}
+            for r, t in enumerate(others):
+                x = conv[r].copy()
+                self.ntt(x, t)
+                ext[t] = x
+            exts.append(ext)
+        return exts
+
+    def rotate_hoisted(self, ct, rs):
+        """READING (hoisting; the paper does not describe bootstrapping, whose
+        linear transforms rotate one ciphertext by many steps): RotL(ct, r)
+        for every r in rs from one ModUp of c1.  For each r the automorphism
+        X -> X^g goes onto c0, onto c1 (each digit's own limbs) and onto every
+        extended limb, then come the inner product with the Galois key and
+        ModDown.  The automorphism of an extended limb differs from the ModUp
+        of the automorphism only by the multiple of the digit modulus that
+        FastBConv leaves, permuted (same size), so each result is a key
+        switching of sigma_g(c1) with the same noise bound as rotate's."""
+        lv = ct.level
+        exts = self.modup_ext(ct.c[1], lv)
+        tgt = list(range(lv + 1)) + self.ctx.special_idx()
+        outs = []
+        for r in rs:
+            g = self.galois(r)
+            if g not in self.gks:
+                raise KeyError("missing Galois key for rotation %d" % r)
+            self.counters["rotations"] += 1
+            self.counters["keyswitches"] += 1
+            ksk = self.gks[g]
+            t0 = np.stack([self.automorph_ntt(ct.c[0, pi], pi, g) for pi in range(lv + 1)])
+            t1 = np.stack([self.automorph_ntt(ct.c[1, pi], pi, g) for pi in range(lv + 1)])
+            acc0 = {t: np.zeros(self.n, dtype=U64) for t in tgt}
+            acc1 = {t: np.zeros(self.n, dtype=U64) for t in tgt}
+            for j, dig in enumerate(self.ctx.digits(lv)):
+                for t in tgt:
+                    x = t1[t] if t in dig else self.automorph_ntt(exts[j][t], t, g)
+                    acc0[t] = self.vadd(acc0[t], self.vmul(x, ksk[j, 0, t], t), t)
+                    acc1[t] = self.vadd(acc1[t], self.vmul(x, ksk[j, 1, t], t), t)
+            k0, k1 = self.moddown(acc0, lv), self.moddown(acc1, lv)
+            c = np.empty((2, lv + 1, self.n), dtype=U64)
+            for pi in range(lv + 1):
+                c[0, pi] = self.vadd(t0[pi], k0[pi], pi)
+                c[1, pi] = k1[pi]
+            outs.append(Ct(c, lv, ct.scale))
+        return outs
+
     def keyswitch(self, d, level, ksk):
         """Hybrid key switching of d with key ksk: ModUp, inner product, then
         ModDown (rounded division by P)."""

@@ -178,12 +178,13 @@ int bsgs(Eval &E, const std::vector<Ct> &xs, const u64 *pts, int ndiag, int bs, 
     const size_t plane = (size_t)(lv + 1) * ctx->n;
     std::vector<std::vector<Ct>> baby(xs.size());
     for (size_t t = 0; t < xs.size(); t++) {
+        // the baby steps of one input share one ModUp (hoisting)
+        std::vector<int> steps;
+        for (int b = 1; b < bs; b++) steps.push_back(b);
+        std::vector<Ct> r;
+        SECPE_CHECK(E.rotate_hoisted(xs[t], steps, r));
         baby[t].push_back(xs[t]);
-        for (int b = 1; b < bs; b++) {
-            Ct r;
-            SECPE_CHECK(E.rotate(xs[t], b, r));
-            baby[t].push_back(r);
-        }
+        for (Ct &c : r) baby[t].push_back(c);
     }
     Ct total;
     for (int g = 0; g < gs; g++) {

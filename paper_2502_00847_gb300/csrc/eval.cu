@@ -251,6 +251,29 @@ int Eval::rotate(const Ct &x, int steps, Ct &out) {
     return SECPE_OK;
 }
 
+int Eval::rotate_hoisted(const Ct &x, const std::vector<int> &steps, std::vector<Ct> &outs) {
+    std::vector<unsigned> gal;
+    std::vector<const u64 *> ks;
+    std::vector<CtB> ov;
+    outs.clear();
+    for (int st : steps) {
+        const unsigned g = galois_elt(ctx, st);
+        const u64 *key = keys ? galois_key(keys, g) : nullptr;
+        if (!key) return SECPE_EKEY;
+        gal.push_back(g);
+        ks.push_back(key);
+    }
+    for (size_t i = 0; i < steps.size(); i++) {
+        Ct o;
+        SECPE_CHECK(ct_alloc(ctx, x.B(), x.level(), x.scale(), o));
+        ov.push_back(o.v);
+        outs.push_back(o);
+    }
+    SECPE_CHECK(::rotate_hoisted(ctx, x.v, gal, ks, ov));
+    ctx->counters.rotations += (unsigned long long)x.B() * steps.size();
+    return SECPE_OK;
+}
+
 int Eval::refresh(const Ct &x, Ct &out) {
     if (ctx->boot) {
         // non-interactive: a bootstrap of the batch replaces the stand-in

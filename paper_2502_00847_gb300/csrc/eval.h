@@ -93,6 +93,8 @@ struct Eval {
     int add_const(const Ct &x, double c, Ct &out);
     int rescale(const Ct &in, Ct &out, const long long *add_k = nullptr);
     int rotate(const Ct &x, int steps, Ct &out);
+    // rotations of x by every step, sharing one ModUp (bootstrapping's baby steps)
+    int rotate_hoisted(const Ct &x, const std::vector<int> &steps, std::vector<Ct> &outs);
     int refresh(const Ct &x, Ct &out);
     int ensure(const Ct &x, int k, Ct &out);
     int poly9(const Ct &x, const double *c, double s_out, Ct &out);
@@ -128,6 +130,10 @@ int keyswitch_acc(secpe_ctx *ctx, const u64 *d, long long d_item_stride, int B, 
 // Relinearise the 3-component tensor d [B][3][lv+1][N] and rescale: out at lv-1.
 int relin_rescale_batch(secpe_ctx *ctx, const u64 *d, int B, int lv, const u64 *key, const CtB &out);
 int rescale_batch(secpe_ctx *ctx, const CtB &in, const CtB &out, const long long *add_k = nullptr);
+// Rotations of x by every Galois element gal[i] with keys[i] into outs[i]
+// (B items, level of x), sharing one ModUp of x's second polynomial.
+int rotate_hoisted(secpe_ctx *ctx, const CtB &x, const std::vector<unsigned> &gal, const std::vector<const u64 *> &keys,
+                   const std::vector<CtB> &outs);
 unsigned galois_elt(const secpe_ctx *ctx, int steps);
 const u64 *galois_key(const secpe_keys *keys, unsigned g);
 int sign_coeffs(double g[5], double f[5]);

@@ -262,6 +262,19 @@ __global__ void k_automorph(DevCtx c, const u64 *x, long long xs, int cap_x, u64
     o[item * os + ((long long)kk * cap_o + i) * c.n + j] = x[item * xs + ((long long)kk * cap_x + i) * c.n + src];
 }
 
+// The same permutation on contiguous limbs [count][N] (any primes: it only
+// moves residues).
+__global__ void k_automorph_flat(DevCtx c, const u64 *x, u64 *o, unsigned g) {
+    const long long li = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= c.n) return;
+    const unsigned sh = 32 - c.log_n;
+    const unsigned ev = 2u * (__brev((unsigned)j) >> sh) + 1u;
+    const unsigned e2 = (unsigned)(((unsigned long long)ev * g) & (2ull * c.n - 1));
+    const unsigned src = __brev((e2 - 1u) >> 1) >> sh;
+    o[li * c.n + j] = x[li * c.n + src];
+}
+
 // ------------------------------------------------------------ rescale
 // y: coefficient form of the last limb (level l) of both polys, [item][2][N].
 // z[item][2][i] = ([y + h]_{q_l} - h) mod q_i for i < l (coefficient form).
@@ -816,6 +829,14 @@ int launch_addconst(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, const st
 int launch_automorph(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, unsigned g) {
     SECPE_LAUNCH(ctx, k_automorph, limb_grid(ctx->n, 1, (long long)x.B * 2 * nl), 256, 0, ctx->dev, x.data,
                  x.stride, x.cap, o.data, o.stride, o.cap, nl, g);
+    return SECPE_OK;
+}
+
+int launch_automorph_flat(secpe_ctx *ctx, const u64 *x, u64 *o, long long nlimbs, unsigned g) {
+    if (nlimbs <= 0) return SECPE_OK;
+    if (nlimbs > 65535) return SECPE_EINVAL;
+    KprofScope kp(ctx, "ew_automorph", 16.0 * ctx->n * nlimbs);
+    SECPE_LAUNCH(ctx, k_automorph_flat, limb_grid(ctx->n, 1, nlimbs), 256, 0, ctx->dev, x, o, g);
     return SECPE_OK;
 }
 

@@ -33,6 +33,8 @@ int launch_sum_cts(secpe_ctx *ctx, const std::vector<const u64 *> &src, const st
 int launch_lincomb(secpe_ctx *ctx, const CtB *xs, const std::vector<long long> *ks, int nt, const CtB &o, int nl);
 int launch_addconst(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, const std::vector<long long> &k);
 int launch_automorph(secpe_ctx *ctx, const CtB &x, const CtB &o, int nl, unsigned g);
+// the automorphism on nlimbs contiguous limbs [nlimbs][N] (NTT form)
+int launch_automorph_flat(secpe_ctx *ctx, const u64 *x, u64 *o, long long nlimbs, unsigned g);
 int launch_rescale_prep(secpe_ctx *ctx, const u64 *y, u64 *z, int B, int lv);
 int launch_rescale_fin(secpe_ctx *ctx, const CtB &x, const u64 *z, const CtB &o, int lv);
 int launch_modup_bconv(secpe_ctx *ctx, const u64 *x, u64 *ext, long long ext_item_stride, int ext_off,

@@ -106,6 +106,28 @@ def test_rotation_direction(toy_oracle):
         o.rotate(ct, 5)
 
 
+def test_hoisted_rotations(toy_oracle):
+    """Rotations sharing one ModUp (bootstrapping's baby steps) rotate the
+    slots like rotate does, and within the linear tolerance of rotate's
+    result; each of them also decrypts to the rotated vector at a lower level."""
+    o = toy_oracle
+    v = np.random.default_rng(5).uniform(-1, 1, 24)
+    full = np.zeros(o.n // 2)
+    full[:24] = v
+    ct = o.encrypt(v, seed=15)
+    outs = o.rotate_hoisted(ct, [1, 2, -2, -4])
+    for r, c in zip([1, 2, -2, -4], outs):
+        assert c.level == ct.level and c.scale == ct.scale
+        got = o.decrypt(c, 40)
+        assert np.max(np.abs(got - np.roll(full, -r)[:40])) < TOL_LINEAR
+        assert np.max(np.abs(got - o.decrypt(o.rotate(ct, r), 40))) < TOL_LINEAR
+    low = o.drop(ct, 3)
+    (c,) = o.rotate_hoisted(low, [1])
+    assert np.max(np.abs(o.decrypt(c, 40) - np.roll(full, -1)[:40])) < TOL_LINEAR
+    with pytest.raises(KeyError):
+        o.rotate_hoisted(ct, [5])
+
+
 def test_rescale_is_rounded_division(toy_oracle):
     o = toy_oracle
     ct = o.encrypt(np.linspace(-1, 1, 8), seed=14)
