@@ -288,6 +288,16 @@ int secpe_rescale_noalloc(secpe_ctx *ctx, const secpe_ct *in, secpe_ct *out, voi
  * SECPE_EKEY when the key was not generated. */
 int secpe_rotate(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *in, int steps,
                  secpe_ct *out, void *stream);
+/* Rotations of one ciphertext by every steps[i] (i < count, count <= 64)
+ * into outs[i] (caller buffers, cap >= in's level + 1, none aliasing in),
+ * sharing one ModUp of in's second polynomial (hoisting, as bootstrapping's
+ * baby steps use it): per step the automorphism goes onto both polynomials
+ * and onto every extended limb, then the key inner product and ModDown.  Each
+ * result decrypts like secpe_rotate's with the same noise bound (its
+ * residues differ: the extended limbs carry FastBConv's multiple of the
+ * digit modulus, permuted).  SECPE_EKEY for a missing Galois key. */
+int secpe_rotate_hoisted(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *in, const int32_t *steps,
+                         int count, secpe_ct *outs, void *stream);
 /* Hybrid key switching of one polynomial d ([cap][N], limbs 0..level, NTT
  * form) with the relinearisation key (galois_step = 0) or the Galois key of
  * a rotation step: writes ks0, ks1 ([cap][N] each). */

@@ -492,6 +492,21 @@ extern "C" int secpe_rotate(secpe_ctx *ctx, const secpe_keys *keys_, const secpe
     return finish(ctx, copy_out(ctx, r, out));
 }
 
+extern "C" int secpe_rotate_hoisted(secpe_ctx *ctx, const secpe_keys *keys_, const secpe_ct *in, const int32_t *steps,
+                                    int count, secpe_ct *outs, void *stream) {
+    if (!ctx || !keys_ || !steps || !outs || count < 1 || count > 64) return SECPE_EINVAL;
+    SECPE_CHECK(check_ct(ctx, in));
+    for (int i = 0; i < count; i++) {
+        if (!outs[i].data || !aligned16(outs[i].data) || outs[i].cap < in->level + 1) return SECPE_EINVAL;
+        if (outs[i].data == in->data) return SECPE_EINVAL;
+    }
+    EVAL_PROLOGUE(ctx, stream);
+    std::vector<Ct> r;
+    SECPE_CHECK(E.rotate_hoisted(view(ctx, in), std::vector<int>(steps, steps + count), r));
+    for (int i = 0; i < count; i++) SECPE_CHECK(copy_out(ctx, r[i], &outs[i]));
+    return finish(ctx, SECPE_OK);
+}
+
 extern "C" int secpe_keyswitch(secpe_ctx *ctx, const secpe_keys *keys, int galois_step, const uint64_t *d,
                                int level, int cap, uint64_t *ks0, uint64_t *ks1, void *stream) {
     if (!ctx || !keys || !d || !ks0 || !ks1 || !aligned16(d) || !aligned16(ks0) || !aligned16(ks1) || level < 0 ||

@@ -35,7 +35,7 @@ EXPORTS = [
     "secpe_linear_apply", "secpe_encrypt_replicated", "secpe_boot_rotation_steps", "secpe_boot_create",
     "secpe_boot_create_coeffs", "secpe_boot_destroy", "secpe_bootstrap_batch", "secpe_bootstrap",
     "secpe_argmax_batch_boot", "secpe_level_plan", "secpe_ntt32_create", "secpe_ntt32_destroy", "secpe_ntt32",
-    "secpe_bconv32",
+    "secpe_bconv32", "secpe_rotate_hoisted",
 ]
 
 
@@ -173,6 +173,7 @@ def lib():
         "secpe_ntt32_destroy": (None, [vp]),
         "secpe_ntt32": (i32, [vp, vp, P(i32), i32, i32, vp]),
         "secpe_bconv32": (i32, [vp, vp, P(i32), i32, vp, P(i32), i32, i32, vp]),
+        "secpe_rotate_hoisted": (i32, [vp, vp, P(CtC), P(i32), i32, P(CtC), vp]),
         "secpe_boot_create": (i32, [vp, i32, P(vp)]),
         "secpe_boot_create_coeffs": (i32, [vp, i32, P(ctypes.c_int64), P(ctypes.c_int64), P(vp)]),
         "secpe_boot_destroy": (None, [vp]),
@@ -614,6 +615,19 @@ def rotate(ctx, keys, a, steps, out=None):
     _check(lib().secpe_rotate(ctx.h, keys.h, ctypes.byref(ca), steps, ctypes.byref(co), _stream()), "secpe_rotate")
     out.update(co)
     return out
+
+
+def rotate_hoisted(ctx, keys, a, steps, outs=None):
+    """secpe_rotate_hoisted: rotations of a by every step from one ModUp."""
+    outs = [ctx.new_ct() for _ in steps] if outs is None else outs
+    ca = a.struct()
+    arr = (CtC * len(steps))(*[o.struct() for o in outs])
+    st = (ctypes.c_int32 * len(steps))(*steps)
+    _check(lib().secpe_rotate_hoisted(ctx.h, keys.h, ctypes.byref(ca), st, len(steps), arr, _stream()),
+           "secpe_rotate_hoisted")
+    for o, c in zip(outs, arr):
+        o.update(c)
+    return outs
 
 
 def keyswitch(ctx, keys, galois_step, d, level):

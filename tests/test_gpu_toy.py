@@ -120,6 +120,28 @@ def test_mul_relin_and_rotation_bit_exact(env):
     same(secpe.rotate(ctx, keys, low, -8), o.rotate(low_o, -8))
 
 
+def test_hoisted_rotations_bit_exact(env):
+    """secpe_rotate_hoisted: one ModUp for several steps, residue for residue
+    the oracle's rotate_hoisted, at the top level and at a lower one; host
+    errors for a missing key and an output aliasing the input."""
+    o, ctx, keys, secpe = env
+    a_o = o.encrypt(np.random.default_rng(6).uniform(-1, 1, 8), seed=33)
+    a = to_gpu(secpe, ctx, a_o)
+    steps = [1, 2, -4, 16, 3]
+    for g, w in zip(secpe.rotate_hoisted(ctx, keys, a, steps), o.rotate_hoisted(a_o, steps)):
+        same(g, w)
+    low_o = o.drop(a_o, 5)
+    low = to_gpu(secpe, ctx, low_o)
+    for g, w in zip(secpe.rotate_hoisted(ctx, keys, low, [-2, 8]), o.rotate_hoisted(low_o, [-2, 8])):
+        same(g, w)
+    with pytest.raises(secpe.SecpeError) as e:
+        secpe.rotate_hoisted(ctx, keys, a, [1, 5])
+    assert e.value.code == -5
+    with pytest.raises(secpe.SecpeError) as e:
+        secpe.rotate_hoisted(ctx, keys, a, [1], outs=[a])
+    assert e.value.code == -1
+
+
 def test_keyswitch_primitive_bit_exact(env):
     import torch
     o, ctx, keys, secpe = env
