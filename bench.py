@@ -767,10 +767,11 @@ def run_clip(secpe, torch, workloads, ctx, key_seed, d=512, C=10, K=80, B=16):
 
 def run_boot(secpe, torch, dev, refresh, n=128, batches=(1, 16)):
     """Sparse-slot CKKS bootstrapping (secpe_bootstrap_batch) at N = 2^16 on
-    the boot16 set (q0 50-bit, 7 x 40-bit computation primes, 16 x 60-bit
-    bootstrapping primes, 6 special, dnum 6, sparse secret h = 32), blocks of
+    the boot16 set (q0 50-bit, 10 x 40-bit computation primes, 16 x 60-bit
+    bootstrapping primes, 5 special, dnum 7, sparse secret h = 32), blocks of
     n = 128 slots (2C' for C' <= 64): one warm-up, then 3 timed batches at
-    each batch size; checked against the input slots."""
+    each batch size (inside the NVTX range "boot_B<size>"); checked against
+    the input slots."""
     from paper_2502_00847_gb300.presets import BOOT16
     ctx = secpe.Context.from_params(BOOT16)
     ctx.autotune()
@@ -799,10 +800,12 @@ def run_boot(secpe, torch, dev, refresh, n=128, batches=(1, 16)):
         assert err < 2.0 ** -16, "bootstrap error %g" % err
         ctx.reset_counters()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("boot_B%d" % B)
         e0.record()
         for _ in range(3):
             bt.bootstrap_batch(keys, x, res)
         e1.record()
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / 3
         cnt = ctx.counters()
@@ -820,13 +823,15 @@ def run_boot(secpe, torch, dev, refresh, n=128, batches=(1, 16)):
     return out
 
 
-def run_noninteractive(secpe, torch, workloads, dev, n_queries, n=128):
+def run_noninteractive(secpe, torch, workloads, dev, n_queries, n=128, n_sets=16):
     """The whole encrypted ensemble Argmax without the interactive stand-in:
     queries of the mix (seed 4, the first n_queries) on boot16, each prompt's
     logits packed into every 2C'-block (inputs 2C'-periodic, at the top
     computation level L - 16), one secpe_argmax_batch_boot call with every
     refresh a batched bootstrap (block n = 128).  One warm-up on 4 queries,
-    one timed call; every query's index checked."""
+    one timed call; every query's index checked.  Then slot-packed: n_sets
+    sets of the mix's tasks with n / (2C') different inputs in every 128-slot
+    block, one timed call, every input's index checked."""
     from paper_2502_00847_gb300.presets import BOOT16
     ctx = secpe.Context.from_params(BOOT16)
     ctx.autotune()
@@ -859,15 +864,54 @@ def run_noninteractive(secpe, torch, workloads, dev, n_queries, n=128):
     cnt = ctx.counters()
     ok = sum(int(np.argmax(secpe.decrypt(ctx, keys, b["z_out"], q.C))) == int(np.argmax(q.logits.mean(0)))
              for q, b in zip(qs, batch))
+    del data, batch
+    out = {"value": n_queries / (ms / 1e3), "unit": "queries/s", "queries": n_queries, "ms": ms,
+           "bootstraps_per_query": cnt["bootstraps"] / n_queries, "relins_per_query": cnt["relins"] / n_queries,
+           "correct_indices": ok,
+           "workload": "the first %d queries of the mix on boot16 (Delta = 2^40, 10 computation levels between "
+                       "bootstraps), inputs packed 2C'-periodic, every refresh a batched bootstrap" % n_queries}
+    # slot-packed: n / (2C') different inputs of one task in every n-block
+    # (the block repeated over the N/2 slots, so the bootstrap's n-periodic
+    # average keeps it), one ciphertext per prompt for all of them
+    sets = workloads.packed_queries(n_sets, n, seed=7)
+    S = ctx.n // 2
+    n_cts = sum(st.K for st in sets)
+    data = torch.empty((n_cts, 2, ctx.L + 1, ctx.n), dtype=torch.int64, device=dev)
+    batch, off = [], 0
+    for st in sets:
+        cts = []
+        for i in range(st.K):
+            c = secpe.Ciphertext(data[off], 0, ctx.scale)
+            secpe.encrypt_logits_packed(ctx, keys, np.tile(st.prompt(i), (S // n, 1)), st.d_min, st.enc_seeds[i],
+                                        out=c)
+            c.level = lv
+            cts.append(c)
+            off += 1
+        batch.append(dict(cts=cts, C=st.C, d_min=st.d_min, d_max=st.d_max, qseed=st.qseed, z_out=ctx.new_ct()))
+    torch.cuda.synchronize()
+    ctx.reset_counters()
+    e0.record()
+    secpe.argmax_batch_boot(ctx, keys, bt, batch)
+    e1.record()
+    torch.cuda.synchronize()
+    msp = e0.elapsed_time(e1)
+    cnt = ctx.counters()
+    inputs = sum(st.P for st in sets)
+    okp = 0
+    for st, b in zip(sets, batch):
+        cp = 1 << (st.C - 1).bit_length()
+        z = secpe.decrypt_packed(ctx, keys, b["z_out"], S // (2 * cp), st.C)
+        okp += sum(int(np.argmax(z[j])) == int(np.argmax(st.logits[j].mean(0))) for j in range(st.P))
+    out["packed"] = {"value": inputs / (msp / 1e3), "unit": "queries/s", "inputs": inputs, "sets": n_sets,
+                     "ms": msp, "bootstraps_per_set": cnt["bootstraps"] / n_sets, "correct_indices": okp,
+                     "workload": "%d sets of the mix's tasks (seed 7), each n / (2C') inputs per 128-slot block "
+                                 "(the block repeated over the slots), on boot16, every refresh a batched "
+                                 "bootstrap" % n_sets}
     bt.close()
     keys.close()
     del data, batch
     ctx.close()
-    return {"value": n_queries / (ms / 1e3), "unit": "queries/s", "queries": n_queries, "ms": ms,
-            "bootstraps_per_query": cnt["bootstraps"] / n_queries, "relins_per_query": cnt["relins"] / n_queries,
-            "correct_indices": ok,
-            "workload": "the first %d queries of the mix on boot16 (Delta = 2^40, 10 computation levels between "
-                        "bootstraps), inputs packed 2C'-periodic, every refresh a batched bootstrap" % n_queries}
+    return out
 
 
 def run_packed(secpe, torch, workloads, ctx, keys, dev, steps, n_sets=256):

@@ -141,3 +141,26 @@ def test_toy_noninteractive_argmax_bit_exact(toy):
     assert int(np.argmax(zd)) == int(np.argmax(q.logits.mean(0)))
     bt.close()
 
+
+def test_toy_noninteractive_packed_distinct_inputs(toy):
+    """Non-interactive Argmax on slot-packed inputs: n / (2C') different
+    inputs in every n-block (the block repeated over the slots, so every
+    bootstrap's n-periodic average keeps it); every input's index exact."""
+    from paper_2502_00847_gb300 import workloads
+    o, plan, ctx, keys, secpe = toy
+    n, S = 16, ctx.n // 2
+    (st,) = workloads.packed_queries(1, n, seed=9, K_choices=(2,), C_choices=(3,))
+    assert st.P == 2
+    lv = ctx.L - 16
+    cts = []
+    for i in range(st.K):
+        c = secpe.encrypt_logits_packed(ctx, keys, np.tile(st.prompt(i), (S // n, 1)), st.d_min, st.enc_seeds[i])
+        cts.append(secpe.Ciphertext(c.data, lv, c.scale))
+    bt = secpe.Boot(ctx, n)
+    b = [dict(cts=cts, C=st.C, d_min=st.d_min, d_max=st.d_max, qseed=st.qseed, z_out=ctx.new_ct())]
+    secpe.argmax_batch_boot(ctx, keys, bt, b)
+    z = secpe.decrypt_packed(ctx, keys, b[0]["z_out"], S // 8, st.C)
+    for j in range(S // 8):
+        assert int(np.argmax(z[j])) == int(np.argmax(st.logits[j % st.P].mean(0))), j
+    bt.close()
+
