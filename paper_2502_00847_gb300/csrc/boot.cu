@@ -190,14 +190,21 @@ int bsgs(Eval &E, const std::vector<Ct> &xs, const u64 *pts, int ndiag, int bs, 
     for (int g = 0; g < gs; g++) {
         Ct acc;
         SECPE_CHECK(ct_alloc(ctx, B, lv, xs[0].scale() * pt_scale, acc));
-        bool first = true;
+        // the inner sum over every input and baby step, one pass per up to
+        // kMaxPlainTerms terms
+        std::vector<CtB> terms;
+        std::vector<const u64 *> tps;
         for (size_t t = 0; t < xs.size(); t++)
             for (int b = 0; b < bs; b++) {
-                const u64 *p = pts + ((size_t)t * ndiag + (size_t)g * bs + b) * plane;
-                const Ct &x = baby[t][b];
-                SECPE_CHECK(launch_mul_plain(ctx, x.v, x.v.stride, p, 0, acc.v, lv + 1, !first));
-                first = false;
+                terms.push_back(baby[t][b].v);
+                tps.push_back(pts + ((size_t)t * ndiag + (size_t)g * bs + b) * plane);
             }
+        for (size_t t0 = 0; t0 < terms.size(); t0 += kMaxPlainTerms) {
+            const size_t t1 = std::min(terms.size(), t0 + kMaxPlainTerms);
+            SECPE_CHECK(launch_mul_plain_sum(ctx, std::vector<CtB>(terms.begin() + t0, terms.begin() + t1),
+                                             std::vector<const u64 *>(tps.begin() + t0, tps.begin() + t1), acc.v,
+                                             lv + 1, t0 > 0));
+        }
         Ct inner;
         SECPE_CHECK(E.rescale(acc, inner));
         acc = Ct();

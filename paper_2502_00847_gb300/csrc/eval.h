@@ -111,6 +111,11 @@ struct Eval {
 int launch_mul_plain(secpe_ctx *ctx, const CtB &x, long long xs, const u64 *p, long long ps, const CtB &o, int nl,
                      bool acc = false);
 int launch_add_plain(secpe_ctx *ctx, const CtB &x, const u64 *p, const CtB &o, int nl);
+// o (+)= sum_t xs[t] (.) ps[t] (Montgomery-form plaintexts [nl][N], one for
+// every item; at most kMaxPlainTerms terms), one pass
+constexpr int kMaxPlainTerms = 32;
+int launch_mul_plain_sum(secpe_ctx *ctx, const std::vector<CtB> &xs, const std::vector<const u64 *> &ps,
+                         const CtB &o, int nl, bool acc);
 // B plaintexts from host int64 coefficients m[B][N]: NTT-form residues of
 // limbs 0..nl-1 (Montgomery form if mont) at dst [B][nl][N]; synchronous.
 int upload_plain(secpe_ctx *ctx, const int64_t *m, int B, int nl, bool mont, u64 *dst);

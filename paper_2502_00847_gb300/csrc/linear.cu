@@ -59,6 +59,52 @@ __global__ void k_mul_plain(DevCtx c, const u64 *x, long long xs, int cap_x, con
     *op = r;
 }
 
+// o (+)= sum_t x_t (.) p_t per residue (the inner sums of a baby-step
+// giant-step linear transform): plaintext p_t limb i at p_t + i*N in
+// Montgomery form, one for every item.  The products are summed in 128 bits
+// and reduced every 15 of them (15 q^2 < q 2^64 for q < 2^60), the partial
+// results added mod q, so the result equals the sequence of k_mul_plain
+// accumulations residue for residue.
+struct PlainSumArgs {
+    const u64 *x[kMaxPlainTerms];
+    long long xs[kMaxPlainTerms];
+    int cap[kMaxPlainTerms];
+    const u64 *p[kMaxPlainTerms];
+    int nt;
+};
+
+__global__ void k_mul_plain_sum(DevCtx c, const __grid_constant__ PlainSumArgs a, u64 *o, long long os, int cap_o,
+                                int nl, int acc) {
+    const int li = blockIdx.y;
+    const int i = li % nl, kk = (li / nl) & 1, item = li / (2 * nl);
+    const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= c.n) return;
+    const u64 q = c.q[i], qi = c.qinv_neg[i];
+    ulonglong2 *op = reinterpret_cast<ulonglong2 *>(o + item * os + ((long long)kk * cap_o + i) * c.n + e);
+    ulonglong2 r = acc ? *op : make_ulonglong2(0, 0);
+    acc128 s0 = {0, 0}, s1 = {0, 0};
+    int cnt = 0;
+#pragma unroll 4
+    for (int t = 0; t < a.nt; t++) {
+        const ulonglong2 v =
+            *reinterpret_cast<const ulonglong2 *>(a.x[t] + item * a.xs[t] + ((long long)kk * a.cap[t] + i) * c.n + e);
+        const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(a.p[t] + (long long)i * c.n + e);
+        mac(s0, v.x, w.x);
+        mac(s1, v.y, w.y);
+        if (++cnt == 15) {
+            r.x = add_mod(r.x, redc(s0.hi, s0.lo, q, qi), q);
+            r.y = add_mod(r.y, redc(s1.hi, s1.lo, q, qi), q);
+            s0 = s1 = acc128{0, 0};
+            cnt = 0;
+        }
+    }
+    if (cnt) {
+        r.x = add_mod(r.x, redc(s0.hi, s0.lo, q, qi), q);
+        r.y = add_mod(r.y, redc(s1.hi, s1.lo, q, qi), q);
+    }
+    *op = r;
+}
+
 // o = x + (p, 0): plaintext limbs (NTT form) added to c0 of every item.
 __global__ void k_add_plain(DevCtx c, const u64 *x, long long xs, int cap_x, const u64 *p, u64 *o, long long os,
                             int cap_o, int nl) {
@@ -130,6 +176,26 @@ int launch_mul_plain(secpe_ctx *ctx, const CtB &x, long long xs, const u64 *p, l
     KprofScope kp(ctx, "ew_mul_plain", 8.0 * ctx->n * o.B * ((acc ? 6.0 : 4.0) * nl + (ps ? (double)nl : 0.0)));
     SECPE_LAUNCH(ctx, k_mul_plain, grid_of(ctx->n, 2, (long long)o.B * 2 * nl), 256, 0, ctx->dev, x.data, xs, x.cap,
                  p, ps, o.data, o.stride, o.cap, nl, acc ? 1 : 0);
+    return SECPE_OK;
+}
+
+int launch_mul_plain_sum(secpe_ctx *ctx, const std::vector<CtB> &xs, const std::vector<const u64 *> &ps,
+                         const CtB &o, int nl, bool acc) {
+    const int nt = (int)xs.size();
+    if (nt < 1 || nt > kMaxPlainTerms || (int)ps.size() != nt) return SECPE_EINVAL;
+    PlainSumArgs a;
+    for (int t = 0; t < nt; t++) {
+        if (xs[t].B != o.B || xs[t].cap < nl) return SECPE_EINVAL;
+        a.x[t] = xs[t].data;
+        a.xs[t] = xs[t].stride;
+        a.cap[t] = xs[t].cap;
+        a.p[t] = ps[t];
+    }
+    a.nt = nt;
+    KprofScope kp(ctx, "ew_mul_plain_sum",
+                  8.0 * ctx->n * nl * ((double)o.B * (2.0 * nt + (acc ? 4.0 : 2.0)) + (double)nt));
+    SECPE_LAUNCH(ctx, k_mul_plain_sum, grid_of(ctx->n, 2, (long long)o.B * 2 * nl), 256, 0, ctx->dev, a, o.data,
+                 o.stride, o.cap, nl, acc ? 1 : 0);
     return SECPE_OK;
 }
 
