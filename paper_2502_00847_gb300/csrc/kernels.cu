@@ -352,15 +352,27 @@ __global__ void k_modup_bconv(DevCtx c, const u64 *x, u64 *ext, long long ext_it
 
 // Inner product with the key over digits: acc[item][0/1][t] for targets
 // t = 0..lv (q_t) and lv+1.. (special primes); key in Montgomery form.
+// With gal != 0 the extended limbs are read through the automorphism
+// X -> X^gal (NTT form: a gather, as k_automorph), so that a hoisted
+// rotation needs no permuted copy of them.
+__device__ __forceinline__ unsigned automorph_src(unsigned j, unsigned g, int log_n, int n) {
+    const unsigned sh = 32 - log_n;
+    const unsigned ev = 2u * (__brev(j) >> sh) + 1u;
+    const unsigned e2 = (unsigned)(((unsigned long long)ev * g) & (2ull * n - 1));
+    return __brev((e2 - 1u) >> 1) >> sh;
+}
+
 __global__ void k_ksk_ip(DevCtx c, const u64 *d, long long d_item_stride, const u64 *ext,
                          long long ext_item_stride, const __grid_constant__ KsDigits dg,
-                         const u64 *key, u64 *acc, int lv) {
+                         const u64 *key, u64 *acc, int lv, unsigned gal) {
     const int nt = lv + 1 + c.np_special;
     const int nitem = gridDim.y / nt;
     // target-major order: the items sharing one key limb run back to back
     const int t = blockIdx.y / nitem, item = blockIdx.y % nitem;
     const int e = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (e >= c.n) return;
+    const unsigned g0 = gal ? automorph_src((unsigned)e, gal, c.log_n, c.n) : 0u;
+    const unsigned g1 = gal ? automorph_src((unsigned)e + 1u, gal, c.log_n, c.n) : 0u;
     const int pt = t <= lv ? t : c.nq + (t - lv - 1);
     const u64 q = c.q[pt], qi = c.qinv_neg[pt];
     acc128 s0a = {0, 0}, s0b = {0, 0}, s1a = {0, 0}, s1b = {0, 0};
@@ -372,7 +384,8 @@ __global__ void k_ksk_ip(DevCtx c, const u64 *d, long long d_item_stride, const 
             xv = ld2(d + item * d_item_stride + (long long)t * c.n + e);
         } else {
             const int tt = t < lo ? t : t - (hi - lo);
-            xv = ld2(ext + item * ext_item_stride + (long long)(dg.off[j] + tt) * c.n + e);
+            const u64 *xl = ext + item * ext_item_stride + (long long)(dg.off[j] + tt) * c.n;
+            xv = gal ? make_ulonglong2(xl[g0], xl[g1]) : ld2(xl + e);
         }
         const u64 *kb = key + (long long)j * 2 * kpoly + (long long)pt * c.n + e;
         const ulonglong2 k0 = ld2(kb), k1 = ld2(kb + kpoly);
@@ -879,14 +892,17 @@ int launch_modup_bconv(secpe_ctx *ctx, const u64 *x, u64 *ext, long long ext_ite
 }
 
 int launch_ksk_ip(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const u64 *ext,
-                  long long ext_item_stride, const KsDigits &dg, const u64 *key, u64 *acc, int B, int lv) {
-    if (ctx->tc_mode)
+                  long long ext_item_stride, const KsDigits &dg, const u64 *key, u64 *acc, int B, int lv,
+                  unsigned gal) {
+    if (ctx->tc_mode) {
+        if (gal) return SECPE_EINVAL;
         return launch_ksk_ip_tc(ctx, d, d_item_stride, ext, ext_item_stride, dg, key, acc, B, lv);
+    }
     const int nt = lv + 1 + ctx->npsp;
     // inputs (one residue per digit and target), key once, outputs (2 polys)
     KprofScope kp(ctx, "ksk_ip", 8.0 * ctx->n * ((double)B * dg.ndig * nt + 2.0 * dg.ndig * nt + 2.0 * B * nt));
     SECPE_LAUNCH(ctx, k_ksk_ip, limb_grid(ctx->n, 2, (long long)B * nt), 256, 0, ctx->dev, d, d_item_stride,
-                 ext, ext_item_stride, dg, key, acc, lv);
+                 ext, ext_item_stride, dg, key, acc, lv, gal);
     return SECPE_OK;
 }
 

@@ -39,8 +39,11 @@ int launch_rescale_prep(secpe_ctx *ctx, const u64 *y, u64 *z, int B, int lv);
 int launch_rescale_fin(secpe_ctx *ctx, const CtB &x, const u64 *z, const CtB &o, int lv);
 int launch_modup_bconv(secpe_ctx *ctx, const u64 *x, u64 *ext, long long ext_item_stride, int ext_off,
                        int B, int lv, int j, int lo, int hi, int ntgt);
+// gal != 0: ext is read through the automorphism X -> X^gal (not with the
+// precision variant)
 int launch_ksk_ip(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const u64 *ext,
-                  long long ext_item_stride, const KsDigits &dg, const u64 *key, u64 *acc, int B, int lv);
+                  long long ext_item_stride, const KsDigits &dg, const u64 *key, u64 *acc, int B, int lv,
+                  unsigned gal = 0);
 // The same inner product as exact 8-bit-limb contractions on the tensor
 // pipe (precision variant, ntt_tc.cu; N = 2^16, at most 8 digits).
 int launch_ksk_ip_tc(secpe_ctx *ctx, const u64 *d, long long d_item_stride, const u64 *ext,

@@ -154,7 +154,7 @@ int rotate_hoisted(secpe_ctx *ctx, const CtB &x, const std::vector<unsigned> &ga
     ext_ls.poly_stride = 0;
     ext_ls.nlimb = tot;
     SECPE_CHECK(ntt_limbset(ctx, ext_ls, false));
-    SECPE_CHECK(sext.alloc(ctx, sizeof(u64) * (size_t)B * tot * n));
+    if (ctx->tc_mode) SECPE_CHECK(sext.alloc(ctx, sizeof(u64) * (size_t)B * tot * n));
     SECPE_CHECK(acc.alloc(ctx, sizeof(u64) * (size_t)B * 2 * nt * n));
     SECPE_CHECK(tmp.alloc(ctx, sizeof(u64) * (size_t)B * 2 * (lv + 1) * n));
     // 3. per rotation: automorphisms, inner product, ModDown
@@ -162,10 +162,17 @@ int rotate_hoisted(secpe_ctx *ctx, const CtB &x, const std::vector<unsigned> &ga
         const CtB &o = outs[i];
         if (o.B != B || o.cap < lv + 1 || !keys[i]) return SECPE_EINVAL;
         SECPE_CHECK(launch_automorph(ctx, x, o, lv + 1, gal[i]));
-        SECPE_CHECK(launch_automorph_flat(ctx, ext.u(), sext.u(), (long long)B * tot, gal[i]));
         ctx->counters.keyswitches++;
-        SECPE_CHECK(launch_ksk_ip(ctx, o.data + o.pstride(), o.stride, sext.u(), ext_stride, dg, keys[i], acc.u(), B,
-                                  lv));
+        if (ctx->tc_mode) {
+            // the precision variant's inner product reads a permuted copy
+            SECPE_CHECK(launch_automorph_flat(ctx, ext.u(), sext.u(), (long long)B * tot, gal[i]));
+            SECPE_CHECK(launch_ksk_ip(ctx, o.data + o.pstride(), o.stride, sext.u(), ext_stride, dg, keys[i],
+                                      acc.u(), B, lv));
+        } else {
+            // the inner product reads the extended limbs through the automorphism
+            SECPE_CHECK(launch_ksk_ip(ctx, o.data + o.pstride(), o.stride, ext.u(), ext_stride, dg, keys[i],
+                                      acc.u(), B, lv, gal[i]));
+        }
         LimbSet pls =
             make_limbset(acc.u() + (size_t)(lv + 1) * n, B, 2ll * nt * n, 2, (long long)nt * n, k, ctx->nq);
         if (fused_path(ctx)) {
