@@ -186,25 +186,43 @@ int bsgs(Eval &E, const std::vector<Ct> &xs, const u64 *pts, int ndiag, int bs, 
         baby[t].push_back(xs[t]);
         for (Ct &c : r) baby[t].push_back(c);
     }
+    // the inner sums over every input and baby step: with at most
+    // kMaxPlainTerms terms, kMaxGiant giant steps per pass (each baby step
+    // read once per pass); otherwise one pass per giant step and term chunk
+    std::vector<CtB> terms;
+    for (size_t t = 0; t < xs.size(); t++)
+        for (int b = 0; b < bs; b++) terms.push_back(baby[t][b].v);
+    auto pt_of = [&](size_t k, int g) {
+        const size_t t = k / bs, b = k % bs;
+        return (const u64 *)(pts + ((size_t)t * ndiag + (size_t)g * bs + b) * plane);
+    };
+    std::vector<Ct> accs(gs);
+    for (int g = 0; g < gs; g++) SECPE_CHECK(ct_alloc(ctx, B, lv, xs[0].scale() * pt_scale, accs[g]));
+    if ((int)terms.size() <= kMaxPlainTerms) {
+        for (int g0 = 0; g0 < gs; g0 += kMaxGiant) {
+            const int g1 = std::min(gs, g0 + kMaxGiant);
+            std::vector<std::vector<const u64 *>> ps(terms.size());
+            std::vector<CtB> os;
+            for (size_t k = 0; k < terms.size(); k++)
+                for (int g = g0; g < g1; g++) ps[k].push_back(pt_of(k, g));
+            for (int g = g0; g < g1; g++) os.push_back(accs[g].v);
+            SECPE_CHECK(launch_bsgs_inner(ctx, terms, ps, os, lv + 1));
+        }
+    } else {
+        for (int g = 0; g < gs; g++)
+            for (size_t t0 = 0; t0 < terms.size(); t0 += kMaxPlainTerms) {
+                const size_t t1 = std::min(terms.size(), t0 + kMaxPlainTerms);
+                std::vector<const u64 *> tps;
+                for (size_t k = t0; k < t1; k++) tps.push_back(pt_of(k, g));
+                SECPE_CHECK(launch_mul_plain_sum(ctx, std::vector<CtB>(terms.begin() + t0, terms.begin() + t1), tps,
+                                                 accs[g].v, lv + 1, t0 > 0));
+            }
+    }
+    baby.clear();
     Ct total;
     for (int g = 0; g < gs; g++) {
-        Ct acc;
-        SECPE_CHECK(ct_alloc(ctx, B, lv, xs[0].scale() * pt_scale, acc));
-        // the inner sum over every input and baby step, one pass per up to
-        // kMaxPlainTerms terms
-        std::vector<CtB> terms;
-        std::vector<const u64 *> tps;
-        for (size_t t = 0; t < xs.size(); t++)
-            for (int b = 0; b < bs; b++) {
-                terms.push_back(baby[t][b].v);
-                tps.push_back(pts + ((size_t)t * ndiag + (size_t)g * bs + b) * plane);
-            }
-        for (size_t t0 = 0; t0 < terms.size(); t0 += kMaxPlainTerms) {
-            const size_t t1 = std::min(terms.size(), t0 + kMaxPlainTerms);
-            SECPE_CHECK(launch_mul_plain_sum(ctx, std::vector<CtB>(terms.begin() + t0, terms.begin() + t1),
-                                             std::vector<const u64 *>(tps.begin() + t0, tps.begin() + t1), acc.v,
-                                             lv + 1, t0 > 0));
-        }
+        Ct acc = accs[g];
+        accs[g] = Ct();
         Ct inner;
         SECPE_CHECK(E.rescale(acc, inner));
         acc = Ct();

@@ -116,6 +116,11 @@ int launch_add_plain(secpe_ctx *ctx, const CtB &x, const u64 *p, const CtB &o, i
 constexpr int kMaxPlainTerms = 32;
 int launch_mul_plain_sum(secpe_ctx *ctx, const std::vector<CtB> &xs, const std::vector<const u64 *> &ps,
                          const CtB &o, int nl, bool acc);
+// os[g] = sum_k xs[k] (.) ps[k][g] for up to kMaxGiant outputs in one pass
+// (every xs[k] read once; all outputs with one layout)
+constexpr int kMaxGiant = 4;
+int launch_bsgs_inner(secpe_ctx *ctx, const std::vector<CtB> &xs, const std::vector<std::vector<const u64 *>> &ps,
+                      const std::vector<CtB> &os, int nl);
 // B plaintexts from host int64 coefficients m[B][N]: NTT-form residues of
 // limbs 0..nl-1 (Montgomery form if mont) at dst [B][nl][N]; synchronous.
 int upload_plain(secpe_ctx *ctx, const int64_t *m, int B, int nl, bool mont, u64 *dst);

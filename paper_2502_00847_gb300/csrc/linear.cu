@@ -105,6 +105,59 @@ __global__ void k_mul_plain_sum(DevCtx c, const __grid_constant__ PlainSumArgs a
     *op = r;
 }
 
+// The inner sums of up to kMaxGiant giant steps in one pass:
+// o_g = sum_k x_k (.) p_{k,g}, every baby-step ciphertext x_k read once for
+// all of them.  One residue per thread; rows ordered limb-major, so the rows
+// that share one limb's plaintexts run back to back and find them in L2.
+// Products summed in 128 bits, reduced every 15 (as k_mul_plain_sum).
+struct BsgsInnerArgs {
+    const u64 *x[kMaxPlainTerms];
+    long long xs[kMaxPlainTerms];
+    int cap[kMaxPlainTerms];
+    const u64 *p[kMaxPlainTerms][kMaxGiant];
+    u64 *o[kMaxGiant];
+    long long os;
+    int cap_o, nt, ng, B;
+};
+
+__global__ void k_bsgs_inner(DevCtx c, const __grid_constant__ BsgsInnerArgs a) {
+    const int li = blockIdx.y;
+    const int i = li / (2 * a.B), rem = li % (2 * a.B);
+    const int item = rem >> 1, kk = rem & 1;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= c.n) return;
+    const u64 q = c.q[i], qi = c.qinv_neg[i];
+    const long long off = (long long)i * c.n + e;
+    acc128 sm[kMaxGiant];
+    u64 r[kMaxGiant];
+#pragma unroll
+    for (int g = 0; g < kMaxGiant; g++) {
+        sm[g] = acc128{0, 0};
+        r[g] = 0;
+    }
+    int cnt = 0;
+    for (int k = 0; k < a.nt; k++) {
+        const u64 v = a.x[k][item * a.xs[k] + ((long long)kk * a.cap[k] + i) * c.n + e];
+#pragma unroll
+        for (int g = 0; g < kMaxGiant; g++)
+            if (g < a.ng) mac(sm[g], v, a.p[k][g][off]);
+        if (++cnt == 15) {
+#pragma unroll
+            for (int g = 0; g < kMaxGiant; g++) {
+                r[g] = add_mod(r[g], redc(sm[g].hi, sm[g].lo, q, qi), q);
+                sm[g] = acc128{0, 0};
+            }
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < kMaxGiant; g++) {
+        if (g >= a.ng) break;
+        if (cnt) r[g] = add_mod(r[g], redc(sm[g].hi, sm[g].lo, q, qi), q);
+        a.o[g][item * a.os + ((long long)kk * a.cap_o + i) * c.n + e] = r[g];
+    }
+}
+
 // o = x + (p, 0): plaintext limbs (NTT form) added to c0 of every item.
 __global__ void k_add_plain(DevCtx c, const u64 *x, long long xs, int cap_x, const u64 *p, u64 *o, long long os,
                             int cap_o, int nl) {
@@ -196,6 +249,34 @@ int launch_mul_plain_sum(secpe_ctx *ctx, const std::vector<CtB> &xs, const std::
                   8.0 * ctx->n * nl * ((double)o.B * (2.0 * nt + (acc ? 4.0 : 2.0)) + (double)nt));
     SECPE_LAUNCH(ctx, k_mul_plain_sum, grid_of(ctx->n, 2, (long long)o.B * 2 * nl), 256, 0, ctx->dev, a, o.data,
                  o.stride, o.cap, nl, acc ? 1 : 0);
+    return SECPE_OK;
+}
+
+int launch_bsgs_inner(secpe_ctx *ctx, const std::vector<CtB> &xs, const std::vector<std::vector<const u64 *>> &ps,
+                      const std::vector<CtB> &os, int nl) {
+    const int nt = (int)xs.size(), ng = (int)os.size();
+    if (nt < 1 || nt > kMaxPlainTerms || ng < 1 || ng > kMaxGiant || (int)ps.size() != nt) return SECPE_EINVAL;
+    BsgsInnerArgs a;
+    const int B = os[0].B;
+    for (int k = 0; k < nt; k++) {
+        if (xs[k].B != B || xs[k].cap < nl || (int)ps[k].size() != ng) return SECPE_EINVAL;
+        a.x[k] = xs[k].data;
+        a.xs[k] = xs[k].stride;
+        a.cap[k] = xs[k].cap;
+        for (int g = 0; g < ng; g++) a.p[k][g] = ps[k][g];
+    }
+    for (int g = 0; g < ng; g++) {
+        if (os[g].B != B || os[g].stride != os[0].stride || os[g].cap != os[0].cap || os[g].cap < nl)
+            return SECPE_EINVAL;
+        a.o[g] = os[g].data;
+    }
+    a.os = os[0].stride;
+    a.cap_o = os[0].cap;
+    a.nt = nt;
+    a.ng = ng;
+    a.B = B;
+    KprofScope kp(ctx, "ew_bsgs_inner", 8.0 * ctx->n * nl * ((double)B * 2.0 * (nt + ng) + (double)nt * ng));
+    SECPE_LAUNCH(ctx, k_bsgs_inner, grid_of(ctx->n, 1, (long long)B * 2 * nl), 256, 0, ctx->dev, a);
     return SECPE_OK;
 }
 
