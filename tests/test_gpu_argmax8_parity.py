@@ -84,7 +84,7 @@ def _same(z, r):
 def test_batched_argmax_every_residue_equals_oracle(run):
     for b, r in zip(run["direct"], run["ref"]):
         _same(b["z_out"], r)
-    # two phase ranges and a refresh inside QuickMax (C = 3: greedy levels run out in round 2)
+    # two phase ranges and a refresh inside QuickMax (C = 3: greedy levels run out in QuickMax round k = 2)
     assert [r["counters"]["refreshes"] for r in run["ref"]][1] >= 2
     for k in ("rotations", "signs", "relins", "refreshes"):
         assert run["counters"][k] == sum(r["counters"][k] for r in run["ref"]), k

@@ -31,8 +31,8 @@ def test_argmax8_plans_by_hand():
     min(5, 2) - 1 = 1 and the final Sign refreshes at its first polynomial,
     as it does from 23); after that refresh the final Sign needs p - 12 >= 5:
     [22, 14, 17].
-    r = 3: as for r = 2, but round 2's first test must still pass:
-    t = min(5, p - 12) - 1 >= 2 gives p = 15; round 2 refreshes at its first
+    r = 3: as for r = 2, but the first test of QuickMax round k = 2 must still pass:
+    t = min(5, p - 12) - 1 >= 2 gives p = 15; round k = 2 refreshes at its first
     polynomial and from p needs p - 12 >= 6, p = 18: [22, 15, 18, 17]."""
     o = Oracle(ARGMAX8)
     assert o.level_plan(1, 22) == [22, 13]
