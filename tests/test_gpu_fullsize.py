@@ -83,6 +83,20 @@ def test_encrypt_mul_rotate_rescale_refresh_bit_exact(env):
     same(secpe.refresh_testonly(ctx, keys, to_gpu(secpe, ctx, o.drop(a_o, 1)), 8, 5), o.refresh(o.drop(a_o, 1), 8))
 
 
+def test_hoisted_rotations_bit_exact(env):
+    """secpe_rotate_hoisted at N = 2^16 (the fused ModDown path): both
+    rotations from one ModUp equal the oracle's rotate_hoisted residue for
+    residue, at the top level and at level 6."""
+    o, ctx, keys, secpe = env
+    a_o = o.encrypt(np.random.default_rng(18).uniform(-1, 1, 16), seed=73)
+    a = to_gpu(secpe, ctx, a_o)
+    for g, w in zip(secpe.rotate_hoisted(ctx, keys, a, ROT), o.rotate_hoisted(a_o, ROT)):
+        same(g, w)
+    low_o = o.drop(a_o, 6)
+    for g, w in zip(secpe.rotate_hoisted(ctx, keys, to_gpu(secpe, ctx, low_o), ROT), o.rotate_hoisted(low_o, ROT)):
+        same(g, w)
+
+
 def test_micro_keyswitch_dnum3_bit_exact():
     import torch
     from paper_2502_00847_gb300 import secpe
