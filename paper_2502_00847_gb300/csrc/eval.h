@@ -118,7 +118,7 @@ int launch_mul_plain_sum(secpe_ctx *ctx, const std::vector<CtB> &xs, const std::
                          const CtB &o, int nl, bool acc);
 // os[g] = sum_k xs[k] (.) ps[k][g] for up to kMaxGiant outputs in one pass
 // (every xs[k] read once; all outputs with one layout)
-constexpr int kMaxGiant = 4;
+constexpr int kMaxGiant = 2;
 int launch_bsgs_inner(secpe_ctx *ctx, const std::vector<CtB> &xs, const std::vector<std::vector<const u64 *>> &ps,
                       const std::vector<CtB> &os, int nl);
 // B plaintexts from host int64 coefficients m[B][N]: NTT-form residues of
