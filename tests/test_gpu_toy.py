@@ -205,6 +205,39 @@ def test_toy_ensemble_argmax_bit_exact(env, C, K, seed):
     assert int(np.argmax(zd)) == int(np.argmax(q.logits.mean(0)))
 
 
+def test_toy_argmax_largest_class_count():
+    """The largest Argmax the slots hold at N = 2^12: C = 1000 classes
+    (ragged: C' = 1024, 2C' = N/2, 10 QuickMax rounds, every refresh range
+    on its level plan), one-query and batched paths bit-exact with the
+    oracle, counters equal, the exact index."""
+    from paper_2502_00847_gb300 import secpe
+    C, K = 1000, 2
+    steps = [-1024] + [1 << i for i in range(10)]
+    o = Oracle(TOY)
+    o.keygen(91, rot_steps=steps)
+    ctx = secpe.Context.from_params(TOY)
+    keys = secpe.Keys(ctx, 91, steps)
+    q = workloads.toy_query(seed=5, K=K, C=C)
+    cts_o = [o.encrypt_logits(q.logits[i], C, q.d_min, seed=q.enc_seeds[i]) for i in range(K)]
+    y_o = o.aggregate(cts_o, q.d_min, q.d_max)
+    o.reset_counters()
+    z_o = o.argmax(y_o, C, qseed=q.qseed)
+    assert o.counters["refreshes"] >= 10
+    cts = [to_gpu(secpe, ctx, c) for c in cts_o]
+    ctx.reset_counters()
+    z = secpe.encrypted_argmax(ctx, keys, secpe.ensemble_aggregate(ctx, cts, q.d_min, q.d_max), C, q.qseed)
+    same(z, z_o)
+    cnt = ctx.counters()
+    for k in ("rotations", "signs", "relins", "refreshes"):
+        assert cnt[k] == o.counters[k], k
+    b = [dict(cts=cts, C=C, d_min=q.d_min, d_max=q.d_max, qseed=q.qseed, z_out=ctx.new_ct())]
+    secpe.argmax_batch(ctx, keys, b)
+    same(b[0]["z_out"], z_o)
+    assert int(np.argmax(secpe.decrypt(ctx, keys, z, C))) == int(np.argmax(q.logits.mean(0)))
+    with pytest.raises(secpe.SecpeError):
+        secpe.encrypted_argmax(ctx, keys, z, 1025, q.qseed)      # 2C' > N/2
+
+
 def test_toy_batch_equals_single(env):
     o, ctx, keys, secpe = env
     qs = [workloads.toy_query(seed=s, K=k, C=c) for s, k, c in ((11, 3, 2), (12, 2, 4), (13, 4, 3), (14, 2, 2))]
