@@ -33,10 +33,10 @@ METRIC = "encrypted ensemble-Argmax/s at N=2^16, batched vs plain; keyswitch GB/
 # inner-product and epilogue passes B), measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) over every family launch of
 # one HMult + relinearise + rescale of 8 ciphertexts at level 23 (q0 + 23 x
-# 50-bit, 8 special primes, dnum = 3): 2.818 GB of DRAM traffic against
+# 50-bit, 8 special primes, dnum = 3): 2.831 GB of DRAM traffic against
 # 3.045 GB read and written.  The step's family launches are the same
 # kernels on more items, so their traffic is taken in the same proportion.
-NTT16_DRAM_PER_MODEL_BYTE = 2.818 / 3.045
+NTT16_DRAM_PER_MODEL_BYTE = 2.831 / 3.045
 # integer multiply pipe: 152 SMs, 64 32-bit multiplies (IMAD-class) per clock per SM
 SM_COUNT = 152
 MUL32_PER_CLK_PER_SM = 64
@@ -587,7 +587,7 @@ def run_ours(args, world, rank, local):
              "frac": gbs / hbm if gbs else None, "peak_kind": hbm_kind,
              "traffic": (NTT16_DRAM_PER_MODEL_BYTE * per_launch(kp["model_bytes"]) if args.kprof == "ntt16" else None),
              "traffic_source": ("ncu dram bytes read+write per byte the family's launches read and write "
-                                "(0.925, one HMult+relin+rescale of 8 ciphertexts), times this step's such bytes "
+                                "(0.930, one HMult+relin+rescale of 8 ciphertexts), times this step's such bytes "
                                 "per launch" if args.kprof == "ntt16" else None),
              "bytes_per_launch": per_launch(kp["bytes"]),
              "traffic_model": per_launch(kp["model_bytes"]),
