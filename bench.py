@@ -1048,6 +1048,17 @@ def word_size_probe(secpe, torch, dev, steps):
     ms64 = _time_ms(torch, fi64, reps)
     nq64 = ctx.n_q
     del x64
+    # 64-bit key switching of 8 ciphertexts' second polynomials at the top level (relinearisation key)
+    keys = secpe.Keys(ctx, 3, [])
+    xk = torch.empty((8, 2, ctx.n_q, n), dtype=torch.int64, device=dev)
+    for i in range(ctx.n_q):
+        xk[:, :, i] = torch.randint(0, p64[i], (8, 2, n), generator=gen, dtype=torch.int64, device=dev)
+    ak = secpe.CtBatch(xk, ctx.L, ctx.scale)
+    ok_ = secpe.CtBatch(torch.zeros_like(xk), 0, ctx.scale)
+    msk64 = _time_ms(torch, lambda: secpe.keyswitch_batch(ctx, keys, 0, ak, ok_), reps)
+    bitsk64 = bits64 + sum(int(q).bit_length() for q in ctx.primes()[ctx.n_q:])
+    del xk, ak, ok_
+    keys.close()
     ctx.close()
     q32, sp32 = secpe.select_primes(**dataclasses.asdict(WORD32))
     t = secpe.Ntt32(q32 + sp32)
@@ -1078,10 +1089,30 @@ def word_size_probe(secpe, torch, dev, steps):
     alg = B * (len(src) + len(dst)) * n * 4
     out["bconv32"] = {"ms": msb, "items": B, "n_in": len(src), "n_out": len(dst), "GBps": alg / (msb / 1e3) / 1e9,
                       "ns_per_output_limb": 1e6 * msb / (B * len(dst))}
+    del xin, xo
+    # 32-bit key switching of 8 polynomials: 40 q primes (1,160 bits), 16 special (464 bits), digits of 14 primes
+    # (406 bits, dnum 3), against argmax8's 24 q (1,221 bits), 8 special (480 bits), digits of 8 x 50 bits
+    qi, pi = list(range(40)), list(range(40, 56))
+    allp = q32 + sp32
+    bitsk32 = sum(int(allp[i]).bit_length() for i in qi + pi)
+    key32 = torch.empty((3, 2, 56, n), dtype=torch.int32, device=dev)
+    for i in range(56):
+        key32[:, :, i] = torch.randint(0, allp[i], (3, 2, n), generator=gen, dtype=torch.int64,
+                                       device=dev).to(torch.int32)
+    d32 = torch.empty((8, 40, n), dtype=torch.int32, device=dev)
+    for i in qi:
+        d32[:, i] = torch.randint(0, allp[i], (8, n), generator=gen, dtype=torch.int64, device=dev).to(torch.int32)
+    o32 = torch.empty((8, 2, 40, n), dtype=torch.int32, device=dev)
+    msk32 = _time_ms(torch, lambda: t.keyswitch(d32, qi, pi, 14, key32, o32), reps)
+    del key32, d32, o32
+    out["keyswitch"] = {"ms_64bit_B8": msk64, "ms_32bit_B8": msk32, "bits_64bit": bitsk64, "bits_32bit": bitsk32,
+                        "speedup_per_modulus_bit": (msk64 / bitsk64) / (msk32 / bitsk32),
+                        "note": "64-bit: the fused key switch (secpe_keyswitch_batch) on argmax8; 32-bit: "
+                                "secpe_keyswitch32, unfused (separate INTT, FastBConv, NTT, inner product and "
+                                "ModDown launches)"}
     out["note"] = ("NTT: forward + inverse, algorithmic bytes 4 x limbs x N x word (read + write per transform); "
                    "bconv32: input + output bytes; 64-bit reference is the library's secpe_ntt on argmax8 primes")
     t.close()
-    del xin, xo
     return out
 
 

@@ -415,6 +415,17 @@ int secpe_ntt32(const secpe_ntt32_table *t, uint32_t *limbs, const int32_t *prim
  * n_out <= 64; device buffers, 16-byte aligned. */
 int secpe_bconv32(const secpe_ntt32_table *t, const uint32_t *in, const int32_t *in_idx, int n_in, uint32_t *out,
                   const int32_t *out_idx, int n_out, int batch, void *stream);
+/* Hybrid key switching on 32-bit residues (the steps of secpe_keyswitch):
+ * for `batch` polynomials d [batch][nq][N] (NTT form, primes q_idx), the
+ * key [dnum][2][nq + np][N] (plain residues, limbs in the order q_idx then
+ * p_idx; digit j = the q primes [j alpha, (j+1) alpha), dnum = ceil(nq /
+ * alpha)), out [batch][2][nq][N] = ModDown(sum_j ModUp_j(d) * key_j) with
+ * ModDown the rounded division by P = prod of the p_idx primes.  nq + np <=
+ * 64, alpha <= 16, np <= 16, primes distinct; device buffers 16-byte
+ * aligned; temporary device memory from the stream-ordered allocator. */
+int secpe_keyswitch32(const secpe_ntt32_table *t, const uint32_t *d, const int32_t *q_idx, int nq,
+                      const int32_t *p_idx, int np, int alpha, const uint32_t *key, uint32_t *out, int batch,
+                      void *stream);
 
 /* ---- SecPE circuit ----------------------------------------------------- */
 /* Sign(x) = f^df(g^dg(x)) (SecPE Eq. comp), each degree-9 polynomial by a

@@ -215,8 +215,9 @@ __global__ void __launch_bounds__(256) k_ntt32_rowpass(const __grid_constant__ N
 }
 
 struct BConv32Args {
-    const uint32_t *in;  // [batch][n_in][N]
-    uint32_t *out;       // [batch][n_out][N]
+    const uint32_t *in;  // item b at in + b * in_stride, limbs [n_in][N]
+    uint32_t *out;       // item b at out + b * out_stride, limbs [n_out][N]
+    long long in_stride, out_stride;
     int n_in, n_out;
     uint32_t qin[kMaxIn32];
     uint2 qhinv[kMaxIn32];            // ([Qhat_i^-1]_{q_i}, Shoup companion)
@@ -235,8 +236,8 @@ __global__ void __launch_bounds__(256) k_bconv32(const __grid_constant__ BConv32
     __syncthreads();
     const int c = (blockIdx.x * 256 + threadIdx.x) * 4;
     const size_t item = blockIdx.y;
-    const uint32_t *__restrict__ in = a.in + item * a.n_in * 65536 + c;
-    uint32_t *__restrict__ out = a.out + item * a.n_out * 65536 + c;
+    const uint32_t *__restrict__ in = a.in + item * a.in_stride + c;
+    uint32_t *__restrict__ out = a.out + item * a.out_stride + c;
     uint32_t y[kMaxIn32][4];
 #pragma unroll
     for (int i = 0; i < kMaxIn32; i++) {
@@ -363,10 +364,11 @@ extern "C" int secpe_ntt32(const secpe_ntt32_table *t, uint32_t *limbs, const in
     return cudaGetLastError() == cudaSuccess ? SECPE_OK : SECPE_ECUDA;
 }
 
-extern "C" int secpe_bconv32(const secpe_ntt32_table *t, const uint32_t *in, const int32_t *in_idx, int n_in,
-                             uint32_t *out, const int32_t *out_idx, int n_out, int batch, void *stream) {
-    SECPE_CHECK(check_limbs(t, in, in_idx, n_in));
-    SECPE_CHECK(check_limbs(t, out, out_idx, n_out));
+namespace {
+
+// FastBConv of `batch` items with the given item strides (in words).
+int bconv32(const secpe_ntt32_table *t, const uint32_t *in, long long in_stride, const int32_t *in_idx, int n_in,
+            uint32_t *out, long long out_stride, const int32_t *out_idx, int n_out, int batch, cudaStream_t stream) {
     if (n_in < 1 || n_in > kMaxIn32 || n_out < 1 || n_out > kMaxOut32 || batch < 1 || batch > 65535)
         return SECPE_EINVAL;
     for (int i = 0; i < n_in; i++)
@@ -375,6 +377,8 @@ extern "C" int secpe_bconv32(const secpe_ntt32_table *t, const uint32_t *in, con
     BConv32Args a;
     a.in = in;
     a.out = out;
+    a.in_stride = in_stride;
+    a.out_stride = out_stride;
     a.n_in = n_in;
     a.n_out = n_out;
     for (int i = 0; i < n_in; i++) {
@@ -400,6 +404,255 @@ extern "C" int secpe_bconv32(const secpe_ntt32_table *t, const uint32_t *in, con
         a.r32[j] = make_uint2(r, shoup32_host(r, pj));
         a.m32[j] = (uint32_t)((1ull << 32) / pj);
     }
-    k_bconv32<<<dim3(t->n / 1024, batch), 256, 0, (cudaStream_t)stream>>>(a);
+    k_bconv32<<<dim3(t->n / 1024, batch), 256, 0, stream>>>(a);
     return cudaGetLastError() == cudaSuccess ? SECPE_OK : SECPE_ECUDA;
+}
+
+}  // namespace
+
+extern "C" int secpe_bconv32(const secpe_ntt32_table *t, const uint32_t *in, const int32_t *in_idx, int n_in,
+                             uint32_t *out, const int32_t *out_idx, int n_out, int batch, void *stream) {
+    SECPE_CHECK(check_limbs(t, in, in_idx, n_in));
+    SECPE_CHECK(check_limbs(t, out, out_idx, n_out));
+    return bconv32(t, in, (long long)n_in * t->n, in_idx, n_in, out, (long long)n_out * t->n, out_idx, n_out, batch,
+                   (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// Hybrid key switching on 32-bit residues (the word-size probe's key switch;
+// the steps of keyswitch.cu on the 64-bit path): INTT of d, per digit
+// FastBConv to every other prime and NTT, the key inner product, then ModDown
+// (rounded division by P: [x + h]_P with h = floor(P/2) on every coefficient
+// of the special limbs, FastBConv to the q primes, minus h on every
+// coefficient, NTT, out_i = (x_i - conv_i) P^-1).
+
+namespace {
+
+constexpr int kMaxDig32 = 16;
+constexpr int kMaxTgt32 = 64;
+
+// x mod p for a 64-bit x = hi 2^32 + lo: [hi 2^32]_p by Shoup, lo by a
+// quotient estimate, each in [0, 2p).
+__device__ __forceinline__ uint32_t red64_32(unsigned long long x, uint32_t p, uint2 r32, uint32_t m32) {
+    const uint32_t hi = (uint32_t)(x >> 32), lo = (uint32_t)x;
+    return red4_32(shoup32(hi, r32.x, r32.y, p) + (lo - __umulhi(lo, m32) * p), p);
+}
+
+struct Ip32Args {
+    const uint32_t *d;    // [B][nq][N] NTT form
+    const uint32_t *ext;  // [B][tot][N]: digit j's other primes at off[j]
+    const uint32_t *key;  // [dnum][2][nt][N]
+    uint32_t *acc;        // [B][2][nt][N]
+    int nq, nt, tot, ndig;
+    int lo[kMaxDig32], hi[kMaxDig32], off[kMaxDig32];
+    uint32_t p[kMaxTgt32];
+    uint2 r32[kMaxTgt32];
+    uint32_t m32[kMaxTgt32];
+};
+
+// grid: (N / 256, nt * B); the items sharing one key limb run back to back
+__global__ void __launch_bounds__(256) k_ip32(const __grid_constant__ Ip32Args a) {
+    const int nitem = gridDim.y / a.nt;
+    const int t = blockIdx.y / nitem, item = blockIdx.y % nitem;
+    const int e = blockIdx.x * 256 + threadIdx.x;
+    unsigned long long s0 = 0, s1 = 0;
+    const size_t plane = (size_t)a.nt * 65536;
+    for (int j = 0; j < a.ndig; j++) {
+        uint32_t x;
+        if (t >= a.lo[j] && t < a.hi[j]) {
+            x = a.d[((size_t)item * a.nq + t) * 65536 + e];
+        } else {
+            const int tt = t < a.lo[j] ? t : t - (a.hi[j] - a.lo[j]);
+            x = a.ext[((size_t)item * a.tot + a.off[j] + tt) * 65536 + e];
+        }
+        const uint32_t *kb = a.key + (size_t)j * 2 * plane + (size_t)t * 65536 + e;
+        s0 += (unsigned long long)x * kb[0];
+        s1 += (unsigned long long)x * kb[plane];
+    }
+    uint32_t *o = a.acc + ((size_t)item * 2 * a.nt + t) * 65536 + e;
+    o[0] = red64_32(s0, a.p[t], a.r32[t], a.m32[t]);
+    o[plane] = red64_32(s1, a.p[t], a.r32[t], a.m32[t]);
+}
+
+// x[row][limb l][N] += c[l] mod prime of limb l (rows of nl limbs)
+struct AddC32Args {
+    uint32_t *x;
+    int nl;
+    uint32_t c[kMaxTgt32], q[kMaxTgt32];
+};
+
+__global__ void __launch_bounds__(256) k_addc32(const __grid_constant__ AddC32Args a) {
+    const int li = blockIdx.y, l = li % a.nl;
+    const int e = blockIdx.x * 256 + threadIdx.x;
+    uint32_t *p = a.x + (size_t)li * 65536 + e;
+    const uint32_t v = *p + a.c[l];
+    *p = v >= a.q[l] ? v - a.q[l] : v;
+}
+
+// out[b][k][i] = (acc[b][k][i] - conv[b][k][i]) * P^-1 mod q_i, conv the
+// NTT of FastBConv([x + h]_P) - h
+struct Epi32Args {
+    const uint32_t *acc;   // [B][2][nt][N]
+    const uint32_t *conv;  // [B][2][nq][N] (NTT form)
+    uint32_t *out;         // [B][2][nq][N]
+    int nq, nt;
+    uint32_t q[kMaxTgt32];
+    uint2 pinv[kMaxTgt32];
+};
+
+__global__ void __launch_bounds__(256) k_epi32(const __grid_constant__ Epi32Args a) {
+    const int li = blockIdx.y;  // (item, poly, i)
+    const int i = li % a.nq, kp = li / a.nq;
+    const int e = blockIdx.x * 256 + threadIdx.x;
+    const uint32_t q = a.q[i];
+    const uint32_t x = a.acc[((size_t)kp * a.nt + i) * 65536 + e];
+    const uint32_t c = a.conv[((size_t)kp * a.nq + i) * 65536 + e];
+    const uint32_t v = x >= c ? x - c : x + q - c;  // [0, q)
+    a.out[((size_t)kp * a.nq + i) * 65536 + e] = red2_32(shoup32(v, a.pinv[i].x, a.pinv[i].y, q), q);
+}
+
+void red_consts(const secpe_ntt32_table *t, int pi, uint32_t &p, uint2 &r, uint32_t &m) {
+    p = t->q[pi];
+    const uint32_t rr = (uint32_t)((1ull << 32) % p);
+    r = make_uint2(rr, shoup32_host(rr, p));
+    m = (uint32_t)((1ull << 32) / p);
+}
+
+}  // namespace
+
+extern "C" int secpe_keyswitch32(const secpe_ntt32_table *t, const uint32_t *d, const int32_t *q_idx, int nq,
+                                 const int32_t *p_idx, int np, int alpha, const uint32_t *key, uint32_t *out,
+                                 int batch, void *stream) {
+    SECPE_CHECK(check_limbs(t, d, q_idx, nq));
+    SECPE_CHECK(check_limbs(t, out, q_idx, nq));
+    SECPE_CHECK(check_limbs(t, key, p_idx, np));
+    const int nt = nq + np, ndig = alpha > 0 ? (nq + alpha - 1) / alpha : 0;
+    if (nq < 1 || np < 1 || nt > kMaxTgt32 || alpha < 1 || alpha > kMaxIn32 || np > kMaxIn32 || ndig > kMaxDig32 ||
+        batch < 1 || (long long)batch * 2 * nt > 65535)
+        return SECPE_EINVAL;
+    const int n = t->n;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> tgt(q_idx, q_idx + nq);
+    tgt.insert(tgt.end(), p_idx, p_idx + np);
+    for (int i = 0; i < nt; i++)
+        for (int k = 0; k < i; k++)
+            if (tgt[i] == tgt[k]) return SECPE_EINVAL;
+    Ip32Args ia;
+    int tot = 0;
+    for (int j = 0; j < ndig; j++) {
+        ia.lo[j] = j * alpha;
+        ia.hi[j] = std::min(nq, (j + 1) * alpha);
+        ia.off[j] = tot;
+        tot += nt - (ia.hi[j] - ia.lo[j]);
+    }
+    uint32_t *coef = nullptr, *ext = nullptr, *acc = nullptr, *spec = nullptr, *conv = nullptr;
+    const size_t W = sizeof(uint32_t) * n;
+    bool ok = cudaMallocAsync((void **)&coef, W * batch * nq, st) == cudaSuccess &&
+              cudaMallocAsync((void **)&ext, W * batch * tot, st) == cudaSuccess &&
+              cudaMallocAsync((void **)&acc, W * batch * 2 * nt, st) == cudaSuccess &&
+              cudaMallocAsync((void **)&spec, W * batch * 2 * np, st) == cudaSuccess &&
+              cudaMallocAsync((void **)&conv, W * batch * 2 * nq, st) == cudaSuccess;
+    int rc = ok ? SECPE_OK : SECPE_ENOMEM;
+    std::vector<int32_t> pidx;
+    // 1. INTT of d
+    if (rc == SECPE_OK && cudaMemcpyAsync(coef, d, W * batch * nq, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        rc = SECPE_ECUDA;
+    for (int b = 0; b < batch; b++) pidx.insert(pidx.end(), q_idx, q_idx + nq);
+    if (rc == SECPE_OK) rc = secpe_ntt32(t, coef, pidx.data(), batch * nq, 1, stream);
+    // 2. ModUp per digit, NTT of the extended limbs
+    std::vector<int32_t> eidx;
+    for (int j = 0; j < ndig && rc == SECPE_OK; j++) {
+        std::vector<int32_t> others;
+        for (int i = 0; i < nt; i++)
+            if (i < ia.lo[j] || i >= ia.hi[j]) others.push_back(tgt[i]);
+        rc = bconv32(t, coef + (size_t)ia.lo[j] * n, (long long)nq * n, q_idx + ia.lo[j], ia.hi[j] - ia.lo[j],
+                     ext + (size_t)ia.off[j] * n, (long long)tot * n, others.data(), (int)others.size(), batch, st);
+        eidx.insert(eidx.end(), others.begin(), others.end());
+    }
+    pidx.clear();
+    for (int b = 0; b < batch; b++) pidx.insert(pidx.end(), eidx.begin(), eidx.end());
+    if (rc == SECPE_OK) rc = secpe_ntt32(t, ext, pidx.data(), batch * tot, 0, stream);
+    // 3. key inner product
+    if (rc == SECPE_OK) {
+        ia.d = d;
+        ia.ext = ext;
+        ia.key = key;
+        ia.acc = acc;
+        ia.nq = nq;
+        ia.nt = nt;
+        ia.tot = tot;
+        ia.ndig = ndig;
+        for (int i = 0; i < nt; i++) red_consts(t, tgt[i], ia.p[i], ia.r32[i], ia.m32[i]);
+        k_ip32<<<dim3(n / 256, nt * batch), 256, 0, st>>>(ia);
+        if (cudaGetLastError() != cudaSuccess) rc = SECPE_ECUDA;
+    }
+    // 4. ModDown of both polynomials
+    if (rc == SECPE_OK &&
+        cudaMemcpy2DAsync(spec, W * np, acc + (size_t)nq * n, W * nt, W * np, (size_t)batch * 2,
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        rc = SECPE_ECUDA;
+    pidx.clear();
+    for (int r = 0; r < 2 * batch; r++) pidx.insert(pidx.end(), p_idx, p_idx + np);
+    if (rc == SECPE_OK) rc = secpe_ntt32(t, spec, pidx.data(), 2 * batch * np, 1, stream);
+    // h = floor(P / 2) mod each prime: P = prod p_r
+    std::vector<u64> hmod(nt);
+    for (int i = 0; i < nt; i++) {
+        const u64 m = t->q[tgt[i]];
+        // floor(P/2) mod m = (P - (P mod 2)) / 2 mod m; P is odd, so (P - 1) * 2^-1 mod m
+        u64 pm = 1;
+        for (int r = 0; r < np; r++) pm = hm::mulmod(pm, t->q[p_idx[r]] % m, m);
+        hmod[i] = hm::mulmod((pm + m - 1) % m, hm::invmod(2, m), m);
+    }
+    if (rc == SECPE_OK) {
+        AddC32Args ca;
+        ca.x = spec;
+        ca.nl = np;
+        for (int r = 0; r < np; r++) {
+            ca.c[r] = (uint32_t)hmod[nq + r];
+            ca.q[r] = t->q[p_idx[r]];
+        }
+        k_addc32<<<dim3(n / 256, 2 * batch * np), 256, 0, st>>>(ca);
+        if (cudaGetLastError() != cudaSuccess) rc = SECPE_ECUDA;
+    }
+    if (rc == SECPE_OK)
+        rc = bconv32(t, spec, (long long)np * n, p_idx, np, conv, (long long)nq * n, q_idx, nq, 2 * batch, st);
+    if (rc == SECPE_OK) {
+        // - h on every coefficient of the conversion
+        AddC32Args ca;
+        ca.x = conv;
+        ca.nl = nq;
+        for (int i = 0; i < nq; i++) {
+            ca.q[i] = t->q[q_idx[i]];
+            ca.c[i] = (uint32_t)((ca.q[i] - hmod[i]) % ca.q[i]);
+        }
+        k_addc32<<<dim3(n / 256, 2 * batch * nq), 256, 0, st>>>(ca);
+        if (cudaGetLastError() != cudaSuccess) rc = SECPE_ECUDA;
+    }
+    pidx.clear();
+    for (int r = 0; r < 2 * batch; r++) pidx.insert(pidx.end(), q_idx, q_idx + nq);
+    if (rc == SECPE_OK) rc = secpe_ntt32(t, conv, pidx.data(), 2 * batch * nq, 0, stream);
+    if (rc == SECPE_OK) {
+        Epi32Args ea;
+        ea.acc = acc;
+        ea.conv = conv;
+        ea.out = out;
+        ea.nq = nq;
+        ea.nt = nt;
+        for (int i = 0; i < nq; i++) {
+            const u64 q = t->q[q_idx[i]];
+            u64 pm = 1;
+            for (int r = 0; r < np; r++) pm = hm::mulmod(pm, t->q[p_idx[r]] % q, q);
+            const u64 pinv = hm::invmod(pm, q);
+            ea.q[i] = (uint32_t)q;
+            ea.pinv[i] = make_uint2((uint32_t)pinv, shoup32_host((uint32_t)pinv, (uint32_t)q));
+        }
+        k_epi32<<<dim3(n / 256, 2 * batch * nq), 256, 0, st>>>(ea);
+        if (cudaGetLastError() != cudaSuccess) rc = SECPE_ECUDA;
+    }
+    cudaFreeAsync(coef, st);
+    cudaFreeAsync(ext, st);
+    cudaFreeAsync(acc, st);
+    cudaFreeAsync(spec, st);
+    cudaFreeAsync(conv, st);
+    return rc;
 }

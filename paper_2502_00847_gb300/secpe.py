@@ -35,7 +35,7 @@ EXPORTS = [
     "secpe_linear_apply", "secpe_encrypt_replicated", "secpe_boot_rotation_steps", "secpe_boot_create",
     "secpe_boot_create_coeffs", "secpe_boot_destroy", "secpe_bootstrap_batch", "secpe_bootstrap",
     "secpe_argmax_batch_boot", "secpe_level_plan", "secpe_ntt32_create", "secpe_ntt32_destroy", "secpe_ntt32",
-    "secpe_bconv32", "secpe_rotate_hoisted",
+    "secpe_bconv32", "secpe_rotate_hoisted", "secpe_keyswitch32",
 ]
 
 
@@ -174,6 +174,7 @@ def lib():
         "secpe_ntt32": (i32, [vp, vp, P(i32), i32, i32, vp]),
         "secpe_bconv32": (i32, [vp, vp, P(i32), i32, vp, P(i32), i32, i32, vp]),
         "secpe_rotate_hoisted": (i32, [vp, vp, P(CtC), P(i32), i32, P(CtC), vp]),
+        "secpe_keyswitch32": (i32, [vp, vp, P(i32), i32, P(i32), i32, i32, vp, vp, i32, vp]),
         "secpe_boot_create": (i32, [vp, i32, P(vp)]),
         "secpe_boot_create_coeffs": (i32, [vp, i32, P(ctypes.c_int64), P(ctypes.c_int64), P(vp)]),
         "secpe_boot_destroy": (None, [vp]),
@@ -1029,6 +1030,12 @@ class Ntt32:
         _check(lib().secpe_bconv32(self.h, ctypes.c_void_p(x.data_ptr()), self._idx(in_idx), len(in_idx),
                                    ctypes.c_void_p(out.data_ptr()), self._idx(out_idx), len(out_idx), x.shape[0],
                                    _stream()), "secpe_bconv32")
+
+    def keyswitch(self, d, q_idx, p_idx, alpha, key, out):
+        """d [batch][nq][N] -> out [batch][2][nq][N] with key [dnum][2][nq+np][N] (uint32 device tensors)."""
+        _check(lib().secpe_keyswitch32(self.h, ctypes.c_void_p(d.data_ptr()), self._idx(q_idx), len(q_idx),
+                                       self._idx(p_idx), len(p_idx), alpha, ctypes.c_void_p(key.data_ptr()),
+                                       ctypes.c_void_p(out.data_ptr()), d.shape[0], _stream()), "secpe_keyswitch32")
 
     def close(self):
         if self.h:

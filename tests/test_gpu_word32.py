@@ -6,6 +6,9 @@ under the about-29-bit primes of the WORD32 prime chain, N = 2^16.
   the input back exactly, and the inverse of the oracle's transform too;
 * the fast base conversion of a 14-limb digit to 42 other primes equals the
   oracle's FastBConv, item by item;
+* the hybrid key switching of 32-bit residues (ModUp, inner product with
+  the oracle's relinearisation key, rounded ModDown) equals the oracle's
+  keyswitch residue for residue;
 * bad tables and arguments are refused on the host."""
 import numpy as np
 import pytest
@@ -75,6 +78,29 @@ def test_bconv32_matches_oracle(env):
     for b in range(B):
         want = o.fast_bconv(x[b], src, dst)
         assert np.array_equal(got[b], want), b
+
+
+def test_keyswitch32_matches_oracle(env):
+    import torch
+    from oracle import Params
+    _, _, _, secpe, _ = env
+    p = Params(log_n=16, q0_bits=29, q_bits=29, n_q=12, p_bits=29, n_p=4, dnum=3, log_scale=29)
+    o = Oracle(p)
+    o.keygen(33)
+    nq, L = p.n_q, p.n_q - 1
+    t = secpe.Ntt32([int(q) for q in o.primes])
+    rng = np.random.default_rng(34)
+    B = 2
+    d = np.stack([np.stack([rng.integers(0, o.primes[i], o.n, dtype=np.uint64) for i in range(nq)])
+                  for _ in range(B)])
+    key = _to_dev(torch, o.rlk)
+    out = torch.zeros((B, 2, nq, o.n), dtype=torch.int32, device="cuda")
+    t.keyswitch(_to_dev(torch, d), list(range(nq)), list(range(nq, nq + p.n_p)), p.alpha, key, out)
+    got = _to_host(out).reshape(B, 2, nq, o.n)
+    for b in range(B):
+        k0, k1 = o.keyswitch(d[b], L, o.rlk)
+        assert np.array_equal(got[b, 0], k0) and np.array_equal(got[b, 1], k1), b
+    t.close()
 
 
 def test_word32_rejects_bad_arguments(env):
