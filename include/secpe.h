@@ -422,10 +422,14 @@ int secpe_bconv32(const secpe_ntt32_table *t, const uint32_t *in, const int32_t 
  * alpha)), out [batch][2][nq][N] = ModDown(sum_j ModUp_j(d) * key_j) with
  * ModDown the rounded division by P = prod of the p_idx primes.  nq + np <=
  * 64, alpha <= 16, np <= 16, primes distinct; device buffers 16-byte
- * aligned; temporary device memory from the stream-ordered allocator. */
+ * aligned; temporary device memory from the stream-ordered allocator.
+ * fused = 0: one launch per step (INTT, FastBConv per digit, NTT, inner
+ * product); fused = 1: the conversion inside the NTT's column pass and the
+ * inner product inside its row pass, as on the 64-bit path (at most 256
+ * extended limbs per item).  Both give the same residues. */
 int secpe_keyswitch32(const secpe_ntt32_table *t, const uint32_t *d, const int32_t *q_idx, int nq,
                       const int32_t *p_idx, int np, int alpha, const uint32_t *key, uint32_t *out, int batch,
-                      void *stream);
+                      int fused, void *stream);
 
 /* ---- SecPE circuit ----------------------------------------------------- */
 /* Sign(x) = f^df(g^dg(x)) (SecPE Eq. comp), each degree-9 polynomial by a

@@ -28,6 +28,7 @@
 struct secpe_ntt32_table {
     int log_n = 0, n = 0, np = 0;
     std::vector<uint32_t> q;
+    std::vector<u64> h_tw1;  // psi^-brv(1) per prime (the inverse's last twiddle)
     uint32_t *d_q = nullptr;
     uint2 *d_twf = nullptr, *d_twi = nullptr;      // [np][N]: (w, w')
     uint2 *d_ninv = nullptr, *d_ninvw1 = nullptr;  // [np]
@@ -112,6 +113,10 @@ struct Ntt32Args {
     const uint2 *tw;  // [np][N], forward or inverse
     const uint2 *ninv, *ninvw1;
     uint8_t prime_of[kMaxLimbs32];
+    // inverse only, optional: limb i's final scaling N^-1 s_i (and its
+    // product with the last twiddle) instead of N^-1, both with Shoup parts
+    int has_scale;
+    uint2 scale[2 * kMaxLimbs32];
 };
 
 // Column-pass shared layout: row r of the 16-column tile at 16 words, rows
@@ -143,7 +148,8 @@ __global__ void __launch_bounds__(256) k_ntt32_colpass(const __grid_constant__ N
 #pragma unroll
         for (int k = 0; k < 16; k++) g[((u << 4) | k) * 256 + c0 + col] = x[k];
     } else {
-        const uint2 ni = a.ninv[pi], nw = a.ninvw1[pi];
+        const uint2 ni = a.has_scale ? a.scale[2 * lid] : a.ninv[pi];
+        const uint2 nw = a.has_scale ? a.scale[2 * lid + 1] : a.ninvw1[pi];
 #pragma unroll
         for (int k = 0; k < 16; k++) x[k] = g[((u << 4) | k) * 256 + c0 + col];
         inv16<8, 0, false>(x, u << 4, tw, 1, q, ni, nw);
@@ -309,6 +315,7 @@ extern "C" int secpe_ntt32_create(int log_n, const uint32_t *primes, int n_prime
             twi[(size_t)s * n + i] = make_uint2((uint32_t)ipw[b], shoup32_host((uint32_t)ipw[b], (uint32_t)q));
         }
         const u64 nv = hm::invmod((u64)n, q), nw1 = hm::mulmod(nv, ipw[hm::bitrev(1, log_n)], q);
+        t->h_tw1.push_back(ipw[hm::bitrev(1, log_n)]);
         ni[s] = make_uint2((uint32_t)nv, shoup32_host((uint32_t)nv, (uint32_t)q));
         niw[s] = make_uint2((uint32_t)nw1, shoup32_host((uint32_t)nw1, (uint32_t)q));
     }
@@ -340,9 +347,23 @@ extern "C" void secpe_ntt32_destroy(secpe_ntt32_table *t) {
     delete t;
 }
 
+namespace {
+int ntt32_run(const secpe_ntt32_table *t, uint32_t *limbs, const int32_t *prime_idx, int count, int inverse,
+              const uint32_t *scale_by, cudaStream_t stream);
+}  // namespace
+
 extern "C" int secpe_ntt32(const secpe_ntt32_table *t, uint32_t *limbs, const int32_t *prime_idx, int count, int inverse,
                            void *stream) {
     SECPE_CHECK(check_limbs(t, limbs, prime_idx, count));
+    return ntt32_run(t, limbs, prime_idx, count, inverse, nullptr, (cudaStream_t)stream);
+}
+
+namespace {
+
+// scale_by (inverse only, optional): limb i's result multiplied by
+// scale_by[i] (a residue of its prime) within the final N^-1 scaling
+int ntt32_run(const secpe_ntt32_table *t, uint32_t *limbs, const int32_t *prime_idx, int count, int inverse,
+              const uint32_t *scale_by, cudaStream_t stream) {
     cudaStream_t s = (cudaStream_t)stream;
     for (int c0 = 0; c0 < count; c0 += kMaxLimbs32) {
         const int nl = std::min(kMaxLimbs32, count - c0);
@@ -353,6 +374,16 @@ extern "C" int secpe_ntt32(const secpe_ntt32_table *t, uint32_t *limbs, const in
         a.ninv = t->d_ninv;
         a.ninvw1 = t->d_ninvw1;
         for (int i = 0; i < nl; i++) a.prime_of[i] = (uint8_t)prime_idx[c0 + i];
+        a.has_scale = scale_by && inverse ? 1 : 0;
+        if (a.has_scale)
+            for (int i = 0; i < nl; i++) {
+                const u64 q = t->q[prime_idx[c0 + i]];
+                const u64 ni = hm::mulmod(hm::invmod((u64)t->n, q), scale_by[c0 + i] % q, q);
+                const u64 w1 = t->h_tw1[prime_idx[c0 + i]];
+                const u64 nw = hm::mulmod(ni, w1, q);
+                a.scale[2 * i] = make_uint2((uint32_t)ni, shoup32_host((uint32_t)ni, (uint32_t)q));
+                a.scale[2 * i + 1] = make_uint2((uint32_t)nw, shoup32_host((uint32_t)nw, (uint32_t)q));
+            }
         if (!inverse) {
             k_ntt32_colpass<false><<<nl * 16, 256, 0, s>>>(a);
             k_ntt32_rowpass<false><<<nl * 16, 256, 0, s>>>(a);
@@ -363,6 +394,8 @@ extern "C" int secpe_ntt32(const secpe_ntt32_table *t, uint32_t *limbs, const in
     }
     return cudaGetLastError() == cudaSuccess ? SECPE_OK : SECPE_ECUDA;
 }
+
+}  // namespace
 
 namespace {
 
@@ -520,9 +553,211 @@ void red_consts(const secpe_ntt32_table *t, int pi, uint32_t &p, uint2 &r, uint3
 
 }  // namespace
 
+// Fused ModUp and inner product (the 64-bit path's k_colpass_bconv and
+// k_rowpass_ip on 32-bit words).  Pass A: for one extended limb (item,
+// digit j, target prime) and 16 columns, the FastBConv of the digit's
+// pre-multiplied coefficients y (the INTT applied [Qhat_i^-1]) straight
+// into registers, then the forward column rounds; pass B + inner product:
+// for one target limb and 16 rows, every digit's row rounds (or the input's
+// own limb) multiplied by the key and accumulated modulo the target prime.
+namespace {
+
+constexpr int kFusedSrc32 = 16;
+
+struct ModUpA32Args {
+    const uint32_t *y;     // [B][nq][N] coefficient form, times [Qhat_i^-1]
+    uint32_t *ext;         // [B][tot][N] pass-A output (lazy, [0, 4p))
+    const uint32_t *q;     // device prime table
+    const uint2 *tw;       // forward twiddles [np][N]
+    int nq, tot;
+    uint8_t lo[kMaxLimbs32], ns[kMaxLimbs32], prime_of[kMaxLimbs32];
+    uint32_t M[kMaxLimbs32][kFusedSrc32];  // [Qhat_r]_p of source r for extended limb l
+    uint2 r32[kMaxLimbs32];
+    uint32_t m32[kMaxLimbs32];
+};
+
+__global__ void __launch_bounds__(256) k_modup_a32(const __grid_constant__ ModUpA32Args a) {
+    __shared__ uint32_t sm[4096];
+    const int lid = blockIdx.x >> 4, c0 = (blockIdx.x & 15) * 16;
+    const int item = lid / a.tot, el = lid % a.tot;
+    const int pi = a.prime_of[el], lo = a.lo[el], ns = a.ns[el];
+    const uint32_t p = a.q[pi];
+    const uint2 *tw = a.tw + (size_t)pi * 65536;
+    const uint32_t *y = a.y + ((size_t)item * a.nq + lo) * 65536;
+    const int col = threadIdx.x & 15, u = threadIdx.x >> 4;
+    uint32_t x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        const int e = ((k << 4) | u) * 256 + c0 + col;
+        unsigned long long acc = 0;
+        for (int r = 0; r < ns; r++) acc += (unsigned long long)y[(size_t)r * 65536 + e] * a.M[el][r];
+        x[k] = red64_32(acc, p, a.r32[el], a.m32[el]);
+    }
+    fwd16<8, 4>(x, u, tw, 1, p);
+#pragma unroll
+    for (int k = 0; k < 16; k++) sm[col_sm((k << 4) | u, col)] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = sm[col_sm((u << 4) | k, col)];
+    fwd16<8, 0>(x, u << 4, tw, 1, p);
+    uint32_t *g = a.ext + ((size_t)item * a.tot + el) * 65536;
+#pragma unroll
+    for (int k = 0; k < 16; k++) g[((u << 4) | k) * 256 + c0 + col] = x[k];
+}
+
+struct IpB32Args {
+    const uint32_t *d;    // [B][nq][N] NTT form
+    const uint32_t *ext;  // pass-A output
+    const uint32_t *key;  // [dnum][2][nt][N]
+    uint32_t *acc;        // [B][2][nt][N]
+    const uint32_t *q;
+    const uint2 *tw;
+    int nq, nt, tot, ndig, B;
+    int lo[kMaxDig32], hi[kMaxDig32], off[kMaxDig32];
+    uint8_t prime_of[kMaxTgt32];
+    uint2 r32[kMaxTgt32];
+    uint32_t m32[kMaxTgt32];
+};
+
+// grid: ((t * 16 + tile) * B + item)
+__global__ void __launch_bounds__(256) k_ip_b32(const __grid_constant__ IpB32Args a) {
+    __shared__ uint32_t sm[16 * 272];
+    const int item = blockIdx.x % a.B, tt16 = blockIdx.x / a.B;
+    const int tile = tt16 & 15, t = tt16 >> 4, r0 = tile * 16;
+    const int pi = a.prime_of[t];
+    const uint32_t p = a.q[pi];
+    const uint2 *tw = a.tw + (size_t)pi * 65536;
+    const int u = threadIdx.x & 15, row = threadIdx.x >> 4, base = 256 + r0 + row;
+    uint32_t *__restrict__ srow = sm + row * 272;
+    const size_t plane = (size_t)a.nt * 65536, toff = (size_t)t * 65536 + (size_t)r0 * 256;
+    uint32_t acc0[16], acc1[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) acc0[i] = acc1[i] = 0;
+    for (int j = 0; j < a.ndig; j++) {
+        const bool own = t >= a.lo[j] && t < a.hi[j];
+        if (!own) {
+            const int ti = t < a.lo[j] ? t : t - (a.hi[j] - a.lo[j]);
+            const uint32_t *g = a.ext + ((size_t)item * a.tot + a.off[j] + ti) * 65536 + (size_t)r0 * 256;
+            uint32_t x[16];
+#pragma unroll
+            for (int k = 0; k < 16; k++) x[k] = g[row * 256 + ((k << 4) | u)];
+            fwd16<8, 4>(x, u, tw, base, p);
+#pragma unroll
+            for (int k = 0; k < 16; k++) srow[PAD17((k << 4) | u)] = x[k];
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < 16; k++) x[k] = srow[PAD17((u << 4) | k)];
+            fwd16<8, 0>(x, u << 4, tw, base, p);
+#pragma unroll
+            for (int k = 0; k < 16; k++) srow[PAD17((u << 4) | k)] = red4_32(x[k], p);
+            __syncthreads();
+        }
+        const uint32_t *kb = a.key + (size_t)j * 2 * plane + toff;
+        const uint32_t *dd = a.d + ((size_t)item * a.nq + t) * 65536 + (size_t)r0 * 256;
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const int e = threadIdx.x + 256 * i;
+            const uint32_t v = own ? dd[e] : sm[(e >> 8) * 272 + PAD17(e & 255)];
+            const uint32_t k0 = kb[e], k1 = kb[plane + e];
+            acc0[i] = red2_32(acc0[i] + red64_32((unsigned long long)v * k0, p, a.r32[t], a.m32[t]), p);
+            acc1[i] = red2_32(acc1[i] + red64_32((unsigned long long)v * k1, p, a.r32[t], a.m32[t]), p);
+        }
+        if (!own) __syncthreads();
+    }
+    uint32_t *o = a.acc + (size_t)item * 2 * plane + toff;
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        const int e = threadIdx.x + 256 * i;
+        o[e] = acc0[i];
+        o[plane + e] = acc1[i];
+    }
+}
+
+// steps 1-3 fused: INTT of d with the ModUp pre-multipliers, pass A with
+// FastBConv for every extended limb, pass B + inner product for every target
+int modup_ip_fused32(const secpe_ntt32_table *t, const uint32_t *d, const int32_t *q_idx, int nq,
+                     const std::vector<int32_t> &tgt, int alpha, int ndig, const Ip32Args &ia, int tot,
+                     const uint32_t *key, uint32_t *coef, uint32_t *ext, uint32_t *acc, int batch, cudaStream_t st) {
+    const int n = t->n, nt = (int)tgt.size();
+    if (tot > kMaxLimbs32 || alpha > kFusedSrc32) return SECPE_EINVAL;
+    // [Qhat_i^-1]_{q_i} of every limb within its digit
+    std::vector<uint32_t> qhinv(nq);
+    for (int j = 0; j < ndig; j++)
+        for (int i = ia.lo[j]; i < ia.hi[j]; i++) {
+            const u64 qi = t->q[q_idx[i]];
+            u64 qh = 1;
+            for (int k = ia.lo[j]; k < ia.hi[j]; k++)
+                if (k != i) qh = hm::mulmod(qh, t->q[q_idx[k]] % qi, qi);
+            qhinv[i] = (uint32_t)hm::invmod(qh, qi);
+        }
+    if (cudaMemcpyAsync(coef, d, sizeof(uint32_t) * n * batch * nq, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return SECPE_ECUDA;
+    std::vector<int32_t> pidx;
+    std::vector<uint32_t> sc;
+    for (int b = 0; b < batch; b++) {
+        pidx.insert(pidx.end(), q_idx, q_idx + nq);
+        sc.insert(sc.end(), qhinv.begin(), qhinv.end());
+    }
+    SECPE_CHECK(ntt32_run(t, coef, pidx.data(), batch * nq, 1, sc.data(), st));
+    ModUpA32Args ma;
+    ma.y = coef;
+    ma.ext = ext;
+    ma.q = t->d_q;
+    ma.tw = t->d_twf;
+    ma.nq = nq;
+    ma.tot = tot;
+    for (int j = 0; j < ndig; j++) {
+        int el = ia.off[j];
+        for (int i = 0; i < nt; i++) {
+            if (i >= ia.lo[j] && i < ia.hi[j]) continue;
+            const u64 pt = t->q[tgt[i]];
+            ma.lo[el] = (uint8_t)ia.lo[j];
+            ma.ns[el] = (uint8_t)(ia.hi[j] - ia.lo[j]);
+            ma.prime_of[el] = (uint8_t)tgt[i];
+            for (int r = 0; r < ia.hi[j] - ia.lo[j]; r++) {
+                u64 m = 1;
+                for (int k = ia.lo[j]; k < ia.hi[j]; k++)
+                    if (k != ia.lo[j] + r) m = hm::mulmod(m, t->q[q_idx[k]] % pt, pt);
+                ma.M[el][r] = (uint32_t)m;
+            }
+            uint32_t pp;
+            red_consts(t, tgt[i], pp, ma.r32[el], ma.m32[el]);
+            el++;
+        }
+    }
+    k_modup_a32<<<(unsigned)(batch * tot * 16), 256, 0, st>>>(ma);
+    if (cudaGetLastError() != cudaSuccess) return SECPE_ECUDA;
+    IpB32Args ib;
+    ib.d = d;
+    ib.ext = ext;
+    ib.key = key;
+    ib.acc = acc;
+    ib.q = t->d_q;
+    ib.tw = t->d_twf;
+    ib.nq = nq;
+    ib.nt = nt;
+    ib.tot = tot;
+    ib.ndig = ndig;
+    ib.B = batch;
+    for (int j = 0; j < ndig; j++) {
+        ib.lo[j] = ia.lo[j];
+        ib.hi[j] = ia.hi[j];
+        ib.off[j] = ia.off[j];
+    }
+    for (int i = 0; i < nt; i++) {
+        uint32_t pp;
+        ib.prime_of[i] = (uint8_t)tgt[i];
+        red_consts(t, tgt[i], pp, ib.r32[i], ib.m32[i]);
+    }
+    k_ip_b32<<<(unsigned)(nt * 16 * batch), 256, 0, st>>>(ib);
+    return cudaGetLastError() == cudaSuccess ? SECPE_OK : SECPE_ECUDA;
+}
+
+}  // namespace
+
 extern "C" int secpe_keyswitch32(const secpe_ntt32_table *t, const uint32_t *d, const int32_t *q_idx, int nq,
                                  const int32_t *p_idx, int np, int alpha, const uint32_t *key, uint32_t *out,
-                                 int batch, void *stream) {
+                                 int batch, int fused, void *stream) {
     SECPE_CHECK(check_limbs(t, d, q_idx, nq));
     SECPE_CHECK(check_limbs(t, out, q_idx, nq));
     SECPE_CHECK(check_limbs(t, key, p_idx, np));
@@ -554,6 +789,10 @@ extern "C" int secpe_keyswitch32(const secpe_ntt32_table *t, const uint32_t *d, 
               cudaMallocAsync((void **)&conv, W * batch * 2 * nq, st) == cudaSuccess;
     int rc = ok ? SECPE_OK : SECPE_ENOMEM;
     std::vector<int32_t> pidx;
+    if (fused) {
+        rc = rc == SECPE_OK ? modup_ip_fused32(t, d, q_idx, nq, tgt, alpha, ndig, ia, tot, key, coef, ext, acc, batch, st)
+                            : rc;
+    } else {
     // 1. INTT of d
     if (rc == SECPE_OK && cudaMemcpyAsync(coef, d, W * batch * nq, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         rc = SECPE_ECUDA;
@@ -585,6 +824,7 @@ extern "C" int secpe_keyswitch32(const secpe_ntt32_table *t, const uint32_t *d, 
         for (int i = 0; i < nt; i++) red_consts(t, tgt[i], ia.p[i], ia.r32[i], ia.m32[i]);
         k_ip32<<<dim3(n / 256, nt * batch), 256, 0, st>>>(ia);
         if (cudaGetLastError() != cudaSuccess) rc = SECPE_ECUDA;
+    }
     }
     // 4. ModDown of both polynomials
     if (rc == SECPE_OK &&

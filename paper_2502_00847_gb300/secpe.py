@@ -174,7 +174,7 @@ def lib():
         "secpe_ntt32": (i32, [vp, vp, P(i32), i32, i32, vp]),
         "secpe_bconv32": (i32, [vp, vp, P(i32), i32, vp, P(i32), i32, i32, vp]),
         "secpe_rotate_hoisted": (i32, [vp, vp, P(CtC), P(i32), i32, P(CtC), vp]),
-        "secpe_keyswitch32": (i32, [vp, vp, P(i32), i32, P(i32), i32, i32, vp, vp, i32, vp]),
+        "secpe_keyswitch32": (i32, [vp, vp, P(i32), i32, P(i32), i32, i32, vp, vp, i32, i32, vp]),
         "secpe_boot_create": (i32, [vp, i32, P(vp)]),
         "secpe_boot_create_coeffs": (i32, [vp, i32, P(ctypes.c_int64), P(ctypes.c_int64), P(vp)]),
         "secpe_boot_destroy": (None, [vp]),
@@ -1031,11 +1031,12 @@ class Ntt32:
                                    ctypes.c_void_p(out.data_ptr()), self._idx(out_idx), len(out_idx), x.shape[0],
                                    _stream()), "secpe_bconv32")
 
-    def keyswitch(self, d, q_idx, p_idx, alpha, key, out):
+    def keyswitch(self, d, q_idx, p_idx, alpha, key, out, fused=True):
         """d [batch][nq][N] -> out [batch][2][nq][N] with key [dnum][2][nq+np][N] (uint32 device tensors)."""
         _check(lib().secpe_keyswitch32(self.h, ctypes.c_void_p(d.data_ptr()), self._idx(q_idx), len(q_idx),
                                        self._idx(p_idx), len(p_idx), alpha, ctypes.c_void_p(key.data_ptr()),
-                                       ctypes.c_void_p(out.data_ptr()), d.shape[0], _stream()), "secpe_keyswitch32")
+                                       ctypes.c_void_p(out.data_ptr()), d.shape[0], int(fused), _stream()),
+               "secpe_keyswitch32")
 
     def close(self):
         if self.h:

@@ -7,8 +7,8 @@ under the about-29-bit primes of the WORD32 prime chain, N = 2^16.
 * the fast base conversion of a 14-limb digit to 42 other primes equals the
   oracle's FastBConv, item by item;
 * the hybrid key switching of 32-bit residues (ModUp, inner product with
-  the oracle's relinearisation key, rounded ModDown) equals the oracle's
-  keyswitch residue for residue;
+  the oracle's relinearisation key, rounded ModDown), unfused and fused,
+  equals the oracle's keyswitch residue for residue;
 * bad tables and arguments are refused on the host."""
 import numpy as np
 import pytest
@@ -94,12 +94,13 @@ def test_keyswitch32_matches_oracle(env):
     d = np.stack([np.stack([rng.integers(0, o.primes[i], o.n, dtype=np.uint64) for i in range(nq)])
                   for _ in range(B)])
     key = _to_dev(torch, o.rlk)
-    out = torch.zeros((B, 2, nq, o.n), dtype=torch.int32, device="cuda")
-    t.keyswitch(_to_dev(torch, d), list(range(nq)), list(range(nq, nq + p.n_p)), p.alpha, key, out)
-    got = _to_host(out).reshape(B, 2, nq, o.n)
-    for b in range(B):
-        k0, k1 = o.keyswitch(d[b], L, o.rlk)
-        assert np.array_equal(got[b, 0], k0) and np.array_equal(got[b, 1], k1), b
+    want = [o.keyswitch(d[b], L, o.rlk) for b in range(B)]
+    for fused in (False, True):
+        out = torch.zeros((B, 2, nq, o.n), dtype=torch.int32, device="cuda")
+        t.keyswitch(_to_dev(torch, d), list(range(nq)), list(range(nq, nq + p.n_p)), p.alpha, key, out, fused)
+        got = _to_host(out).reshape(B, 2, nq, o.n)
+        for b in range(B):
+            assert np.array_equal(got[b, 0], want[b][0]) and np.array_equal(got[b, 1], want[b][1]), (fused, b)
     t.close()
 
 
