@@ -1021,6 +1021,20 @@ def _time_ms(torch, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def _graph_of(torch, fn):
+    """fn captured once as a CUDA graph (after one eager warm-up call); returns its replay."""
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g.replay
+
+
 def word_size_probe(secpe, torch, dev, steps):
     """The word-size lever: the negacyclic NTT (forward + inverse) on the
     64-bit residues of argmax8 (q0 60-bit + 23 x 50-bit, 1210 bits) against
@@ -1103,13 +1117,19 @@ def word_size_probe(secpe, torch, dev, steps):
     for i in qi:
         d32[:, i] = torch.randint(0, allp[i], (8, n), generator=gen, dtype=torch.int64, device=dev).to(torch.int32)
     o32 = torch.empty((8, 2, 40, n), dtype=torch.int32, device=dev)
-    msk32 = _time_ms(torch, lambda: t.keyswitch(d32, qi, pi, 14, key32, o32), reps)
+    # timed as CUDA-graph replays: the call builds its constant tables on the host every time (a probe
+    # without a plan object), which would otherwise leave the GPU idle between its launches
+    msk32u = _time_ms(torch, _graph_of(torch, lambda: t.keyswitch(d32, qi, pi, 14, key32, o32, False)), reps)
+    msk32 = _time_ms(torch, _graph_of(torch, lambda: t.keyswitch(d32, qi, pi, 14, key32, o32, True)), reps)
     del key32, d32, o32
-    out["keyswitch"] = {"ms_64bit_B8": msk64, "ms_32bit_B8": msk32, "bits_64bit": bitsk64, "bits_32bit": bitsk32,
+    out["keyswitch"] = {"ms_64bit_B8": msk64, "ms_32bit_B8": msk32, "ms_32bit_unfused_B8": msk32u,
+                        "bits_64bit": bitsk64, "bits_32bit": bitsk32,
                         "speedup_per_modulus_bit": (msk64 / bitsk64) / (msk32 / bitsk32),
-                        "note": "64-bit: the fused key switch (secpe_keyswitch_batch) on argmax8; 32-bit: "
-                                "secpe_keyswitch32, unfused (separate INTT, FastBConv, NTT, inner product and "
-                                "ModDown launches)"}
+                        "speedup_per_modulus_bit_unfused": (msk64 / bitsk64) / (msk32u / bitsk32),
+                        "note": "64-bit: the fused key switch (secpe_keyswitch_batch) on argmax8, direct calls; "
+                                "32-bit: secpe_keyswitch32 as CUDA-graph replays, ModUp conversion in the column "
+                                "pass and the inner product in the row pass (unfused: separate INTT, FastBConv, "
+                                "NTT and inner-product launches); ModDown unfused in both 32-bit forms"}
     out["note"] = ("NTT: forward + inverse, algorithmic bytes 4 x limbs x N x word (read + write per transform); "
                    "bconv32: input + output bytes; 64-bit reference is the library's secpe_ntt on argmax8 primes")
     t.close()
