@@ -503,8 +503,10 @@ int secpe_encrypt_replicated(secpe_ctx *ctx, const secpe_keys *keys, const doubl
  * of the ciphertext right after refresh j; *count = refreshes + 1 (with
  * targets null only *count is written).  secpe_encrypted_argmax,
  * secpe_argmax_batch and the server follow it with refresh_level = L, and
- * secpe_argmax_batch_boot with L - 16.  SECPE_EINVAL for bad arguments or
- * capacity < *count, SECPE_ELEVEL if a refresh leaves too few levels. */
+ * secpe_argmax_batch_boot with L - 16.  SECPE_EINVAL for bad arguments
+ * (log_n outside 4..17, C above N/4, which leaves no room for the 2 C'
+ * slots of Alg. 1) or capacity < *count, SECPE_ELEVEL if a refresh leaves
+ * too few levels. */
 int secpe_level_plan(const secpe_params *p, int C, int entry_level, int refresh_level, int32_t *targets,
                      int capacity, int *count);
 

@@ -279,7 +279,7 @@ extern "C" int secpe_encrypt(secpe_ctx *ctx, const secpe_keys *keys, const doubl
 
 extern "C" int secpe_encrypt_logits(secpe_ctx *ctx, const secpe_keys *keys, const double *v, int C, double d_min,
                                     uint64_t seed, secpe_ct *out, void *stream) {
-    if (!ctx || !v || C < 1) return SECPE_EINVAL;
+    if (!ctx || !v || C < 1 || C > ctx->n / 2) return SECPE_EINVAL;
     int cp = 1;
     while (cp < C) cp <<= 1;
     if (cp > ctx->n / 2) return SECPE_EINVAL;
@@ -299,7 +299,9 @@ static int pow2_at_least(int C) {
 
 extern "C" int secpe_packed_capacity(int log_n, int C) {
     if (log_n < 4 || log_n > 17 || C < 1) return SECPE_EINVAL;
-    const long long slots = 1ll << (log_n - 1), cp = pow2_at_least(C);
+    const long long slots = 1ll << (log_n - 1);
+    if (C > slots / 2) return 0;  // 2 C' > slots; also keeps C' far from int overflow
+    const long long cp = pow2_at_least(C);
     return 2 * cp > slots ? 0 : (int)(slots / (2 * cp));
 }
 
@@ -599,6 +601,8 @@ extern "C" int secpe_level_plan(const secpe_params *p, int C, int entry_level, i
     if (!p || !count || C < 2 || p->reserve < 1 || p->sign_dg < 0 || p->sign_df < 0 || p->sign_dg + p->sign_df < 1 ||
         entry_level < 0 || entry_level >= p->n_q || refresh_level < 1 || refresh_level >= p->n_q)
         return SECPE_EINVAL;
+    // 2 C' slots must fit in the N/2 of the ring: C <= N/4 (N <= 2^17)
+    if (p->log_n < 4 || p->log_n > 17 || C > (1 << (p->log_n - 2))) return SECPE_EINVAL;
     int r = 0;
     while ((1 << r) < C) r++;
     LevelPlan lp;
@@ -641,6 +645,7 @@ extern "C" int secpe_argmax_batch_boot(secpe_ctx *ctx, const secpe_keys *keys, c
                                        const secpe_query *q, int n_queries, void *stream) {
     if (!ctx || !bt || !q || n_queries < 0) return SECPE_EINVAL;
     for (int i = 0; i < n_queries; i++) {
+        if (q[i].C > boot_block(bt)) return SECPE_EINVAL;
         int cp = 1;
         while (cp < q[i].C) cp <<= 1;
         if (2 * cp > boot_block(bt)) return SECPE_EINVAL;

@@ -503,7 +503,7 @@ static int log2_ceil_pow(int C, int &cp) {
 }
 
 int Eval::argmax(const Ct &y, int C, Ct &out) {
-    if (C < 2) return SECPE_EINVAL;
+    if (C < 2 || C > ctx->n / 2) return SECPE_EINVAL;
     int cp;
     const int r = log2_ceil_pow(C, cp);
     if (2 * cp > ctx->n / 2) return SECPE_EINVAL;
@@ -544,7 +544,7 @@ int Eval::argmax(const Ct &y, int C, Ct &out) {
 // stream(qseed_b, DOM_PHOENIX, i), the final Sign from stream(qseed_b,
 // DOM_PHOENIX, 0), each counting refreshes from 0.
 int Eval::phoenix(const Ct &y, int C, Ct &out) {
-    if (C < 2) return SECPE_EINVAL;
+    if (C < 2 || C > ctx->n / 2) return SECPE_EINVAL;
     int cp;
     log2_ceil_pow(C, cp);
     if (2 * cp > ctx->n / 2) return SECPE_EINVAL;
@@ -642,7 +642,7 @@ static int sort_queries(const secpe_ctx *ctx, const secpe_query *q, int nq_, std
     rr.resize(nq_);
     cps.resize(nq_);
     for (int b = 0; b < nq_; b++) {
-        if (q[b].C < 2 || q[b].K < 1 || !q[b].cts || !q[b].z_out || !q[b].z_out->data || !aligned16(q[b].z_out->data))
+        if (q[b].C < 2 || q[b].C > n / 2 || q[b].K < 1 || !q[b].cts || !q[b].z_out || !q[b].z_out->data || !aligned16(q[b].z_out->data))
             return SECPE_EINVAL;
         rr[b] = log2_ceil_pow(q[b].C, cps[b]);
         if (2 * cps[b] > n / 2) return SECPE_EINVAL;

@@ -309,7 +309,8 @@ bool ct_ok(const secpe_ctx *ctx, const secpe_ct *c) {
 
 extern "C" int secpe_linear_create_coeffs(secpe_ctx *ctx, const int64_t *W_m, const int64_t *mask_m,
                                           const int64_t *pad_m, int K, int C, int d, secpe_linear **out) {
-    if (!ctx || !W_m || !mask_m || !pad_m || !out || K < 1 || K > SECPE_MAX_BATCH_CONST || C < 1 || !is_pow2(d))
+    if (!ctx || !W_m || !mask_m || !pad_m || !out || K < 1 || K > SECPE_MAX_BATCH_CONST || C < 1 || !is_pow2(d) ||
+        C > ctx->n / 2)
         return SECPE_EINVAL;
     const int cp = pow2_ceil(C), L = ctx->L, n = ctx->n;
     if ((long long)d * cp > n / 2) return SECPE_EINVAL;
@@ -342,7 +343,7 @@ extern "C" int secpe_linear_create_coeffs(secpe_ctx *ctx, const int64_t *W_m, co
 
 extern "C" int secpe_linear_create(secpe_ctx *ctx, const double *T, int K, int C, int d, double d_min,
                                    secpe_linear **out) {
-    if (!ctx || !T || !out || K < 1 || C < 1 || !is_pow2(d)) return SECPE_EINVAL;
+    if (!ctx || !T || !out || K < 1 || C < 1 || !is_pow2(d) || C > ctx->n / 2) return SECPE_EINVAL;
     const int cp = pow2_ceil(C), L = ctx->L, n = ctx->n;
     if ((long long)d * cp > n / 2 || L < 2) return SECPE_EINVAL;
     const int nv = d * cp;
@@ -420,7 +421,7 @@ extern "C" int secpe_linear_apply(secpe_ctx *ctx, const secpe_keys *keys, const 
 
 extern "C" int secpe_encrypt_replicated(secpe_ctx *ctx, const secpe_keys *keys, const double *x, int d, int C,
                                         uint64_t seed, secpe_ct *out, void *stream) {
-    if (!ctx || !x || C < 1 || !is_pow2(d)) return SECPE_EINVAL;
+    if (!ctx || !x || C < 1 || !is_pow2(d) || C > ctx->n / 2) return SECPE_EINVAL;
     const int cp = pow2_ceil(C), n = ctx->n;
     if ((long long)d * cp > n / 2) return SECPE_EINVAL;
     std::vector<double> v((size_t)d * cp);

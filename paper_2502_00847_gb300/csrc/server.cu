@@ -248,6 +248,7 @@ extern "C" int secpe_server_submit(secpe_server *s, const secpe_query *q, int64_
         q->C < 2 || !(q->d_max > q->d_min))
         return SECPE_EINVAL;
     const secpe_ctx *ctx = s->ctx;
+    if (q->C > ctx->n / 2) return SECPE_EINVAL;
     int r;
     const int cp = cp_of(q->C, r);
     if (2 * cp > ctx->n / 2) return SECPE_EINVAL;

@@ -76,7 +76,10 @@ class _Top:
 
 def test_library_plan_rejects_bad_arguments(lib):
     d = _as_dict(TOY)
-    for C, entry, top in ((1, 10, 11), (4, -1, 11), (4, 10, 12), (4, 10, 0)):
+    # C = 1; entry below 0; refresh level above L or 0; C above N/4 (no room
+    # for 2 C' slots, and far beyond: C' would overflow 32 bits)
+    for C, entry, top in ((1, 10, 11), (4, -1, 11), (4, 10, 12), (4, 10, 0), (1025, 10, 11),
+                          (2 ** 30 + 1, 10, 11), (2 ** 31 - 1, 10, 11)):
         with pytest.raises(secpe.SecpeError):
             secpe.level_plan(C, entry, top, **d)
 

@@ -43,6 +43,17 @@ def test_packed_capacity_rule():
         if 2 * cp <= 2048 and C > 1:
             assert o.packed_capacity(C) == secpe.packed_capacity(12, C)
     assert secpe.packed_capacity(16, 64) == 256 and secpe.packed_capacity(16, 2) == 8192
+    # class counts far beyond any slot count (C' would overflow 32 bits) fit nowhere
+    for C in (2 ** 30, 2 ** 30 + 1, 2 ** 31 - 1):
+        assert secpe.packed_capacity(16, C) == 0 and secpe.packed_capacity(17, C) == 0
+    # ... and the encoder refuses them before reading its input
+    import ctypes
+    one = np.zeros(1)
+    m = np.zeros(1 << 12, dtype=np.int64)
+    code = secpe.lib().secpe_encode_packed(12, ctypes.c_double(2.0 ** 40),
+                                           one.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1, 2 ** 31 - 1,
+                                           ctypes.c_double(-1.0), m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    assert code == -1
 
 
 @pytest.mark.parametrize("log_n,C,fill", [(8, 3, 1.0), (12, 2, 1.0), (12, 14, 0.5)])
