@@ -203,7 +203,8 @@ int secpe_encrypt_logits_packed(secpe_ctx *ctx, const secpe_keys *keys, const do
  * block.  Synchronous. */
 int secpe_decrypt_packed(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *ct, int P, int C, double *out,
                          void *stream);
-/* Seeded ciphertexts: c1 of a fresh encryption is the uniform polynomial
+/* Seeded ciphertexts (a transport form of the user's encryption, Sec. 3.1
+ * step 1): c1 of a fresh encryption is the uniform polynomial
  * drawn from the stream of its encryption seed, so a client can send c0 and
  * the 8-byte seed only.  This regenerates c1 (limbs 0..level) on the device
  * for `batch` ciphertexts at base + i*ct_stride words ([2][cap][N] each),
@@ -245,16 +246,27 @@ int secpe_ntt_cts(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, i
  * allocator. */
 int secpe_ntt_tc(secpe_ctx *ctx, uint64_t *limbs, const int32_t *prime_idx, int count, int inverse,
                  void *stream);
+/* secpe_ntt_cts on the tensor pipe: same layout and arguments, bit-identical. */
 int secpe_ntt_cts_tc(secpe_ctx *ctx, uint64_t *base, int batch, size_t ct_stride, int cap, int level,
                      int inverse, void *stream);
+/* Homomorphic addition and subtraction (SecPE Sec. 2.2, the slot-wise sum of
+ * the aggregation, Sec. 3.1 step 3): out = a + b or a - b limb by limb at
+ * level min(level_a, level_b), scale of a; out may be a or b.  SECPE_ESCALE
+ * when the scales differ by more than 2^-40 relative. */
 int secpe_add(secpe_ctx *ctx, const secpe_ct *a, const secpe_ct *b, secpe_ct *out, void *stream);
 int secpe_sub(secpe_ctx *ctx, const secpe_ct *a, const secpe_ct *b, secpe_ct *out, void *stream);
 /* out = a * c landing at out_level with scale exactly `target_scale`
  * (constant round(c * target/scale_a * q_{out_level+1}), then rescale). */
 int secpe_mul_const(secpe_ctx *ctx, const secpe_ct *a, double c, double target_scale,
                     int out_level, secpe_ct *out, void *stream);
+/* out = a + c in every slot (Sec. 2.2 addition of a plaintext constant, as in
+ * Alg. 1's final + 1): c encodes as the constant polynomial round(c * scale)
+ * added to c0; level and scale of a.  SECPE_EINVAL if |c * scale| >= 4e18. */
 int secpe_add_const(secpe_ctx *ctx, const secpe_ct *a, double c, secpe_ct *out, void *stream);
-/* Tensor, relinearise, rescale: out at level min(level_a, level_b) - 1. */
+/* Homomorphic product (SecPE Sec. 2.2 Mult): tensor, relinearise by hybrid
+ * key switching with the relinearisation key, rescale; out at level
+ * min(level_a, level_b) - 1 with scale s_a s_b / q_l.  SECPE_ELEVEL when
+ * the inputs' level is below 1 + reserve, SECPE_EKEY without a key. */
 int secpe_mul_relin(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *a, const secpe_ct *b,
                     secpe_ct *out, void *stream);
 /* Rescale (SecPE Sec. 2.2: after a product the scale is divided by the last
@@ -327,8 +339,13 @@ typedef struct {
     double scale;
     uint64_t stride;  /* words between items, >= 2*cap*N */
 } secpe_ctbatch;
-/* Key switching of polynomial 0 of every item of d (limbs 0..level); item i
- * of out receives (ks0, ks1) in its polynomials 0 and 1 at d's level. */
+/* Hybrid key switching (the ModUp, key inner product and ModDown behind
+ * Sec. 2.2's relinearisation and rotations) of polynomial 0 of every item
+ * of d (limbs 0..level); item i of out receives (ks0, ks1) in its
+ * polynomials 0 and 1 at d's level.  galois_step 0 selects the
+ * relinearisation key, any other value the Galois key of that rotation
+ * (SECPE_EKEY if it was not generated).  SECPE_EINVAL for batch outside
+ * 1..1024, a bad layout, or out->batch != d->batch. */
 int secpe_keyswitch_batch(secpe_ctx *ctx, const secpe_keys *keys, int galois_step, const secpe_ctbatch *d,
                           secpe_ctbatch *out, void *stream);
 /* Precision variant of secpe_keyswitch_batch (N = 2^16, dnum <= 8): every
@@ -341,10 +358,15 @@ int secpe_keyswitch_batch(secpe_ctx *ctx, const secpe_keys *keys, int galois_ste
  * layout and errors; SECPE_EINVAL for other ring sizes or dnum > 8. */
 int secpe_keyswitch_batch_tc(secpe_ctx *ctx, const secpe_keys *keys, int galois_step, const secpe_ctbatch *d,
                              secpe_ctbatch *out, void *stream);
+/* secpe_mul_relin on item i of a and item i of b for every i, one launch
+ * per step for the whole batch; errors as secpe_mul_relin, plus
+ * SECPE_EINVAL for batch outside 1..1024 or a bad layout. */
 int secpe_mul_relin_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ctbatch *a,
                           const secpe_ctbatch *b, secpe_ctbatch *out, void *stream);
+/* secpe_rotate (RotL for steps > 0, RotR for steps < 0) of every item. */
 int secpe_rotate_batch(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ctbatch *in, int steps,
                        secpe_ctbatch *out, void *stream);
+/* secpe_rescale of every item (SECPE_ELEVEL at level 0). */
 int secpe_rescale_batch(secpe_ctx *ctx, const secpe_ctbatch *in, secpe_ctbatch *out, void *stream);
 
 /* ---- bootstrapping --------------------------------------------------------- */
