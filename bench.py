@@ -605,7 +605,8 @@ def run_ours(args, world, rank, local):
              "probe_note": "secpe_mul32_probe: 128-bit multiply-accumulate chains (8 32-bit multiplies each) "
                            "on register data, all SMs",
              "mul32_per_launch": per_launch(kp["mul32"]),
-             "traffic": None}
+             # the same launches' DRAM traffic (a property of the kernels, whichever roofline binds)
+             "traffic": r_hbm["traffic"], "traffic_source": r_hbm["traffic_source"]}
     common = {"launches_per_step": kp["launches"] / kp_steps, "kernel_ms_per_step": kp["total_ms"] / kp_steps,
               "family_share_of_step": (kp["total_ms"] / kp_steps) / ms_per_step}
     r_hbm.update(common)
