@@ -346,7 +346,8 @@ secpe_boot *new_plan(secpe_ctx *ctx, int n) {
     return bt;
 }
 
-bool block_ok(const secpe_ctx *ctx, int n) { return n >= 2 && (n & (n - 1)) == 0 && 2 * n <= ctx->n / 2; }
+// 2n <= N/2, written as n <= N/4 so that no n near 2^30 overflows
+bool block_ok(const secpe_ctx *ctx, int n) { return n >= 2 && (n & (n - 1)) == 0 && n <= ctx->n / 4; }
 
 }  // namespace
 

@@ -69,6 +69,7 @@ def test_bootstrap_and_batch_errors(env):
     bctx = secpe.Context.from_params(BOOT_TOY)
     assert _code(lambda: secpe.Boot(bctx, 12)) == EINVAL         # block not a power of two
     assert _code(lambda: secpe.Boot(bctx, 2048)) == EINVAL       # 2n > N/2
+    assert _code(lambda: secpe.Boot(bctx, 1 << 30)) == EINVAL    # 2n beyond 32 bits
     bk = secpe.Keys(bctx, 3, [1, -2])
     bt = secpe.Boot(bctx, 16)
     ct = secpe.encrypt(bctx, bk, np.zeros(16), 4)
