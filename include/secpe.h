@@ -168,7 +168,7 @@ int secpe_encrypt(secpe_ctx *ctx, const secpe_keys *keys, const double *v, int n
                   secpe_ct *out, void *stream);
 /* One prompt's logits (SecPE Sec. 3.1 step 1 / Eq. argmax layout): slots
  * 0..C-1 hold v, slots C..C'-1 hold d_min (C' = next power of two), zeros
- * beyond. */
+ * beyond.  SECPE_EINVAL for C < 1 or C' > N/2. */
 int secpe_encrypt_logits(secpe_ctx *ctx, const secpe_keys *keys, const double *v, int C,
                          double d_min, uint64_t seed, secpe_ct *out, void *stream);
 /* Slot packing (SecPE Sec. 3.2, the paragraph after Alg. 1: one ciphertext
@@ -468,8 +468,9 @@ int secpe_ensemble_aggregate(secpe_ctx *ctx, const secpe_ct *cts, int K, double 
                              double d_max, secpe_ct *out, void *stream);
 /* SecPE Alg. 1 on a normalised ciphertext y with C >= 2 classes: returns z
  * with z ~ 1 at the argmax slot and ~ 0 at the other slots 0..C-1.
- * Needs Galois keys for RotR(C') and RotL(2^i), i < log2 C'.  Levels follow
- * secpe_level_plan (refresh level L). */
+ * Needs Galois keys for RotR(C') and RotL(2^i), i < log2 C' (SECPE_EKEY
+ * otherwise).  Levels follow secpe_level_plan (refresh level L).
+ * SECPE_EINVAL for C < 2 or 2 C' > N/2 (no room for the duplicated copy). */
 int secpe_encrypted_argmax(secpe_ctx *ctx, const secpe_keys *keys, const secpe_ct *y, int C,
                            uint64_t qseed, secpe_ct *z_out, void *stream);
 
