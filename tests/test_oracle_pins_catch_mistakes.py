@@ -1,0 +1,155 @@
+"""Planted mistakes: the pins are sensitive, not only passed.
+
+Each case plants one plausible slip in a copy of the oracle, on the CPU, and
+runs the pin that covers that step, which must fail:
+
+* the rescale and the ModDown without their rounding term (floor division)
+  against the big-integer rounded-division pins;
+* rotations in the wrong direction (5^-r for 5^r) against np.roll;
+* the tensor product without one cross term against the plaintext product;
+* the transform without its psi^k twist (a cyclic instead of a negacyclic
+  NTT, self-consistent: encryption and decryption still work) against the
+  plaintext product;
+* the slot order on powers of 3 instead of 5 (self-consistent: the
+  encode/decode round trip still passes) against the monomial's closed form;
+* a digit typo in the f_4 and g_4 coefficient tables against the closed form
+  and g_4's pinned values."""
+import numpy as np
+import pytest
+
+import test_oracle_ckks as ckks_pins
+import test_oracle_sign as sign_pins
+from oracle import TOY, Oracle
+from oracle import signpoly
+from oracle.ckks import Ct
+
+KEY_SEED = 20250201
+ROT = [1, 2, 3, -2, -4, -8]
+
+
+class FloorRescale(Oracle):
+    def rescale(self, ct):
+        lv, ql = ct.level, self.primes[ct.level]
+        out = np.empty((2, lv, self.n), dtype=np.uint64)
+        for k in range(2):
+            y = ct.c[k, lv].copy()
+            self.intt(y, lv)
+            for pi in range(lv):
+                z = self.vreduce(y, pi)          # [c]_{q_l}: no + q_l/2
+                self.ntt(z, pi)
+                t = self.vsub(ct.c[k, pi], z, pi)
+                out[k, pi] = self.vscale(t, pow(ql % self.primes[pi], -1, self.primes[pi]), pi)
+        return Ct(out, lv - 1, ct.scale / float(ql))
+
+
+class FloorModDown(Oracle):
+    def moddown(self, acc, level):
+        sp = self.ctx.special_idx()
+        pc = np.stack([acc[t].copy() for t in sp])
+        for r, t in enumerate(sp):
+            self.intt(pc[r], t)                  # no + P/2
+        conv = self.fast_bconv(pc, sp, list(range(level + 1)))
+        out = np.empty((level + 1, self.n), dtype=np.uint64)
+        for pi in range(level + 1):
+            q = self.primes[pi]
+            x = conv[pi].copy()
+            self.ntt(x, pi)
+            out[pi] = self.vscale(self.vsub(acc[pi], x, pi), pow(self.ctx.P % q, -1, q), pi)
+        return out
+
+
+class WrongDirection(Oracle):
+    def galois(self, r):
+        return super().galois(-r)
+
+
+class DroppedCrossTerm(Oracle):
+    def tensor(self, a, b):
+        d = super().tensor(a, b)
+        lv = d.level
+        a, b = self.drop(a, lv), self.drop(b, lv)
+        for pi in range(lv + 1):
+            d.c[1, pi] = self.vmul(a.c[0, pi], b.c[1, pi], pi)    # a1 b0 dropped
+        return d
+
+
+class DroppedTwist(Oracle):
+    _tw = {}
+
+    def _twist(self, a, pi, e):
+        key = (self.primes[pi], e)
+        if key not in self._tw:
+            q = self.primes[pi]
+            w = pow(self.ctx.psi[pi], e, q)
+            t, x = np.empty(self.n, dtype=np.uint64), 1
+            for k in range(self.n):
+                t[k] = x
+                x = x * w % q
+            self._tw[key] = t
+        a[:] = self.vmul(np.ascontiguousarray(a), self._tw[key], pi)
+
+    def ntt(self, a, pi):
+        self._twist(a, pi, -1)                   # undoes the twist the transform applies
+        super().ntt(a, pi)
+
+    def intt(self, a, pi):
+        super().intt(a, pi)
+        self._twist(a, pi, 1)
+
+
+def _keyed(cls, rot=()):
+    o = cls(TOY)
+    o.keygen(KEY_SEED, rot_steps=list(rot))
+    return o
+
+
+def test_floor_rescale_fails_the_rounding_pin():
+    with pytest.raises(AssertionError):
+        ckks_pins.test_rescale_is_rounded_division(_keyed(FloorRescale))
+
+
+def test_floor_moddown_fails_the_rounding_pin():
+    with pytest.raises(AssertionError):
+        ckks_pins.test_moddown_is_rounded_division_by_P(_keyed(FloorModDown))
+
+
+def test_wrong_rotation_direction_fails_the_roll_pin():
+    with pytest.raises(AssertionError):
+        ckks_pins.test_rotation_direction(_keyed(WrongDirection, ROT))
+
+
+def test_dropped_cross_term_fails_the_product_pin():
+    with pytest.raises(AssertionError):
+        ckks_pins.test_encrypt_decrypt_and_linear_ops(_keyed(DroppedCrossTerm))
+
+
+def test_dropped_twist_fails_the_product_pin():
+    o = _keyed(DroppedTwist)
+    # self-consistent: a fresh ciphertext still decrypts
+    v = np.random.default_rng(8).uniform(-1, 1, 8)
+    assert np.max(np.abs(o.decrypt(o.encrypt(v, seed=3), 8) - v)) < 2.0 ** -20
+    with pytest.raises(AssertionError):
+        ckks_pins.test_keyswitch_noise_small(o)
+
+
+def test_slot_order_on_powers_of_3_fails_the_monomial_pin(monkeypatch):
+    def pow3(self, count):
+        return np.array([pow(3, j, 2 * self.n) for j in range(count)], dtype=np.int64)
+
+    monkeypatch.setattr(Oracle, "_pow5", pow3)
+    # self-consistent: the round trip alone does not see it
+    ckks_pins.test_encode_decode_roundtrip(Oracle(TOY))
+    with pytest.raises(AssertionError):
+        ckks_pins.test_decode_of_monomial_is_root_ordering()
+
+
+def test_f4_digit_typo_fails_the_closed_form_pin(monkeypatch):
+    monkeypatch.setattr(signpoly, "F4_NUM", (315, -420, 387, -180, 35))
+    with pytest.raises(AssertionError):
+        sign_pins.test_f4_table_equals_closed_form()
+
+
+def test_g4_digit_typo_fails_its_pin(monkeypatch):
+    monkeypatch.setattr(signpoly, "G4_NUM", (5850, -34974, 97051, -113492, 46623))
+    with pytest.raises(AssertionError):
+        sign_pins.test_g4_pinning_properties()
