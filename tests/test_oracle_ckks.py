@@ -134,6 +134,13 @@ def test_rescale_is_rounded_division(toy_oracle):
     lv = ct.level
     r = o.rescale(ct)
     ql = o.primes[lv]
+    # the scale is divided by q_l, and a ciphertext at scale Delta q_l keeps its
+    # slot values at scale Delta
+    assert r.level == lv - 1 and r.scale == ct.scale / ql
+    big = o.encrypt(np.linspace(-1, 1, 8), seed=14, scale=o.p.scale * ql)
+    rb = o.rescale(big)
+    assert rb.scale == big.scale / ql
+    assert np.max(np.abs(o.decrypt(rb, 8) - np.linspace(-1, 1, 8))) < TOL_LINEAR
     for k in range(2):
         before = []
         for pi in range(lv + 1):

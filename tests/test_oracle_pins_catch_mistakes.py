@@ -13,7 +13,12 @@ runs the pin that covers that step, which must fail:
 * the slot order on powers of 3 instead of 5 (self-consistent: the
   encode/decode round trip still passes) against the monomial's closed form;
 * a digit typo in the f_4 and g_4 coefficient tables against the closed form
-  and g_4's pinned values."""
+  and g_4's pinned values;
+* a rescale that does not divide the scale, against the rounded-division pin
+  (which also checks the scale and the decoded values);
+* the aggregation without its 1/K, Alg. 1 without its final + 1, and Max
+  without the 1/2 folded into Sign's last polynomial, against the toy
+  circuit's plaintext simulation and Max's plaintext values."""
 import numpy as np
 import pytest
 
@@ -56,6 +61,22 @@ class FloorModDown(Oracle):
             self.ntt(x, pi)
             out[pi] = self.vscale(self.vsub(acc[pi], x, pi), pow(self.ctx.P % q, -1, q), pi)
         return out
+
+
+class ScaleKept(Oracle):
+    def rescale(self, ct):
+        r = super().rescale(ct)
+        r.scale = ct.scale                       # forgot to divide by q_l
+        return r
+
+
+class MaxUnhalved(Oracle):
+    def max(self, a, y):
+        d = self.sub(a, y)
+        s = self.sign(d, 1, last_factor=1.0)     # the 1/2 of (a-y)/2 Sign(a-y) dropped
+        t = self.mul(d, s)
+        u = self.mul_const(self.add(a, y), 0.5, t.scale, t.level)
+        return self.add(t, u)
 
 
 class WrongDirection(Oracle):
@@ -153,3 +174,36 @@ def test_g4_digit_typo_fails_its_pin(monkeypatch):
     monkeypatch.setattr(signpoly, "G4_NUM", (5850, -34974, 97051, -113492, 46623))
     with pytest.raises(AssertionError):
         sign_pins.test_g4_pinning_properties()
+
+
+def test_rescale_keeping_the_scale_fails_the_rescale_pin():
+    with pytest.raises(AssertionError):
+        ckks_pins.test_rescale_is_rounded_division(_keyed(ScaleKept))
+
+
+def test_aggregation_without_1_over_K_fails_the_circuit_pin(monkeypatch):
+    agg = Oracle.aggregate
+
+    def without_k(self, cts, d_min, d_max):
+        # weight 1/(d_max - d_min) instead of 1/(K (d_max - d_min))
+        return agg(self, cts, d_min, d_min + (d_max - d_min) / len(cts))
+
+    monkeypatch.setattr(Oracle, "aggregate", without_k)
+    with pytest.raises(AssertionError):
+        ckks_pins.test_toy_argmax_circuit(2, 1)
+
+
+def test_argmax_without_the_final_plus_one_fails_the_circuit_pin(monkeypatch):
+    argmax = Oracle.argmax
+
+    def without_plus_one(self, y, n_classes, qseed):
+        return self.add_const(argmax(self, y, n_classes, qseed), -1.0)
+
+    monkeypatch.setattr(Oracle, "argmax", without_plus_one)
+    with pytest.raises(AssertionError):
+        ckks_pins.test_toy_argmax_circuit(2, 1)
+
+
+def test_max_without_its_half_fails_the_max_pin():
+    with pytest.raises(AssertionError):
+        ckks_pins.test_max_keeps_the_scale(_keyed(MaxUnhalved, ROT))
