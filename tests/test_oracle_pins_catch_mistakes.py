@@ -18,13 +18,17 @@ runs the pin that covers that step, which must fail:
   (which also checks the scale and the decoded values);
 * the aggregation without its 1/K, Alg. 1 without its final + 1, and Max
   without the 1/2 folded into Sign's last polynomial, against the toy
-  circuit's plaintext simulation and Max's plaintext values."""
+  circuit's plaintext simulation and Max's plaintext values;
+* bootstrapping's CoeffToSlot built on powers of 3 instead of 5 against the
+  raised plaintext's subring coefficients (big-integer decryption)."""
 import numpy as np
 import pytest
 
+import test_oracle_boot as boot_pins
 import test_oracle_ckks as ckks_pins
 import test_oracle_sign as sign_pins
-from oracle import TOY, Oracle
+from oracle import BOOT_TOY, TOY, Oracle
+from oracle import boot as oboot
 from oracle import signpoly
 from oracle.ckks import Ct
 
@@ -207,3 +211,22 @@ def test_argmax_without_the_final_plus_one_fails_the_circuit_pin(monkeypatch):
 def test_max_without_its_half_fails_the_max_pin():
     with pytest.raises(AssertionError):
         ckks_pins.test_max_keeps_the_scale(_keyed(MaxUnhalved, ROT))
+
+
+def test_coeff_to_slot_on_powers_of_3_fails_its_pin(monkeypatch):
+    def vandermonde3(n):
+        e = np.array([pow(3, j, 4 * n) for j in range(n)], dtype=np.int64)
+        a = np.arange(n, dtype=np.int64)
+        return np.exp(1j * np.pi * ((np.outer(e, a) % (4 * n)).astype(np.float64)) / (2 * n))
+
+    monkeypatch.setattr(oboot, "subring_vandermonde", vandermonde3)
+    n = boot_pins.N_BLOCK
+    o = Oracle(BOOT_TOY)
+    plan = oboot.BootPlan(o, n)
+    o.keygen(99, rot_steps=plan.rotation_steps())
+    v = np.random.default_rng(1).uniform(-1, 1, n)
+    ct = o.drop(o.encrypt(np.tile(v, (o.n // 2) // n), seed=5, level=7), 0)
+    x = plan.mod_raise(ct)
+    xs = plan.sub_sum(x)
+    with pytest.raises(AssertionError):
+        boot_pins.test_coeff_to_slot_gives_subring_coefficients(dict(o=o, x=x, xs=xs, u=plan.coeff_to_slot(xs)))
