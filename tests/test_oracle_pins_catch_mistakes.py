@@ -20,12 +20,16 @@ runs the pin that covers that step, which must fail:
   without the 1/2 folded into Sign's last polynomial, against the toy
   circuit's plaintext simulation and Max's plaintext values;
 * bootstrapping's CoeffToSlot built on powers of 3 instead of 5 against the
-  raised plaintext's subring coefficients (big-integer decryption)."""
+  raised plaintext's subring coefficients (big-integer decryption);
+* slot packing in blocks of C' slots (no room for Alg. 1's duplication),
+  packed and read back consistently, against the packed plaintext
+  pipeline."""
 import numpy as np
 import pytest
 
 import test_oracle_boot as boot_pins
 import test_oracle_ckks as ckks_pins
+import test_oracle_packing as packing_pins
 import test_oracle_sign as sign_pins
 from oracle import BOOT_TOY, TOY, Oracle
 from oracle import boot as oboot
@@ -81,6 +85,23 @@ class MaxUnhalved(Oracle):
         t = self.mul(d, s)
         u = self.mul_const(self.add(a, y), 0.5, t.scale, t.level)
         return self.add(t, u)
+
+
+class TightBlocks(Oracle):
+    def pack_slots(self, V, d_min):
+        V = np.asarray(V, dtype=np.float64)
+        P, C = V.shape
+        cp = 1 << (C - 1).bit_length()
+        out = np.zeros(P * 2 * cp, dtype=np.float64)
+        for b in range(P):                       # stride C' instead of 2 C'
+            out[b * cp: b * cp + C] = V[b]
+            out[b * cp + C: (b + 1) * cp] = d_min
+        return out
+
+    def decrypt_packed(self, ct, P, n_classes):
+        cp = 1 << (n_classes - 1).bit_length()
+        s = self.decrypt(ct, P * 2 * cp)
+        return np.stack([s[b * cp: b * cp + n_classes] for b in range(P)])
 
 
 class WrongDirection(Oracle):
@@ -230,3 +251,8 @@ def test_coeff_to_slot_on_powers_of_3_fails_its_pin(monkeypatch):
     xs = plan.sub_sum(x)
     with pytest.raises(AssertionError):
         boot_pins.test_coeff_to_slot_gives_subring_coefficients(dict(o=o, x=x, xs=xs, u=plan.coeff_to_slot(xs)))
+
+
+def test_packing_without_room_for_the_duplication_fails_the_packed_pin():
+    with pytest.raises(AssertionError):
+        packing_pins.test_oracle_packed_argmax_every_input(_keyed(TightBlocks, ROT))
