@@ -6,14 +6,17 @@ the CUDA library; the ring arithmetic is the plain C in ring.c, the rest is
 numpy / Python integers in the order the paper (or the stated reading) gives.
 
 Parity status per function:
-  ring ops, NTT, basis conversion, rescale, key switching, encode/decode,
-  Sign/Max/QuickMax/Argmax, the Phoenix baseline, slot packing, the
-  CLIP-style linear step and bootstrapping (boot.py): pinned (see
-  tests/test_oracle_*.py).
-  Residue-level intermediate values of the encrypted circuit: the paper prints
-  none (its worked example is a missing figure), so residues are defined by
-  this oracle; the decoded values and the returned index are pinned by
-  mathematics (plaintext simulation, exact argmax).
+  ring ops, NTT, basis conversion, rescale, key switching (plain and
+  hoisted), encode/decode, Sign/Max/QuickMax/Argmax, the level plan, the
+  Phoenix baseline, slot packing, the CLIP-style linear step and
+  bootstrapping (boot.py): pinned (see tests/test_oracle_*.py and
+  tests/test_level_plan.py; tests/test_oracle_pins_catch_mistakes.py plants
+  mistakes that those pins catch).
+  Residue-level intermediate values of the encrypted circuit: parity
+  unpinned at that layer.  The paper prints none (its worked example is a
+  missing figure), so residues are defined by this oracle; the decoded
+  values and the returned index are pinned by mathematics (plaintext
+  simulation, exact argmax).
 
 Scheme summary (SecPE Sec. 2.2 and Sec. 3.2, readings where the paper is
 silent are marked READING):
