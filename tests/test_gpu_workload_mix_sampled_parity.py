@@ -19,6 +19,7 @@ step 3, Eq. norm, Alg. 1, Eq. max, Eq. comp), and the decoded z agrees with
 the oracle's decoding and with the FP64 plaintext simulation.  Every query
 of the mix gets its exact argmax.  The oracle's queries run in spawned
 worker processes while the GPU works."""
+import gc
 import multiprocessing
 
 import numpy as np
@@ -62,6 +63,7 @@ def _gpu_step(qs, sample, own):
     pkg_build.build()
     torch.cuda.set_device(0)
     # start from an empty cache and pool: earlier test modules may have left both full
+    gc.collect()
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     secpe.pool_usage(trim=True)
